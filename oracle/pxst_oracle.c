@@ -1,0 +1,354 @@
+/*
+ * pxst_oracle.c -- plain FP64 CPU oracle for the PXST hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path calls this file: only the
+ * tests, the smoke check and the CPU-baseline leg of the benchmark load it. It shares
+ * no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (Morgan et al., "speckle-tracking: a software suite for
+ * ptychographic X-ray speckle tracking"):
+ *   - the bilinear weights of section "Sub-pixel interpolation" (2x2 matrix form) and
+ *     its masked, renormalised variant (same section, the f_M / M quotient);
+ *   - make_object_map, the "Make reference image" pseudo code: scatter M*W*I and
+ *     M*W^2 with bilinear weights to u - Delta_n, then divide (section "Make reference
+ *     image" plus the assignment rule at the end of "Sub-pixel interpolation");
+ *   - update_pixel_map, the "Update pixel mapping" pseudo code: brute-force search of
+ *     error/var over an integer window centred on the current u, argmin, and the
+ *     optional 3x3 paraboloid ("quadratic_refinement") for sub-pixel precision;
+ *   - iterate: steps (i) and (ii) of the main loop, repeated.
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   R1  the bilinear weight multiplies both the M*W*I term and the M*W^2 term;
+ *   R2  scatter corners outside [0,Ry) x [0,Rx) are dropped from both sums;
+ *   R3  I_ref = 0 where the accumulated weight w is exactly 0 (uncovered);
+ *   R4  the doubled brackets "]]" in the pseudo code are typos;
+ *   R5  window centre = (floor(u0 + 1/2), floor(u1 + 1/2)); candidates are
+ *       centre + (a, b), a in [-Sy, Sy], b in [-Sx, Sx];
+ *   R6  I_ref is read at c - Delta_n by the masked renormalised bilinear gather with
+ *       mask V = (inside the grid) and (w > 0); if the weights of the valid corners sum
+ *       to zero, frame n does not enter error or var for that candidate;
+ *   R7  zero valid frames => e = +inf; var == 0 => e = error (not divided);
+ *   R8  argmin = first minimum in row-major window order (a outer, b inner), strict <;
+ *       if every candidate is +inf the pixel keeps its u;
+ *   R9  pixels with M = 0 keep their u (error and var would both be 0);
+ *   R10 the paraboloid is the least-squares fit of c0 + c1 a + c2 b + c3 a^2 + c4 ab
+ *       + c5 b^2 to the 3x3 errors about the argmin; if a neighbour is missing (window
+ *       edge or +inf) or the Hessian is not positive definite, each axis is fitted alone
+ *       by a 3-point parabola (0 shift if a point is missing or the curvature is <= 0);
+ *       a shift larger than 1 on an axis is set to 0 on that axis.
+ *
+ * Array conventions: frames float32 [N][ny][nx]; W float32 [ny][nx]; M uint8 [ny][nx];
+ * u float64 [2][ny][nx] (u[0] rows, u[1] columns, reference-pixel units);
+ * delta float64 [N][2]; Iref, w float64 [Ry][Rx].
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fast-math, no fused
+ * multiply-add, so the x86 and Arm builds round identically).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------------------------- */
+/* bilinear weights (section "Sub-pixel interpolation")                               */
+/* ---------------------------------------------------------------------------------- */
+
+/* For the point (a, b): i0 = floor(a), j0 = floor(b), x = a - i0, y = b - j0.
+ * f(a,b) ~ [1-x, x] . [[f00, f01], [f10, f11]] . [1-y, y]^T, so corner (di, dj)
+ * carries weight (di ? x : 1-x) * (dj ? y : 1-y). Order: 00, 01, 10, 11. */
+void pxst_oracle_bilinear(double a, double b, int64_t *i0, int64_t *j0, double wt[4])
+{
+    double fi = floor(a), fj = floor(b);
+    double x = a - fi, y = b - fj;
+    *i0 = (int64_t)fi;
+    *j0 = (int64_t)fj;
+    wt[0] = (1.0 - x) * (1.0 - y);
+    wt[1] = (1.0 - x) * y;
+    wt[2] = x * (1.0 - y);
+    wt[3] = x * y;
+}
+
+/* Masked, renormalised gather: sum_k wt_k V_k f_k / sum_k wt_k V_k, with
+ * V = inside the grid and w > 0 (reading R6). Returns 1 and stores the value if the
+ * valid weights sum to more than zero, else returns 0 (frame invalid). */
+int pxst_oracle_gather(const double *Iref, const double *w, int64_t Ry, int64_t Rx,
+                       double q0, double q1, double *out)
+{
+    int64_t i0, j0;
+    double wt[4];
+    pxst_oracle_bilinear(q0, q1, &i0, &j0, wt);
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int64_t ii = i0 + (k >> 1), jj = j0 + (k & 1);
+        if (wt[k] == 0.0) continue;                 /* contributes nothing either way */
+        if (ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;
+        double wc = w[ii * Rx + jj];
+        if (!(wc > 0.0)) continue;
+        num += wt[k] * Iref[ii * Rx + jj];
+        den += wt[k];
+    }
+    if (!(den > 0.0)) return 0;
+    *out = num / den;
+    return 1;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* make_object_map (section "Make reference image")                                  */
+/* ---------------------------------------------------------------------------------- */
+
+void pxst_oracle_make_object_map(int N, int ny, int nx, int Ry, int Rx,
+                                 const float *frames, const float *W, const uint8_t *M,
+                                 const double *u, const double *delta,
+                                 double *Iref, double *w)
+{
+    const int64_t P = (int64_t)ny * nx, R = (int64_t)Ry * Rx;
+    memset(Iref, 0, sizeof(double) * R);
+    memset(w, 0, sizeof(double) * R);
+    for (int n = 0; n < N; ++n) {
+        for (int i = 0; i < ny; ++i) {
+            for (int j = 0; j < nx; ++j) {
+                const int64_t p = (int64_t)i * nx + j;
+                /* M is 0 or 1: for M = 0 both added terms are exactly 0 */
+                if (!M[p]) continue;
+                const double m = 1.0;
+                const double Wv = (double)W[p];
+                const double I = (double)frames[(int64_t)n * P + p];
+                const double a = u[p] - delta[2 * n + 0];
+                const double b = u[P + p] - delta[2 * n + 1];
+                int64_t i0, j0;
+                double wt[4];
+                pxst_oracle_bilinear(a, b, &i0, &j0, wt);
+                for (int k = 0; k < 4; ++k) {
+                    int64_t ii = i0 + (k >> 1), jj = j0 + (k & 1);
+                    if (ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;   /* R2 */
+                    Iref[ii * Rx + jj] += wt[k] * m * Wv * I;                  /* R1 */
+                    w[ii * Rx + jj] += wt[k] * m * Wv * Wv;
+                }
+            }
+        }
+    }
+    for (int64_t c = 0; c < R; ++c)                                            /* R3 */
+        Iref[c] = (w[c] > 0.0) ? Iref[c] / w[c] : 0.0;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* quadratic refinement (end of section "Update pixel mapping")                      */
+/* ---------------------------------------------------------------------------------- */
+
+static int finite_(double v) { return isfinite(v); }
+
+/* f[9]: normalised errors at (da, db) in {-1,0,1}^2, da outer, db inner; +inf marks
+ * a missing neighbour. Returns the sub-pixel shift (da, db) of the minimum (R10). */
+void pxst_oracle_quadratic_fit(const double f[9], double *da_out, double *db_out)
+{
+    double da = 0.0, db = 0.0;
+    int complete = 1;
+    for (int k = 0; k < 9; ++k) complete &= finite_(f[k]);
+    int done = 0;
+    if (complete) {
+        double s = 0, sa = 0, sb = 0, sab = 0, a2 = 0, b2 = 0;
+        for (int ia = -1; ia <= 1; ++ia)
+            for (int ib = -1; ib <= 1; ++ib) {
+                double v = f[(ia + 1) * 3 + (ib + 1)];
+                s += v;
+                sa += ia * v;
+                sb += ib * v;
+                sab += ia * ib * v;
+                if (ia != 0) a2 += v;
+                if (ib != 0) b2 += v;
+            }
+        double c1 = sa / 6.0, c2 = sb / 6.0, c4 = sab / 4.0;
+        double c3 = (a2 - 2.0 * (s - a2)) / 6.0;
+        double c5 = (b2 - 2.0 * (s - b2)) / 6.0;
+        double det = 4.0 * c3 * c5 - c4 * c4;
+        if (c3 > 0.0 && det > 0.0) {
+            /* [2c3 c4; c4 2c5] (da, db)^T = -(c1, c2)^T */
+            da = (-2.0 * c5 * c1 + c4 * c2) / det;
+            db = (-2.0 * c3 * c2 + c4 * c1) / det;
+            done = 1;
+        }
+    }
+    if (!done) {
+        double fm = f[1], f0 = f[4], fp = f[7];           /* along a, db = 0 */
+        da = 0.0;
+        if (finite_(fm) && finite_(fp) && finite_(f0)) {
+            double k = fm - 2.0 * f0 + fp;
+            if (k > 0.0) da = (fm - fp) / (2.0 * k);
+        }
+        fm = f[3]; fp = f[5];                             /* along b, da = 0 */
+        db = 0.0;
+        if (finite_(fm) && finite_(fp) && finite_(f0)) {
+            double k = fm - 2.0 * f0 + fp;
+            if (k > 0.0) db = (fm - fp) / (2.0 * k);
+        }
+    }
+    if (!(fabs(da) <= 1.0)) da = 0.0;
+    if (!(fabs(db) <= 1.0)) db = 0.0;
+    *da_out = da;
+    *db_out = db;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* update_pixel_map (section "Update pixel mapping")                                 */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    int N, ny, nx, Ry, Rx, Sy, Sx;
+    const float *frames, *W;
+    const uint8_t *M;
+    const double *Iref, *w, *delta, *u;
+} upm_ctx;
+
+/* The whole error window of pixel p: e[(a+Sy)*(2Sx+1) + (b+Sx)] (R5-R7). */
+static void pixel_window(const upm_ctx *c, int64_t p, double *e, int64_t *ci, int64_t *cj)
+{
+    const int64_t P = (int64_t)c->ny * c->nx;
+    const int wx = 2 * c->Sx + 1;
+    *ci = (int64_t)floor(c->u[p] + 0.5);
+    *cj = (int64_t)floor(c->u[P + p] + 0.5);
+    const double Wv = (double)c->W[p];
+    for (int a = -c->Sy; a <= c->Sy; ++a) {
+        for (int b = -c->Sx; b <= c->Sx; ++b) {
+            double error = 0.0, var = 0.0;
+            int nvalid = 0;
+            for (int n = 0; n < c->N; ++n) {
+                double R;
+                double q0 = (double)(*ci + a) - c->delta[2 * n + 0];
+                double q1 = (double)(*cj + b) - c->delta[2 * n + 1];
+                if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) continue;
+                const double I = (double)c->frames[(int64_t)n * P + p];
+                const double d = I - Wv * R;
+                const double v = I - Wv;
+                error += d * d;
+                var += v * v;
+                nvalid += 1;
+            }
+            double ev;
+            if (nvalid == 0) ev = INFINITY;
+            else if (var > 0.0) ev = error / var;
+            else ev = error;
+            e[(a + c->Sy) * wx + (b + c->Sx)] = ev;
+        }
+    }
+}
+
+/* Search + argmin + optional fit for one pixel; writes u_out[0..1] and *err. */
+static void update_one(const upm_ctx *c, int quadratic, int64_t p, double *e,
+                       double *u0_out, double *u1_out, double *err)
+{
+    const int64_t P = (int64_t)c->ny * c->nx;
+    if (!c->M[p]) {                                          /* R9 */
+        *u0_out = c->u[p];
+        *u1_out = c->u[P + p];
+        *err = NAN;
+        return;
+    }
+    int64_t ci, cj;
+    pixel_window(c, p, e, &ci, &cj);
+    const int wy = 2 * c->Sy + 1, wx = 2 * c->Sx + 1;
+    int best = 0;
+    for (int k = 1; k < wy * wx; ++k)                          /* R8 */
+        if (e[k] < e[best]) best = k;
+    if (!(e[best] < INFINITY)) {
+        *u0_out = c->u[p];
+        *u1_out = c->u[P + p];
+        *err = INFINITY;
+        return;
+    }
+    const int ia = best / wx, ib = best % wx;
+    double da = 0.0, db = 0.0;
+    if (quadratic) {
+        double f[9];
+        for (int sa = -1; sa <= 1; ++sa)
+            for (int sb = -1; sb <= 1; ++sb) {
+                int na = ia + sa, nb = ib + sb;
+                f[(sa + 1) * 3 + (sb + 1)] =
+                    (na < 0 || na >= wy || nb < 0 || nb >= wx) ? INFINITY : e[na * wx + nb];
+            }
+        pxst_oracle_quadratic_fit(f, &da, &db);
+    }
+    *u0_out = (double)(ci + ia - c->Sy) + da;
+    *u1_out = (double)(cj + ib - c->Sx) + db;
+    *err = e[best];
+}
+
+/* Error window of one pixel (for tests): e has (2Sy+1)(2Sx+1) entries. */
+void pxst_oracle_pixel_window(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx,
+                              const float *frames, const float *W, const uint8_t *M,
+                              const double *Iref, const double *w, const double *delta,
+                              const double *u, int64_t p, double *e, int64_t *centre)
+{
+    upm_ctx c = {N, ny, nx, Ry, Rx, Sy, Sx, frames, W, M, Iref, w, delta, u};
+    pixel_window(&c, p, e, &centre[0], &centre[1]);
+}
+
+/* update_pixel_map over rows [row0, row1); u is read from u_in and written to u_out
+ * (they may alias: each pixel reads only its own entries). err_out may be NULL. */
+void pxst_oracle_update_pixel_map(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx,
+                                  int quadratic, const float *frames, const float *W,
+                                  const uint8_t *M, const double *Iref, const double *w,
+                                  const double *delta, const double *u_in, double *u_out,
+                                  double *err_out, int row0, int row1, int nthreads)
+{
+    upm_ctx c = {N, ny, nx, Ry, Rx, Sy, Sx, frames, W, M, Iref, w, delta, u_in};
+    const int64_t P = (int64_t)ny * nx;
+    const int nwin = (2 * Sy + 1) * (2 * Sx + 1);
+    if (nthreads <= 0) nthreads = 1;
+    #pragma omp parallel num_threads(nthreads)
+    {
+        double *e = (double *)malloc(sizeof(double) * nwin);
+        #pragma omp for schedule(dynamic, 1)
+        for (int i = row0; i < row1; ++i) {
+            for (int j = 0; j < nx; ++j) {
+                const int64_t p = (int64_t)i * nx + j;
+                double u0, u1, er;
+                update_one(&c, quadratic, p, e, &u0, &u1, &er);
+                u_out[p] = u0;
+                u_out[P + p] = u1;
+                if (err_out) err_out[p] = er;
+            }
+        }
+        free(e);
+    }
+}
+
+/* The same update for an arbitrary list of pixels (sampled parity at full size):
+ * writes u_out[2*k+0..1] and err_out[k] for pixel pix[k]. */
+void pxst_oracle_update_pixels(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx,
+                               int quadratic, const float *frames, const float *W,
+                               const uint8_t *M, const double *Iref, const double *w,
+                               const double *delta, const double *u, const int64_t *pix,
+                               int64_t npix, double *u_out, double *err_out, int nthreads)
+{
+    upm_ctx c = {N, ny, nx, Ry, Rx, Sy, Sx, frames, W, M, Iref, w, delta, u};
+    const int nwin = (2 * Sy + 1) * (2 * Sx + 1);
+    if (nthreads <= 0) nthreads = 1;
+    #pragma omp parallel num_threads(nthreads)
+    {
+        double *e = (double *)malloc(sizeof(double) * nwin);
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t k = 0; k < npix; ++k)
+            update_one(&c, quadratic, pix[k], e, &u_out[2 * k], &u_out[2 * k + 1], &err_out[k]);
+        free(e);
+    }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* iterate: main loop steps (i) and (ii)                                              */
+/* ---------------------------------------------------------------------------------- */
+
+void pxst_oracle_iterate(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx, int quadratic,
+                         int n_iter, const float *frames, const float *W, const uint8_t *M,
+                         const double *delta, double *u_inout, double *Iref, double *w,
+                         double *err_out, int nthreads)
+{
+    for (int it = 0; it < n_iter; ++it) {
+        pxst_oracle_make_object_map(N, ny, nx, Ry, Rx, frames, W, M, u_inout, delta, Iref, w);
+        pxst_oracle_update_pixel_map(N, ny, nx, Ry, Rx, Sy, Sx, quadratic, frames, W, M, Iref,
+                                     w, delta, u_inout, u_inout, err_out, 0, ny, nthreads);
+    }
+    /* I_ref and w are those built in the last iteration's step (i) */
+}

@@ -1,0 +1,332 @@
+"""Pins for the FP64 oracle: checks against what the paper and the mathematics fix.
+
+Each ``pin_*`` takes an oracle library handle ``L`` (the real build, or a build of a copy
+of the source with a planted mistake) and raises AssertionError if the oracle disagrees
+with a value or property that does not come from the oracle itself:
+
+  * worked values of the paper's bilinear formulas (tests/golden/*.txt),
+  * closed forms (bilinear interpolation reproduces a + b x + c y + d x y exactly; a least
+    squares paraboloid through an exact paraboloid returns its vertex; a quadratic error
+    surface has its minimum at the true shift),
+  * invariants (conservation of the scattered weight and of its first moment, a
+    constant reference is returned unchanged),
+  * exact special cases (integer maps reproduce the reference exactly; noiseless data
+    with integer truth has zero error at the truth),
+  * the same error computed a second way (plain array indexing for integer shifts),
+  * statistical truth recovery on noiseless data (0.01 px RMS at 400 frames).
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import gen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rows(name):
+    out = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                out.append(line.split())
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# bilinear interpolation and assignment (section "Sub-pixel interpolation")
+# ---------------------------------------------------------------------------------------
+
+def pin_bilinear_golden(L):
+    for r in _rows("bilinear_masked.txt"):
+        f = np.array([float(v) for v in r[0:4]]).reshape(2, 2)
+        m = np.array([float(v) for v in r[4:8]]).reshape(2, 2)
+        x, y = float(r[8]), float(r[9])
+        got = oracle.gather(f * m, m, x, y, L=L)
+        if r[10] == "none":
+            assert got is None, (r, got)
+        else:
+            assert got is not None and abs(got - float(r[10])) < 1e-14, (r, got)
+
+
+def pin_bilinear_exact_on_bilinear_functions(L):
+    """a + b i + c j + d i j is reproduced exactly at any point inside the grid."""
+    rng = np.random.default_rng(1)
+    a, b, c, d = rng.normal(size=4)
+    ii, jj = np.meshgrid(np.arange(7.0), np.arange(9.0), indexing="ij")
+    F = a + b * ii + c * jj + d * ii * jj
+    ones = np.ones_like(F)
+    for _ in range(200):
+        q0, q1 = rng.uniform(0, 6), rng.uniform(0, 8)
+        got = oracle.gather(F, ones, q0, q1, L=L)
+        want = a + b * q0 + c * q1 + d * q0 * q1
+        assert got is not None and abs(got - want) < 1e-12, (q0, q1, got, want)
+
+
+def pin_scatter_golden(L):
+    frames = np.array([[[6.0]]], dtype=np.float32)
+    W = np.array([[2.0]], dtype=np.float32)
+    M = np.ones((1, 1), np.uint8)
+    u = np.array([[[0.25]], [[0.5]]])
+    delta = np.zeros((1, 2))
+    Iref, w = oracle.make_object_map(frames, W, M, u, delta, (2, 2), L=L)
+    for r in _rows("scatter_single.txt"):
+        i, j, wv, iv = int(r[0]), int(r[1]), float(r[2]), float(r[3])
+        assert abs(w[i, j] - wv) < 1e-14 and abs(Iref[i, j] - iv) < 1e-14, (r, w, Iref)
+
+
+# ---------------------------------------------------------------------------------------
+# make_object_map (section "Make reference image")
+# ---------------------------------------------------------------------------------------
+
+def _integer_scan(rng, N=9, ny=12, nx=10, R=(40, 44)):
+    """Integer map and translations; every value exactly representable in float32."""
+    Iref = rng.integers(32, 97, size=R).astype(np.float64) / 64.0
+    W = (2.0 ** rng.integers(0, 4, size=(ny, nx))).astype(np.float32)
+    M = (rng.random((ny, nx)) > 0.15).astype(np.uint8)
+    uy = 9 + np.arange(ny) * 2          # magnification 2 along rows, 1 along columns
+    ux = 7 + np.arange(nx)
+    u = np.empty((2, ny, nx))
+    u[0] = uy[:, None]
+    u[1] = ux[None, :]
+    delta = np.stack([rng.integers(0, 6, N), rng.integers(-3, 4, N)], axis=1).astype(np.float64)
+    frames = np.empty((N, ny, nx), np.float32)
+    for n in range(N):
+        frames[n] = W * Iref[(u[0] - delta[n, 0]).astype(int), (u[1] - delta[n, 1]).astype(int)]
+    return frames, W, M, u, delta, Iref
+
+
+def pin_omap_integer_identity(L):
+    """Integer u - Delta: every frame lands on grid points with weight 1, so I_ref is
+    reproduced exactly wherever it is covered, and w = sum of W^2 over the hits."""
+    rng = np.random.default_rng(2)
+    frames, W, M, u, delta, Iref_true = _integer_scan(rng)
+    Iref, w = oracle.make_object_map(frames, W, M, u, delta, Iref_true.shape, L=L)
+    hits = np.zeros(Iref_true.shape)
+    for n in range(frames.shape[0]):
+        qi = (u[0] - delta[n, 0]).astype(int)
+        qj = (u[1] - delta[n, 1]).astype(int)
+        np.add.at(hits, (qi[M > 0], qj[M > 0]), (W.astype(np.float64) ** 2)[M > 0])
+    cov = hits > 0
+    assert cov.sum() > 50
+    assert np.array_equal(Iref[cov], Iref_true[cov]), np.abs(Iref - Iref_true)[cov].max()
+    assert np.array_equal(w, hits)
+    assert np.all(Iref[~cov] == 0.0)
+
+
+def _fractional_scan(rng, N=7, ny=9, nx=11, R=(48, 52), const=None):
+    u = np.empty((2, ny, nx))
+    u[0] = 12 + 1.37 * np.arange(ny)[:, None] + 0.3 * rng.random((ny, nx))
+    u[1] = 10 + 1.61 * np.arange(nx)[None, :] + 0.3 * rng.random((ny, nx))
+    delta = rng.uniform(0, 8, size=(N, 2))
+    W = rng.integers(20, 200, size=(ny, nx)).astype(np.float32)   # W * const exact in float32
+    M = (rng.random((ny, nx)) > 0.1).astype(np.uint8)
+    if const is None:
+        frames = rng.uniform(10, 300, size=(N, ny, nx)).astype(np.float32)
+    else:
+        frames = np.broadcast_to(W * np.float32(const), (N, ny, nx)).astype(np.float32)
+    return frames, W, M, u, delta, R
+
+
+def pin_omap_constant_reference(L):
+    """I = W c  =>  sum b W (W c) / sum b W^2 = c on every covered cell, for any
+    fractional positions and any whitefield."""
+    rng = np.random.default_rng(3)
+    frames, W, M, u, delta, R = _fractional_scan(rng, const=0.75)
+    Iref, w = oracle.make_object_map(frames, W, M, u, delta, R, L=L)
+    cov = w > 0
+    assert cov.sum() > 100
+    np.testing.assert_allclose(Iref[cov], 0.75, rtol=1e-12)
+
+
+def pin_omap_moments(L):
+    """The bilinear weights sum to 1 and their centroid is the point itself, so with every
+    corner inside the grid: sum w = sum M W^2, sum I_ref w = sum M W I, and
+    sum_c c w(c) = sum M W^2 (u - Delta) on each axis."""
+    rng = np.random.default_rng(4)
+    frames, W, M, u, delta, R = _fractional_scan(rng)
+    Iref, w = oracle.make_object_map(frames, W, M, u, delta, R, L=L)
+    Wd, Md, Fd = W.astype(np.float64), M.astype(np.float64), frames.astype(np.float64)
+    N = frames.shape[0]
+    np.testing.assert_allclose(w.sum(), N * (Md * Wd ** 2).sum(), rtol=1e-12)
+    np.testing.assert_allclose((Iref * w).sum(), (Md * Wd * Fd).sum(), rtol=1e-12)
+    ci, cj = np.meshgrid(np.arange(R[0]), np.arange(R[1]), indexing="ij")
+    for axis, cc in ((0, ci), (1, cj)):
+        want = sum((Md * Wd ** 2 * (u[axis] - delta[n, axis])).sum() for n in range(N))
+        np.testing.assert_allclose((cc * w).sum(), want, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# update_pixel_map (section "Update pixel mapping")
+# ---------------------------------------------------------------------------------------
+
+def _direct_window(frames, W, Iref, w, delta, u, window, i, j):
+    """e over the window by plain indexing (integer translations only): frames whose
+    sample c - Delta_n is outside the grid or uncovered are left out of both sums."""
+    Sy, Sx = window
+    ci = int(np.floor(u[0, i, j] + 0.5))
+    cj = int(np.floor(u[1, i, j] + 0.5))
+    e = np.empty((2 * Sy + 1, 2 * Sx + 1))
+    Wv = float(W[i, j])
+    for a in range(-Sy, Sy + 1):
+        for b in range(-Sx, Sx + 1):
+            err = var = 0.0
+            nv = 0
+            for n in range(frames.shape[0]):
+                qi, qj = ci + a - int(delta[n, 0]), cj + b - int(delta[n, 1])
+                if not (0 <= qi < Iref.shape[0] and 0 <= qj < Iref.shape[1]) or w[qi, qj] <= 0:
+                    continue
+                I = float(frames[n, i, j])
+                err += (I - Wv * Iref[qi, qj]) ** 2
+                var += (I - Wv) ** 2
+                nv += 1
+            e[a + Sy, b + Sx] = np.inf if nv == 0 else (err / var if var > 0 else err)
+    return e, (ci, cj)
+
+
+def pin_upm_window_by_indexing(L):
+    rng = np.random.default_rng(5)
+    frames, W, M, u, delta, Iref = _integer_scan(rng)
+    frames = rng.poisson(frames.astype(np.float64) * 50).astype(np.float32)
+    W = (W * 50).astype(np.float32)
+    u = u + rng.uniform(-0.49, 0.49, size=u.shape)
+    w = np.ones_like(Iref)
+    w[20:24, 15:30] = 0.0                     # a hole: frames landing there drop out
+    window = (2, 3)
+    for (i, j) in [(0, 0), (5, 4), (11, 9), (7, 2), (3, 8)]:
+        e, c = oracle.pixel_window(frames, W, M, Iref, w, delta, u, window, i * frames.shape[2] + j, L=L)
+        want, cw = _direct_window(frames, W, Iref, w, delta, u, window, i, j)
+        assert c == cw, (c, cw)
+        np.testing.assert_allclose(e, want, rtol=1e-12)
+
+
+def pin_upm_exact_search(L):
+    """Noiseless frames rendered from the grid at integer positions: the error at the
+    truth is 0 and the argmin lands on the truth, starting anywhere in the window."""
+    rng = np.random.default_rng(6)
+    frames, W, M, u_true, delta, Iref = _integer_scan(rng)
+    w = np.ones_like(Iref)
+    u0 = u_true + rng.integers(-2, 3, size=u_true.shape) + rng.uniform(-0.4, 0.4, size=u_true.shape)
+    u, err = oracle.update_pixel_map(frames, W, M, Iref, w, delta, u0, (3, 3), quadratic=False, L=L)
+    good = M > 0
+    assert np.array_equal(u[:, good], u_true[:, good])
+    assert np.all(err[good] == 0.0)
+    assert np.array_equal(u[:, ~good], u0[:, ~good])          # M = 0 keeps its u
+    assert np.all(np.isnan(err[~good]))
+
+
+def pin_upm_linear_field_exact(L):
+    """Reference linear along the columns: the error is exactly quadratic in the column
+    shift (bilinear reads of a linear function are exact, even at fractional
+    translations), so the refined column coordinate equals the truth."""
+    rng = np.random.default_rng(7)
+    N, ny, nx, R = 6, 5, 7, (30, 60)
+    alpha, beta = 0.4, 0.013
+    Iref = alpha + beta * np.broadcast_to(np.arange(R[1], dtype=np.float64), R)
+    u = np.empty((2, ny, nx))
+    u[0] = 10 + np.arange(ny)[:, None]
+    u[1] = 15 + 1.3 * np.arange(nx)[None, :] + rng.uniform(-0.45, 0.45, (ny, nx))
+    delta = np.stack([np.zeros(N), rng.uniform(0, 9, N)], axis=1)
+    W = rng.uniform(50, 150, (ny, nx))
+    frames = np.stack([W * (alpha + beta * (u[1] - delta[n, 1])) for n in range(N)])
+    frames32 = frames.astype(np.float32)
+    # float32 frames: compare against the exact shift of the rounded data
+    W32 = W.astype(np.float32)
+    M = np.ones((ny, nx), np.uint8)
+    u0 = u.copy()
+    u0[1] += rng.integers(-2, 3, (ny, nx))
+    # a one-row window: the error does not depend on the row, so rows are not searched
+    got, err = oracle.update_pixel_map(frames32, W32, M, Iref, np.ones(R), delta, u0, (0, 4),
+                                       quadratic=True, L=L)
+    np.testing.assert_array_equal(got[0], u[0])
+    np.testing.assert_allclose(got[1], u[1], atol=2e-6)
+
+
+def pin_upm_tie_break(L):
+    """Reference periodic with period 2 along the columns and constant along the rows:
+    every candidate with the right column parity has error 0; the first one in row-major
+    window order (smallest row offset, then smallest column offset) must win."""
+    N, ny, nx, R = 4, 3, 4, (30, 40)
+    Iref = 1.0 + 0.5 * (np.arange(R[1]) % 2)[None, :] * np.ones((R[0], 1))
+    u = np.empty((2, ny, nx))
+    u[0] = 12 + np.arange(ny)[:, None]
+    u[1] = 15 + np.arange(nx)[None, :]
+    delta = np.array([[0, 0], [1, 2], [2, 4], [0, 6]], dtype=np.float64)
+    W = np.full((ny, nx), 100.0, np.float32)
+    frames = np.stack([W * Iref[(u[0] - d[0]).astype(int), (u[1] - d[1]).astype(int)] for d in delta]).astype(np.float32)
+    M = np.ones((ny, nx), np.uint8)
+    got, err = oracle.update_pixel_map(frames, W, M, Iref, np.ones(R), delta, u, (2, 3), quadratic=False, L=L)
+    # column offsets -3..3 with even offset give error 0; first is -2; row offset -2 wins
+    np.testing.assert_array_equal(got[0], u[0] - 2)
+    np.testing.assert_array_equal(got[1], u[1] - 2)
+
+
+def pin_upm_degenerate(L):
+    """No valid frame for any candidate: e = +inf everywhere and u is kept."""
+    N, ny, nx, R = 3, 2, 2, (10, 10)
+    frames = np.full((N, ny, nx), 100, np.float32)
+    W = np.full((ny, nx), 90, np.float32)
+    M = np.ones((ny, nx), np.uint8)
+    u = np.full((2, ny, nx), 5.2)
+    delta = np.zeros((N, 2))
+    got, err = oracle.update_pixel_map(frames, W, M, np.ones(R), np.zeros(R), delta, u, (1, 1), L=L)
+    assert np.array_equal(got, u) and np.all(np.isinf(err))
+
+
+# ---------------------------------------------------------------------------------------
+# quadratic refinement
+# ---------------------------------------------------------------------------------------
+
+def pin_fit_exact_paraboloid(L):
+    rng = np.random.default_rng(8)
+    a, b = np.meshgrid([-1.0, 0.0, 1.0], [-1.0, 0.0, 1.0], indexing="ij")
+    for _ in range(100):
+        A = rng.normal(size=(2, 2))
+        H = A @ A.T + 0.2 * np.eye(2)                     # positive definite
+        v = rng.uniform(-0.5, 0.5, 2)
+        f0 = rng.uniform(0, 3)
+        d = np.stack([a - v[0], b - v[1]])
+        f = f0 + 0.5 * np.einsum("i...,ij,j...->...", d, H, d)
+        da, db = oracle.quadratic_fit(f, L=L)
+        assert abs(da - v[0]) < 1e-10 and abs(db - v[1]) < 1e-10, (da, db, v)
+
+
+def pin_fit_fallbacks(L):
+    # a missing corner: the separable parabola is fitted per axis through the cross
+    f = np.array([[np.inf, 1.0, 2.0], [0.5, 0.1, 0.9], [2.0, 0.6, 2.0]])
+    da, db = oracle.quadratic_fit(f, L=L)
+    assert abs(da - (1.0 - 0.6) / (2 * (1.0 - 0.2 + 0.6))) < 1e-14
+    assert abs(db - (0.5 - 0.9) / (2 * (0.5 - 0.2 + 0.9))) < 1e-14
+    # flat along one axis and a saddle overall: no shift on the flat axis
+    f = np.array([[1.0, 0.0, 1.0], [1.0, 0.0, 1.0], [1.0, 0.0, 1.0]])
+    assert oracle.quadratic_fit(f, L=L) == (0.0, 0.0)
+    # an edge argmin (missing neighbours on one axis only)
+    f = np.array([[np.inf, np.inf, np.inf], [0.7, 0.2, 0.3], [0.9, 0.5, 0.8]])
+    da, db = oracle.quadratic_fit(f, L=L)
+    assert da == 0.0 and abs(db - (0.7 - 0.3) / (2 * (0.7 - 0.4 + 0.3))) < 1e-14
+
+
+# ---------------------------------------------------------------------------------------
+# truth recovery on noiseless data with the true reference
+# ---------------------------------------------------------------------------------------
+
+def pin_truth_recovery(L):
+    """400 frames of noiseless data rendered from the continuous field (not from its
+    grid), the grid as I_ref: one update recovers the fractional truth to 0.01 px RMS
+    with no bias beyond 0.002 px."""
+    s = gen.tiny2d(n_side=20, det=32, step=2, ref=120, sigma=2.0, mag=1.5, offset=50.0,
+                   aberr=3.0, noise=False, seed=gen.BASE_SEED + 100)
+    u, err = oracle.update_pixel_map(s.frames, s.W, s.M, s.Iref_true, np.ones(s.ref_shape), s.delta,
+                                     s.u_true, s.window, L=L)
+    d = (u - s.u_true)[:, 2:-2, 2:-2]
+    rms = float(np.sqrt((d ** 2).mean()))
+    assert rms < 0.01, rms
+    assert abs(float(d.mean())) < 0.002, d.mean()
+    assert float(np.abs(d).max()) < 0.05, np.abs(d).max()
+
+
+ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
