@@ -1,0 +1,328 @@
+"""Benchmark of the PXST main loop on GB300: one step = one iteration (make_object_map +
+update_pixel_map) of the 1-D lens scan (121 frames of 512 x 1536, window +-1 x +-24),
+synthetic data from the seeded generator.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pxst|reference]
+
+Prints one JSON line (rank 0). `value` is pixel-shift-frame evaluations per second over
+the whole job; `ms_per_step` the iteration time. Under torchrun each rank runs its own
+scan (seed + rank): weak scaling, no collective on the data path.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+METRIC = "PXST iteration time & pixel·shift·frame evals/s; served scans/s, p50/p99"
+UNIT = "pixel·shift·frame evals/s"
+KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/csrc/omap.cu",
+                  "paper_2003_12726_gb300/csrc/pxst_common.cuh"]
+
+
+def evals_per_step(s):
+    Sy, Sx = s.window
+    return int(s.M.sum()) * (2 * Sy + 1) * (2 * Sx + 1) * s.frames.shape[0]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0=None, t1=None):
+        rows = [p for (t, p) in self.rows if (t0 is None or t >= t0) and (t1 is None or t <= t1)]
+        busy = [p for p in rows if p[4].isdigit() and int(p[4]) > 0] or rows
+        if not busy:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in busy if num(p[1]) is not None]
+        mx = [num(p[2]) for p in busy if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in busy for i in range(4) if p[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(busy)}
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_sample(s, target_s=12.0, max_rows=None, threads=None):
+    """The oracle as it stands on a stripe of detector rows: make_object_map from the
+    stripe's pixels, then update_pixel_map of the stripe. Rows are added until about
+    target_s seconds of CPU work; returns (evals/s, rows, seconds, threads)."""
+    import oracle
+    threads = threads or oracle.default_threads()
+    ny = s.frames.shape[1]
+    rows_active = np.flatnonzero(s.M.any(axis=1))
+    r0 = int(rows_active[len(rows_active) // 2]) if rows_active.size else 0
+    n_rows, spent, evals = 1, 0.0, 0
+    Sy, Sx = s.window
+    nwin = (2 * Sy + 1) * (2 * Sx + 1)
+    while True:
+        r1 = min(ny, r0 + n_rows)
+        sl = slice(r0, r1)
+        fr = np.ascontiguousarray(s.frames[:, sl])
+        t = time.perf_counter()
+        Iref, w = oracle.make_object_map(fr, s.W[sl], s.M[sl], s.u_init[:, sl], s.delta, s.ref_shape)
+        oracle.update_pixel_map(fr, s.W[sl], s.M[sl], Iref, w, s.delta, s.u_init[:, sl], s.window,
+                                threads=threads)
+        dt = time.perf_counter() - t
+        spent, evals = dt, int(s.M[sl].sum()) * nwin * s.frames.shape[0]
+        if dt >= target_s * 0.5 or r1 >= ny or (max_rows and n_rows >= max_rows):
+            break
+        n_rows = max(n_rows + 1, int(n_rows * min(8.0, target_s / max(dt, 1e-3))))
+    return evals / spent, r1 - r0, spent, threads
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    s = gen.config_lens1d()
+    per_step = []
+    rows = None
+    for k in range(args.warmup + args.steps):
+        rate, rows, sec, threads = cpu_sample(s, target_s=args.ref_step_s, max_rows=rows)
+        if k >= args.warmup:
+            per_step.append((rate, sec))
+    value = float(np.mean([r for r, _ in per_step]))
+    ms = float(np.mean([t for _, t in per_step]) * 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": s.name, "frames": int(s.frames.shape[0]), "detector": list(s.frames.shape[1:]),
+                       "window": list(s.window), "reference": list(s.ref_shape)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{rows} detector rows of {s.frames.shape[1]} per step "
+                                       "(make_object_map of the stripe + update_pixel_map of the stripe)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def load_traffic(name, khash):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(name)
+        if e and e.get("kernel_hash") == khash:
+            return e.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def pxst_arm(args, rank, world, local_rank):
+    import torch
+    import paper_2003_12726_gb300 as px
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    s = gen.config_lens1d(seed=gen.BASE_SEED + 1 + rank)
+    ev_step = evals_per_step(s)
+    rec = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window)
+    u0 = rec.u.clone()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    for _ in range(args.warmup):
+        rec.run(1)
+    torch.cuda.synchronize()
+    code, bits = px.get_status(rec.ws)
+    if code != 0:
+        raise RuntimeError(f"device status {code} bits {bits}")
+
+    # ---- device-resident timed region -------------------------------------------------
+    rec.u.copy_(u0)
+    px.timing_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rec.run(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall1 = time.time()
+    ms = e0.elapsed_time(e1)
+    ktimes = px.timing_read()
+    px.timing_enable(False)
+    n_exact = px.last_exact_count(rec.ws)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ev_step * world / (ms / 1e3) * args.steps
+
+    # ---- end to end through the public API with pinned host buffers ------------------------
+    rec.pin_host_buffers(s.frames, s.W, s.M, s.delta, s.u_init)
+    h2d, d2h = rec.run_host(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        rec.run_host(1)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+        dist.barrier()
+    e2e_value = ev_step * world / (ms_e2e / 1e3) * args.steps
+    if sampler:
+        sampler.stop()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ------------------------------------------------
+    pk, basis = peaks()
+    name = max(ktimes, key=lambda k: ktimes[k][1])
+    launches, tot = ktimes[name]
+    avg_ms = tot / max(launches, 1)
+    props = torch.cuda.get_device_properties(local_rank)
+    sms = props.multi_processor_count
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    if name in ("upm_search", "upm_exact"):
+        flop = 4.0 * ev_step                                  # 2 FP32 FMA per evaluation
+        achieved = flop / (avg_ms * 1e-3) / 1e12
+        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12            # FP32 lanes x FMA x clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
+    else:
+        P = s.frames.shape[1] * s.frames.shape[2]
+        R = s.ref_shape[0] * s.ref_shape[1]
+        nbytes = 4.0 * s.frames.shape[0] * P + 21.0 * P + 32.0 * R
+        achieved = nbytes / (avg_ms * 1e-3) / 1e9
+        peak = float(pk["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "kernel": name, "avg_launch_ms": avg_ms, "peak_basis": f"{basis} HBM copy bandwidth"}
+    roof["traffic"] = load_traffic(name, kernel_hash())
+
+    clocks = sampler.summary(t_wall0 - 0.2, t_wall1 + 0.2) if sampler else None
+    if clocks and clocks.get("samples", 0) == 0:
+        clocks = sampler.summary()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, rows, sec, threads = cpu_sample(s, target_s=args.cpu_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{rows} detector rows of {s.frames.shape[1]}: make_object_map of the stripe + "
+                         f"update_pixel_map of the stripe, {sec:.1f} s"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": s.name, "frames": int(s.frames.shape[0]),
+                       "detector": list(s.frames.shape[1:]), "window": list(s.window),
+                       "reference": list(s.ref_shape), "form": "fp32", "quadratic": True,
+                       "evals_per_step": ev_step, "parallelism": f"replicas{world}",
+                       "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": ms_e2e / args.steps},
+            "gpu_launches": int(sum(v[0] for v in ktimes.values())),
+            "kernel_ms": {k: (v[1] / v[0] if v[0] else 0.0) for k, v in ktimes.items()},
+            "exact_path_pixels": n_exact, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="pxst", choices=["pxst", "reference"])
+    ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-step-s", type=float, default=6.0, help="oracle seconds per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        pxst_arm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * pxst.h -- C ABI of the GB300 (sm_103a) PXST hot-path library, libpxst.so.
+ *
+ * The method is ptychographic X-ray speckle tracking as described in Morgan et al.,
+ * "speckle-tracking: a software suite for ptychographic X-ray speckle tracking".
+ * The library implements steps (i) and (ii) of the main loop (section "Main loop"):
+ * make the reference image, then update the pixel map, on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Array pointers are DEVICE pointers into C-contiguous arrays owned by the caller.
+ *     The library never allocates device memory: scratch space is the caller's
+ *     `workspace` buffer, at least pxst_workspace_size() bytes, 256-byte aligned.
+ *   - Layouts (discrete forward model of section "Initialisation"):
+ *       frames  float32 [n_frames][ny][nx]   I[n, i, j]
+ *       W       float32 [ny][nx]             whitefield
+ *       mask    uint8   [ny][nx]             M: 1 = good pixel, 0 = excluded
+ *       u       float64 [2][ny][nx]          pixel map; u[0] = row (slow scan, i),
+ *                                            u[1] = column (fast scan, j), in units of
+ *                                            reference-image pixels
+ *       delta   float64 [n_frames][2]        (Delta_i[n], Delta_j[n]), same units
+ *       I_ref   float32 [ref_ny][ref_nx]     reference image
+ *       w       float32 [ref_ny][ref_nx]     accumulated weight sum_n sum_x b M W^2
+ *                                            (0 = the reference pixel is not covered)
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *     Argument and shape errors are detected on the host and returned before anything
+ *     is launched. Problems found on the device (a non-finite or out-of-range pixel-map
+ *     entry, a wait that timed out) set bits in a status word inside the workspace;
+ *     pxst_get_status() synchronises the stream and returns and clears them.
+ *   - The workspace must not be shared by calls that may run concurrently.
+ */
+#ifndef PXST_H
+#define PXST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pxst_status;
+#define PXST_OK            0
+#define PXST_ERR_ARG      (-1)   /* null pointer, negative size, bad option value      */
+#define PXST_ERR_SHAPE    (-2)   /* inconsistent or unsupported dimensions             */
+#define PXST_ERR_RANGE    (-3)   /* device saw a non-finite / out-of-range map entry   */
+#define PXST_ERR_CUDA     (-4)   /* a CUDA runtime call failed                         */
+#define PXST_ERR_NOMEM    (-5)   /* workspace smaller than pxst_workspace_size()       */
+#define PXST_ERR_TIMEOUT  (-6)   /* a device-side wait gave up                         */
+
+/* Device status bits (pxst_get_status reports the most severe as a pxst_status). */
+#define PXST_DEV_NONFINITE_U  0x1
+#define PXST_DEV_U_RANGE      0x2
+#define PXST_DEV_TIMEOUT      0x4
+
+typedef struct {
+    int32_t n_frames;   /* N  >= 1 */
+    int32_t ny, nx;     /* detector rows (slow scan) and columns (fast scan) */
+    int32_t ref_ny, ref_nx;   /* reference-image grid */
+} pxst_dims;
+
+/* Arithmetic form of the candidate search. */
+#define PXST_FORM_FP32  0   /* direct sum of (I - W R)^2 in FP32 on CUDA cores */
+
+typedef struct {
+    int32_t win_y, win_x;  /* search window half-widths S_y, S_x: candidates are the
+                              integers c = round(u) + (a, b), |a| <= S_y, |b| <= S_x */
+    int32_t quadratic;     /* 1: 3x3 paraboloid sub-pixel refinement, 0: integer argmin */
+    int32_t form;          /* PXST_FORM_* */
+    int32_t rescore_k;     /* reserved for the reduced-precision forms (0 = default) */
+    int32_t reserved;
+    int64_t timeout_ns;    /* reserved for device-side waits (0 = default) */
+} pxst_options;
+
+/* Bytes of workspace needed by every entry point below for these sizes. */
+size_t pxst_workspace_size(const pxst_dims *dims, const pxst_options *opts);
+
+/*
+ * make_object_map -- "Make reference image" (section "Main loop", its first
+ * pseudo-code block, with the bilinear assignment rule of section "Sub-pixel
+ * interpolation"). For every frame n and pixel (i, j) with M = 1, the point
+ * u[:, i, j] - Delta[n] distributes M W I[n,i,j] into a numerator and M W^2 into w over
+ * the four surrounding reference pixels with bilinear weights; corners outside the grid
+ * are dropped. Then I_ref = numerator / w where w > 0 and 0 elsewhere.
+ * Outputs I_ref and w are overwritten. Accumulation: FP32 in shared memory per tile,
+ * FP64 in global memory, FP64 division.
+ */
+pxst_status pxst_make_object_map(const pxst_dims *dims, const float *frames, const float *W,
+                                 const uint8_t *mask, const double *u, const double *delta,
+                                 float *I_ref, float *w, void *workspace, size_t ws_bytes,
+                                 void *stream);
+
+/*
+ * update_pixel_map -- "Update pixel mapping" (section "Main loop", second pseudo-code
+ * block, and the quadratic_refinement option described right after it). For every pixel
+ * with M = 1 and each integer candidate c in the window centred on round(u) (halves
+ * round up): error(c) = sum_n (I - W R_n(c))^2 and var(c) = sum_n (I - W)^2, where
+ * R_n(c) reads I_ref at c - Delta[n] by the masked, renormalised bilinear rule of
+ * section "Sub-pixel interpolation" (mask: inside the grid and w > 0); frames whose
+ * read has no valid corner are left out of both sums. e = error / var (error if
+ * var = 0, +inf if no frame is valid). u becomes the first minimum in row-major window
+ * order, refined by a least-squares paraboloid through the 3x3 errors about it when
+ * opts->quadratic is set (per-axis parabolas where the 3x3 is incomplete or not convex).
+ * u_inout is updated in place; pixels with M = 0, or without any valid candidate, keep
+ * their u. err_out (nullable) receives e at the chosen integer candidate (NaN where
+ * M = 0, +inf where nothing was valid).
+ */
+pxst_status pxst_update_pixel_map(const pxst_dims *dims, const pxst_options *opts,
+                                  const float *frames, const float *W, const uint8_t *mask,
+                                  const float *I_ref, const float *w, const double *delta,
+                                  double *u_inout, float *err_out, void *workspace,
+                                  size_t ws_bytes, void *stream);
+
+/*
+ * iterate -- n_iter passes of the main loop's steps (i) and (ii): make_object_map from
+ * the current u, then update_pixel_map with that reference (section "Main loop").
+ * On return I_ref and w hold the reference built in the last pass, u_inout the map
+ * after the last update and err_out (nullable) its errors.
+ */
+pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_t n_iter,
+                         const float *frames, const float *W, const uint8_t *mask,
+                         const double *delta, double *u_inout, float *I_ref, float *w,
+                         float *err_out, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * reference_terms -- the per-candidate sums that turn the error of the update step
+ * into a cross term plus separable parts (expanding the square of the "Update pixel
+ * mapping" error): T[c] = sum_n V_n(c) R_n(c)^2 and n_valid[c] = sum_n V_n(c) for every
+ * reference pixel c, with R_n(c) and V_n(c) the masked bilinear read of I_ref at
+ * c - Delta[n] and its validity, as in pxst_update_pixel_map.
+ * T float32 [ref_ny][ref_nx], n_valid int32 [ref_ny][ref_nx], both overwritten.
+ */
+pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, const float *w,
+                                 const double *delta, float *T, int32_t *n_valid,
+                                 void *workspace, size_t ws_bytes, void *stream);
+
+/* Synchronise `stream`, then return (and clear) the device status word in `workspace`:
+ * PXST_OK, PXST_ERR_RANGE or PXST_ERR_TIMEOUT. `bits_out` (nullable) gets the raw bits. */
+pxst_status pxst_get_status(void *workspace, void *stream, int32_t *bits_out);
+
+/* Number of pixels the last update on this workspace handed to the exact (slow) search
+ * because a candidate read an uncovered or out-of-grid reference pixel, or because the
+ * tile's reference window did not fit in shared memory. Synchronises `stream`. */
+pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_out);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream.
+ * pxst_timing_enable(1) starts recording (and clears earlier records);
+ * pxst_timing_read() synchronises the recorded events and returns, for kernel k,
+ * the number of launches and their summed duration in ms. Kernel ids: */
+#define PXST_K_PREPARE    0   /* per-frame shift table */
+#define PXST_K_SCATTER    1   /* make_object_map scatter (includes the accumulator clear) */
+#define PXST_K_NORMALISE  2   /* make_object_map normalisation */
+#define PXST_K_SEARCH     3   /* update_pixel_map candidate search + refinement */
+#define PXST_K_EXACT      4   /* update_pixel_map exact path */
+#define PXST_K_REFTERMS   5   /* reference_terms */
+#define PXST_K_COUNT      6
+pxst_status pxst_timing_enable(int32_t enable);
+pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
+const char *pxst_kernel_name(int32_t k);
+
+/* Human-readable text for a status code. */
+const char *pxst_status_string(pxst_status s);
+
+/* Library version string and the CUDA architecture it was compiled for. */
+const char *pxst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PXST_H */

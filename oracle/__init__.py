@@ -53,6 +53,7 @@ def _bind(L):
     L.pxst_oracle_update_pixel_map.argtypes = [i32] * 8 + [P] * 9 + [i32, i32, i32]
     L.pxst_oracle_update_pixels.argtypes = [i32] * 8 + [P] * 7 + [P, i64, P, P, i32]
     L.pxst_oracle_iterate.argtypes = [i32] * 9 + [P] * 7 + [P, i32]
+    L.pxst_oracle_reference_terms.argtypes = [i32] * 3 + [P] * 5 + [i32]
     return L
 
 
@@ -186,3 +187,14 @@ def iterate(frames, W, M, delta, u, ref_shape, window, n_iter, quadratic=True, t
                               _p(frames), _p(W), _p(M), _p(delta), _p(u), _p(Iref), _p(w),
                               _p(err), int(threads or default_threads()))
     return u, Iref, w, err
+
+
+def reference_terms(Iref, w, delta, threads=None, L=None):
+    """(T float64 [Ry][Rx], nvalid int32 [Ry][Rx]): sum_n V R^2 and sum_n V."""
+    Iref, w, delta = _f64(Iref), _f64(w), _f64(delta)
+    Ry, Rx = Iref.shape
+    T = np.empty((Ry, Rx))
+    nv = np.empty((Ry, Rx), dtype=np.int32)
+    (L or lib()).pxst_oracle_reference_terms(delta.shape[0], Ry, Rx, _p(Iref), _p(w), _p(delta),
+                                             _p(T), _p(nv), int(threads or default_threads()))
+    return T, nv

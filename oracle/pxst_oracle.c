@@ -337,6 +337,37 @@ void pxst_oracle_update_pixels(int N, int ny, int nx, int Ry, int Rx, int Sy, in
 }
 
 /* ---------------------------------------------------------------------------------- */
+/* reference terms: expanding the square of the update step's error,                  */
+/* sum_n V (I - W R)^2 = sum_n V I^2 - 2 W sum_n V I R + W^2 sum_n V R^2, the last sum */
+/* depends on the candidate c only.                                                   */
+/* ---------------------------------------------------------------------------------- */
+
+/* T[c] = sum_n V_n(c) R_n(c)^2 and nvalid[c] = sum_n V_n(c) for every reference pixel
+ * c, with R_n(c) the masked renormalised read of I_ref at c - Delta_n (reading R6). */
+void pxst_oracle_reference_terms(int N, int Ry, int Rx, const double *Iref, const double *w,
+                                 const double *delta, double *T, int32_t *nvalid, int nthreads)
+{
+    if (nthreads <= 0) nthreads = 1;
+    #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (int cy = 0; cy < Ry; ++cy) {
+        for (int cx = 0; cx < Rx; ++cx) {
+            double t = 0.0;
+            int nv = 0;
+            for (int n = 0; n < N; ++n) {
+                double R;
+                if (!pxst_oracle_gather(Iref, w, Ry, Rx, (double)cy - delta[2 * n + 0],
+                                        (double)cx - delta[2 * n + 1], &R))
+                    continue;
+                t += R * R;
+                nv += 1;
+            }
+            T[(int64_t)cy * Rx + cx] = t;
+            nvalid[(int64_t)cy * Rx + cx] = nv;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------------- */
 /* iterate: main loop steps (i) and (ii)                                              */
 /* ---------------------------------------------------------------------------------- */
 

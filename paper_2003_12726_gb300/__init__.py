@@ -1,0 +1,308 @@
+"""Python binding of libpxst.so, the GB300 PXST hot-path library (see include/pxst.h).
+
+Argument marshalling only: every step of make_object_map / update_pixel_map / iterate
+runs in the library's CUDA kernels. PyTorch supplies device memory and the stream.
+There is no CPU fallback: if the library is missing or no GPU is present the calls
+raise.
+
+Tensor conventions (all CUDA, C-contiguous):
+    frames float32 [N][ny][nx], W float32 [ny][nx], M uint8 [ny][nx],
+    u float64 [2][ny][nx], delta float64 [N][2], I_ref / w float32 [Ry][Rx].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "invalid shape", -3: "range", -4: "cuda error",
+          -5: "workspace too small", -6: "timeout"}
+FORM_FP32 = 0
+KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms"]
+
+
+class PxstError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"pxst: {what} failed with status {code} ({STATUS.get(code, '?')})")
+
+
+class _Dims(C.Structure):
+    _fields_ = [("n_frames", C.c_int32), ("ny", C.c_int32), ("nx", C.c_int32),
+                ("ref_ny", C.c_int32), ("ref_nx", C.c_int32)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("win_y", C.c_int32), ("win_x", C.c_int32), ("quadratic", C.c_int32),
+                ("form", C.c_int32), ("rescore_k", C.c_int32), ("reserved", C.c_int32),
+                ("timeout_ns", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libpxst.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libpxst.so is missing: the CUDA extension was not built")
+        L = C.CDLL(path)
+        P, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+        D, O = C.POINTER(_Dims), C.POINTER(_Opts)
+        L.pxst_workspace_size.argtypes = [D, O]
+        L.pxst_workspace_size.restype = sz
+        L.pxst_make_object_map.argtypes = [D] + [P] * 8 + [sz, P]
+        L.pxst_make_object_map.restype = i32
+        L.pxst_update_pixel_map.argtypes = [D, O] + [P] * 9 + [sz, P]
+        L.pxst_update_pixel_map.restype = i32
+        L.pxst_iterate.argtypes = [D, O, i32] + [P] * 9 + [sz, P]
+        L.pxst_iterate.restype = i32
+        L.pxst_reference_terms.argtypes = [D] + [P] * 6 + [sz, P]
+        L.pxst_reference_terms.restype = i32
+        L.pxst_get_status.argtypes = [P, P, C.POINTER(i32)]
+        L.pxst_get_status.restype = i32
+        L.pxst_last_exact_count.argtypes = [P, P, C.POINTER(i64)]
+        L.pxst_last_exact_count.restype = i32
+        L.pxst_timing_enable.argtypes = [i32]
+        L.pxst_timing_enable.restype = i32
+        L.pxst_timing_read.argtypes = [C.POINTER(i64), C.POINTER(C.c_double), i32]
+        L.pxst_timing_read.restype = i32
+        L.pxst_kernel_name.argtypes = [i32]
+        L.pxst_kernel_name.restype = C.c_char_p
+        L.pxst_status_string.argtypes = [i32]
+        L.pxst_status_string.restype = C.c_char_p
+        L.pxst_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_update_pixel_map",
+            "pxst_iterate", "pxst_reference_terms", "pxst_get_status", "pxst_last_exact_count",
+            "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
+            "pxst_version"]
+
+
+# ---------------------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _check(t, dtype, shape, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ptr_or_null(t, dtype, shape, name):
+    return C.c_void_p(None) if t is None else _check(t, dtype, shape, name)
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Dims:
+    n_frames: int
+    ny: int
+    nx: int
+    ref_ny: int
+    ref_nx: int
+
+    def c(self):
+        return _Dims(self.n_frames, self.ny, self.nx, self.ref_ny, self.ref_nx)
+
+
+@dataclass
+class Options:
+    win_y: int
+    win_x: int
+    quadratic: bool = True
+    form: int = FORM_FP32
+
+    def c(self):
+        return _Opts(self.win_y, self.win_x, 1 if self.quadratic else 0, self.form, 0, 0, 0)
+
+
+def workspace_size(dims: Dims, opts: Options | None = None):
+    o = opts.c() if opts is not None else None
+    return int(lib().pxst_workspace_size(C.byref(dims.c()), C.byref(o) if o is not None else None))
+
+
+def workspace(dims: Dims, opts: Options | None = None, device=None):
+    """A caller-owned workspace tensor (uint8, 256-byte aligned by the torch allocator)."""
+    torch = _torch()
+    n = workspace_size(dims, opts)
+    if n == 0:
+        raise PxstError(-2, "workspace_size")
+    ws = torch.zeros(n, dtype=torch.uint8, device=device or "cuda")
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+def _raise(code, what):
+    if code != 0:
+        raise PxstError(code, what)
+
+
+def make_object_map(dims: Dims, frames, W, M, u, delta, I_ref, w, ws, stream=None):
+    """pxst_make_object_map: fills I_ref and w (float32 [Ry][Rx])."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    args = [_check(frames, torch.float32, (N, ny, nx), "frames"), _check(W, torch.float32, (ny, nx), "W"),
+            _check(M, torch.uint8, (ny, nx), "M"), _check(u, torch.float64, (2, ny, nx), "u"),
+            _check(delta, torch.float64, (N, 2), "delta"), _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+            _check(w, torch.float32, (Ry, Rx), "w")]
+    _raise(lib().pxst_make_object_map(C.byref(dims.c()), *args, C.c_void_p(ws.data_ptr()), ws.numel(),
+                                      _stream(stream)), "make_object_map")
+
+
+def update_pixel_map(dims: Dims, opts: Options, frames, W, M, I_ref, w, delta, u, err=None, ws=None,
+                     stream=None):
+    """pxst_update_pixel_map: updates u (float64 [2][ny][nx]) in place; err optional."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    args = [_check(frames, torch.float32, (N, ny, nx), "frames"), _check(W, torch.float32, (ny, nx), "W"),
+            _check(M, torch.uint8, (ny, nx), "M"), _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+            _check(w, torch.float32, (Ry, Rx), "w"), _check(delta, torch.float64, (N, 2), "delta"),
+            _check(u, torch.float64, (2, ny, nx), "u"), _ptr_or_null(err, torch.float32, (ny, nx), "err")]
+    _raise(lib().pxst_update_pixel_map(C.byref(dims.c()), C.byref(opts.c()), *args,
+                                       C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+           "update_pixel_map")
+
+
+def iterate(dims: Dims, opts: Options, n_iter, frames, W, M, delta, u, I_ref, w, err=None, ws=None,
+            stream=None):
+    """pxst_iterate: n_iter x (make_object_map, update_pixel_map), all on the device."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    args = [_check(frames, torch.float32, (N, ny, nx), "frames"), _check(W, torch.float32, (ny, nx), "W"),
+            _check(M, torch.uint8, (ny, nx), "M"), _check(delta, torch.float64, (N, 2), "delta"),
+            _check(u, torch.float64, (2, ny, nx), "u"), _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+            _check(w, torch.float32, (Ry, Rx), "w"), _ptr_or_null(err, torch.float32, (ny, nx), "err")]
+    _raise(lib().pxst_iterate(C.byref(dims.c()), C.byref(opts.c()), int(n_iter), *args,
+                              C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)), "iterate")
+
+
+def reference_terms(dims: Dims, I_ref, w, delta, T, n_valid, ws, stream=None):
+    """pxst_reference_terms: T = sum_n V R^2 (float32) and n_valid = sum_n V (int32)."""
+    torch = _torch()
+    N, Ry, Rx = dims.n_frames, dims.ref_ny, dims.ref_nx
+    args = [_check(I_ref, torch.float32, (Ry, Rx), "I_ref"), _check(w, torch.float32, (Ry, Rx), "w"),
+            _check(delta, torch.float64, (N, 2), "delta"), _check(T, torch.float32, (Ry, Rx), "T"),
+            _check(n_valid, torch.int32, (Ry, Rx), "n_valid")]
+    _raise(lib().pxst_reference_terms(C.byref(dims.c()), *args, C.c_void_p(ws.data_ptr()), ws.numel(),
+                                      _stream(stream)), "reference_terms")
+
+
+def get_status(ws, stream=None):
+    """(status code, raw device bits); synchronises the stream and clears the bits."""
+    bits = C.c_int32()
+    code = lib().pxst_get_status(C.c_void_p(ws.data_ptr()), _stream(stream), C.byref(bits))
+    return int(code), int(bits.value)
+
+
+def last_exact_count(ws, stream=None):
+    n = C.c_int64()
+    _raise(lib().pxst_last_exact_count(C.c_void_p(ws.data_ptr()), _stream(stream), C.byref(n)),
+           "last_exact_count")
+    return int(n.value)
+
+
+def timing_enable(on=True):
+    _raise(lib().pxst_timing_enable(1 if on else 0), "timing_enable")
+
+
+def timing_read():
+    """{kernel name: (launches, total ms)} since timing_enable(True)."""
+    k = len(KERNELS)
+    n = (C.c_int64 * k)()
+    t = (C.c_double * k)()
+    _raise(lib().pxst_timing_read(n, t, k), "timing_read")
+    return {KERNELS[i]: (int(n[i]), float(t[i])) for i in range(k)}
+
+
+def version():
+    return lib().pxst_version().decode()
+
+
+# ---------------------------------------------------------------------------------------
+class Reconstruction:
+    """Device-resident state of one scan (frames, whitefield, mask, translations, map,
+    reference image and workspace), for callers that hold their data on the host.
+
+    ``run(n_iter)`` executes the main loop on the GPU; ``run_host`` is the end-to-end
+    form: it copies the inputs from pinned host memory, iterates and copies the map
+    and the error back, all on one stream.
+    """
+
+    def __init__(self, frames, W, M, delta, u, ref_shape, window, quadratic=True, device="cuda"):
+        torch = _torch()
+        self.dims = Dims(int(frames.shape[0]), int(frames.shape[1]), int(frames.shape[2]),
+                         int(ref_shape[0]), int(ref_shape[1]))
+        self.opts = Options(int(window[0]), int(window[1]), bool(quadratic))
+        dev = torch.device(device)
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt).contiguous()
+        self.frames = t(frames, torch.float32)
+        self.W = t(W, torch.float32)
+        self.M = t(M, torch.uint8)
+        self.delta = t(delta, torch.float64)
+        self.u = t(u, torch.float64)
+        Ry, Rx = ref_shape
+        self.I_ref = torch.zeros((Ry, Rx), dtype=torch.float32, device=dev)
+        self.w = torch.zeros((Ry, Rx), dtype=torch.float32, device=dev)
+        self.err = torch.zeros((self.dims.ny, self.dims.nx), dtype=torch.float32, device=dev)
+        self.ws = workspace(self.dims, self.opts, dev)
+        self._pinned = None
+
+    def run(self, n_iter, stream=None):
+        iterate(self.dims, self.opts, n_iter, self.frames, self.W, self.M, self.delta, self.u,
+                self.I_ref, self.w, self.err, self.ws, stream)
+
+    def pin_host_buffers(self, frames, W, M, delta, u):
+        """Pinned host copies of the per-step inputs and the outputs (for run_host)."""
+        torch = _torch()
+        pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dt).pin_memory()
+        self._pinned = dict(frames=pin(frames, torch.float32), W=pin(W, torch.float32),
+                            M=pin(M, torch.uint8), delta=pin(delta, torch.float64), u=pin(u, torch.float64),
+                            u_out=torch.empty((2, self.dims.ny, self.dims.nx), dtype=torch.float64).pin_memory(),
+                            err_out=torch.empty((self.dims.ny, self.dims.nx), dtype=torch.float32).pin_memory())
+        return self._pinned
+
+    def run_host(self, n_iter, stream=None):
+        """Host -> device inputs, n_iter iterations, device -> host map and error.
+        Returns (h2d bytes, d2h bytes); the host results are in the pinned buffers."""
+        torch = _torch()
+        h = self._pinned
+        s = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            for k in ("frames", "W", "M", "delta", "u"):
+                getattr(self, k).copy_(h[k], non_blocking=True)
+            self.run(n_iter, s)
+            h["u_out"].copy_(self.u, non_blocking=True)
+            h["err_out"].copy_(self.err, non_blocking=True)
+        h2d = sum(h[k].numel() * h[k].element_size() for k in ("frames", "W", "M", "delta", "u"))
+        d2h = h["u_out"].numel() * 8 + h["err_out"].numel() * 4
+        return h2d, d2h

@@ -1,0 +1,312 @@
+// api.cu -- the extern "C" boundary of libpxst.so: argument checks, workspace carving,
+// launch sequencing, device status, and per-kernel event timing.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "pxst_common.cuh"
+
+using namespace pxst;
+
+namespace {
+
+bool dims_ok(const pxst_dims *d) {
+    if (!d) return false;
+    if (d->n_frames < 1 || d->ny < 1 || d->nx < 1 || d->ref_ny < 1 || d->ref_nx < 1) return false;
+    if ((long long)d->ny * d->nx >= (1LL << 31)) return false;           // int pixel indices
+    if ((long long)d->ref_ny * d->ref_nx >= (1LL << 31)) return false;   // int window math
+    return true;
+}
+
+bool opts_ok(const pxst_options *o) {
+    if (!o) return false;
+    if (o->win_y < 0 || o->win_x < 0 || o->win_y > 4096 || o->win_x > 4096) return false;
+    if ((long long)(2 * o->win_y + 1) * (2 * o->win_x + 1) >= (1LL << 30)) return false;
+    if (o->quadratic != 0 && o->quadratic != 1) return false;
+    if (o->form != PXST_FORM_FP32) return false;
+    return true;
+}
+
+struct Ws {
+    WsHeader *hdr;
+    FrameShift *shifts;
+    int *exact_list;
+    double *num, *den;
+};
+
+pxst_status carve(const pxst_dims &d, void *workspace, size_t ws_bytes, Ws &w) {
+    if (!workspace) return PXST_ERR_ARG;
+    if (((uintptr_t)workspace & 255) != 0) return PXST_ERR_ARG;
+    const WsLayout L = ws_layout(d);
+    if (ws_bytes < L.total) return PXST_ERR_NOMEM;
+    char *b = static_cast<char *>(workspace);
+    w.hdr = reinterpret_cast<WsHeader *>(b + L.header);
+    w.shifts = reinterpret_cast<FrameShift *>(b + L.shifts);
+    w.exact_list = reinterpret_cast<int *>(b + L.exact_list);
+    w.num = reinterpret_cast<double *>(b + L.num);
+    w.den = reinterpret_cast<double *>(b + L.den);
+    return PXST_OK;
+}
+
+// ---- per-kernel timing -------------------------------------------------------------
+struct Rec {
+    int k;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+constexpr size_t kMaxRecs = 1 << 16;
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Timed {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int k;
+    cudaStream_t s;
+    Timed(int kernel, cudaStream_t st) : k(kernel), s(st) {
+        std::lock_guard<std::mutex> g(g_tmu);
+        if (g_timing && g_recs.size() < kMaxRecs) {
+            a = take_event();
+            b = take_event();
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Timed() {
+        if (!a) return;
+        std::lock_guard<std::mutex> g(g_tmu);
+        cudaEventRecord(b, s);
+        g_recs.push_back({k, a, b});
+    }
+};
+
+pxst_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PXST_OK;
+    std::fprintf(stderr, "pxst: CUDA error %s\n", cudaGetErrorString(e));
+    return PXST_ERR_CUDA;
+}
+
+#define PXST_TRY(expr)                                   \
+    do {                                                 \
+        cudaError_t _e = (expr);                         \
+        if (_e != cudaSuccess) return cuda_status(_e);   \
+    } while (0)
+
+pxst_status run_prepare(const pxst_dims &d, const double *delta, Ws &w, cudaStream_t s) {
+    Timed t(PXST_K_PREPARE, s);
+    PXST_TRY(launch_prepare(d, delta, w.hdr, w.shifts, 1, s));
+    return PXST_OK;
+}
+
+pxst_status run_omap(const pxst_dims &d, const float *frames, const float *W,
+                     const uint8_t *mask, const double *u, float *I_ref, float *wout, Ws &w,
+                     cudaStream_t s) {
+    {
+        Timed t(PXST_K_SCATTER, s);
+        PXST_TRY(launch_scatter(d, frames, W, mask, u, w.shifts, w.hdr, w.num, w.den, s));
+    }
+    {
+        Timed t(PXST_K_NORMALISE, s);
+        PXST_TRY(launch_normalise(d, w.num, w.den, I_ref, wout, s));
+    }
+    return PXST_OK;
+}
+
+pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *frames,
+                       const float *W, const uint8_t *mask, const float *I_ref, const float *wref,
+                       double *u, float *err_out, Ws &w, cudaStream_t s) {
+    PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, sizeof(int), s));
+    if (d.n_frames <= search_max_frames()) {
+        {
+            Timed t(PXST_K_SEARCH, s);
+            PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr,
+                                   w.exact_list, u, err_out, s));
+        }
+        Timed t(PXST_K_EXACT, s);
+        PXST_TRY(launch_exact(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list,
+                              u, err_out, s));
+    } else {
+        // too many frames to stage a tile on chip: every pixel takes the exact path
+        Timed t(PXST_K_EXACT, s);
+        PXST_TRY(launch_exact(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, nullptr, u,
+                              err_out, s));
+    }
+    return PXST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pxst_workspace_size(const pxst_dims *dims, const pxst_options *opts) {
+    (void)opts;
+    if (!dims_ok(dims)) return 0;
+    return ws_layout(*dims).total;
+}
+
+pxst_status pxst_make_object_map(const pxst_dims *dims, const float *frames, const float *W,
+                                 const uint8_t *mask, const double *u, const double *delta,
+                                 float *I_ref, float *w, void *workspace, size_t ws_bytes,
+                                 void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!frames || !W || !mask || !u || !delta || !I_ref || !w) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    return run_omap(*dims, frames, W, mask, u, I_ref, w, ws, s);
+}
+
+pxst_status pxst_update_pixel_map(const pxst_dims *dims, const pxst_options *opts,
+                                  const float *frames, const float *W, const uint8_t *mask,
+                                  const float *I_ref, const float *w, const double *delta,
+                                  double *u_inout, float *err_out, void *workspace,
+                                  size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!opts_ok(opts)) return PXST_ERR_ARG;
+    if (!frames || !W || !mask || !I_ref || !w || !delta || !u_inout) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    return run_update(*dims, *opts, frames, W, mask, I_ref, w, u_inout, err_out, ws, s);
+}
+
+pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_t n_iter,
+                         const float *frames, const float *W, const uint8_t *mask,
+                         const double *delta, double *u_inout, float *I_ref, float *w,
+                         float *err_out, void *workspace, size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!opts_ok(opts) || n_iter < 0) return PXST_ERR_ARG;
+    if (!frames || !W || !mask || !delta || !u_inout || !I_ref || !w) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    for (int it = 0; it < n_iter; ++it) {
+        st = run_omap(*dims, frames, W, mask, u_inout, I_ref, w, ws, s);
+        if (st != PXST_OK) return st;
+        st = run_update(*dims, *opts, frames, W, mask, I_ref, w, u_inout, err_out, ws, s);
+        if (st != PXST_OK) return st;
+    }
+    return PXST_OK;
+}
+
+pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, const float *w,
+                                 const double *delta, float *T, int32_t *n_valid,
+                                 void *workspace, size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!I_ref || !w || !delta || !T || !n_valid) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    Timed t(PXST_K_REFTERMS, s);
+    PXST_TRY(launch_refterms(*dims, I_ref, w, ws.shifts, T, n_valid, s));
+    return PXST_OK;
+}
+
+pxst_status pxst_get_status(void *workspace, void *stream, int32_t *bits_out) {
+    if (!workspace) return PXST_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader *hdr = static_cast<WsHeader *>(workspace);
+    int bits = 0;
+    PXST_TRY(cudaStreamSynchronize(s));
+    PXST_TRY(cudaMemcpy(&bits, &hdr->status, sizeof(int), cudaMemcpyDeviceToHost));
+    PXST_TRY(cudaMemset(&hdr->status, 0, sizeof(int)));
+    if (bits_out) *bits_out = bits;
+    if (bits & PXST_DEV_TIMEOUT) return PXST_ERR_TIMEOUT;
+    if (bits & (PXST_DEV_NONFINITE_U | PXST_DEV_U_RANGE)) return PXST_ERR_RANGE;
+    return PXST_OK;
+}
+
+pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_out) {
+    if (!workspace || !count_out) return PXST_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader *hdr = static_cast<WsHeader *>(workspace);
+    int n = 0;
+    PXST_TRY(cudaStreamSynchronize(s));
+    PXST_TRY(cudaMemcpy(&n, &hdr->n_exact, sizeof(int), cudaMemcpyDeviceToHost));
+    *count_out = n;
+    return PXST_OK;
+}
+
+pxst_status pxst_timing_enable(int32_t enable) {
+    std::lock_guard<std::mutex> g(g_tmu);
+    for (auto &r : g_recs) {
+        cudaEventSynchronize(r.b);
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    g_timing = enable != 0;
+    return PXST_OK;
+}
+
+pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels) {
+    if (!launches || !total_ms || n_kernels < 0) return PXST_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_tmu);
+    for (int k = 0; k < n_kernels; ++k) {
+        launches[k] = 0;
+        total_ms[k] = 0.0;
+    }
+    for (auto &r : g_recs) {
+        if (r.k >= n_kernels) continue;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_status(e);
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_status(e);
+        launches[r.k] += 1;
+        total_ms[r.k] += ms;
+    }
+    return PXST_OK;
+}
+
+const char *pxst_kernel_name(int32_t k) {
+    switch (k) {
+        case PXST_K_PREPARE: return "prepare";
+        case PXST_K_SCATTER: return "omap_scatter";
+        case PXST_K_NORMALISE: return "omap_normalise";
+        case PXST_K_SEARCH: return "upm_search";
+        case PXST_K_EXACT: return "upm_exact";
+        case PXST_K_REFTERMS: return "reference_terms";
+        default: return "?";
+    }
+}
+
+const char *pxst_status_string(pxst_status s) {
+    switch (s) {
+        case PXST_OK: return "ok";
+        case PXST_ERR_ARG: return "invalid argument";
+        case PXST_ERR_SHAPE: return "invalid or unsupported dimensions";
+        case PXST_ERR_RANGE: return "non-finite or out-of-range pixel map on the device";
+        case PXST_ERR_CUDA: return "CUDA runtime error";
+        case PXST_ERR_NOMEM: return "workspace too small";
+        case PXST_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char *pxst_version(void) { return "pxst 0.1 (sm_103a)"; }
+
+}  // extern "C"

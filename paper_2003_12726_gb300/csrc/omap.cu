@@ -1,0 +1,299 @@
+// omap.cu -- make_object_map ("Make reference image", section "Main loop") and the
+// per-candidate reference terms, for sm_103a.
+//
+//   prepare    : -Delta[n] -> (integer shift, fraction) per frame, and their range.
+//   scatter    : each CTA owns a 32 x 32 pixel tile and a chunk of frames. It privatises
+//                the tile's reference footprint (its u range widened by the chunk's
+//                translation range, +1 for the bilinear corner) in shared memory, adds
+//                b*M*W*I and b*M*W^2 there with FP32 shared-memory atomics, then flushes
+//                the non-zero cells to the FP64 accumulators in global memory with FP64
+//                atomics. A tile whose footprint does not fit adds straight to global.
+//   normalise  : I_ref = num / den (FP64 divide) where den > 0, else 0; w = den.
+//   refterms   : T[c] = sum_n V R^2 and n_valid[c] = sum_n V over the reference grid.
+#include <climits>
+
+#include "pxst_common.cuh"
+
+namespace pxst {
+namespace {
+
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restrict__ delta,
+                                                  WsHeader *hdr, FrameShift *shifts,
+                                                  int reset_exact) {
+    __shared__ int s[4];
+    if (threadIdx.x == 0) {
+        s[0] = INT_MAX; s[1] = INT_MIN; s[2] = INT_MAX; s[3] = INT_MIN;
+    }
+    __syncthreads();
+    int mn_y = INT_MAX, mx_y = INT_MIN, mn_x = INT_MAX, mx_x = INT_MIN;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        FrameShift fs;
+        split_neg_delta(delta[2 * n + 0], fs.ky, fs.fy);
+        split_neg_delta(delta[2 * n + 1], fs.kx, fs.fx);
+        shifts[n] = fs;
+        mn_y = min(mn_y, fs.ky); mx_y = max(mx_y, fs.ky);
+        mn_x = min(mn_x, fs.kx); mx_x = max(mx_x, fs.kx);
+    }
+    atomicMin(&s[0], mn_y); atomicMax(&s[1], mx_y);
+    atomicMin(&s[2], mn_x); atomicMax(&s[3], mx_x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        hdr->kmin_y = s[0]; hdr->kmax_y = s[1];
+        hdr->kmin_x = s[2]; hdr->kmax_x = s[3];
+        if (reset_exact) hdr->n_exact = 0;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+constexpr int SC_TX = 32, SC_TY = 8, SC_PPT = 4;      // 32 x 32 pixels, 256 threads
+constexpr int SC_THREADS = SC_TX * SC_TY;
+constexpr int SC_CAP = 16384;                          // cells (num + den: 128 KB)
+
+struct ScatterArgs {
+    int N, ny, nx, Ry, Rx, chunk;
+    const float *frames, *W;
+    const uint8_t *mask;
+    const double *u;
+    const FrameShift *shifts;
+    WsHeader *hdr;
+    double *num, *den;
+};
+
+__global__ void __launch_bounds__(SC_THREADS) k_scatter(ScatterArgs a) {
+    extern __shared__ float sm[];
+    float *s_num = sm;
+    float *s_den = sm + SC_CAP;
+    __shared__ int s_rng[8];
+
+    const int tx = threadIdx.x % SC_TX, ty = threadIdx.x / SC_TX;
+    const int x = blockIdx.x * SC_TX + tx;
+    const int n0 = blockIdx.z * a.chunk, n1 = min(a.N, n0 + a.chunk);
+    const size_t P = (size_t)a.ny * a.nx;
+
+    if (threadIdx.x < 8) s_rng[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    __syncthreads();
+
+    int iy[SC_PPT], ix[SC_PPT];
+    float fy[SC_PPT], fx[SC_PPT], Wv[SC_PPT];
+    bool act[SC_PPT];
+    int any = 0;
+#pragma unroll
+    for (int q = 0; q < SC_PPT; ++q) {
+        const int y = blockIdx.y * (SC_TY * SC_PPT) + ty + SC_TY * q;
+        act[q] = false;
+        iy[q] = ix[q] = 0;
+        fy[q] = fx[q] = Wv[q] = 0.0f;
+        if (y >= a.ny || x >= a.nx) continue;
+        const size_t p = (size_t)y * a.nx + x;
+        if (!a.mask[p]) continue;
+        const double u0 = a.u[p], u1 = a.u[P + p];
+        if (!isfinite(u0) || !isfinite(u1)) {
+            atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
+            continue;
+        }
+        if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
+            atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
+            continue;
+        }
+        const double f0 = floor(u0), f1 = floor(u1);
+        iy[q] = (int)f0; ix[q] = (int)f1;
+        fy[q] = (float)(u0 - f0); fx[q] = (float)(u1 - f1);
+        if (fy[q] >= 1.0f) { fy[q] = 0.0f; iy[q] += 1; }
+        if (fx[q] >= 1.0f) { fx[q] = 0.0f; ix[q] += 1; }
+        Wv[q] = a.W[p];
+        act[q] = true;
+        any = 1;
+    }
+    int mn_y = INT_MAX, mx_y = INT_MIN, mn_x = INT_MAX, mx_x = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < SC_PPT; ++q)
+        if (act[q]) {
+            mn_y = min(mn_y, iy[q]); mx_y = max(mx_y, iy[q]);
+            mn_x = min(mn_x, ix[q]); mx_x = max(mx_x, ix[q]);
+        }
+    if (any) {
+        atomicMin(&s_rng[0], mn_y); atomicMax(&s_rng[1], mx_y);
+        atomicMin(&s_rng[2], mn_x); atomicMax(&s_rng[3], mx_x);
+    }
+    int kmn_y = INT_MAX, kmx_y = INT_MIN, kmn_x = INT_MAX, kmx_x = INT_MIN;
+    for (int n = n0 + threadIdx.x; n < n1; n += SC_THREADS) {
+        const FrameShift s = a.shifts[n];
+        kmn_y = min(kmn_y, s.ky); kmx_y = max(kmx_y, s.ky);
+        kmn_x = min(kmn_x, s.kx); kmx_x = max(kmx_x, s.kx);
+    }
+    if (n0 + (int)threadIdx.x < n1) {
+        atomicMin(&s_rng[4], kmn_y); atomicMax(&s_rng[5], kmx_y);
+        atomicMin(&s_rng[6], kmn_x); atomicMax(&s_rng[7], kmx_x);
+    }
+    __syncthreads();
+    if (s_rng[0] == INT_MAX || n0 >= n1) return;      // no active pixel in the tile
+
+    // footprint: floor(u) + k (+1 carry, +1 corner)
+    const long long r0 = (long long)s_rng[0] + s_rng[4];
+    const long long r1 = (long long)s_rng[1] + s_rng[5] + 2;
+    const long long c0 = (long long)s_rng[2] + s_rng[6];
+    const long long c1 = (long long)s_rng[3] + s_rng[7] + 2;
+    const long long H = r1 - r0 + 1, Wd = c1 - c0 + 1;
+    const bool fits = H * Wd <= SC_CAP;
+    const int Wdi = (int)Wd;
+
+    if (fits) {
+        for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
+            s_num[c] = 0.0f;
+            s_den[c] = 0.0f;
+        }
+        __syncthreads();
+    }
+
+    for (int n = n0; n < n1; ++n) {
+        const FrameShift s = a.shifts[n];
+        const float *fr = a.frames + (size_t)n * P;
+#pragma unroll
+        for (int q = 0; q < SC_PPT; ++q) {
+            if (!act[q]) continue;
+            const int y = blockIdx.y * (SC_TY * SC_PPT) + ty + SC_TY * q;
+            const float I = __ldg(fr + (size_t)y * a.nx + x);
+            int by = iy[q] + s.ky, bx = ix[q] + s.kx;
+            float sy = fy[q] + s.fy, sx = fx[q] + s.fx;
+            if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
+            if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
+            const float WI = Wv[q] * I, W2 = Wv[q] * Wv[q];
+            const float wt[4] = {(1.0f - sy) * (1.0f - sx), (1.0f - sy) * sx, sy * (1.0f - sx), sy * sx};
+            if (fits) {
+                const int base = (int)((by - r0) * Wd + (bx - c0));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = base + (k >> 1) * Wdi + (k & 1);
+                    atomicAdd(&s_num[c], wt[k] * WI);
+                    atomicAdd(&s_den[c], wt[k] * W2);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int gy = by + (k >> 1), gx = bx + (k & 1);
+                    if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx || wt[k] == 0.0f) continue;
+                    const size_t g = (size_t)gy * a.Rx + gx;
+                    atomicAdd(&a.num[g], (double)(wt[k] * WI));
+                    atomicAdd(&a.den[g], (double)(wt[k] * W2));
+                }
+            }
+        }
+    }
+    if (!fits) return;
+    __syncthreads();
+    for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
+        const float dn = s_den[c], nm = s_num[c];
+        if (dn == 0.0f && nm == 0.0f) continue;
+        const long long gy = r0 + c / Wdi, gx = c0 + c % Wdi;
+        if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;   // corners off the grid
+        const size_t g = (size_t)gy * a.Rx + gx;
+        atomicAdd(&a.num[g], (double)nm);
+        atomicAdd(&a.den[g], (double)dn);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_normalise(size_t R, const double *__restrict__ num,
+                                                   const double *__restrict__ den,
+                                                   float *__restrict__ I_ref,
+                                                   float *__restrict__ w) {
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < R;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const double d = den[c];
+        I_ref[c] = d > 0.0 ? (float)(num[c] / d) : 0.0f;
+        w[c] = (float)d;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_refterms(int N, int Ry, int Rx,
+                                                  const float *__restrict__ Iref,
+                                                  const float *__restrict__ w,
+                                                  const FrameShift *__restrict__ shifts,
+                                                  float *__restrict__ T,
+                                                  int32_t *__restrict__ n_valid) {
+    const size_t R = (size_t)Ry * Rx;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < R;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const int cy = (int)(c / Rx), cx = (int)(c % Rx);
+        float t = 0.0f;
+        int nv = 0;
+        for (int n = 0; n < N; ++n) {
+            const FrameShift s = shifts[n];
+            float Rv;
+            if (gather_masked(Iref, w, Ry, Rx, cy + s.ky, cx + s.kx, s.fy, s.fx, Rv)) {
+                t = fmaf(Rv, Rv, t);
+                ++nv;
+            }
+        }
+        T[c] = t;
+        n_valid[c] = nv;
+    }
+}
+
+int grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    return (int)(b > 152 * 16 ? 152 * 16 : (b == 0 ? 1 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_prepare(const pxst_dims &d, const double *delta, WsHeader *hdr,
+                           FrameShift *shifts, int reset_exact, cudaStream_t stream) {
+    k_prepare<<<1, 1024, 0, stream>>>(d.n_frames, delta, hdr, shifts, reset_exact);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float *W,
+                           const uint8_t *mask, const double *u, const FrameShift *shifts,
+                           WsHeader *hdr, double *num, double *den, cudaStream_t stream) {
+    const size_t R = (size_t)d.ref_ny * d.ref_nx;
+    cudaError_t e = cudaMemsetAsync(num, 0, sizeof(double) * R, stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(den, 0, sizeof(double) * R, stream);
+    if (e != cudaSuccess) return e;
+    static bool attr = false;
+    const int smem = 2 * SC_CAP * (int)sizeof(float);
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    ScatterArgs a;
+    a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
+    a.frames = frames; a.W = W; a.mask = mask; a.u = u; a.shifts = shifts; a.hdr = hdr;
+    a.num = num; a.den = den;
+    const int gx = (d.nx + SC_TX - 1) / SC_TX;
+    const int gy = (d.ny + SC_TY * SC_PPT - 1) / (SC_TY * SC_PPT);
+    const long long tiles = (long long)gx * gy;
+    // enough CTAs for two waves on 152 SMs; chunks of at least 8 frames
+    long long nch = (304 + tiles - 1) / tiles;
+    nch = nch < 1 ? 1 : nch;
+    const long long maxch = (d.n_frames + 7) / 8;
+    if (nch > maxch) nch = maxch;
+    if (nch > 65535) nch = 65535;
+    a.chunk = (int)((d.n_frames + nch - 1) / nch);
+    nch = (d.n_frames + a.chunk - 1) / a.chunk;
+    dim3 grid(gx, gy, (unsigned)nch);
+    k_scatter<<<grid, SC_THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalise(const pxst_dims &d, const double *num, const double *den,
+                             float *I_ref, float *w, cudaStream_t stream) {
+    const size_t R = (size_t)d.ref_ny * d.ref_nx;
+    k_normalise<<<grid_for(R, 256), 256, 0, stream>>>(R, num, den, I_ref, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float *w,
+                            const FrameShift *shifts, float *T, int32_t *n_valid,
+                            cudaStream_t stream) {
+    const size_t R = (size_t)d.ref_ny * d.ref_nx;
+    k_refterms<<<grid_for(R, 256), 256, 0, stream>>>(d.n_frames, d.ref_ny, d.ref_nx, I_ref, w,
+                                                     shifts, T, n_valid);
+    return cudaGetLastError();
+}
+
+}  // namespace pxst

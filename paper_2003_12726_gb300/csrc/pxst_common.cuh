@@ -1,0 +1,116 @@
+// pxst_common.cuh -- device helpers and the workspace layout shared by the kernels of
+// libpxst.so (sm_103a). Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pxst.h"
+
+namespace pxst {
+
+// -Delta[n] split per axis into an integer part and a fraction in [0, 1):
+//   -Delta = k + f.  A reference read at integer candidate c then touches the corners
+//   c + k and c + k + 1 with weights (1 - f) and f, and a scatter of u - Delta touches
+//   floor(u) + k (+1) with the fraction frac(u) + f (carried into k when >= 1).
+struct FrameShift {
+    int ky, kx;
+    float fy, fx;
+};
+
+// Workspace header: the device status word and a few per-call scalars.
+struct WsHeader {
+    int status;        // PXST_DEV_* bits, sticky until pxst_get_status
+    int n_exact;       // pixels appended to the exact-path list by the last update
+    int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
+    int pad[58];
+};
+static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
+
+// Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
+struct WsLayout {
+    size_t header, shifts, exact_list, num, den, total;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+inline WsLayout ws_layout(const pxst_dims &d) {
+    WsLayout L;
+    size_t off = 0;
+    L.header = off;     off += align256(sizeof(WsHeader));
+    L.shifts = off;     off += align256(sizeof(FrameShift) * (size_t)d.n_frames);
+    L.exact_list = off; off += align256(sizeof(int) * (size_t)d.ny * d.nx);
+    L.num = off;        off += align256(sizeof(double) * (size_t)d.ref_ny * d.ref_nx);
+    L.den = off;        off += align256(sizeof(double) * (size_t)d.ref_ny * d.ref_nx);
+    L.total = off;
+    return L;
+}
+
+__device__ __forceinline__ void split_neg_delta(double delta, int &k, float &f) {
+    const double nd = -delta;
+    double fl = floor(nd);
+    float fr = (float)(nd - fl);
+    if (fr >= 1.0f) {          // a fraction just below 1 rounded up in float32
+        fr = 0.0f;
+        fl += 1.0;
+    }
+    k = (int)fl;
+    f = fr;
+}
+
+// |u| beyond this is rejected (status bit) so integer window arithmetic cannot overflow.
+constexpr double kMaxCoord = 1.0e8;
+
+// Launch-time configuration of the search kernel.
+constexpr int kSearchSmemBudget = 200 * 1024;   // dynamic shared memory per CTA (bytes)
+
+// Launch helpers implemented in the .cu files (all asynchronous on `stream`).
+cudaError_t launch_prepare(const pxst_dims &d, const double *delta, WsHeader *hdr,
+                           FrameShift *shifts, int reset_exact, cudaStream_t stream);
+cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float *W,
+                           const uint8_t *mask, const double *u, const FrameShift *shifts,
+                           WsHeader *hdr, double *num, double *den, cudaStream_t stream);
+cudaError_t launch_normalise(const pxst_dims &d, const double *num, const double *den,
+                             float *I_ref, float *w, cudaStream_t stream);
+cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float *frames,
+                          const float *W, const uint8_t *mask, const float *I_ref,
+                          const float *w, const FrameShift *shifts, WsHeader *hdr,
+                          int *exact_list, double *u, float *err_out, cudaStream_t stream);
+cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float *frames,
+                         const float *W, const uint8_t *mask, const float *I_ref,
+                         const float *w, const FrameShift *shifts, WsHeader *hdr,
+                         const int *exact_list, double *u, float *err_out, cudaStream_t stream);
+int search_max_frames();
+cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float *w,
+                            const FrameShift *shifts, float *T, int32_t *n_valid,
+                            cudaStream_t stream);
+
+}  // namespace pxst
+
+namespace pxst {
+
+// Masked, renormalised bilinear read of I_ref (section "Sub-pixel interpolation"):
+// corners (i0, j0), (i0, j0+1), (i0+1, j0), (i0+1, j0+1) with weights
+// (1-fy)(1-fx), (1-fy)fx, fy(1-fx), fy fx; a corner counts if its weight is nonzero,
+// it lies inside the grid and its coverage w is > 0. Returns false if none counts.
+__device__ __forceinline__ bool gather_masked(const float *__restrict__ Iref,
+                                              const float *__restrict__ w, int Ry, int Rx,
+                                              int i0, int j0, float fy, float fx, float &R) {
+    const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx), fy * fx};
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
+        if (wt[k] == 0.0f || ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;
+        const size_t c = (size_t)ii * Rx + jj;
+        if (!(__ldg(w + c) > 0.0f)) continue;
+        num = fmaf(wt[k], __ldg(Iref + c), num);
+        den += wt[k];
+    }
+    if (!(den > 0.0f)) return false;
+    R = num / den;
+    return true;
+}
+
+}  // namespace pxst

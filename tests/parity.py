@@ -1,0 +1,83 @@
+"""Parity criteria between the CUDA path and the FP64 oracle.
+
+  * integer argmin: identical on >= 99.9 % of the pixels with M = 1; every other pixel must
+    be a near-tie: the oracle's own error at the GPU's pick is within
+    1e-5 * e_min + 1e-7 * (sum_n I^2 / var) of the oracle's minimum;
+  * sub-pixel u: within 1e-3 px wherever the integer picks agree;
+  * normalised error at the pick: relative 1e-4 (FP32 sums of at most a few hundred positive
+    terms, each rounded at 2^-24, stay well inside it);
+  * I_ref: relative L2 <= 1e-5 over reference pixels whose oracle weight exceeds
+    1e-4 * max w (a few barely-covered edge pixels would otherwise dominate).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+ARGMIN_AGREE = 0.999
+U_TOL = 1e-3
+ERR_RTOL = 1e-4
+IREF_RL2 = 1e-5
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2)) / max(np.sqrt(np.sum(b ** 2)), 1e-300))
+
+
+def check_omap(Iref_gpu, w_gpu, Iref_or, w_or):
+    sel = w_or > 1e-4 * w_or.max()
+    r_i = rel_l2(Iref_gpu.astype(np.float64)[sel], Iref_or[sel])
+    r_w = rel_l2(w_gpu.astype(np.float64), w_or)
+    cov_mismatch = int(np.count_nonzero((w_gpu > 0) != (w_or > 0)))
+    assert r_i <= IREF_RL2, f"I_ref relative L2 {r_i:.3e}"
+    assert r_w <= IREF_RL2, f"w relative L2 {r_w:.3e}"
+    # coverage may differ only where the weight is zero up to rounding
+    assert cov_mismatch <= max(2, int(1e-4 * w_or.size)), cov_mismatch
+    return dict(iref_rel_l2=r_i, w_rel_l2=r_w, coverage_mismatch=cov_mismatch)
+
+
+def check_update(inp, pix, u_gpu_int, err_gpu_int, u_gpu_q, err_gpu_q):
+    """inp: dict(frames, W, M, Iref, w, delta, u, window) -- the oracle's inputs (Iref/w as
+    used by both sides); pix: flat pixel indices to compare (all M = 1 pixels, or a sample);
+    u_gpu_*: [2][K] for those pixels; err_gpu_*: [K]."""
+    frames, W, M, Iref, w, delta, u, window = (inp[k] for k in
+                                               ("frames", "W", "M", "Iref", "w", "delta", "u", "window"))
+    pix = np.asarray(pix, dtype=np.int64)
+    uo_int, eo_int = oracle.update_pixels(frames, W, M, Iref, w, delta, u, window, pix, quadratic=False)
+    uo_q, eo_q = oracle.update_pixels(frames, W, M, Iref, w, delta, u, window, pix, quadratic=True)
+    uo_int, uo_q = uo_int.T, uo_q.T
+    same = np.all(u_gpu_int == uo_int, axis=0)
+    agree = float(np.mean(same)) if pix.size else 1.0
+    bad = np.nonzero(~same)[0]
+    ny, nx = M.shape
+    Sy, Sx = window
+    worst_gap = 0.0
+    for k in bad:
+        p = int(pix[k])
+        e, (ci, cj) = oracle.pixel_window(frames, W, M, Iref, w, delta, u, window, p)
+        a = int(round(u_gpu_int[0, k])) - ci + Sy
+        b = int(round(u_gpu_int[1, k])) - cj + Sx
+        assert 0 <= a <= 2 * Sy and 0 <= b <= 2 * Sx, (p, a, b)
+        I = frames[:, p // nx, p % nx].astype(np.float64)
+        Wv = float(W.ravel()[p])
+        scale = float(np.sum(I * I) / max(np.sum((I - Wv) ** 2), 1e-300))
+        emin = float(np.min(e))
+        gap = float(e[a, b] - emin)
+        tol = 1e-5 * emin + 1e-7 * scale
+        assert gap <= tol, f"pixel {p}: GPU pick is {gap:.3e} above the minimum (tolerance {tol:.3e})"
+        worst_gap = max(worst_gap, gap / max(tol, 1e-300))
+    assert agree >= ARGMIN_AGREE, f"integer argmin agreement {agree:.5f}"
+    # sub-pixel map where the integer picks agree
+    du = np.abs(u_gpu_q - uo_q)[:, same]
+    max_du = float(du.max()) if du.size else 0.0
+    assert max_du <= U_TOL, f"sub-pixel u differs by {max_du:.3e} px"
+    fin = same & np.isfinite(eo_int)
+    rel = np.abs(err_gpu_int[fin] - eo_int[fin]) / np.maximum(np.abs(eo_int[fin]), 1e-30)
+    max_rel = float(rel.max()) if rel.size else 0.0
+    assert max_rel <= ERR_RTOL, f"error at the pick differs by {max_rel:.3e} (relative)"
+    # non-finite errors (no valid candidate) must match exactly
+    assert np.array_equal(np.isinf(err_gpu_int[same]), np.isinf(eo_int[same]))
+    return dict(pixels=int(pix.size), argmin_agree=agree, near_ties=int(bad.size),
+                max_du=max_du, rms_du=float(np.sqrt(np.mean(du ** 2))) if du.size else 0.0,
+                max_err_rel=max_rel, worst_tie_ratio=worst_gap)

@@ -277,6 +277,31 @@ def pin_upm_degenerate(L):
     assert np.array_equal(got, u) and np.all(np.isinf(err))
 
 
+def pin_reference_terms(L):
+    """Integer translations: T[c] = sum over frames whose sample c - Delta_n is inside
+    and covered of I_ref[c - Delta_n]^2, counted by plain indexing; fractional
+    translations of a constant reference give T = n_valid * const^2."""
+    rng = np.random.default_rng(9)
+    R = (14, 17)
+    Iref = rng.uniform(0.5, 1.5, R)
+    w = (rng.random(R) > 0.2).astype(np.float64)
+    delta = np.array([[0, 0], [2, -1], [-3, 4], [5, 5], [1, 9]], dtype=np.float64)
+    T, nv = oracle.reference_terms(Iref, w, delta, L=L)
+    for cy in range(R[0]):
+        for cx in range(R[1]):
+            t, k = 0.0, 0
+            for d in delta.astype(int):
+                qy, qx = cy - d[0], cx - d[1]
+                if 0 <= qy < R[0] and 0 <= qx < R[1] and w[qy, qx] > 0:
+                    t += Iref[qy, qx] ** 2
+                    k += 1
+            assert nv[cy, cx] == k and abs(T[cy, cx] - t) < 1e-12, (cy, cx)
+    frac = rng.uniform(-3, 3, (6, 2))
+    T, nv = oracle.reference_terms(np.full(R, 0.8), np.ones(R), frac, L=L)
+    np.testing.assert_allclose(T, nv * 0.64, rtol=1e-12)
+    assert nv.max() == 6 and nv.min() >= 0
+
+
 # ---------------------------------------------------------------------------------------
 # quadratic refinement
 # ---------------------------------------------------------------------------------------

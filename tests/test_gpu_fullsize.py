@@ -1,0 +1,42 @@
+"""Parity at the full sizes of the 1-D lens scan (121 x 512 x 1536, window +-1 x +-24) and
+the 2-D precision scan (400 x 1024 x 1024, window +-16 x +-16), in the launch configuration
+bench.py times: the whole detector runs on the GPU, the oracle checks a sample of pixels
+(one by one) and the whole reference image."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import parity
+from gpu_util import gpu_make_object_map, gpu_update
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _sample(M, k, seed):
+    rng = np.random.default_rng(seed)
+    good = np.flatnonzero(M.ravel())
+    ny, nx = M.shape
+    # the first and last rows and columns of the mask (window and coverage edges) + random
+    yy, xx = np.divmod(good, nx)
+    edge = good[(yy == yy.min()) | (yy == yy.max()) | (xx == xx.min()) | (xx == xx.max())]
+    pick = rng.choice(good, size=min(k, good.size), replace=False)
+    return np.unique(np.concatenate([pick, edge[:: max(1, edge.size // 400)]]))
+
+
+@pytest.mark.parametrize("name,k", [("lens1d", 3000), ("precision2d", 600)])
+def test_full_size(name, k):
+    s = gen.CONFIGS[name]()
+    Ig, wg = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    print(name, "make_object_map", parity.check_omap(Ig, wg, Io, wo))
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    inp = dict(frames=s.frames, W=s.W, M=s.M, Iref=I32.astype(np.float64), w=w32.astype(np.float64),
+               delta=s.delta, u=s.u_init, window=s.window)
+    ug_i, eg_i, n_exact = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window,
+                                     quadratic=False, return_exact=True)
+    ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True)
+    pix = _sample(s.M, k, gen.BASE_SEED + 55)
+    rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
+                              ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
+    print(name, "update_pixel_map", rep, "exact-path pixels:", n_exact)

@@ -1,0 +1,130 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+The oracle's inputs never come from the CUDA path: the reference image fed to both
+update steps is the oracle's own make_object_map result rounded to float32.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import parity
+from gpu_util import gpu_iterate, gpu_make_object_map, gpu_update
+
+pytestmark = pytest.mark.gpu
+
+
+def ragged2d(seed=gen.BASE_SEED + 21):
+    """Ragged detector (37 x 45: neither a multiple of the tile height nor of 32), seven
+    frames with fractional translations on both axes (the full bilinear read), window
+    3 x 5, magnification 1.3."""
+    rng = np.random.default_rng(seed)
+    ny, nx = 37, 45
+    y = np.arange(ny, dtype=np.float64)
+    x = np.arange(nx, dtype=np.float64)
+    uy = 14.0 + 1.3 * y + 0.8 * np.sin(y / 7.0)
+    ux = 12.0 + 1.3 * x + 0.8 * np.cos(x / 9.0)
+    delta = rng.uniform(0, 9, size=(7, 2))
+    yy, xx = np.meshgrid(y - 18, x - 22, indexing="ij")
+    W = 800.0 * np.exp(-(yy ** 2 + xx ** 2) / (2 * 30.0 ** 2))
+    return gen.make_scan("ragged2d", ny=ny, nx=nx, ref_shape=(80, 90), sigma=2.0, delta=delta,
+                         uy=uy, ux=ux, uy0=uy - 0.6, ux0=ux + 0.7, W=W, window=(3, 5), n_iter=3,
+                         seed=seed)
+
+
+SCANS = {
+    "small": lambda: gen.config_small(),
+    "ragged2d": ragged2d,
+    "lens1d-48x768": lambda: gen.config_lens1d(ny=48, nx=768),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(SCANS))
+def scan(request):
+    return SCANS[request.param]()
+
+
+def test_make_object_map_parity(scan):
+    s = scan
+    Ig, wg = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    rep = parity.check_omap(Ig, wg, Io, wo)
+    print(s.name, rep)
+
+
+def _update_inputs(s, hole=False):
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    if hole:
+        # an uncovered patch inside the reference: candidates reading it lose frames
+        Ry, Rx = s.ref_shape
+        w32[Ry // 2 - 3:Ry // 2 + 3, Rx // 2 - 4:Rx // 2 + 4] = 0.0
+        I32[w32 == 0] = 0.0
+    return dict(frames=s.frames, W=s.W, M=s.M, Iref=I32.astype(np.float64), w=w32.astype(np.float64),
+                delta=s.delta, u=s.u_init, window=s.window), I32, w32
+
+
+@pytest.mark.parametrize("hole", [False, True])
+def test_update_pixel_map_parity(scan, hole):
+    s = scan
+    inp, I32, w32 = _update_inputs(s, hole)
+    ug_i, eg_i, n_exact = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window,
+                                     quadratic=False, return_exact=True)
+    ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True)
+    pix = np.flatnonzero(s.M.ravel())
+    rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
+                              ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
+    # M = 0 pixels keep their map and report NaN
+    off = s.M == 0
+    assert np.array_equal(ug_q[:, off], s.u_init[:, off])
+    assert np.all(np.isnan(eg_q[off]))
+    if hole:
+        assert n_exact > 0
+    print(s.name, "hole" if hole else "", rep, "exact-path pixels:", n_exact)
+
+
+def test_iterate_parity(scan):
+    """One full iteration (both steps) through pxst_iterate against the oracle's."""
+    s = scan
+    ug, Ig, wg, eg = gpu_iterate(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, 1)
+    uo, Io, wo, eo = oracle.iterate(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, 1)
+    parity.check_omap(Ig, wg, Io, wo)
+    good = s.M > 0
+    same = np.all(np.abs(ug - uo) <= parity.U_TOL, axis=0)[good]
+    # the two sides' references differ by float32 rounding, so near-ties may flip
+    assert same.mean() >= parity.ARGMIN_AGREE - 0.004, same.mean()
+
+
+def test_reference_terms_parity(scan):
+    import paper_2003_12726_gb300 as px
+    import torch
+    from gpu_util import dev, dims_of
+    s = scan
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    To, no = oracle.reference_terms(I32.astype(np.float64), w32.astype(np.float64), s.delta)
+    d = dims_of(s.frames, s.ref_shape)
+    T = torch.empty(s.ref_shape, dtype=torch.float32, device="cuda")
+    nv = torch.empty(s.ref_shape, dtype=torch.int32, device="cuda")
+    ws = px.workspace(d)
+    px.reference_terms(d, dev(I32, torch.float32), dev(w32, torch.float32), dev(s.delta, torch.float64), T, nv, ws)
+    Tg, ng = T.cpu().numpy(), nv.cpu().numpy()
+    assert np.count_nonzero(ng != no) <= max(2, int(1e-4 * no.size))
+    same = ng == no
+    np.testing.assert_allclose(Tg[same], To[same], rtol=2e-5, atol=1e-6)
+
+
+def test_iterations_approach_the_truth():
+    """Main loop on the small 2-D workload (5 iterations): the GPU's map error against the
+    truth (global offset removed) matches the oracle's within 10 %."""
+    s = gen.config_small()
+    ug, *_ = gpu_iterate(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, s.n_iter)
+    uo, *_ = oracle.iterate(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, s.n_iter)
+
+    def gauge_rms(u):
+        d = (u - s.u_true)[:, 4:-4, 4:-4]
+        d = d - d.mean(axis=(1, 2), keepdims=True)
+        return float(np.sqrt((d ** 2).mean()))
+    rg, ro, r0 = gauge_rms(ug), gauge_rms(uo), gauge_rms(s.u_init)
+    print("map error vs truth (gauge removed): init %.4f  oracle %.4f  gpu %.4f" % (r0, ro, rg))
+    assert rg < r0 and abs(rg - ro) <= 0.1 * ro + 1e-3

@@ -41,6 +41,7 @@ MUTANTS = {
                             "double c3 = (a2 - 2.0 * (s - a2)) / 4.0;"),
     "fallback_parabola_sign": ("if (k > 0.0) db = (fm - fp) / (2.0 * k);",
                                "if (k > 0.0) db = (fp - fm) / (2.0 * k);"),
+    "refterms_not_squared": ("t += R * R;", "t += R;"),
     "invalid_frame_counted": ("if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) continue;",
                               "if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) R = 0.0;"),
 }
