@@ -185,7 +185,7 @@ def tiny2d(n_side=4, det=64, step=6, ref=160, sigma=2.0, mag=1.5, offset=30.0, a
     u = offset + mag*x + aberr*t^3 with t = (x - c)/c on each axis, Gaussian whitefield."""
     x = np.arange(det, dtype=np.float64)
     c = (det - 1) / 2.0
-    t = (x - c) / c
+    t = (x - c) / max(c, 1.0)
     u = offset + mag * x + aberr * t ** 3
     u0 = offset + mag * x
     ws = w_sigma if w_sigma is not None else 22.0 * det / 64.0

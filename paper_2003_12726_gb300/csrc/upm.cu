@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
     if (sub == 0) {
         int st = 0, ci = 0, cj = 0;
         float Wv = 0.0f;
+        if (inb && !a.mask[pix] && a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
         if (inb && a.mask[pix]) {
             const double u0 = a.u[pix], u1 = a.u[P + pix];
             if (!isfinite(u0) || !isfinite(u1)) {
@@ -333,8 +334,6 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
                 a.u[P + pix] = (double)(s_cj[p] + ib - a.Sx) + db;
                 if (a.err_out) a.err_out[pix] = be;
             }
-        } else if (a.err_out && !a.mask[pix]) {
-            a.err_out[pix] = __int_as_float(0x7fc00000);
         }
     }
 }

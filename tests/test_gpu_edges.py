@@ -59,7 +59,8 @@ def test_nothing_covered_keeps_u_and_reports_inf():
 def test_map_outside_the_reference():
     """Pixels whose whole window falls off the reference keep their map (every candidate
     has no valid frame); their neighbours near the border lose frames individually."""
-    s = gen.tiny2d(n_side=3, det=32, ref=70, offset=-20.0, window=3, seed=gen.BASE_SEED + 35)
+    s = gen.tiny2d(n_side=3, det=32, ref=100, offset=20.0, window=3, seed=gen.BASE_SEED + 35)
+    s.u_init -= 30.0          # a poor initial map: many pixels now point off the reference
     Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
     Ig, wg = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
     parity.check_omap(Ig, wg, Io, wo)
