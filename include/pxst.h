@@ -90,6 +90,27 @@ pxst_status pxst_make_object_map(const pxst_dims *dims, const float *frames, con
                                  void *stream);
 
 /*
+ * make_object_map_noalloc -- the same computation as pxst_make_object_map, for callers
+ * that cannot allocate device memory: for example an acquisition plug-in running inside a
+ * host framework that owns all of the GPU's memory, or a real-time loop that cannot accept
+ * the implicit synchronisation and latency of cudaMalloc. It takes no workspace and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call); its scratch is
+ * one fixed device array inside libpxst.so, about 16.1 MiB, which every GPU that loads the
+ * library holds until the process exits. The paper has no counterpart to this entry point.
+ *   Limits: n_frames <= 8192 and ref_ny * ref_nx <= 1048576; larger sizes return
+ *   PXST_ERR_NOMEM (with a message on stderr) before anything is launched.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents (each call clears
+ *   what it accumulates into): calls that may overlap on the GPU, on any stream, race.
+ *   Device-side status bits of this call are not reported (there is no workspace to read).
+ */
+pxst_status pxst_make_object_map_noalloc(const pxst_dims *dims, const float *frames,
+                                         const float *W, const uint8_t *mask, const double *u,
+                                         const double *delta, float *I_ref, float *w,
+                                         void *stream);
+
+/*
  * update_pixel_map -- "Update pixel mapping" (section "Main loop", second pseudo-code
  * block, and the quadratic_refinement option described right after it). For every pixel
  * with M = 1 and each integer candidate c in the window centred on round(u) (halves

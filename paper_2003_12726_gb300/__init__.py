@@ -63,6 +63,8 @@ def lib():
         L.pxst_workspace_size.restype = sz
         L.pxst_make_object_map.argtypes = [D] + [P] * 8 + [sz, P]
         L.pxst_make_object_map.restype = i32
+        L.pxst_make_object_map_noalloc.argtypes = [D] + [P] * 8
+        L.pxst_make_object_map_noalloc.restype = i32
         L.pxst_update_pixel_map.argtypes = [D, O] + [P] * 9 + [sz, P]
         L.pxst_update_pixel_map.restype = i32
         L.pxst_iterate.argtypes = [D, O, i32] + [P] * 9 + [sz, P]
@@ -86,7 +88,8 @@ def lib():
     return _lib
 
 
-EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_update_pixel_map",
+EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map_noalloc",
+            "pxst_update_pixel_map",
             "pxst_iterate", "pxst_reference_terms", "pxst_get_status", "pxst_last_exact_count",
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version"]
@@ -177,6 +180,20 @@ def make_object_map(dims: Dims, frames, W, M, u, delta, I_ref, w, ws, stream=Non
             _check(w, torch.float32, (Ry, Rx), "w")]
     _raise(lib().pxst_make_object_map(C.byref(dims.c()), *args, C.c_void_p(ws.data_ptr()), ws.numel(),
                                       _stream(stream)), "make_object_map")
+
+
+def make_object_map_noalloc(dims: Dims, frames, W, M, u, delta, I_ref, w, stream=None):
+    """pxst_make_object_map_noalloc: as make_object_map, for callers that cannot allocate
+    device memory (its scratch is a fixed array inside the library; at most 8192 frames and
+    1048576 reference pixels; calls that overlap on the GPU race)."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    args = [_check(frames, torch.float32, (N, ny, nx), "frames"), _check(W, torch.float32, (ny, nx), "W"),
+            _check(M, torch.uint8, (ny, nx), "M"), _check(u, torch.float64, (2, ny, nx), "u"),
+            _check(delta, torch.float64, (N, 2), "delta"), _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+            _check(w, torch.float32, (Ry, Rx), "w")]
+    _raise(lib().pxst_make_object_map_noalloc(C.byref(dims.c()), *args, _stream(stream)),
+           "make_object_map_noalloc")
 
 
 def update_pixel_map(dims: Dims, opts: Options, frames, W, M, I_ref, w, delta, u, err=None, ws=None,
