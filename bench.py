@@ -34,6 +34,17 @@ KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/
                   "paper_2003_12726_gb300/csrc/pxst_common.cuh"]
 
 
+WORKLOADS = {"lens1d": (gen.config_lens1d, 1), "small": (gen.config_small, 0),
+             "precision2d": (gen.config_precision2d, 2)}
+
+
+def make_workload(name, rank):
+    fn, idx = WORKLOADS[name]
+    if name == "small":
+        return gen.tiny2d(seed=gen.BASE_SEED + idx + 1000 * rank, name="2d-16x64x64-w4")
+    return fn(seed=gen.BASE_SEED + idx + 1000 * rank)
+
+
 def evals_per_step(s):
     Sy, Sx = s.window
     return int(s.M.sum()) * (2 * Sy + 1) * (2 * Sx + 1) * s.frames.shape[0]
@@ -132,7 +143,7 @@ def cpu_sample(s, target_s=12.0, max_rows=None, threads=None):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    s = gen.config_lens1d()
+    s = make_workload(args.workload, 0)
     per_step = []
     rows = None
     for k in range(args.warmup + args.steps):
@@ -184,7 +195,7 @@ def pxst_arm(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    s = gen.config_lens1d(seed=gen.BASE_SEED + 1 + rank)
+    s = make_workload(args.workload, rank)
     ev_step = evals_per_step(s)
     rec = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window)
     u0 = rec.u.clone()
@@ -310,6 +321,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="pxst", choices=["pxst", "reference"])
+    ap.add_argument("--workload", default="lens1d", choices=sorted(WORKLOADS),
+                    help="lens1d (the benchmark workload) or a smaller/larger scan for profiling")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")

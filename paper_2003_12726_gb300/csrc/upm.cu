@@ -10,12 +10,15 @@
 //     (a plain load for integer translations, a lerp for fractional ones, selected per
 //     frame), d = I - W R, err += d^2: two FP32 FMAs per evaluation;
 //   * a NaN error means some frame read an invalid reference pixel, where the paper's
-//     rule drops that frame instead; such pixels are handed to the exact path. A valid
-//     window needs no per-frame check, so the check costs nothing in the inner loop;
+//     rule drops that corner (or the whole frame) instead; only such strips are evaluated
+//     again with the rule applied per frame. Valid strips need no per-frame check, so the
+//     check costs nothing in the inner loop;
 //   * the argmin (first minimum in row-major order) is reduced in registers, then over
 //     the TPP threads; the 3x3 about it is re-evaluated and fitted in FP64.
-// Exact path (k_exact): one warp per listed pixel, candidates over lanes, per-frame
+// Global path (k_exact): one warp per listed pixel, candidates over lanes, per-frame
 // masked renormalised reads from global memory, lexicographic warp argmin, FP64 fit.
+// It serves tiles whose reference window does not fit in shared memory and scans with
+// too many frames to stage.
 #include <climits>
 #include <cmath>
 
@@ -144,6 +147,54 @@ __device__ __forceinline__ void eval_strip(const float *__restrict__ fr, int TP,
     }
 }
 
+// The same strip with the validity rule applied per frame: a window value that is NaN
+// (off the grid or uncovered) drops its corner, the remaining corners are renormalised,
+// and a frame with no valid corner is left out of both the error and var. Used only for
+// strips in which the fast evaluation produced a NaN. e[k] = err / var (err if var = 0,
+// +inf if no frame is valid).
+template <int L>
+__device__ __noinline__ void eval_strip_exact(const float *__restrict__ fr, int TP, int p,
+                                              const FrameShift *__restrict__ sh, int N,
+                                              const float *__restrict__ win, int WS, float Wv,
+                                              float (&e)[L]) {
+    float err[L], var[L];
+    int nv[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        err[k] = 0.0f;
+        var[k] = 0.0f;
+        nv[k] = 0;
+    }
+    for (int n = 0; n < N; ++n) {
+        const FrameShift s = sh[n];
+        const float I = fr[n * TP + p];
+        const float t = I - Wv;
+        const float *wp = win + s.ky * WS + s.kx;
+        const float wt[4] = {(1.0f - s.fy) * (1.0f - s.fx), (1.0f - s.fy) * s.fx,
+                             s.fy * (1.0f - s.fx), s.fy * s.fx};
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const float v[4] = {wp[k], wp[k + 1], wp[WS + k], wp[WS + k + 1]};
+            float num = 0.0f, den = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (wt[c] == 0.0f || isnan(v[c])) continue;
+                num = fmaf(wt[c], v[c], num);
+                den += wt[c];
+            }
+            if (den > 0.0f) {
+                const float d = fmaf(-Wv, num / den, I);
+                err[k] = fmaf(d, d, err[k]);
+                var[k] = fmaf(t, t, var[k]);
+                nv[k] += 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < L; ++k)
+        e[k] = nv[k] == 0 ? INFINITY : (var[k] > 0.0f ? err[k] / var[k] : err[k]);
+}
+
 __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
     return e < e2 || (e == e2 && i < i2);
 }
@@ -244,32 +295,34 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
     const int wxn = 2 * a.Sx + 1;
     float best_e = INFINITY;
     int best_i = INT_MAX;
-    bool bad = false;
     const int st0 = s_state[p];
-    __syncthreads();                               // every thread has read the state
     if (st0 == 1) {
         const int ci = s_ci[p], cj = s_cj[p];
         const float Wv = s_W[p], var = s_var[p];
         for (int item = sub; item < a.nitems; item += TPP) {
             const int aa = item / a.nstrips - a.Sy;
             const int b0 = (item % a.nstrips) * L - a.Sx;
+            const float *wstrip = win + (ci + aa - wy0) * WS + (cj + b0 - wx0);
             float acc[L];
-            eval_strip<L>(fr, TP, p, sh, a.N, win + (ci + aa - wy0) * WS + (cj + b0 - wx0), WS, Wv,
-                          acc);
+            eval_strip<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv, acc);
+            bool nan_seen = false;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                acc[k] = var > 0.0f ? acc[k] / var : acc[k];
+                nan_seen = nan_seen || (isnan(acc[k]) && b0 + k <= a.Sx);
+            }
+            if (nan_seen) eval_strip_exact<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv, acc);
 #pragma unroll
             for (int k = 0; k < L; ++k) {
                 const int b = b0 + k;
                 if (b > a.Sx) break;
-                const float e = var > 0.0f ? acc[k] / var : acc[k];
                 const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
-                if (isnan(e)) bad = true;
-                else if (e < best_e) { best_e = e; best_i = idx; }
+                if (acc[k] < best_e) { best_e = acc[k]; best_i = idx; }
             }
         }
     }
     s_be[sub][p] = best_e;
     s_bi[sub][p] = best_i;
-    if (bad) s_state[p] = 2;
     __syncthreads();
     if (sub == 0 && s_state[p] >= 1) {
         float be = s_be[0][p];
@@ -285,7 +338,6 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
     if (a.quadratic) {
         const int st = s_state[p];
         const float be = s_be[0][p];
-        __syncthreads();                           // every thread has read the state
         if (st == 1 && be < INFINITY) {
             const int bi = s_bi[0][p];
             const int ia = bi / wxn, ib = bi % wxn;
@@ -299,11 +351,14 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
                 } else if (j == 4) {
                     e = be;
                 } else {
+                    const float *wn = win + (ci + na - a.Sy - wy0) * WS + (cj + nb - a.Sx - wx0);
                     float acc[1];
-                    eval_strip<1>(fr, TP, p, sh, a.N,
-                                  win + (ci + na - a.Sy - wy0) * WS + (cj + nb - a.Sx - wx0), WS, Wv, acc);
+                    eval_strip<1>(fr, TP, p, sh, a.N, wn, WS, Wv, acc);
                     e = var > 0.0f ? acc[0] / var : acc[0];
-                    if (isnan(e)) s_state[p] = 2;
+                    if (isnan(e)) {
+                        eval_strip_exact<1>(fr, TP, p, sh, a.N, wn, WS, Wv, acc);
+                        e = acc[0];
+                    }
                 }
                 s_nb[j][p] = e;
             }
@@ -313,10 +368,7 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
 
     if (sub == 0 && inb) {
         const int st = s_state[p];
-        if (st == 2) {
-            const int k = atomicAdd(&a.hdr->n_exact, 1);
-            a.exact_list[k] = (int)pix;
-        } else if (st == 1) {
+        if (st == 1) {
             const float be = s_be[0][p];
             if (!(be < INFINITY)) {
                 if (a.err_out) a.err_out[pix] = INFINITY;
