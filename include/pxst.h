@@ -158,9 +158,10 @@ pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, cons
  * PXST_OK, PXST_ERR_RANGE or PXST_ERR_TIMEOUT. `bits_out` (nullable) gets the raw bits. */
 pxst_status pxst_get_status(void *workspace, void *stream, int32_t *bits_out);
 
-/* Number of pixels the last update on this workspace handed to the exact (slow) search
- * because a candidate read an uncovered or out-of-grid reference pixel, or because the
- * tile's reference window did not fit in shared memory. Synchronises `stream`. */
+/* Number of pixels of the last update on this workspace that needed the per-frame
+ * validity rule (a candidate read an uncovered or off-grid reference pixel), plus those
+ * handled by the global-memory path (tile window too large for shared memory, or too many
+ * frames to stage). Synchronises `stream`. */
 pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_out);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream.

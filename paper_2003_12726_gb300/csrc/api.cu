@@ -126,7 +126,7 @@ pxst_status run_omap(const pxst_dims &d, const float *frames, const float *W,
 pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *frames,
                        const float *W, const uint8_t *mask, const float *I_ref, const float *wref,
                        double *u, float *err_out, Ws &w, cudaStream_t s) {
-    PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, sizeof(int), s));
+    PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, 2 * sizeof(int), s));   // n_exact, n_exact_cta
     if (d.n_frames <= search_max_frames()) {
         {
             Timed t(PXST_K_SEARCH, s);
@@ -243,10 +243,10 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
     if (!workspace || !count_out) return PXST_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WsHeader *hdr = static_cast<WsHeader *>(workspace);
-    int n = 0;
+    int n[2] = {0, 0};
     PXST_TRY(cudaStreamSynchronize(s));
-    PXST_TRY(cudaMemcpy(&n, &hdr->n_exact, sizeof(int), cudaMemcpyDeviceToHost));
-    *count_out = n;
+    PXST_TRY(cudaMemcpy(n, &hdr->n_exact, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    *count_out = (int64_t)n[0] + n[1];
     return PXST_OK;
 }
 

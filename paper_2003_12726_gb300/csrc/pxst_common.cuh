@@ -22,9 +22,10 @@ struct FrameShift {
 // Workspace header: the device status word and a few per-call scalars.
 struct WsHeader {
     int status;        // PXST_DEV_* bits, sticky until pxst_get_status
-    int n_exact;       // pixels appended to the exact-path list by the last update
+    int n_exact;       // pixels appended to the global-path list by the last update
+    int n_exact_cta;   // pixels of the last update with a strip evaluated by the per-frame rule
     int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
-    int pad[58];
+    int pad[57];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 

@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
     __shared__ float s_be[TPP][TP];
     __shared__ int s_bi[TPP][TP];
     __shared__ float s_nb[9][TP];
+    __shared__ int s_slow[TP];
 
     const int tid = threadIdx.x, p = tid % TP, sub = tid / TP;
     const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
             }
         }
         s_state[p] = st;
+        s_slow[p] = 0;
         s_ci[p] = ci;
         s_cj[p] = cj;
         s_W[p] = Wv;
@@ -311,7 +313,10 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
                 acc[k] = var > 0.0f ? acc[k] / var : acc[k];
                 nan_seen = nan_seen || (isnan(acc[k]) && b0 + k <= a.Sx);
             }
-            if (nan_seen) eval_strip_exact<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv, acc);
+            if (nan_seen) {
+                eval_strip_exact<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv, acc);
+                s_slow[p] = 1;
+            }
 #pragma unroll
             for (int k = 0; k < L; ++k) {
                 const int b = b0 + k;
@@ -358,6 +363,7 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
                     if (isnan(e)) {
                         eval_strip_exact<1>(fr, TP, p, sh, a.N, wn, WS, Wv, acc);
                         e = acc[0];
+                        s_slow[p] = 1;
                     }
                 }
                 s_nb[j][p] = e;
@@ -368,6 +374,7 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
 
     if (sub == 0 && inb) {
         const int st = s_state[p];
+        if (s_slow[p]) atomicAdd(&a.hdr->n_exact_cta, 1);
         if (st == 1) {
             const float be = s_be[0][p];
             if (!(be < INFINITY)) {
