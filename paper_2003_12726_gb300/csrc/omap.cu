@@ -2,12 +2,14 @@
 // per-candidate reference terms, for sm_103a.
 //
 //   prepare    : -Delta[n] -> (integer shift, fraction) per frame, and their range.
-//   scatter    : each CTA owns a 32 x 32 pixel tile and a chunk of frames. It privatises
-//                the tile's reference footprint (its u range widened by the chunk's
-//                translation range, +1 for the bilinear corner) in shared memory, adds
+//   scatter    : each CTA (1024 threads, one pixel each) owns a 32 x 32 pixel tile and a
+//                chunk of frames, cut into groups of consecutive frames whose reference
+//                footprint (the tile's u range widened by the group's translation range,
+//                +1 for the bilinear corner) fits in shared memory. Each group adds
 //                b*M*W*I and b*M*W^2 there with FP32 shared-memory atomics, then flushes
 //                the non-zero cells to the FP64 accumulators in global memory with FP64
-//                atomics. A tile whose footprint does not fit adds straight to global.
+//                atomics. A single frame whose footprint does not fit adds straight to
+//                global memory.
 //   normalise  : I_ref = num / den (FP64 divide) where den > 0, else 0; w = den.
 //   refterms   : T[c] = sum_n V R^2 and n_valid[c] = sum_n V over the reference grid.
 #include <climits>
@@ -46,9 +48,10 @@ __global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restric
 }
 
 // ------------------------------------------------------------------------------------
-constexpr int SC_TX = 32, SC_TY = 8, SC_PPT = 4;      // 32 x 32 pixels, 256 threads
+constexpr int SC_TX = 32, SC_TY = 32;                  // 32 x 32 pixels, one per thread
 constexpr int SC_THREADS = SC_TX * SC_TY;
 constexpr int SC_CAP = 16384;                          // cells (num + den: 128 KB)
+constexpr int SC_PREFETCH = 4;                         // frames loaded ahead of their scatter
 
 struct ScatterArgs {
     int N, ny, nx, Ry, Rx, chunk;
@@ -60,136 +63,143 @@ struct ScatterArgs {
     double *num, *den;
 };
 
+// One CTA per 32 x 32 pixel tile and chunk of frames. The chunk is cut into consecutive
+// groups of frames whose footprint (the tile's floor(u) range widened by the group's
+// integer shifts, +1 for a carry and +1 for the second corner) fits in shared memory;
+// each group is accumulated there with FP32 atomics and flushed to the FP64 accumulators.
 __global__ void __launch_bounds__(SC_THREADS) k_scatter(ScatterArgs a) {
     extern __shared__ float sm[];
     float *s_num = sm;
     float *s_den = sm + SC_CAP;
-    __shared__ int s_rng[8];
+    __shared__ int s_rng[4];
+    __shared__ int s_grp[6];       // group [start, end), footprint origin r0, c0, height, width
 
-    const int tx = threadIdx.x % SC_TX, ty = threadIdx.x / SC_TX;
-    const int x = blockIdx.x * SC_TX + tx;
+    const int x = blockIdx.x * SC_TX + (threadIdx.x % SC_TX);
+    const int y = blockIdx.y * SC_TY + (threadIdx.x / SC_TX);
     const int n0 = blockIdx.z * a.chunk, n1 = min(a.N, n0 + a.chunk);
     const size_t P = (size_t)a.ny * a.nx;
 
-    if (threadIdx.x < 8) s_rng[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    if (threadIdx.x < 4) s_rng[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
     __syncthreads();
 
-    int iy[SC_PPT], ix[SC_PPT];
-    float fy[SC_PPT], fx[SC_PPT], Wv[SC_PPT];
-    bool act[SC_PPT];
-    int any = 0;
-#pragma unroll
-    for (int q = 0; q < SC_PPT; ++q) {
-        const int y = blockIdx.y * (SC_TY * SC_PPT) + ty + SC_TY * q;
-        act[q] = false;
-        iy[q] = ix[q] = 0;
-        fy[q] = fx[q] = Wv[q] = 0.0f;
-        if (y >= a.ny || x >= a.nx) continue;
-        const size_t p = (size_t)y * a.nx + x;
-        if (!a.mask[p]) continue;
-        const double u0 = a.u[p], u1 = a.u[P + p];
-        if (!isfinite(u0) || !isfinite(u1)) {
-            atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
-            continue;
-        }
-        if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
-            atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
-            continue;
-        }
-        const double f0 = floor(u0), f1 = floor(u1);
-        iy[q] = (int)f0; ix[q] = (int)f1;
-        fy[q] = (float)(u0 - f0); fx[q] = (float)(u1 - f1);
-        if (fy[q] >= 1.0f) { fy[q] = 0.0f; iy[q] += 1; }
-        if (fx[q] >= 1.0f) { fx[q] = 0.0f; ix[q] += 1; }
-        Wv[q] = a.W[p];
-        act[q] = true;
-        any = 1;
-    }
-    int mn_y = INT_MAX, mx_y = INT_MIN, mn_x = INT_MAX, mx_x = INT_MIN;
-#pragma unroll
-    for (int q = 0; q < SC_PPT; ++q)
-        if (act[q]) {
-            mn_y = min(mn_y, iy[q]); mx_y = max(mx_y, iy[q]);
-            mn_x = min(mn_x, ix[q]); mx_x = max(mx_x, ix[q]);
-        }
-    if (any) {
-        atomicMin(&s_rng[0], mn_y); atomicMax(&s_rng[1], mx_y);
-        atomicMin(&s_rng[2], mn_x); atomicMax(&s_rng[3], mx_x);
-    }
-    int kmn_y = INT_MAX, kmx_y = INT_MIN, kmn_x = INT_MAX, kmx_x = INT_MIN;
-    for (int n = n0 + threadIdx.x; n < n1; n += SC_THREADS) {
-        const FrameShift s = a.shifts[n];
-        kmn_y = min(kmn_y, s.ky); kmx_y = max(kmx_y, s.ky);
-        kmn_x = min(kmn_x, s.kx); kmx_x = max(kmx_x, s.kx);
-    }
-    if (n0 + (int)threadIdx.x < n1) {
-        atomicMin(&s_rng[4], kmn_y); atomicMax(&s_rng[5], kmx_y);
-        atomicMin(&s_rng[6], kmn_x); atomicMax(&s_rng[7], kmx_x);
-    }
-    __syncthreads();
-    if (s_rng[0] == INT_MAX || n0 >= n1) return;      // no active pixel in the tile
-
-    // footprint: floor(u) + k (+1 carry, +1 corner)
-    const long long r0 = (long long)s_rng[0] + s_rng[4];
-    const long long r1 = (long long)s_rng[1] + s_rng[5] + 2;
-    const long long c0 = (long long)s_rng[2] + s_rng[6];
-    const long long c1 = (long long)s_rng[3] + s_rng[7] + 2;
-    const long long H = r1 - r0 + 1, Wd = c1 - c0 + 1;
-    const bool fits = H * Wd <= SC_CAP;
-    const int Wdi = (int)Wd;
-
-    if (fits) {
-        for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
-            s_num[c] = 0.0f;
-            s_den[c] = 0.0f;
-        }
-        __syncthreads();
-    }
-
-    for (int n = n0; n < n1; ++n) {
-        const FrameShift s = a.shifts[n];
-        const float *fr = a.frames + (size_t)n * P;
-#pragma unroll
-        for (int q = 0; q < SC_PPT; ++q) {
-            if (!act[q]) continue;
-            const int y = blockIdx.y * (SC_TY * SC_PPT) + ty + SC_TY * q;
-            const float I = __ldg(fr + (size_t)y * a.nx + x);
-            int by = iy[q] + s.ky, bx = ix[q] + s.kx;
-            float sy = fy[q] + s.fy, sx = fx[q] + s.fx;
-            if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
-            if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
-            const float WI = Wv[q] * I, W2 = Wv[q] * Wv[q];
-            const float wt[4] = {(1.0f - sy) * (1.0f - sx), (1.0f - sy) * sx, sy * (1.0f - sx), sy * sx};
-            if (fits) {
-                const int base = (int)((by - r0) * Wd + (bx - c0));
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int c = base + (k >> 1) * Wdi + (k & 1);
-                    atomicAdd(&s_num[c], wt[k] * WI);
-                    atomicAdd(&s_den[c], wt[k] * W2);
-                }
+    int iy = 0, ix = 0;
+    float fy = 0.0f, fx = 0.0f, Wv = 0.0f;
+    bool act = false;
+    size_t pix = 0;
+    if (y < a.ny && x < a.nx) {
+        pix = (size_t)y * a.nx + x;
+        if (a.mask[pix]) {
+            const double u0 = a.u[pix], u1 = a.u[P + pix];
+            if (!isfinite(u0) || !isfinite(u1)) {
+                atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
+            } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
+                atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
             } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int gy = by + (k >> 1), gx = bx + (k & 1);
-                    if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx || wt[k] == 0.0f) continue;
-                    const size_t g = (size_t)gy * a.Rx + gx;
-                    atomicAdd(&a.num[g], (double)(wt[k] * WI));
-                    atomicAdd(&a.den[g], (double)(wt[k] * W2));
-                }
+                const double f0 = floor(u0), f1 = floor(u1);
+                iy = (int)f0;
+                ix = (int)f1;
+                fy = (float)(u0 - f0);
+                fx = (float)(u1 - f1);
+                if (fy >= 1.0f) { fy = 0.0f; iy += 1; }
+                if (fx >= 1.0f) { fx = 0.0f; ix += 1; }
+                Wv = a.W[pix];
+                act = true;
+                atomicMin(&s_rng[0], iy); atomicMax(&s_rng[1], iy);
+                atomicMin(&s_rng[2], ix); atomicMax(&s_rng[3], ix);
             }
         }
     }
-    if (!fits) return;
     __syncthreads();
-    for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
-        const float dn = s_den[c], nm = s_num[c];
-        if (dn == 0.0f && nm == 0.0f) continue;
-        const long long gy = r0 + c / Wdi, gx = c0 + c % Wdi;
-        if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;   // corners off the grid
-        const size_t g = (size_t)gy * a.Rx + gx;
-        atomicAdd(&a.num[g], (double)nm);
-        atomicAdd(&a.den[g], (double)dn);
+    if (s_rng[0] == INT_MAX || n0 >= n1) return;      // no active pixel in the tile
+    const float WW = Wv * Wv;
+
+    for (int gs = n0; gs < n1;) {
+        if (threadIdx.x == 0) {
+            // extend the group while its footprint fits (at least one frame per group)
+            int kmn_y = INT_MAX, kmx_y = INT_MIN, kmn_x = INT_MAX, kmx_x = INT_MIN;
+            int ge = gs;
+            long long H = 0, Wd = 0;
+            while (ge < n1) {
+                const FrameShift f = a.shifts[ge];
+                const int a0 = min(kmn_y, f.ky), a1 = max(kmx_y, f.ky);
+                const int b0 = min(kmn_x, f.kx), b1 = max(kmx_x, f.kx);
+                const long long h = (long long)s_rng[1] + a1 + 2 - ((long long)s_rng[0] + a0) + 1;
+                const long long wd = (long long)s_rng[3] + b1 + 2 - ((long long)s_rng[2] + b0) + 1;
+                if (ge > gs && h * wd > SC_CAP) break;
+                kmn_y = a0; kmx_y = a1; kmn_x = b0; kmx_x = b1;
+                H = h; Wd = wd;
+                ++ge;
+            }
+            s_grp[0] = gs;
+            s_grp[1] = ge;
+            s_grp[2] = s_rng[0] + kmn_y;
+            s_grp[3] = s_rng[2] + kmn_x;
+            s_grp[4] = (H * Wd <= SC_CAP) ? (int)H : -1;     // -1: add straight to global
+            s_grp[5] = (int)Wd;
+        }
+        __syncthreads();
+        const int g0 = s_grp[0], g1 = s_grp[1], r0 = s_grp[2], c0 = s_grp[3];
+        const int H = s_grp[4], Wd = s_grp[5];
+        const bool fits = H > 0;
+        if (fits)
+            for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
+                s_num[c] = 0.0f;
+                s_den[c] = 0.0f;
+            }
+        __syncthreads();
+        if (act) {
+            for (int n = g0; n < g1; n += SC_PREFETCH) {
+                float I[SC_PREFETCH];
+                FrameShift S[SC_PREFETCH];
+#pragma unroll
+                for (int j = 0; j < SC_PREFETCH; ++j)
+                    if (n + j < g1) {
+                        I[j] = __ldg(a.frames + (size_t)(n + j) * P + pix);
+                        S[j] = a.shifts[n + j];
+                    }
+#pragma unroll
+                for (int j = 0; j < SC_PREFETCH; ++j) {
+                    if (n + j >= g1) break;
+                    int by = iy + S[j].ky, bx = ix + S[j].kx;
+                    float sy = fy + S[j].fy, sx = fx + S[j].fx;
+                    if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
+                    if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
+                    const float WI = Wv * I[j];
+                    const float wt[4] = {(1.0f - sy) * (1.0f - sx), (1.0f - sy) * sx, sy * (1.0f - sx), sy * sx};
+                    if (fits) {
+                        const int base = (by - r0) * Wd + (bx - c0);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int c = base + (k >> 1) * Wd + (k & 1);
+                            atomicAdd(&s_num[c], wt[k] * WI);
+                            atomicAdd(&s_den[c], wt[k] * WW);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int gy = by + (k >> 1), gx = bx + (k & 1);
+                            if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx || wt[k] == 0.0f) continue;
+                            const size_t gi = (size_t)gy * a.Rx + gx;
+                            atomicAdd(&a.num[gi], (double)(wt[k] * WI));
+                            atomicAdd(&a.den[gi], (double)(wt[k] * WW));
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (fits)
+            for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
+                const float dn = s_den[c], nm = s_num[c];
+                if (dn == 0.0f && nm == 0.0f) continue;
+                const int gy = r0 + c / Wd, gx = c0 + c % Wd;
+                if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;   // corners off the grid
+                const size_t gi = (size_t)gy * a.Rx + gx;
+                atomicAdd(&a.num[gi], (double)nm);
+                atomicAdd(&a.den[gi], (double)dn);
+            }
+        __syncthreads();
+        gs = g1;
     }
 }
 
@@ -253,21 +263,17 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(den, 0, sizeof(double) * R, stream);
     if (e != cudaSuccess) return e;
-    static bool attr = false;
     const int smem = 2 * SC_CAP * (int)sizeof(float);
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     ScatterArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.frames = frames; a.W = W; a.mask = mask; a.u = u; a.shifts = shifts; a.hdr = hdr;
     a.num = num; a.den = den;
     const int gx = (d.nx + SC_TX - 1) / SC_TX;
-    const int gy = (d.ny + SC_TY * SC_PPT - 1) / (SC_TY * SC_PPT);
+    const int gy = (d.ny + SC_TY - 1) / SC_TY;
     const long long tiles = (long long)gx * gy;
-    // enough CTAs for two waves on 152 SMs; chunks of at least 8 frames
+    // split the frames only when there are too few tiles to fill 152 SMs twice
     long long nch = (304 + tiles - 1) / tiles;
     nch = nch < 1 ? 1 : nch;
     const long long maxch = (d.n_frames + 7) / 8;

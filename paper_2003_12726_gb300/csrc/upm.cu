@@ -1,20 +1,21 @@
 // upm.cu -- update_pixel_map ("Update pixel mapping", section "Main loop") on sm_103a.
 //
-// Fast path (k_search): one CTA per tile of TY x 32 pixels. Each pixel has TPP threads
-// that share its candidate strips (one candidate row, L consecutive columns per strip).
+// Fast path (k_search): one CTA of 256 threads per tile of TY x 32 pixels.
 //   * the tile's frames, all N of them, are staged once in shared memory;
 //   * the tile's reference window (every candidate of every pixel of the tile, widened
 //     by the range of integer frame shifts and one bilinear corner) is staged once, with
 //     uncovered or off-grid reference pixels stored as NaN;
-//   * per candidate and frame: R = bilinear read of the window at the frame's shift
-//     (a plain load for integer translations, a lerp for fractional ones, selected per
-//     frame), d = I - W R, err += d^2: two FP32 FMAs per evaluation;
+//   * groups of 4 neighbouring pixels of a row share strips of L absolute reference
+//     columns on one reference row: per frame one window read and, for fractional
+//     translations, one lerp per column serve the 4 pixels, then d = I - W R and
+//     err += d^2 are two FP32 FMAs per evaluation;
 //   * a NaN error means some frame read an invalid reference pixel, where the paper's
 //     rule drops that corner (or the whole frame) instead; only such strips are evaluated
 //     again with the rule applied per frame. Valid strips need no per-frame check, so the
 //     check costs nothing in the inner loop;
-//   * the argmin (first minimum in row-major order) is reduced in registers, then over
-//     the TPP threads; the 3x3 about it is re-evaluated and fitted in FP64.
+//   * per-pixel argmins (first minimum in row-major window order) are combined with a
+//     packed 64-bit atomicMin in shared memory; the 3x3 about the minimum is re-evaluated
+//     and fitted in FP64.
 // Global path (k_exact): one warp per listed pixel, candidates over lanes, per-frame
 // masked renormalised reads from global memory, lexicographic warp argmin, FP64 fit.
 // It serves tiles whose reference window does not fit in shared memory and scans with
@@ -199,56 +200,133 @@ __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
     return e < e2 || (e == e2 && i < i2);
 }
 
-template <int L, int TY, int TPP>
-__global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
+constexpr int kGroup = 4;            // pixels per thread: consecutive columns of one row
+constexpr int kSearchThreads = 256;
+
+// One strip of L consecutive absolute reference columns on one reference row, for the
+// kGroup pixels of a group, over all frames: acc[p][k] = sum_n (I_p - W_p R_n(col_k))^2.
+// `win` points at the window position of the strip's first column for a zero shift.
+// One window read (and one lerp for fractional translations) serves all kGroup pixels.
+template <int L>
+__device__ __forceinline__ void eval_group(const float *__restrict__ fr, int TP, int g0,
+                                           const FrameShift *__restrict__ sh, int N,
+                                           const float *__restrict__ win, int WS,
+                                           const float (&Wv)[kGroup], float (&acc)[kGroup][L]) {
+#pragma unroll
+    for (int p = 0; p < kGroup; ++p)
+#pragma unroll
+        for (int k = 0; k < L; ++k) acc[p][k] = 0.0f;
+    for (int n = 0; n < N; ++n) {
+        const FrameShift s = sh[n];
+        const float4 I4 = *reinterpret_cast<const float4 *>(fr + n * TP + g0);
+        const float I[kGroup] = {I4.x, I4.y, I4.z, I4.w};
+        const float *wp = win + s.ky * WS + s.kx;
+        float G[L];
+        if (s.fy == 0.0f) {
+            if (s.fx == 0.0f) {
+#pragma unroll
+                for (int k = 0; k < L; ++k) G[k] = wp[k];
+            } else {
+                float a0 = wp[0];
+#pragma unroll
+                for (int k = 0; k < L; ++k) {
+                    const float b0 = wp[k + 1];
+                    G[k] = fmaf(s.fx, b0 - a0, a0);
+                    a0 = b0;
+                }
+            }
+        } else {
+            const float *wq = wp + WS;
+            if (s.fx == 0.0f) {
+#pragma unroll
+                for (int k = 0; k < L; ++k) G[k] = fmaf(s.fy, wq[k] - wp[k], wp[k]);
+            } else {
+                float a0 = wp[0], a1 = wq[0];
+#pragma unroll
+                for (int k = 0; k < L; ++k) {
+                    const float b0 = wp[k + 1], b1 = wq[k + 1];
+                    const float t0 = fmaf(s.fx, b0 - a0, a0);
+                    const float t1 = fmaf(s.fx, b1 - a1, a1);
+                    G[k] = fmaf(s.fy, t1 - t0, t0);
+                    a0 = b0;
+                    a1 = b1;
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kGroup; ++p)
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const float d = fmaf(-Wv[p], G[k], I[p]);
+                acc[p][k] = fmaf(d, d, acc[p][k]);
+            }
+    }
+}
+
+__device__ __forceinline__ unsigned long long pack_key(float e, int idx) {
+    // e >= 0 (or +inf): its bit pattern orders like the value, so (e, idx) compares
+    // lexicographically as one unsigned 64-bit key
+    return ((unsigned long long)__float_as_uint(e) << 32) | (unsigned int)idx;
+}
+
+// Fast path. One CTA per tile of TY rows x 32 columns of pixels, 256 threads.
+// Groups of kGroup neighbouring pixels share the strips of the union of their windows
+// (absolute reference rows and columns); strips are dealt to threads round-robin. Each
+// candidate of each pixel is evaluated exactly once; per-pixel argmins are combined with
+// a packed (error, window index) 64-bit atomicMin in shared memory, which keeps the
+// first minimum in row-major window order.
+template <int L, int TY>
+__global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
     constexpr int TP = 32 * TY;
-    constexpr int NT = TP * TPP;
+    constexpr int NG = TP / kGroup;
+    constexpr int NT = kSearchThreads;
     extern __shared__ __align__(16) unsigned char smraw[];
     FrameShift *sh = reinterpret_cast<FrameShift *>(smraw);
     float *fr = reinterpret_cast<float *>(sh + a.N);
     float *win = fr + (size_t)a.N * TP;
 
     __shared__ int s_box[4];
-    __shared__ int s_ci[TP], s_cj[TP], s_state[TP];
+    __shared__ int s_ci[TP], s_cj[TP], s_act[TP], s_slow[TP];
     __shared__ float s_W[TP], s_var[TP];
-    __shared__ float s_be[TPP][TP];
-    __shared__ int s_bi[TPP][TP];
+    __shared__ unsigned long long s_key[TP];
     __shared__ float s_nb[9][TP];
-    __shared__ int s_slow[TP];
+    __shared__ int s_gr0[NG], s_gc0[NG], s_gns[NG], s_goff[NG + 1];
 
-    const int tid = threadIdx.x, p = tid % TP, sub = tid / TP;
-    const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
+    const int tid = threadIdx.x;
     const size_t P = (size_t)a.ny * a.nx;
-    const size_t pix = (size_t)y * a.nx + x;
-    const bool inb = x < a.nx && y < a.ny;
+    const int wxn = 2 * a.Sx + 1;
 
     if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
     for (int n = tid; n < a.N; n += NT) sh[n] = a.shifts[n];
     __syncthreads();
-    if (sub == 0) {
-        int st = 0, ci = 0, cj = 0;
+    for (int p = tid; p < TP; p += NT) {
+        const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
+        int act = 0, ci = 0, cj = 0;
         float Wv = 0.0f;
-        if (inb && !a.mask[pix] && a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
-        if (inb && a.mask[pix]) {
-            const double u0 = a.u[pix], u1 = a.u[P + pix];
-            if (!isfinite(u0) || !isfinite(u1)) {
-                atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
-            } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
-                atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
+        if (x < a.nx && y < a.ny) {
+            const size_t pix = (size_t)y * a.nx + x;
+            if (!a.mask[pix]) {
+                if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
             } else {
-                ci = (int)floor(u0 + 0.5);
-                cj = (int)floor(u1 + 0.5);
-                Wv = a.W[pix];
-                st = 1;
-                atomicMin(&s_box[0], ci); atomicMax(&s_box[1], ci);
-                atomicMin(&s_box[2], cj); atomicMax(&s_box[3], cj);
+                const double u0 = a.u[pix], u1 = a.u[P + pix];
+                if (!isfinite(u0) || !isfinite(u1)) {
+                    atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
+                } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
+                    atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
+                } else {
+                    ci = (int)floor(u0 + 0.5);
+                    cj = (int)floor(u1 + 0.5);
+                    Wv = a.W[pix];
+                    act = 1;
+                }
             }
         }
-        s_state[p] = st;
-        s_slow[p] = 0;
+        s_act[p] = act;
         s_ci[p] = ci;
         s_cj[p] = cj;
         s_W[p] = Wv;
+        s_slow[p] = 0;
+        s_key[p] = ~0ull;
     }
     // the tile's frames: [n][TP], coalesced 128-byte rows
     for (int idx = tid; idx < a.N * TP; idx += NT) {
@@ -257,18 +335,60 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
         fr[idx] = (xx < a.nx && yy < a.ny) ? __ldg(a.frames + (size_t)n * P + (size_t)yy * a.nx + xx) : 0.0f;
     }
     __syncthreads();
+    for (int p = tid; p < TP; p += NT) {
+        if (!s_act[p]) continue;
+        const float Wv = s_W[p];
+        float v = 0.0f;
+        for (int n = 0; n < a.N; ++n) {
+            const float t = fr[n * TP + p] - Wv;
+            v = fmaf(t, t, v);
+        }
+        s_var[p] = v;
+    }
+    for (int g = tid; g < NG; g += NT) {
+        int mn_i = INT_MAX, mx_i = INT_MIN, mn_j = INT_MAX, mx_j = INT_MIN;
+        for (int q = 0; q < kGroup; ++q) {
+            const int p = g * kGroup + q;
+            if (!s_act[p]) continue;
+            mn_i = min(mn_i, s_ci[p]); mx_i = max(mx_i, s_ci[p]);
+            mn_j = min(mn_j, s_cj[p]); mx_j = max(mx_j, s_cj[p]);
+        }
+        int cnt = 0;
+        if (mn_i != INT_MAX) {
+            const int uy = mx_i - mn_i + 2 * a.Sy + 1, ux = mx_j - mn_j + wxn;
+            const int ns = (ux + L - 1) / L;
+            s_gr0[g] = mn_i - a.Sy;
+            s_gc0[g] = mn_j - a.Sx;
+            s_gns[g] = ns;
+            cnt = uy * ns;
+            atomicMin(&s_box[0], mn_i);
+            atomicMax(&s_box[1], mx_i);
+            atomicMin(&s_box[2], mn_j);
+            atomicMax(&s_box[3], mn_j - a.Sx + ns * L - 1);
+        }
+        s_goff[g + 1] = cnt;
+    }
+    __syncthreads();
     if (s_box[0] == INT_MAX) return;                 // no active pixel in this tile
+    if (tid == 0) {
+        s_goff[0] = 0;
+        for (int g = 0; g < NG; ++g) s_goff[g + 1] += s_goff[g];
+    }
 
     const int wy0 = s_box[0] - a.Sy + a.hdr->kmin_y;
     const int wy1 = s_box[1] + a.Sy + a.hdr->kmax_y + 1;
     const int wx0 = s_box[2] - a.Sx + a.hdr->kmin_x;
-    const int wx1 = s_box[3] - a.Sx + a.nstrips * L - 1 + a.hdr->kmax_x + 1;
-    const long long WHl = (long long)wy1 - wy0 + 1, WSl = (long long)wx1 - wx0 + 1;
+    const int wx1 = s_box[3] + a.hdr->kmax_x + 1;
+    long long WSl = (long long)wx1 - wx0 + 1;
+    WSl += (WSl & 1) ? 0 : 1;                        // odd row pitch: fewer bank conflicts
+    const long long WHl = (long long)wy1 - wy0 + 1;
     if (WHl * WSl > a.win_cap) {
-        // the window does not fit: every active pixel of the tile takes the exact path
-        if (sub == 0 && s_state[p] == 1) {
+        // the window does not fit: every active pixel of the tile takes the global path
+        for (int p = tid; p < TP; p += NT) {
+            if (!s_act[p]) continue;
+            const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
             const int k = atomicAdd(&a.hdr->n_exact, 1);
-            a.exact_list[k] = (int)pix;
+            a.exact_list[k] = y * a.nx + x;
         }
         return;
     }
@@ -283,117 +403,116 @@ __global__ void __launch_bounds__(32 * TY * TPP) k_search(SearchArgs a) {
         }
         win[idx] = v;
     }
-    if (sub == 0 && s_state[p] == 1) {
-        const float Wv = s_W[p];
-        float v = 0.0f;
-        for (int n = 0; n < a.N; ++n) {
-            const float t = fr[n * TP + p] - Wv;
-            v = fmaf(t, t, v);
-        }
-        s_var[p] = v;
-    }
     __syncthreads();
 
-    const int wxn = 2 * a.Sx + 1;
-    float best_e = INFINITY;
-    int best_i = INT_MAX;
-    const int st0 = s_state[p];
-    if (st0 == 1) {
-        const int ci = s_ci[p], cj = s_cj[p];
-        const float Wv = s_W[p], var = s_var[p];
-        for (int item = sub; item < a.nitems; item += TPP) {
-            const int aa = item / a.nstrips - a.Sy;
-            const int b0 = (item % a.nstrips) * L - a.Sx;
-            const float *wstrip = win + (ci + aa - wy0) * WS + (cj + b0 - wx0);
-            float acc[L];
-            eval_strip<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv, acc);
+    // ---- search: strips of the groups' window unions ------------------------------------
+    const int total = s_goff[NG];
+    for (int t = tid; t < total; t += NT) {
+        int lo = 0, hi = NG - 1;                     // group g with s_goff[g] <= t < s_goff[g+1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_goff[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int g = lo, g0 = g * kGroup;
+        const int loc = t - s_goff[g], ns = s_gns[g];
+        const int r = s_gr0[g] + loc / ns, c = s_gc0[g] + (loc % ns) * L;
+        float Wv[kGroup];
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) Wv[q] = s_W[g0 + q];
+        const float *wstrip = win + (r - wy0) * WS + (c - wx0);
+        float acc[kGroup][L];
+        eval_group<L>(fr, TP, g0, sh, a.N, wstrip, WS, Wv, acc);
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) {
+            const int p = g0 + q;
+            if (!s_act[p]) continue;
+            const int aa = r - s_ci[p];
+            if (aa < -a.Sy || aa > a.Sy) continue;
+            const int bofs = c - s_cj[p];
+            const float var = s_var[p];
+            float e[L];
             bool nan_seen = false;
 #pragma unroll
             for (int k = 0; k < L; ++k) {
-                acc[k] = var > 0.0f ? acc[k] / var : acc[k];
-                nan_seen = nan_seen || (isnan(acc[k]) && b0 + k <= a.Sx);
+                e[k] = var > 0.0f ? acc[q][k] / var : acc[q][k];
+                const int b = bofs + k;
+                nan_seen = nan_seen || (isnan(e[k]) && b >= -a.Sx && b <= a.Sx);
             }
             if (nan_seen) {
-                eval_strip_exact<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv, acc);
+                eval_strip_exact<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv[q], e);
                 s_slow[p] = 1;
             }
+            float be = INFINITY;
+            int bi = -1;
 #pragma unroll
             for (int k = 0; k < L; ++k) {
-                const int b = b0 + k;
-                if (b > a.Sx) break;
-                const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
-                if (acc[k] < best_e) { best_e = acc[k]; best_i = idx; }
+                const int b = bofs + k;
+                if (b < -a.Sx || b > a.Sx) continue;
+                if (bi < 0 || e[k] < be) {
+                    be = e[k];
+                    bi = (aa + a.Sy) * wxn + (b + a.Sx);
+                }
             }
+            if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
         }
-    }
-    s_be[sub][p] = best_e;
-    s_bi[sub][p] = best_i;
-    __syncthreads();
-    if (sub == 0 && s_state[p] >= 1) {
-        float be = s_be[0][p];
-        int bi = s_bi[0][p];
-#pragma unroll
-        for (int t = 1; t < TPP; ++t)
-            if (lex_less(s_be[t][p], s_bi[t][p], be, bi)) { be = s_be[t][p]; bi = s_bi[t][p]; }
-        s_be[0][p] = be;
-        s_bi[0][p] = bi;
     }
     __syncthreads();
 
+    // ---- 3x3 about each pixel's minimum ---------------------------------------------------
     if (a.quadratic) {
-        const int st = s_state[p];
-        const float be = s_be[0][p];
-        if (st == 1 && be < INFINITY) {
-            const int bi = s_bi[0][p];
-            const int ia = bi / wxn, ib = bi % wxn;
-            const int ci = s_ci[p], cj = s_cj[p];
-            const float Wv = s_W[p], var = s_var[p];
-            for (int j = sub; j < 9; j += TPP) {
-                const int na = ia + j / 3 - 1, nb = ib + j % 3 - 1;
-                float e;
-                if (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) {
-                    e = INFINITY;
-                } else if (j == 4) {
-                    e = be;
-                } else {
-                    const float *wn = win + (ci + na - a.Sy - wy0) * WS + (cj + nb - a.Sx - wx0);
-                    float acc[1];
-                    eval_strip<1>(fr, TP, p, sh, a.N, wn, WS, Wv, acc);
-                    e = var > 0.0f ? acc[0] / var : acc[0];
-                    if (isnan(e)) {
-                        eval_strip_exact<1>(fr, TP, p, sh, a.N, wn, WS, Wv, acc);
-                        e = acc[0];
-                        s_slow[p] = 1;
-                    }
+        for (int q = tid; q < TP * 9; q += NT) {
+            const int p = q / 9, j = q % 9;
+            if (!s_act[p]) continue;
+            const unsigned long long key = s_key[p];
+            const float be = __uint_as_float((unsigned int)(key >> 32));
+            if (!(be < INFINITY)) continue;
+            const int bi = (int)(key & 0xffffffffu);
+            const int na = bi / wxn + j / 3 - 1, nb = bi % wxn + j % 3 - 1;
+            float e;
+            if (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) {
+                e = INFINITY;
+            } else if (j == 4) {
+                e = be;
+            } else {
+                const float *wn = win + (s_ci[p] + na - a.Sy - wy0) * WS + (s_cj[p] + nb - a.Sx - wx0);
+                float acc1[1];
+                eval_strip<1>(fr, TP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                const float var = s_var[p];
+                e = var > 0.0f ? acc1[0] / var : acc1[0];
+                if (isnan(e)) {
+                    eval_strip_exact<1>(fr, TP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                    e = acc1[0];
+                    s_slow[p] = 1;
                 }
-                s_nb[j][p] = e;
             }
+            s_nb[j][p] = e;
         }
         __syncthreads();
     }
 
-    if (sub == 0 && inb) {
-        const int st = s_state[p];
+    for (int p = tid; p < TP; p += NT) {
+        if (!s_act[p]) continue;
+        const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
+        const size_t pix = (size_t)y * a.nx + x;
         if (s_slow[p]) atomicAdd(&a.hdr->n_exact_cta, 1);
-        if (st == 1) {
-            const float be = s_be[0][p];
-            if (!(be < INFINITY)) {
-                if (a.err_out) a.err_out[pix] = INFINITY;
-            } else {
-                const int bi = s_bi[0][p];
-                const int ia = bi / wxn, ib = bi % wxn;
-                double da = 0.0, db = 0.0;
-                if (a.quadratic) {
-                    float f[9];
-#pragma unroll
-                    for (int j = 0; j < 9; ++j) f[j] = s_nb[j][p];
-                    refine3x3(f, da, db);
-                }
-                a.u[pix] = (double)(s_ci[p] + ia - a.Sy) + da;
-                a.u[P + pix] = (double)(s_cj[p] + ib - a.Sx) + db;
-                if (a.err_out) a.err_out[pix] = be;
-            }
+        const unsigned long long key = s_key[p];
+        const float be = __uint_as_float((unsigned int)(key >> 32));
+        if (!(be < INFINITY)) {
+            if (a.err_out) a.err_out[pix] = INFINITY;
+            continue;
         }
+        const int bi = (int)(key & 0xffffffffu);
+        const int ia = bi / wxn, ib = bi % wxn;
+        double da = 0.0, db = 0.0;
+        if (a.quadratic) {
+            float f[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) f[j] = s_nb[j][p];
+            refine3x3(f, da, db);
+        }
+        a.u[pix] = (double)(s_ci[p] + ia - a.Sy) + da;
+        a.u[P + pix] = (double)(s_cj[p] + ib - a.Sx) + db;
+        if (a.err_out) a.err_out[pix] = be;
     }
 }
 
@@ -496,39 +615,41 @@ __global__ void __launch_bounds__(256) k_exact(ExactArgs a) {
 // host-side planning
 
 struct Plan {
-    int L, TY, TPP, nstrips, nitems;
+    int L, TY, nstrips;
     size_t smem;
     int win_cap;
 };
 
+// Strip length: odd (bank-friendly), chosen to waste the fewest columns on the union of
+// a group's windows (window width plus the few columns its kGroup centres spread over).
 int pick_strip(int wxn) {
-    const int cand[5] = {11, 9, 8, 7, 4};
-    int best = 4, waste = INT_MAX;
+    const int cand[3] = {11, 9, 7};
+    const int ux = wxn + kGroup;
+    int best = 7, waste = INT_MAX;
     for (int L : cand) {
-        const int ns = (wxn + L - 1) / L;
-        const int wst = ns * L - wxn;
+        const int wst = ((ux + L - 1) / L) * L - ux;
         if (wst < waste) { waste = wst; best = L; }
     }
     return best;
 }
 
-template <int L, int TY, int TPP>
+template <int L, int TY>
 cudaError_t launch_one(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
-    auto kern = k_search<L, TY, TPP>;
+    auto kern = k_search<L, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + 31) / 32, (a.ny + TY - 1) / TY);
-    kern<<<grid, 32 * TY * TPP, pl.smem, stream>>>(a);
+    kern<<<grid, kSearchThreads, pl.smem, stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int L>
 cudaError_t launch_L(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
     switch (pl.TY) {
-        case 8: return launch_one<L, 8, 1>(a, pl, stream);
-        case 4: return launch_one<L, 4, 2>(a, pl, stream);
-        case 2: return launch_one<L, 2, 4>(a, pl, stream);
-        default: return launch_one<L, 1, 8>(a, pl, stream);
+        case 8: return launch_one<L, 8>(a, pl, stream);
+        case 4: return launch_one<L, 4>(a, pl, stream);
+        case 2: return launch_one<L, 2>(a, pl, stream);
+        default: return launch_one<L, 1>(a, pl, stream);
     }
 }
 
@@ -542,16 +663,13 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, cudaStream_t stream) {
     Plan pl;
-    const int wxn = 2 * o.win_x + 1, wyn = 2 * o.win_y + 1;
+    const int wxn = 2 * o.win_x + 1;
     pl.L = pick_strip(wxn);
-    pl.nstrips = (wxn + pl.L - 1) / pl.L;
-    pl.nitems = wyn * pl.nstrips;
-    const size_t per_frame = 16;                 // FrameShift
+    const size_t per_frame = sizeof(FrameShift);
     // largest tile whose frames take at most ~110 KB of shared memory
     pl.TY = 1;
     for (int ty = 8; ty >= 1; ty >>= 1)
         if ((size_t)d.n_frames * 32 * ty * 4 <= 110 * 1024) { pl.TY = ty; break; }
-    pl.TPP = 8 / pl.TY;
     const size_t fixed = (size_t)d.n_frames * (per_frame + 32 * pl.TY * 4);
     // two CTAs per SM when the frames leave room for a useful window, else one
     size_t total = fixed + 24 * 1024 <= 100 * 1024 ? 100 * 1024 : (size_t)kSearchSmemBudget;
@@ -562,15 +680,13 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     SearchArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
-    a.nstrips = pl.nstrips; a.nitems = pl.nitems; a.win_cap = pl.win_cap;
+    a.nstrips = 0; a.nitems = 0; a.win_cap = pl.win_cap;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.exact_list = exact_list; a.u = u; a.err_out = err_out;
     switch (pl.L) {
         case 11: return launch_L<11>(a, pl, stream);
         case 9: return launch_L<9>(a, pl, stream);
-        case 8: return launch_L<8>(a, pl, stream);
-        case 7: return launch_L<7>(a, pl, stream);
-        default: return launch_L<4>(a, pl, stream);
+        default: return launch_L<7>(a, pl, stream);
     }
 }
 
