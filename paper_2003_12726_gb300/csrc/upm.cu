@@ -29,7 +29,7 @@ namespace pxst {
 namespace {
 
 struct SearchArgs {
-    int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, nstrips, nitems, win_cap;
+    int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ebuf, win_cap;
     const float *frames, *W;
     const uint8_t *mask;
     const float *Iref, *w;
@@ -98,7 +98,7 @@ __device__ void refine3x3(const float *f, double &da_out, double &db_out) {
 // One strip of L candidates (same row, consecutive columns) over all frames.
 // win points at the window row/column of the strip's first candidate for a zero shift.
 template <int L>
-__device__ __forceinline__ void eval_strip(const float *__restrict__ fr, int TP, int p,
+__device__ __forceinline__ void eval_strip(const float *__restrict__ fr, int pitch, int p,
                                            const FrameShift *__restrict__ sh, int N,
                                            const float *__restrict__ win, int WS, float Wv,
                                            float (&acc)[L]) {
@@ -106,7 +106,7 @@ __device__ __forceinline__ void eval_strip(const float *__restrict__ fr, int TP,
     for (int k = 0; k < L; ++k) acc[k] = 0.0f;
     for (int n = 0; n < N; ++n) {
         const FrameShift s = sh[n];
-        const float I = fr[n * TP + p];
+        const float I = fr[n * pitch + p];
         const float *wp = win + s.ky * WS + s.kx;
         float G[L];
         if (s.fy == 0.0f) {
@@ -154,7 +154,7 @@ __device__ __forceinline__ void eval_strip(const float *__restrict__ fr, int TP,
 // strips in which the fast evaluation produced a NaN. e[k] = err / var (err if var = 0,
 // +inf if no frame is valid).
 template <int L>
-__device__ __noinline__ void eval_strip_exact(const float *__restrict__ fr, int TP, int p,
+__device__ __noinline__ void eval_strip_exact(const float *__restrict__ fr, int pitch, int p,
                                               const FrameShift *__restrict__ sh, int N,
                                               const float *__restrict__ win, int WS, float Wv,
                                               float (&e)[L]) {
@@ -168,7 +168,7 @@ __device__ __noinline__ void eval_strip_exact(const float *__restrict__ fr, int 
     }
     for (int n = 0; n < N; ++n) {
         const FrameShift s = sh[n];
-        const float I = fr[n * TP + p];
+        const float I = fr[n * pitch + p];
         const float t = I - Wv;
         const float *wp = win + s.ky * WS + s.kx;
         const float wt[4] = {(1.0f - s.fy) * (1.0f - s.fx), (1.0f - s.fy) * s.fx,
@@ -200,25 +200,28 @@ __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
     return e < e2 || (e == e2 && i < i2);
 }
 
-constexpr int kGroup = 4;            // pixels per thread: consecutive columns of one row
+constexpr int kGroup = 4;            // pixels per group: consecutive columns of one row
+constexpr int kSplit = 4;            // lanes that share one strip, each taking every 4th frame
 constexpr int kSearchThreads = 256;
+static_assert(kSplit == kGroup, "the reduce-scatter hands lane j the sums of pixel j");
 
 // One strip of L consecutive absolute reference columns on one reference row, for the
-// kGroup pixels of a group, over all frames: acc[p][k] = sum_n (I_p - W_p R_n(col_k))^2.
-// `win` points at the window position of the strip's first column for a zero shift.
-// One window read (and one lerp for fractional translations) serves all kGroup pixels.
+// kGroup pixels of a group, over the frames n = n0, n0 + kSplit, ...:
+// acc[p][k] = sum_n (I_p - W_p R_n(col_k))^2. `win` points at the window position of the
+// strip's first column for a zero shift; frame rows of `fr` are FP floats apart. One
+// window read (and one lerp for fractional translations) serves all kGroup pixels.
 template <int L>
-__device__ __forceinline__ void eval_group(const float *__restrict__ fr, int TP, int g0,
-                                           const FrameShift *__restrict__ sh, int N,
+__device__ __forceinline__ void eval_group(const float *__restrict__ fr, int FP, int g0,
+                                           const FrameShift *__restrict__ sh, int n0, int N,
                                            const float *__restrict__ win, int WS,
                                            const float (&Wv)[kGroup], float (&acc)[kGroup][L]) {
 #pragma unroll
     for (int p = 0; p < kGroup; ++p)
 #pragma unroll
         for (int k = 0; k < L; ++k) acc[p][k] = 0.0f;
-    for (int n = 0; n < N; ++n) {
+    for (int n = n0; n < N; n += kSplit) {
         const FrameShift s = sh[n];
-        const float4 I4 = *reinterpret_cast<const float4 *>(fr + n * TP + g0);
+        const float4 I4 = *reinterpret_cast<const float4 *>(fr + n * FP + g0);
         const float I[kGroup] = {I4.x, I4.y, I4.z, I4.w};
         const float *wp = win + s.ky * WS + s.kx;
         float G[L];
@@ -263,6 +266,28 @@ __device__ __forceinline__ void eval_group(const float *__restrict__ fr, int TP,
     }
 }
 
+// Reduce-scatter over the kSplit = 4 lanes of a strip: afterwards lane j (j = lane & 3)
+// holds in out[k] the sum over the 4 lanes of acc[j][k]. Every lane of the warp calls it.
+template <int L>
+__device__ __forceinline__ void reduce_scatter4(const float (&acc)[kGroup][L], int j, float (&out)[L]) {
+    const bool b0 = j & 1, b1 = (j >> 1) & 1;
+    float h[2][L];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const float send = b0 ? acc[2 * q][k] : acc[2 * q + 1][k];
+            const float keep = b0 ? acc[2 * q + 1][k] : acc[2 * q][k];
+            h[q][k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const float send = b1 ? h[0][k] : h[1][k];
+        const float keep = b1 ? h[1][k] : h[0][k];
+        out[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+}
+
 __device__ __forceinline__ unsigned long long pack_key(float e, int idx) {
     // e >= 0 (or +inf): its bit pattern orders like the value, so (e, idx) compares
     // lexicographically as one unsigned 64-bit key
@@ -271,19 +296,24 @@ __device__ __forceinline__ unsigned long long pack_key(float e, int idx) {
 
 // Fast path. One CTA per tile of TY rows x 32 columns of pixels, 256 threads.
 // Groups of kGroup neighbouring pixels share the strips of the union of their windows
-// (absolute reference rows and columns); strips are dealt to threads round-robin. Each
-// candidate of each pixel is evaluated exactly once; per-pixel argmins are combined with
-// a packed (error, window index) 64-bit atomicMin in shared memory, which keeps the
-// first minimum in row-major window order.
+// (absolute reference rows and columns); each strip is evaluated by kSplit lanes that
+// split the frames, then reduce-scatter so that lane j finishes pixel j of the group.
+// Each candidate of each pixel is evaluated exactly once; per-pixel argmins are combined
+// with a packed (error, window index) 64-bit atomicMin in shared memory, which keeps the
+// first minimum in row-major window order. With a.ebuf every error is also kept in
+// shared memory, so the 3x3 about the minimum is read back instead of re-evaluated.
 template <int L, int TY>
 __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
     constexpr int TP = 32 * TY;
+    constexpr int FP = TP + 4;            // frame pitch: the 4 lanes of a strip hit 4 banks
     constexpr int NG = TP / kGroup;
     constexpr int NT = kSearchThreads;
     extern __shared__ __align__(16) unsigned char smraw[];
     FrameShift *sh = reinterpret_cast<FrameShift *>(smraw);
     float *fr = reinterpret_cast<float *>(sh + a.N);
-    float *win = fr + (size_t)a.N * TP;
+    const int wxn = 2 * a.Sx + 1, nwin = (2 * a.Sy + 1) * wxn;
+    float *ebuf = fr + (size_t)a.N * FP;
+    float *win = ebuf + (a.ebuf ? (size_t)TP * nwin : 0);
 
     __shared__ int s_box[4];
     __shared__ int s_ci[TP], s_cj[TP], s_act[TP], s_slow[TP];
@@ -294,7 +324,6 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
 
     const int tid = threadIdx.x;
     const size_t P = (size_t)a.ny * a.nx;
-    const int wxn = 2 * a.Sx + 1;
 
     if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
     for (int n = tid; n < a.N; n += NT) sh[n] = a.shifts[n];
@@ -328,11 +357,11 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
         s_slow[p] = 0;
         s_key[p] = ~0ull;
     }
-    // the tile's frames: [n][TP], coalesced 128-byte rows
+    // the tile's frames: [n][FP], coalesced 128-byte rows
     for (int idx = tid; idx < a.N * TP; idx += NT) {
         const int n = idx / TP, q = idx % TP;
         const int xx = blockIdx.x * 32 + (q & 31), yy = blockIdx.y * TY + (q >> 5);
-        fr[idx] = (xx < a.nx && yy < a.ny) ? __ldg(a.frames + (size_t)n * P + (size_t)yy * a.nx + xx) : 0.0f;
+        fr[n * FP + q] = (xx < a.nx && yy < a.ny) ? __ldg(a.frames + (size_t)n * P + (size_t)yy * a.nx + xx) : 0.0f;
     }
     __syncthreads();
     for (int p = tid; p < TP; p += NT) {
@@ -340,7 +369,7 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
         const float Wv = s_W[p];
         float v = 0.0f;
         for (int n = 0; n < a.N; ++n) {
-            const float t = fr[n * TP + p] - Wv;
+            const float t = fr[n * FP + p] - Wv;
             v = fmaf(t, t, v);
         }
         s_var[p] = v;
@@ -405,87 +434,101 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
     }
     __syncthreads();
 
-    // ---- search: strips of the groups' window unions ------------------------------------
-    const int total = s_goff[NG];
-    for (int t = tid; t < total; t += NT) {
-        int lo = 0, hi = NG - 1;                     // group g with s_goff[g] <= t < s_goff[g+1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_goff[mid] <= t) lo = mid; else hi = mid - 1;
-        }
-        const int g = lo, g0 = g * kGroup;
-        const int loc = t - s_goff[g], ns = s_gns[g];
-        const int r = s_gr0[g] + loc / ns, c = s_gc0[g] + (loc % ns) * L;
-        float Wv[kGroup];
-#pragma unroll
-        for (int q = 0; q < kGroup; ++q) Wv[q] = s_W[g0 + q];
-        const float *wstrip = win + (r - wy0) * WS + (c - wx0);
+    // ---- search: strips of the groups' window unions, 4 lanes per strip ----------------
+    const int j = tid & (kSplit - 1);
+    const int units = s_goff[NG] * kSplit;
+    for (int u0 = 0; u0 < units; u0 += NT) {
+        const int t = u0 + tid;
+        const bool valid = t < units;               // uniform over each strip's 4 lanes
+        const int item = t / kSplit;
+        int g = 0, r = 0, c = 0;
         float acc[kGroup][L];
-        eval_group<L>(fr, TP, g0, sh, a.N, wstrip, WS, Wv, acc);
-#pragma unroll
-        for (int q = 0; q < kGroup; ++q) {
-            const int p = g0 + q;
-            if (!s_act[p]) continue;
-            const int aa = r - s_ci[p];
-            if (aa < -a.Sy || aa > a.Sy) continue;
-            const int bofs = c - s_cj[p];
-            const float var = s_var[p];
-            float e[L];
-            bool nan_seen = false;
-#pragma unroll
-            for (int k = 0; k < L; ++k) {
-                e[k] = var > 0.0f ? acc[q][k] / var : acc[q][k];
-                const int b = bofs + k;
-                nan_seen = nan_seen || (isnan(e[k]) && b >= -a.Sx && b <= a.Sx);
+        if (valid) {
+            int lo = 0, hi = NG - 1;                 // group g with s_goff[g] <= item < s_goff[g+1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_goff[mid] <= item) lo = mid; else hi = mid - 1;
             }
-            if (nan_seen) {
-                eval_strip_exact<L>(fr, TP, p, sh, a.N, wstrip, WS, Wv[q], e);
-                s_slow[p] = 1;
-            }
-            float be = INFINITY;
-            int bi = -1;
+            g = lo;
+            const int loc = item - s_goff[g], ns = s_gns[g];
+            r = s_gr0[g] + loc / ns;
+            c = s_gc0[g] + (loc % ns) * L;
+            float Wv[kGroup];
 #pragma unroll
-            for (int k = 0; k < L; ++k) {
-                const int b = bofs + k;
-                if (b < -a.Sx || b > a.Sx) continue;
-                if (bi < 0 || e[k] < be) {
-                    be = e[k];
-                    bi = (aa + a.Sy) * wxn + (b + a.Sx);
-                }
-            }
-            if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
+            for (int q = 0; q < kGroup; ++q) Wv[q] = s_W[g * kGroup + q];
+            eval_group<L>(fr, FP, g * kGroup, sh, j, a.N, win + (r - wy0) * WS + (c - wx0), WS, Wv, acc);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q)
+#pragma unroll
+                for (int k = 0; k < L; ++k) acc[q][k] = 0.0f;
         }
+        float e[L];
+        reduce_scatter4<L>(acc, j, e);
+        const int p = g * kGroup + j;
+        if (!valid || !s_act[p]) continue;
+        const int aa = r - s_ci[p];
+        if (aa < -a.Sy || aa > a.Sy) continue;
+        const int bofs = c - s_cj[p];
+        const float var = s_var[p];
+        bool nan_seen = false;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            e[k] = var > 0.0f ? e[k] / var : e[k];
+            const int b = bofs + k;
+            nan_seen = nan_seen || (isnan(e[k]) && b >= -a.Sx && b <= a.Sx);
+        }
+        if (nan_seen) {
+            eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], e);
+            s_slow[p] = 1;
+        }
+        float be = INFINITY;
+        int bi = -1;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const int b = bofs + k;
+            if (b < -a.Sx || b > a.Sx) continue;
+            const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
+            if (a.ebuf) ebuf[p * nwin + idx] = e[k];
+            if (bi < 0 || e[k] < be) {
+                be = e[k];
+                bi = idx;
+            }
+        }
+        if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
     }
     __syncthreads();
 
     // ---- 3x3 about each pixel's minimum ---------------------------------------------------
     if (a.quadratic) {
         for (int q = tid; q < TP * 9; q += NT) {
-            const int p = q / 9, j = q % 9;
+            const int p = q / 9, jn = q % 9;
             if (!s_act[p]) continue;
             const unsigned long long key = s_key[p];
             const float be = __uint_as_float((unsigned int)(key >> 32));
             if (!(be < INFINITY)) continue;
             const int bi = (int)(key & 0xffffffffu);
-            const int na = bi / wxn + j / 3 - 1, nb = bi % wxn + j % 3 - 1;
-            float e;
+            const int na = bi / wxn + jn / 3 - 1, nb = bi % wxn + jn % 3 - 1;
+            float ev;
             if (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) {
-                e = INFINITY;
-            } else if (j == 4) {
-                e = be;
+                ev = INFINITY;
+            } else if (jn == 4) {
+                ev = be;
+            } else if (a.ebuf) {
+                ev = ebuf[p * nwin + na * wxn + nb];
             } else {
                 const float *wn = win + (s_ci[p] + na - a.Sy - wy0) * WS + (s_cj[p] + nb - a.Sx - wx0);
                 float acc1[1];
-                eval_strip<1>(fr, TP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                eval_strip<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
                 const float var = s_var[p];
-                e = var > 0.0f ? acc1[0] / var : acc1[0];
-                if (isnan(e)) {
-                    eval_strip_exact<1>(fr, TP, p, sh, a.N, wn, WS, s_W[p], acc1);
-                    e = acc1[0];
+                ev = var > 0.0f ? acc1[0] / var : acc1[0];
+                if (isnan(ev)) {
+                    eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                    ev = acc1[0];
                     s_slow[p] = 1;
                 }
             }
-            s_nb[j][p] = e;
+            s_nb[jn][p] = ev;
         }
         __syncthreads();
     }
@@ -507,7 +550,7 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
         if (a.quadratic) {
             float f[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) f[j] = s_nb[j][p];
+            for (int jn = 0; jn < 9; ++jn) f[jn] = s_nb[jn][p];
             refine3x3(f, da, db);
         }
         a.u[pix] = (double)(s_ci[p] + ia - a.Sy) + da;
@@ -656,7 +699,7 @@ cudaError_t launch_L(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
 }  // namespace
 
 // Largest frame count the fast path can stage (a 1 x 32 tile in shared memory).
-int search_max_frames() { return (kSearchSmemBudget - 16 * 1024) / (32 * 4 + 16); }
+int search_max_frames() { return (kSearchSmemBudget - 16 * 1024) / (36 * 4 + 16); }
 
 cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float *frames,
                           const float *W, const uint8_t *mask, const float *I_ref,
@@ -664,15 +707,26 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           int *exact_list, double *u, float *err_out, cudaStream_t stream) {
     Plan pl;
     const int wxn = 2 * o.win_x + 1;
+    const size_t nwin = (size_t)(2 * o.win_y + 1) * wxn;
     pl.L = pick_strip(wxn);
-    const size_t per_frame = sizeof(FrameShift);
-    // largest tile whose frames take at most ~110 KB of shared memory
-    pl.TY = 1;
-    for (int ty = 8; ty >= 1; ty >>= 1)
-        if ((size_t)d.n_frames * 32 * ty * 4 <= 110 * 1024) { pl.TY = ty; break; }
-    const size_t fixed = (size_t)d.n_frames * (per_frame + 32 * pl.TY * 4);
-    // two CTAs per SM when the frames leave room for a useful window, else one
-    size_t total = fixed + 24 * 1024 <= 100 * 1024 ? 100 * 1024 : (size_t)kSearchSmemBudget;
+    const size_t N = (size_t)d.n_frames, shifts_b = N * sizeof(FrameShift);
+    auto frames_b = [&](int ty) { return N * (32 * ty + 4) * 4; };
+    // Prefer a tile whose frames and full error buffer leave a 2-CTA/SM budget for the
+    // window; otherwise the largest tile whose frames fit, without the error buffer.
+    int ebuf = 0;
+    pl.TY = 0;
+    for (int ty = 8; ty >= 2 && !pl.TY; ty >>= 1)
+        if (shifts_b + frames_b(ty) + 32 * ty * nwin * 4 + 16 * 1024 <= 100 * 1024) {
+            pl.TY = ty;
+            ebuf = 1;
+        }
+    if (!pl.TY) {
+        pl.TY = 1;
+        for (int ty = 8; ty >= 1; ty >>= 1)
+            if (frames_b(ty) <= 110 * 1024) { pl.TY = ty; break; }
+    }
+    const size_t fixed = shifts_b + frames_b(pl.TY) + (ebuf ? (size_t)32 * pl.TY * nwin * 4 : 0);
+    size_t total = fixed + 16 * 1024 <= 100 * 1024 ? 100 * 1024 : (size_t)kSearchSmemBudget;
     if (fixed + 4096 > total) total = fixed + 4096;
     pl.smem = total;
     pl.win_cap = (int)((total - fixed) / 4);
@@ -680,7 +734,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     SearchArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
-    a.nstrips = 0; a.nitems = 0; a.win_cap = pl.win_cap;
+    a.ebuf = ebuf; a.win_cap = pl.win_cap;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.exact_list = exact_list; a.u = u; a.err_out = err_out;
     switch (pl.L) {
