@@ -151,49 +151,67 @@ __device__ __forceinline__ void eval_strip(const float *__restrict__ fr, int pit
 // The same strip with the validity rule applied per frame: a window value that is NaN
 // (off the grid or uncovered) drops its corner, the remaining corners are renormalised,
 // and a frame with no valid corner is left out of both the error and var. Used only for
-// strips in which the fast evaluation produced a NaN. e[k] = err / var (err if var = 0,
-// +inf if no frame is valid).
+// strips in which the fast evaluation produced a NaN. Accumulates frames
+// n = n0, n0 + step, ... into err/var/nv (which the caller zeroes and later reduces).
+template <int L>
+__device__ __forceinline__ void accum_strip_exact(const float *__restrict__ fr, int pitch, int p,
+                                                  const FrameShift *__restrict__ sh, int n0,
+                                                  int step, int N, const float *__restrict__ win,
+                                                  int WS, float Wv, float (&err)[L],
+                                                  float (&var)[L], float (&nv)[L]) {
+    for (int n = n0; n < N; n += step) {
+        const FrameShift s = sh[n];
+        const float I = fr[n * pitch + p];
+        const float t = I - Wv, t2 = t * t;
+        const float *wp = win + s.ky * WS + s.kx;
+        const float w00 = (1.0f - s.fy) * (1.0f - s.fx), w01 = (1.0f - s.fy) * s.fx;
+        const float w10 = s.fy * (1.0f - s.fx), w11 = s.fy * s.fx;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            float num = 0.0f, den = 0.0f;
+            const float v00 = wp[k];
+            if (!isnan(v00)) { num = w00 * v00; den = w00; }
+            if (s.fx != 0.0f) {
+                const float v01 = wp[k + 1];
+                if (!isnan(v01)) { num = fmaf(w01, v01, num); den += w01; }
+            }
+            if (s.fy != 0.0f) {
+                const float v10 = wp[WS + k];
+                if (!isnan(v10)) { num = fmaf(w10, v10, num); den += w10; }
+                if (s.fx != 0.0f) {
+                    const float v11 = wp[WS + k + 1];
+                    if (!isnan(v11)) { num = fmaf(w11, v11, num); den += w11; }
+                }
+            }
+            if (den > 0.0f) {
+                const float d = fmaf(-Wv, num / den, I);
+                err[k] = fmaf(d, d, err[k]);
+                var[k] += t2;
+                nv[k] += 1.0f;
+            }
+        }
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void finish_exact(const float (&err)[L], const float (&var)[L],
+                                             const float (&nv)[L], float (&e)[L]) {
+#pragma unroll
+    for (int k = 0; k < L; ++k)
+        e[k] = nv[k] == 0.0f ? INFINITY : (var[k] > 0.0f ? err[k] / var[k] : err[k]);
+}
+
+// Whole-strip exact evaluation by one thread (over all frames).
 template <int L>
 __device__ __noinline__ void eval_strip_exact(const float *__restrict__ fr, int pitch, int p,
                                               const FrameShift *__restrict__ sh, int N,
                                               const float *__restrict__ win, int WS, float Wv,
                                               float (&e)[L]) {
-    float err[L], var[L];
-    int nv[L];
+    float err[L], var[L], nv[L];
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-        err[k] = 0.0f;
-        var[k] = 0.0f;
-        nv[k] = 0;
-    }
-    for (int n = 0; n < N; ++n) {
-        const FrameShift s = sh[n];
-        const float I = fr[n * pitch + p];
-        const float t = I - Wv;
-        const float *wp = win + s.ky * WS + s.kx;
-        const float wt[4] = {(1.0f - s.fy) * (1.0f - s.fx), (1.0f - s.fy) * s.fx,
-                             s.fy * (1.0f - s.fx), s.fy * s.fx};
-#pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const float v[4] = {wp[k], wp[k + 1], wp[WS + k], wp[WS + k + 1]};
-            float num = 0.0f, den = 0.0f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (wt[c] == 0.0f || isnan(v[c])) continue;
-                num = fmaf(wt[c], v[c], num);
-                den += wt[c];
-            }
-            if (den > 0.0f) {
-                const float d = fmaf(-Wv, num / den, I);
-                err[k] = fmaf(d, d, err[k]);
-                var[k] = fmaf(t, t, var[k]);
-                nv[k] += 1;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < L; ++k)
-        e[k] = nv[k] == 0 ? INFINITY : (var[k] > 0.0f ? err[k] / var[k] : err[k]);
+    for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
+    accum_strip_exact<L>(fr, pitch, p, sh, 0, 1, N, win, WS, Wv, err, var, nv);
+    finish_exact<L>(err, var, nv, e);
 }
 
 __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
@@ -203,6 +221,7 @@ __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
 constexpr int kGroup = 4;            // pixels per group: consecutive columns of one row
 constexpr int kSplit = 4;            // lanes that share one strip, each taking every 4th frame
 constexpr int kSearchThreads = 256;
+constexpr int kExactList = 512;      // strips per CTA queued for the exact phase
 static_assert(kSplit == kGroup, "the reduce-scatter hands lane j the sums of pixel j");
 
 // One strip of L consecutive absolute reference columns on one reference row, for the
@@ -215,14 +234,17 @@ __device__ __forceinline__ void eval_group(const float *__restrict__ fr, int FP,
                                            const FrameShift *__restrict__ sh, int n0, int N,
                                            const float *__restrict__ win, int WS,
                                            const float (&Wv)[kGroup], float (&acc)[kGroup][L]) {
+    // pixels (0,1) and (2,3) are packed in float2 lanes: one FFMA2 advances two pixels
+    const float2 nW[2] = {make_float2(-Wv[0], -Wv[1]), make_float2(-Wv[2], -Wv[3])};
+    float2 acc2[2][L];
 #pragma unroll
-    for (int p = 0; p < kGroup; ++p)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int k = 0; k < L; ++k) acc[p][k] = 0.0f;
+        for (int k = 0; k < L; ++k) acc2[h][k] = make_float2(0.0f, 0.0f);
     for (int n = n0; n < N; n += kSplit) {
         const FrameShift s = sh[n];
         const float4 I4 = *reinterpret_cast<const float4 *>(fr + n * FP + g0);
-        const float I[kGroup] = {I4.x, I4.y, I4.z, I4.w};
+        const float2 I2[2] = {make_float2(I4.x, I4.y), make_float2(I4.z, I4.w)};
         const float *wp = win + s.ky * WS + s.kx;
         float G[L];
         if (s.fy == 0.0f) {
@@ -257,12 +279,21 @@ __device__ __forceinline__ void eval_group(const float *__restrict__ fr, int FP,
             }
         }
 #pragma unroll
-        for (int p = 0; p < kGroup; ++p)
+        for (int k = 0; k < L; ++k) {
+            const float2 GG = make_float2(G[k], G[k]);
 #pragma unroll
-            for (int k = 0; k < L; ++k) {
-                const float d = fmaf(-Wv[p], G[k], I[p]);
-                acc[p][k] = fmaf(d, d, acc[p][k]);
+            for (int h = 0; h < 2; ++h) {
+                const float2 d = __ffma2_rn(nW[h], GG, I2[h]);      // I - W R, two pixels
+                acc2[h][k] = __ffma2_rn(d, d, acc2[h][k]);          // += d^2
             }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        acc[0][k] = acc2[0][k].x;
+        acc[1][k] = acc2[0][k].y;
+        acc[2][k] = acc2[1][k].x;
+        acc[3][k] = acc2[1][k].y;
     }
 }
 
@@ -321,11 +352,14 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
     __shared__ unsigned long long s_key[TP];
     __shared__ float s_nb[9][TP];
     __shared__ int s_gr0[NG], s_gc0[NG], s_gns[NG], s_goff[NG + 1];
+    __shared__ int s_nx;                             // strips waiting for the exact phase
+    __shared__ int3 s_xl[kExactList];                // (pixel, reference row, first column)
 
     const int tid = threadIdx.x;
     const size_t P = (size_t)a.ny * a.nx;
 
     if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
+    if (tid == 0) s_nx = 0;
     for (int n = tid; n < a.N; n += NT) sh[n] = a.shifts[n];
     __syncthreads();
     for (int p = tid; p < TP; p += NT) {
@@ -479,9 +513,57 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
             nan_seen = nan_seen || (isnan(e[k]) && b >= -a.Sx && b <= a.Sx);
         }
         if (nan_seen) {
-            eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], e);
             s_slow[p] = 1;
+            const int slot = atomicAdd(&s_nx, 1);
+            if (slot < kExactList) {                 // evaluated by the whole CTA below
+                s_xl[slot] = make_int3(p, r, c);
+                continue;
+            }
+            eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], e);
         }
+        float be = INFINITY;
+        int bi = -1;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const int b = bofs + k;
+            if (b < -a.Sx || b > a.Sx) continue;
+            const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
+            if (a.ebuf) ebuf[p * nwin + idx] = e[k];
+            if (bi < 0 || e[k] < be) {
+                be = e[k];
+                bi = idx;
+            }
+        }
+        if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
+    }
+    __syncthreads();
+
+    // ---- strips that read invalid reference pixels: per-frame rule, 4 lanes per strip ----
+    const int nx_list = min(s_nx, kExactList);
+    for (int u0 = 0; u0 < nx_list * kSplit; u0 += NT) {
+        const int t = u0 + tid;
+        const bool valid = t < nx_list * kSplit;
+        float err[L], var[L], nv[L];
+#pragma unroll
+        for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
+        int3 x3 = make_int3(0, 0, 0);
+        if (valid) {
+            x3 = s_xl[t / kSplit];
+            accum_strip_exact<L>(fr, FP, x3.x, sh, j, kSplit, a.N, win + (x3.y - wy0) * WS + (x3.z - wx0),
+                                 WS, s_W[x3.x], err, var, nv);
+        }
+#pragma unroll
+        for (int k = 0; k < L; ++k)
+#pragma unroll
+            for (int off = 1; off < kSplit; off <<= 1) {
+                err[k] += __shfl_xor_sync(0xffffffffu, err[k], off);
+                var[k] += __shfl_xor_sync(0xffffffffu, var[k], off);
+                nv[k] += __shfl_xor_sync(0xffffffffu, nv[k], off);
+            }
+        if (!valid || j != 0) continue;
+        const int p = x3.x, aa = x3.y - s_ci[p], bofs = x3.z - s_cj[p];
+        float e[L];
+        finish_exact<L>(err, var, nv, e);
         float be = INFINITY;
         int bi = -1;
 #pragma unroll
