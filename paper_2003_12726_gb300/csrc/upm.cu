@@ -221,7 +221,7 @@ __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
 constexpr int kGroup = 4;            // pixels per group: consecutive columns of one row
 constexpr int kSplit = 4;            // lanes that share one strip, each taking every 4th frame
 constexpr int kSearchThreads = 256;
-constexpr int kExactList = 512;      // strips per CTA queued for the exact phase
+constexpr int kExactWords = 512;     // bitmask of strips for the exact phase (16384 bits)
 static_assert(kSplit == kGroup, "the reduce-scatter hands lane j the sums of pixel j");
 
 // One strip of L consecutive absolute reference columns on one reference row, for the
@@ -334,7 +334,7 @@ __device__ __forceinline__ unsigned long long pack_key(float e, int idx) {
 // first minimum in row-major window order. With a.ebuf every error is also kept in
 // shared memory, so the 3x3 about the minimum is read back instead of re-evaluated.
 template <int L, int TY>
-__global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
+__global__ void __launch_bounds__(kSearchThreads, 2) k_search(SearchArgs a) {
     constexpr int TP = 32 * TY;
     constexpr int FP = TP + 4;            // frame pitch: the 4 lanes of a strip hit 4 banks
     constexpr int NG = TP / kGroup;
@@ -352,14 +352,13 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
     __shared__ unsigned long long s_key[TP];
     __shared__ float s_nb[9][TP];
     __shared__ int s_gr0[NG], s_gc0[NG], s_gns[NG], s_goff[NG + 1];
-    __shared__ int s_nx;                             // strips waiting for the exact phase
-    __shared__ int3 s_xl[kExactList];                // (pixel, reference row, first column)
+    __shared__ unsigned int s_xbits[kExactWords];    // bit 4*item + j: strip needs the exact phase
 
     const int tid = threadIdx.x;
     const size_t P = (size_t)a.ny * a.nx;
 
     if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
-    if (tid == 0) s_nx = 0;
+    for (int q = tid; q < kExactWords; q += NT) s_xbits[q] = 0u;
     for (int n = tid; n < a.N; n += NT) sh[n] = a.shifts[n];
     __syncthreads();
     for (int p = tid; p < TP; p += NT) {
@@ -514,9 +513,9 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
         }
         if (nan_seen) {
             s_slow[p] = 1;
-            const int slot = atomicAdd(&s_nx, 1);
-            if (slot < kExactList) {                 // evaluated by the whole CTA below
-                s_xl[slot] = make_int3(p, r, c);
+            const int bit = item * kSplit + j;
+            if (bit < kExactWords * 32) {            // evaluated by the whole CTA below
+                atomicOr(&s_xbits[bit >> 5], 1u << (bit & 31));
                 continue;
             }
             eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], e);
@@ -539,45 +538,70 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(SearchArgs a) {
     __syncthreads();
 
     // ---- strips that read invalid reference pixels: per-frame rule, 4 lanes per strip ----
-    const int nx_list = min(s_nx, kExactList);
-    for (int u0 = 0; u0 < nx_list * kSplit; u0 += NT) {
-        const int t = u0 + tid;
-        const bool valid = t < nx_list * kSplit;
-        float err[L], var[L], nv[L];
+    // Each warp drains bitmask words in a fixed order, 8 strips at a time; every exact
+    // error is formed by the same frame split and reduction, so results do not depend on
+    // scheduling.
+    {
+        const int lane = tid & 31, warp = tid >> 5, slot = lane >> 2;
+        const int nwords = min((units + 31) >> 5, kExactWords);
+        for (int wd = warp; wd < nwords; wd += NT / 32) {
+            unsigned int m = s_xbits[wd];
+            while (m) {                              // m is the same in every lane of the warp
+                int mybit = -1;
 #pragma unroll
-        for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
-        int3 x3 = make_int3(0, 0, 0);
-        if (valid) {
-            x3 = s_xl[t / kSplit];
-            accum_strip_exact<L>(fr, FP, x3.x, sh, j, kSplit, a.N, win + (x3.y - wy0) * WS + (x3.z - wx0),
-                                 WS, s_W[x3.x], err, var, nv);
-        }
+                for (int q = 0; q < 8; ++q) {
+                    if (!m) break;
+                    const int b = __ffs(m) - 1;
+                    if (q == slot) mybit = b;
+                    m &= m - 1;
+                }
+                const bool valid = mybit >= 0;
+                float err[L], var[L], nv[L];
 #pragma unroll
-        for (int k = 0; k < L; ++k)
+                for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
+                int p = 0, r = 0, c = 0;
+                if (valid) {
+                    const int bit = wd * 32 + mybit, item = bit / kSplit;
+                    int lo = 0, hi = NG - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_goff[mid] <= item) lo = mid; else hi = mid - 1;
+                    }
+                    const int loc = item - s_goff[lo], ns = s_gns[lo];
+                    r = s_gr0[lo] + loc / ns;
+                    c = s_gc0[lo] + (loc % ns) * L;
+                    p = lo * kGroup + (bit % kSplit);
+                    accum_strip_exact<L>(fr, FP, p, sh, j, kSplit, a.N, win + (r - wy0) * WS + (c - wx0),
+                                         WS, s_W[p], err, var, nv);
+                }
 #pragma unroll
-            for (int off = 1; off < kSplit; off <<= 1) {
-                err[k] += __shfl_xor_sync(0xffffffffu, err[k], off);
-                var[k] += __shfl_xor_sync(0xffffffffu, var[k], off);
-                nv[k] += __shfl_xor_sync(0xffffffffu, nv[k], off);
+                for (int k = 0; k < L; ++k)
+#pragma unroll
+                    for (int off = 1; off < kSplit; off <<= 1) {
+                        err[k] += __shfl_xor_sync(0xffffffffu, err[k], off);
+                        var[k] += __shfl_xor_sync(0xffffffffu, var[k], off);
+                        nv[k] += __shfl_xor_sync(0xffffffffu, nv[k], off);
+                    }
+                if (!valid || j != 0) continue;
+                const int aa = r - s_ci[p], bofs = c - s_cj[p];
+                float e[L];
+                finish_exact<L>(err, var, nv, e);
+                float be = INFINITY;
+                int bi = -1;
+#pragma unroll
+                for (int k = 0; k < L; ++k) {
+                    const int b = bofs + k;
+                    if (b < -a.Sx || b > a.Sx) continue;
+                    const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
+                    if (a.ebuf) ebuf[p * nwin + idx] = e[k];
+                    if (bi < 0 || e[k] < be) {
+                        be = e[k];
+                        bi = idx;
+                    }
+                }
+                if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
             }
-        if (!valid || j != 0) continue;
-        const int p = x3.x, aa = x3.y - s_ci[p], bofs = x3.z - s_cj[p];
-        float e[L];
-        finish_exact<L>(err, var, nv, e);
-        float be = INFINITY;
-        int bi = -1;
-#pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const int b = bofs + k;
-            if (b < -a.Sx || b > a.Sx) continue;
-            const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
-            if (a.ebuf) ebuf[p * nwin + idx] = e[k];
-            if (bi < 0 || e[k] < be) {
-                be = e[k];
-                bi = idx;
-            }
         }
-        if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
     }
     __syncthreads();
 

@@ -128,3 +128,20 @@ def test_iterations_approach_the_truth():
     rg, ro, r0 = gauge_rms(ug), gauge_rms(uo), gauge_rms(s.u_init)
     print("map error vs truth (gauge removed): init %.4f  oracle %.4f  gpu %.4f" % (r0, ro, rg))
     assert rg < r0 and abs(rg - ro) <= 0.1 * ro + 1e-3
+
+
+def test_update_is_deterministic(scan):
+    """Repeated calls on the same inputs give bit-identical maps and errors (no result may
+    depend on the order in which threads or CTAs run)."""
+    s = scan
+    inp, I32, w32 = _update_inputs(s, hole=True)
+    runs = [gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=q)
+            for q in (True, True, True, False, False)]
+    for k in (1, 2):
+        assert np.array_equal(runs[0][0], runs[k][0])
+        assert np.array_equal(runs[0][1], runs[k][1], equal_nan=True)
+    assert np.array_equal(runs[3][0], runs[4][0])
+    Ia, wa = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    Ib, wb = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    # the reference image sums FP64 atomics: equal to rounding, not necessarily bitwise
+    assert parity.rel_l2(Ib.astype(np.float64), Ia.astype(np.float64)) < 1e-6
