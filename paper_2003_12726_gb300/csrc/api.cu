@@ -1,5 +1,7 @@
 // api.cu -- the extern "C" boundary of libpxst.so: argument checks, workspace carving,
 // launch sequencing, device status, and per-kernel event timing.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -91,6 +93,54 @@ struct Timed {
     }
 };
 
+// ---- integer frame-shift span per translation array -----------------------------------
+// The search kernel's shared-memory window spans the range of the integer parts of
+// -Delta; the host learns it once per (device, translation pointer, frame count) with a
+// synchronous read of Delta, and plans the launch with it. During stream capture no read
+// is possible: an unknown span plans for the largest window.
+struct SpanKey {
+    int dev;
+    const double *delta;
+    int n;
+    bool operator==(const SpanKey &o) const { return dev == o.dev && delta == o.delta && n == o.n; }
+};
+std::mutex g_smu;
+std::vector<std::pair<SpanKey, std::pair<int, int>>> g_spans;
+
+void shift_span(const pxst_dims &d, const double *delta, cudaStream_t s, int &sy, int &sx) {
+    sy = sx = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    const SpanKey key{dev, delta, d.n_frames};
+    {
+        std::lock_guard<std::mutex> g(g_smu);
+        for (auto &e : g_spans)
+            if (e.first == key) {
+                sy = e.second.first;
+                sx = e.second.second;
+                return;
+            }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    std::vector<double> h((size_t)2 * d.n_frames);
+    if (cudaMemcpyAsync(h.data(), delta, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return;
+    double mn[2] = {1e300, 1e300}, mx[2] = {-1e300, -1e300};
+    for (int n = 0; n < d.n_frames; ++n)
+        for (int a = 0; a < 2; ++a) {
+            const double k = std::floor(-h[2 * n + a]);
+            mn[a] = std::min(mn[a], k);
+            mx[a] = std::max(mx[a], k);
+        }
+    sy = (int)std::min(mx[0] - mn[0] + 1, 1e6);     // +1: a fraction rounding up to 1
+    sx = (int)std::min(mx[1] - mn[1] + 1, 1e6);
+    std::lock_guard<std::mutex> g(g_smu);
+    if (g_spans.size() > 256) g_spans.clear();
+    g_spans.push_back({key, {sy, sx}});
+}
+
 pxst_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return PXST_OK;
     std::fprintf(stderr, "pxst: CUDA error %s\n", cudaGetErrorString(e));
@@ -125,13 +175,15 @@ pxst_status run_omap(const pxst_dims &d, const float *frames, const float *W,
 
 pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *frames,
                        const float *W, const uint8_t *mask, const float *I_ref, const float *wref,
-                       double *u, float *err_out, Ws &w, cudaStream_t s) {
+                       const double *delta, double *u, float *err_out, Ws &w, cudaStream_t s) {
     PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, 2 * sizeof(int), s));   // n_exact, n_exact_cta
     if (d.n_frames <= search_max_frames()) {
+        int sy, sx;
+        shift_span(d, delta, s, sy, sx);
         {
             Timed t(PXST_K_SEARCH, s);
             PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr,
-                                   w.exact_list, u, err_out, s));
+                                   w.exact_list, u, err_out, sy, sx, s));
         }
         Timed t(PXST_K_EXACT, s);
         PXST_TRY(launch_exact(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list,
@@ -184,7 +236,7 @@ pxst_status pxst_update_pixel_map(const pxst_dims *dims, const pxst_options *opt
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = run_prepare(*dims, delta, ws, s);
     if (st != PXST_OK) return st;
-    return run_update(*dims, *opts, frames, W, mask, I_ref, w, u_inout, err_out, ws, s);
+    return run_update(*dims, *opts, frames, W, mask, I_ref, w, delta, u_inout, err_out, ws, s);
 }
 
 pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_t n_iter,
@@ -203,7 +255,7 @@ pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_
     for (int it = 0; it < n_iter; ++it) {
         st = run_omap(*dims, frames, W, mask, u_inout, I_ref, w, ws, s);
         if (st != PXST_OK) return st;
-        st = run_update(*dims, *opts, frames, W, mask, I_ref, w, u_inout, err_out, ws, s);
+        st = run_update(*dims, *opts, frames, W, mask, I_ref, w, delta, u_inout, err_out, ws, s);
         if (st != PXST_OK) return st;
     }
     return PXST_OK;

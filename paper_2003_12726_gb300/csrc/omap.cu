@@ -147,42 +147,77 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(ScatterArgs a) {
                 s_den[c] = 0.0f;
             }
         __syncthreads();
-        if (act) {
-            for (int n = g0; n < g1; n += SC_PREFETCH) {
-                float I[SC_PREFETCH];
-                FrameShift S[SC_PREFETCH];
+        // Every lane of a warp (one pixel row, consecutive columns) runs the frame loop so
+        // that neighbouring lanes can merge contributions: when lane l+1's left corner is
+        // the cell right of lane l's left corner on the same row, lane l hands its right
+        // corners to lane l+1, which adds both with one atomic per row. Corners whose
+        // bilinear weight is exactly zero are skipped.
+        const int lane = threadIdx.x & 31;
+        for (int n = g0; n < g1; n += SC_PREFETCH) {
+            float I[SC_PREFETCH];
+            FrameShift S[SC_PREFETCH];
 #pragma unroll
-                for (int j = 0; j < SC_PREFETCH; ++j)
-                    if (n + j < g1) {
-                        I[j] = __ldg(a.frames + (size_t)(n + j) * P + pix);
-                        S[j] = a.shifts[n + j];
+            for (int jf = 0; jf < SC_PREFETCH; ++jf)
+                if (n + jf < g1) {
+                    S[jf] = a.shifts[n + jf];
+                    I[jf] = act ? __ldg(a.frames + (size_t)(n + jf) * P + pix) : 0.0f;
+                }
+#pragma unroll
+            for (int jf = 0; jf < SC_PREFETCH; ++jf) {
+                if (n + jf >= g1) break;                    // uniform over the CTA
+                int by = iy + S[jf].ky, bx = ix + S[jf].kx;
+                float sy = fy + S[jf].fy, sx = fx + S[jf].fx;
+                if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
+                if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
+                if (!act) { by = INT_MIN; bx = INT_MIN; }
+                const float WI = Wv * I[jf];
+                // right corners (top, bottom) and left corners, numerator and weight
+                float rn0 = (1.0f - sy) * sx * WI, rd0 = (1.0f - sy) * sx * WW;
+                float rn1 = sy * sx * WI, rd1 = sy * sx * WW;
+                float ln0 = (1.0f - sy) * (1.0f - sx) * WI, ld0 = (1.0f - sy) * (1.0f - sx) * WW;
+                float ln1 = sy * (1.0f - sx) * WI, ld1 = sy * (1.0f - sx) * WW;
+                const int pbx = __shfl_up_sync(0xffffffffu, bx, 1);
+                const int pby = __shfl_up_sync(0xffffffffu, by, 1);
+                const float prn0 = __shfl_up_sync(0xffffffffu, rn0, 1);
+                const float prd0 = __shfl_up_sync(0xffffffffu, rd0, 1);
+                const float prn1 = __shfl_up_sync(0xffffffffu, rn1, 1);
+                const float prd1 = __shfl_up_sync(0xffffffffu, rd1, 1);
+                const bool take = act && lane > 0 && pby == by && pbx != INT_MIN && pbx + 1 == bx;
+                const bool given = __shfl_down_sync(0xffffffffu, take ? 1 : 0, 1) && lane < 31;
+                if (take) {
+                    ln0 += prn0; ld0 += prd0;
+                    ln1 += prn1; ld1 += prd1;
+                }
+                if (!act) continue;
+                const bool row1 = sy != 0.0f;                // bottom corners carry weight
+                const bool right = sx != 0.0f && !given;     // right corners not handed over
+                if (fits) {
+                    const int c00 = (by - r0) * Wd + (bx - c0);
+                    atomicAdd(&s_num[c00], ln0);
+                    atomicAdd(&s_den[c00], ld0);
+                    if (right) {
+                        atomicAdd(&s_num[c00 + 1], rn0);
+                        atomicAdd(&s_den[c00 + 1], rd0);
                     }
+                    if (row1 || (take && (prn1 != 0.0f || prd1 != 0.0f))) {
+                        atomicAdd(&s_num[c00 + Wd], ln1);
+                        atomicAdd(&s_den[c00 + Wd], ld1);
+                    }
+                    if (row1 && right) {
+                        atomicAdd(&s_num[c00 + Wd + 1], rn1);
+                        atomicAdd(&s_den[c00 + Wd + 1], rd1);
+                    }
+                } else {
+                    const float vn[4] = {ln0, right ? rn0 : 0.0f, ln1, right ? rn1 : 0.0f};
+                    const float vd[4] = {ld0, right ? rd0 : 0.0f, ld1, right ? rd1 : 0.0f};
 #pragma unroll
-                for (int j = 0; j < SC_PREFETCH; ++j) {
-                    if (n + j >= g1) break;
-                    int by = iy + S[j].ky, bx = ix + S[j].kx;
-                    float sy = fy + S[j].fy, sx = fx + S[j].fx;
-                    if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
-                    if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
-                    const float WI = Wv * I[j];
-                    const float wt[4] = {(1.0f - sy) * (1.0f - sx), (1.0f - sy) * sx, sy * (1.0f - sx), sy * sx};
-                    if (fits) {
-                        const int base = (by - r0) * Wd + (bx - c0);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int c = base + (k >> 1) * Wd + (k & 1);
-                            atomicAdd(&s_num[c], wt[k] * WI);
-                            atomicAdd(&s_den[c], wt[k] * WW);
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int gy = by + (k >> 1), gx = bx + (k & 1);
-                            if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx || wt[k] == 0.0f) continue;
-                            const size_t gi = (size_t)gy * a.Rx + gx;
-                            atomicAdd(&a.num[gi], (double)(wt[k] * WI));
-                            atomicAdd(&a.den[gi], (double)(wt[k] * WW));
-                        }
+                    for (int k = 0; k < 4; ++k) {
+                        const int gy = by + (k >> 1), gx = bx + (k & 1);
+                        if (vd[k] == 0.0f && vn[k] == 0.0f) continue;
+                        if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;
+                        const size_t gi = (size_t)gy * a.Rx + gx;
+                        atomicAdd(&a.num[gi], (double)vn[k]);
+                        atomicAdd(&a.den[gi], (double)vd[k]);
                     }
                 }
             }

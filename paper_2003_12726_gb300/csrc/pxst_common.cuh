@@ -74,10 +74,13 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
                            WsHeader *hdr, double *num, double *den, cudaStream_t stream);
 cudaError_t launch_normalise(const pxst_dims &d, const double *num, const double *den,
                              float *I_ref, float *w, cudaStream_t stream);
+// span_y / span_x: range of the integer frame shifts (for sizing the shared-memory
+// window; a smaller guess costs speed, never correctness). Negative = unknown.
 cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float *frames,
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
-                          int *exact_list, double *u, float *err_out, cudaStream_t stream);
+                          int *exact_list, double *u, float *err_out, int span_y, int span_x,
+                          cudaStream_t stream);
 cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float *frames,
                          const float *W, const uint8_t *mask, const float *I_ref,
                          const float *w, const FrameShift *shifts, WsHeader *hdr,

@@ -792,6 +792,36 @@ cudaError_t launch_one(const SearchArgs &a, const Plan &pl, cudaStream_t stream)
     return cudaGetLastError();
 }
 
+// Static shared memory and the register-limited number of resident CTAs of one variant.
+template <int L, int TY>
+cudaError_t variant_info(size_t &static_smem, int &ctas_by_regs) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_search<L, TY>);
+    if (e != cudaSuccess) return e;
+    static_smem = fa.sharedSizeBytes;
+    const int regs = (fa.numRegs + 7) & ~7;          // allocated per thread in units of 8
+    ctas_by_regs = 65536 / (regs * kSearchThreads);
+    return cudaSuccess;
+}
+
+template <int L>
+cudaError_t variant_info_L(int TY, size_t &st, int &cr) {
+    switch (TY) {
+        case 8: return variant_info<L, 8>(st, cr);
+        case 4: return variant_info<L, 4>(st, cr);
+        case 2: return variant_info<L, 2>(st, cr);
+        default: return variant_info<L, 1>(st, cr);
+    }
+}
+
+cudaError_t variant_info_any(int L, int TY, size_t &st, int &cr) {
+    switch (L) {
+        case 11: return variant_info_L<11>(TY, st, cr);
+        case 9: return variant_info_L<9>(TY, st, cr);
+        default: return variant_info_L<7>(TY, st, cr);
+    }
+}
+
 template <int L>
 cudaError_t launch_L(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
     switch (pl.TY) {
@@ -810,37 +840,60 @@ int search_max_frames() { return (kSearchSmemBudget - 16 * 1024) / (36 * 4 + 16)
 cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float *frames,
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
-                          int *exact_list, double *u, float *err_out, cudaStream_t stream) {
+                          int *exact_list, double *u, float *err_out, int span_y, int span_x,
+                          cudaStream_t stream) {
     Plan pl;
     const int wxn = 2 * o.win_x + 1;
     const size_t nwin = (size_t)(2 * o.win_y + 1) * wxn;
     pl.L = pick_strip(wxn);
     const size_t N = (size_t)d.n_frames, shifts_b = N * sizeof(FrameShift);
-    auto frames_b = [&](int ty) { return N * (32 * ty + 4) * 4; };
-    // Prefer a tile whose frames and full error buffer leave a 2-CTA/SM budget for the
-    // window; otherwise the largest tile whose frames fit, without the error buffer.
-    int ebuf = 0;
-    pl.TY = 0;
-    for (int ty = 8; ty >= 2 && !pl.TY; ty >>= 1)
-        if (shifts_b + frames_b(ty) + 32 * ty * nwin * 4 + 16 * 1024 <= 100 * 1024) {
-            pl.TY = ty;
-            ebuf = 1;
+    const size_t sm_per_sm = 228 * 1024;
+    // window estimate for a local magnification up to 2 (unknown span: the largest window)
+    auto window_est = [&](int ty) -> size_t {
+        if (span_y < 0 || span_x < 0) return (size_t)kSearchSmemBudget;
+        const size_t rows = 2 * ty + 2 * o.win_y + span_y + 4;
+        const size_t cols = 64 + wxn + pl.L + span_x + 6;
+        return rows * cols * 4;
+    };
+    // Choose (tile height, error buffer) for the most resident CTAs per SM, then prefer
+    // keeping the errors (no 3x3 re-evaluation), then taller tiles; the window gets the
+    // rest of the CTA's share of shared memory.
+    int best_score = -1;
+    pl.TY = 1;
+    pl.smem = 0;
+    int best_ebuf = 0;
+    for (int ebuf = 1; ebuf >= 0; --ebuf)
+        for (int ty = 8; ty >= 1; ty >>= 1) {
+            size_t st = 0;
+            int cr = 1;
+            cudaError_t e = variant_info_any(pl.L, ty, st, cr);
+            if (e != cudaSuccess) return e;
+            const size_t fixed = shifts_b + N * (32 * ty + 4) * 4 + (ebuf ? (size_t)32 * ty * nwin * 4 : 0);
+            for (int k = 3; k >= 1; --k) {
+                if (k > cr) continue;
+                size_t per_cta = sm_per_sm / k - 1024 - st;
+                if (per_cta > (size_t)kSearchSmemBudget) per_cta = kSearchSmemBudget;
+                const size_t need = fixed + window_est(ty);
+                if (need > per_cta && !(k == 1 && fixed + 4096 <= per_cta && window_est(ty) >= (size_t)kSearchSmemBudget))
+                    continue;
+                const int score = k * 100 + ebuf * 10 + ty;
+                if (score > best_score) {
+                    best_score = score;
+                    pl.TY = ty;
+                    best_ebuf = ebuf;
+                    pl.smem = per_cta;
+                }
+                break;
+            }
         }
-    if (!pl.TY) {
-        pl.TY = 1;
-        for (int ty = 8; ty >= 1; ty >>= 1)
-            if (frames_b(ty) <= 110 * 1024) { pl.TY = ty; break; }
-    }
-    const size_t fixed = shifts_b + frames_b(pl.TY) + (ebuf ? (size_t)32 * pl.TY * nwin * 4 : 0);
-    size_t total = fixed + 16 * 1024 <= 100 * 1024 ? 100 * 1024 : (size_t)kSearchSmemBudget;
-    if (fixed + 4096 > total) total = fixed + 4096;
-    pl.smem = total;
-    pl.win_cap = (int)((total - fixed) / 4);
+    if (best_score < 0) return cudaErrorInvalidConfiguration;   // callers check frame count first
+    const size_t fixed = shifts_b + N * (32 * pl.TY + 4) * 4 + (best_ebuf ? (size_t)32 * pl.TY * nwin * 4 : 0);
+    pl.win_cap = (int)((pl.smem - fixed) / 4);
 
     SearchArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
-    a.ebuf = ebuf; a.win_cap = pl.win_cap;
+    a.ebuf = best_ebuf; a.win_cap = pl.win_cap;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.exact_list = exact_list; a.u = u; a.err_out = err_out;
     switch (pl.L) {
