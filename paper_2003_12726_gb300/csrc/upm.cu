@@ -334,7 +334,7 @@ __device__ __forceinline__ unsigned long long pack_key(float e, int idx) {
 // first minimum in row-major window order. With a.ebuf every error is also kept in
 // shared memory, so the 3x3 about the minimum is read back instead of re-evaluated.
 template <int L, int TY>
-__global__ void __launch_bounds__(kSearchThreads, 2) k_search(SearchArgs a) {
+__global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(SearchArgs a) {
     constexpr int TP = 32 * TY;
     constexpr int FP = TP + 4;            // frame pitch: the 4 lanes of a strip hit 4 banks
     constexpr int NG = TP / kGroup;
