@@ -120,7 +120,7 @@ def cpu_sample(s, target_s=12.0, max_rows=None, threads=None):
     threads = threads or oracle.default_threads()
     ny = s.frames.shape[1]
     rows_active = np.flatnonzero(s.M.any(axis=1))
-    r0 = int(rows_active[len(rows_active) // 2]) if rows_active.size else 0
+    r0 = int(rows_active[0]) if rows_active.size else 0
     n_rows, spent, evals = 1, 0.0, 0
     Sy, Sx = s.window
     nwin = (2 * Sy + 1) * (2 * Sx + 1)
