@@ -60,6 +60,10 @@ typedef struct {
 
 /* Arithmetic form of the candidate search. */
 #define PXST_FORM_FP32  0   /* direct sum of (I - W R)^2 in FP32 on CUDA cores */
+#define PXST_FORM_BF16  1   /* cross term on tensor cores, BF16 operands, FP32 accumulation;
+                               the best rescore_k candidates per pixel, the 3x3 about the
+                               minimum and the fit are then evaluated exactly as in FP32 */
+#define PXST_FORM_TF32  2   /* as PXST_FORM_BF16 with TF32 operands */
 
 typedef struct {
     int32_t win_y, win_x;  /* search window half-widths S_y, S_x: candidates are the
@@ -178,6 +182,15 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);
+
+/* Diagnostic of the tensor-core contraction used by the BF16 / TF32 forms: one CTA
+ * computes D[128][256] = A[128][K] . B[256][K]^T (D float32 row-major) with the same TMA,
+ * tcgen05.mma and TMEM path as the search. A and B are row-major device arrays of
+ * bfloat16 (form PXST_FORM_BF16) or float32 read as TF32 (PXST_FORM_TF32); K * element
+ * size must be a multiple of 16 bytes and the pointers 16-byte aligned. *status (device
+ * int) gets PXST_DEV_TIMEOUT if a wait ran out. Not part of the method: a self-check. */
+pxst_status pxst_tensor_check(int32_t form, int32_t K, const void *A, const void *B, float *D,
+                              int32_t *status, void *stream);
 
 /* Human-readable text for a status code. */
 const char *pxst_status_string(pxst_status s);

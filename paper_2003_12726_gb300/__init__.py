@@ -22,6 +22,8 @@ from . import build as _build
 STATUS = {0: "ok", -1: "invalid argument", -2: "invalid shape", -3: "range", -4: "cuda error",
           -5: "workspace too small", -6: "timeout"}
 FORM_FP32 = 0
+FORM_BF16 = 1
+FORM_TF32 = 2
 KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms"]
 
 
@@ -84,6 +86,8 @@ def lib():
         L.pxst_status_string.argtypes = [i32]
         L.pxst_status_string.restype = C.c_char_p
         L.pxst_version.restype = C.c_char_p
+        L.pxst_tensor_check.argtypes = [i32, i32, P, P, P, P, P]
+        L.pxst_tensor_check.restype = i32
         _lib = L
     return _lib
 
@@ -92,7 +96,7 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_update_pixel_map",
             "pxst_iterate", "pxst_reference_terms", "pxst_get_status", "pxst_last_exact_count",
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
-            "pxst_version"]
+            "pxst_version", "pxst_tensor_check"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -323,3 +327,18 @@ class Reconstruction:
         h2d = sum(h[k].numel() * h[k].element_size() for k in ("frames", "W", "M", "delta", "u"))
         d2h = h["u_out"].numel() * 8 + h["err_out"].numel() * 4
         return h2d, d2h
+
+
+def tensor_check(form, A, B, stream=None):
+    """pxst_tensor_check: D = A . B^T on the tensor cores (A [128][K], B [256][K], CUDA
+    tensors of bfloat16 for FORM_BF16 or float32 for FORM_TF32). Returns (D, status bits)."""
+    torch = _torch()
+    K = int(A.shape[1])
+    dt = torch.bfloat16 if form == FORM_BF16 else torch.float32
+    a = _check(A, dt, (128, K), "A")
+    b = _check(B, dt, (256, K), "B")
+    D = torch.empty((128, 256), dtype=torch.float32, device=A.device)
+    st = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _raise(lib().pxst_tensor_check(int(form), K, a, b, C.c_void_p(D.data_ptr()), C.c_void_p(st.data_ptr()),
+                                   _stream(stream)), "tensor_check")
+    return D, int(st.item())
