@@ -70,7 +70,8 @@ typedef struct {
                               integers c = round(u) + (a, b), |a| <= S_y, |b| <= S_x */
     int32_t quadratic;     /* 1: 3x3 paraboloid sub-pixel refinement, 0: integer argmin */
     int32_t form;          /* PXST_FORM_* */
-    int32_t rescore_k;     /* reserved for the reduced-precision forms (0 = default) */
+    int32_t rescore_k;     /* tensor forms: candidates per pixel re-evaluated in FP32
+                              (0 = default = 4; only 4 is supported) */
     int32_t reserved;
     int64_t timeout_ns;    /* reserved for device-side waits (0 = default) */
 } pxst_options;
@@ -178,7 +179,11 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 #define PXST_K_SEARCH     3   /* update_pixel_map candidate search + refinement */
 #define PXST_K_EXACT      4   /* update_pixel_map exact path */
 #define PXST_K_REFTERMS   5   /* reference_terms */
-#define PXST_K_COUNT      6
+#define PXST_K_TPREP      6   /* tensor forms: centred frames, once per call */
+#define PXST_K_GTABLE     7   /* tensor forms: shifted reference per frame, T~ and n_valid */
+#define PXST_K_TSEARCH    8   /* tensor forms: tensor-core ranking of every candidate */
+#define PXST_K_RESCORE    9   /* tensor forms: exact FP32 evaluation of the best candidates */
+#define PXST_K_COUNT      10
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);

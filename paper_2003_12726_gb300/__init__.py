@@ -24,7 +24,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "invalid shape", -3: "range", -4:
 FORM_FP32 = 0
 FORM_BF16 = 1
 FORM_TF32 = 2
-KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms"]
+KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms",
+           "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore"]
 
 
 class PxstError(RuntimeError):

@@ -26,7 +26,8 @@ bool opts_ok(const pxst_options *o) {
     if (o->win_y < 0 || o->win_x < 0 || o->win_y > 4096 || o->win_x > 4096) return false;
     if ((long long)(2 * o->win_y + 1) * (2 * o->win_x + 1) >= (1LL << 30)) return false;
     if (o->quadratic != 0 && o->quadratic != 1) return false;
-    if (o->form != PXST_FORM_FP32) return false;
+    if (o->form != PXST_FORM_FP32 && o->form != PXST_FORM_BF16 && o->form != PXST_FORM_TF32) return false;
+    if (o->rescore_k != 0 && o->rescore_k != 4) return false;     // the tensor forms keep 4
     return true;
 }
 
@@ -35,12 +36,17 @@ struct Ws {
     FrameShift *shifts;
     int *exact_list;
     double *num, *den;
+    void *At, *G;
+    float *Tt;
+    int *nvalid, *cand;
+    uint8_t *edge;
+    int Npad;
 };
 
-pxst_status carve(const pxst_dims &d, void *workspace, size_t ws_bytes, Ws &w) {
+pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes, Ws &w) {
     if (!workspace) return PXST_ERR_ARG;
     if (((uintptr_t)workspace & 255) != 0) return PXST_ERR_ARG;
-    const WsLayout L = ws_layout(d);
+    const WsLayout L = ws_layout(d, form);
     if (ws_bytes < L.total) return PXST_ERR_NOMEM;
     char *b = static_cast<char *>(workspace);
     w.hdr = reinterpret_cast<WsHeader *>(b + L.header);
@@ -48,6 +54,13 @@ pxst_status carve(const pxst_dims &d, void *workspace, size_t ws_bytes, Ws &w) {
     w.exact_list = reinterpret_cast<int *>(b + L.exact_list);
     w.num = reinterpret_cast<double *>(b + L.num);
     w.den = reinterpret_cast<double *>(b + L.den);
+    w.At = b + L.At;
+    w.G = b + L.G;
+    w.Tt = reinterpret_cast<float *>(b + L.Tt);
+    w.nvalid = reinterpret_cast<int *>(b + L.nvalid);
+    w.cand = reinterpret_cast<int *>(b + L.cand);
+    w.edge = reinterpret_cast<uint8_t *>(b + L.edge);
+    w.Npad = L.Npad;
     return PXST_OK;
 }
 
@@ -175,15 +188,40 @@ pxst_status run_omap(const pxst_dims &d, const float *frames, const float *W,
 
 pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *frames,
                        const float *W, const uint8_t *mask, const float *I_ref, const float *wref,
-                       const double *delta, double *u, float *err_out, Ws &w, cudaStream_t s) {
+                       const double *delta, double *u, float *err_out, Ws &w, cudaStream_t s,
+                       bool operands_ready = false) {
     PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, 2 * sizeof(int), s));   // n_exact, n_exact_cta
     if (d.n_frames <= search_max_frames()) {
         int sy, sx;
         shift_span(d, delta, s, sy, sx);
-        {
+        if (o.form == PXST_FORM_FP32) {
             Timed t(PXST_K_SEARCH, s);
             PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr,
-                                   w.exact_list, u, err_out, sy, sx, s));
+                                   w.exact_list, u, err_out, sy, sx, 0, nullptr, nullptr, 0, s));
+        } else {
+            // tensor-core ranking of every candidate, then exact FP32 evaluation of the best
+            // four per pixel (and of every candidate of pixels touching invalid reference pixels)
+            if (!operands_ready) {
+                Timed t(PXST_K_TPREP, s);
+                PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, s));
+            }
+            {
+                Timed t(PXST_K_GTABLE, s);
+                PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.G, w.Tt, w.nvalid, s));
+            }
+            {
+                Timed t(PXST_K_TSEARCH, s);
+                PXST_TRY(launch_tsearch(d, o, w.Npad, w.At, w.G, mask, u, w.Tt, w.nvalid, w.hdr, w.cand,
+                                        w.edge, s));
+            }
+            {
+                Timed t(PXST_K_RESCORE, s);
+                PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list, u,
+                                       err_out, sy, sx, 1, w.cand, w.edge, 0, s));
+            }
+            Timed t(PXST_K_SEARCH, s);
+            PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list, u,
+                                   err_out, sy, sx, 0, nullptr, w.edge, 1, s));
         }
         Timed t(PXST_K_EXACT, s);
         PXST_TRY(launch_exact(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list,
@@ -202,9 +240,8 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
 extern "C" {
 
 size_t pxst_workspace_size(const pxst_dims *dims, const pxst_options *opts) {
-    (void)opts;
     if (!dims_ok(dims)) return 0;
-    return ws_layout(*dims).total;
+    return ws_layout(*dims, opts ? opts->form : PXST_FORM_FP32).total;
 }
 
 pxst_status pxst_make_object_map(const pxst_dims *dims, const float *frames, const float *W,
@@ -214,7 +251,7 @@ pxst_status pxst_make_object_map(const pxst_dims *dims, const float *frames, con
     if (!dims_ok(dims)) return PXST_ERR_SHAPE;
     if (!frames || !W || !mask || !u || !delta || !I_ref || !w) return PXST_ERR_ARG;
     Ws ws;
-    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    pxst_status st = carve(*dims, PXST_FORM_FP32, workspace, ws_bytes, ws);
     if (st != PXST_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = run_prepare(*dims, delta, ws, s);
@@ -231,7 +268,7 @@ pxst_status pxst_update_pixel_map(const pxst_dims *dims, const pxst_options *opt
     if (!opts_ok(opts)) return PXST_ERR_ARG;
     if (!frames || !W || !mask || !I_ref || !w || !delta || !u_inout) return PXST_ERR_ARG;
     Ws ws;
-    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    pxst_status st = carve(*dims, opts->form, workspace, ws_bytes, ws);
     if (st != PXST_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = run_prepare(*dims, delta, ws, s);
@@ -247,15 +284,19 @@ pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_
     if (!opts_ok(opts) || n_iter < 0) return PXST_ERR_ARG;
     if (!frames || !W || !mask || !delta || !u_inout || !I_ref || !w) return PXST_ERR_ARG;
     Ws ws;
-    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    pxst_status st = carve(*dims, opts->form, workspace, ws_bytes, ws);
     if (st != PXST_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = run_prepare(*dims, delta, ws, s);
     if (st != PXST_OK) return st;
+    if (opts->form != PXST_FORM_FP32 && n_iter > 0) {
+        Timed t(PXST_K_TPREP, s);
+        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, s));
+    }
     for (int it = 0; it < n_iter; ++it) {
         st = run_omap(*dims, frames, W, mask, u_inout, I_ref, w, ws, s);
         if (st != PXST_OK) return st;
-        st = run_update(*dims, *opts, frames, W, mask, I_ref, w, delta, u_inout, err_out, ws, s);
+        st = run_update(*dims, *opts, frames, W, mask, I_ref, w, delta, u_inout, err_out, ws, s, true);
         if (st != PXST_OK) return st;
     }
     return PXST_OK;
@@ -267,7 +308,7 @@ pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, cons
     if (!dims_ok(dims)) return PXST_ERR_SHAPE;
     if (!I_ref || !w || !delta || !T || !n_valid) return PXST_ERR_ARG;
     Ws ws;
-    pxst_status st = carve(*dims, workspace, ws_bytes, ws);
+    pxst_status st = carve(*dims, PXST_FORM_FP32, workspace, ws_bytes, ws);
     if (st != PXST_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = run_prepare(*dims, delta, ws, s);
@@ -342,6 +383,10 @@ const char *pxst_kernel_name(int32_t k) {
         case PXST_K_SEARCH: return "upm_search";
         case PXST_K_EXACT: return "upm_exact";
         case PXST_K_REFTERMS: return "reference_terms";
+        case PXST_K_TPREP: return "tensor_prep";
+        case PXST_K_GTABLE: return "tensor_gtable";
+        case PXST_K_TSEARCH: return "tensor_search";
+        case PXST_K_RESCORE: return "upm_rescore";
         default: return "?";
     }
 }

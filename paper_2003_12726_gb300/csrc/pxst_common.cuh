@@ -31,19 +31,42 @@ static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
-    size_t header, shifts, exact_list, num, den, total;
+    size_t header, shifts, exact_list, num, den;
+    // precision forms only (zero size otherwise)
+    size_t At, G, Tt, nvalid, cand, edge;
+    int Npad;
+    size_t total;
 };
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-inline WsLayout ws_layout(const pxst_dims &d) {
+// frames padded to whole 128-byte operand rows of the tensor-core form
+inline int tensor_npad(int n_frames, int form) {
+    const int kb = form == PXST_FORM_TF32 ? 32 : 64;
+    return (n_frames + kb - 1) / kb * kb;
+}
+
+inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     WsLayout L;
+    const size_t P = (size_t)d.ny * d.nx, R = (size_t)d.ref_ny * d.ref_nx;
     size_t off = 0;
     L.header = off;     off += align256(sizeof(WsHeader));
     L.shifts = off;     off += align256(sizeof(FrameShift) * (size_t)d.n_frames);
-    L.exact_list = off; off += align256(sizeof(int) * (size_t)d.ny * d.nx);
-    L.num = off;        off += align256(sizeof(double) * (size_t)d.ref_ny * d.ref_nx);
-    L.den = off;        off += align256(sizeof(double) * (size_t)d.ref_ny * d.ref_nx);
+    L.exact_list = off; off += align256(sizeof(int) * P);
+    L.num = off;        off += align256(sizeof(double) * R);
+    L.den = off;        off += align256(sizeof(double) * R);
+    L.Npad = 0;
+    L.At = L.G = L.Tt = L.nvalid = L.cand = L.edge = off;
+    if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
+        const size_t es = form == PXST_FORM_TF32 ? 4 : 2;
+        L.Npad = tensor_npad(d.n_frames, form);
+        L.At = off;     off += align256(es * P * L.Npad);
+        L.G = off;      off += align256(es * R * L.Npad);
+        L.Tt = off;     off += align256(sizeof(float) * R);
+        L.nvalid = off; off += align256(sizeof(int) * R);
+        L.cand = off;   off += align256(sizeof(int) * 4 * P);
+        L.edge = off;   off += align256(P);
+    }
     L.total = off;
     return L;
 }
@@ -80,7 +103,16 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
+                          int mode, const int *cand, const uint8_t *sel, int sel_value,
                           cudaStream_t stream);
+// precision forms (tensor.cu)
+cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
+                         const uint8_t *mask, void *At, cudaStream_t stream);
+cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
+                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, cudaStream_t stream);
+cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *G,
+                           const uint8_t *mask, const double *u, const float *Tt, const int *nvalid,
+                           WsHeader *hdr, int *cand, uint8_t *edge, cudaStream_t stream);
 cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float *frames,
                          const float *W, const uint8_t *mask, const float *I_ref,
                          const float *w, const FrameShift *shifts, WsHeader *hdr,

@@ -1,14 +1,17 @@
 // tensor.cu -- tensor-core (tcgen05) precision forms of update_pixel_map on sm_103a.
 //
-// This file holds the diagnostic contraction used to check the tcgen05 machinery: one
-// CTA computes D[128][256] = A[128][K] . B[256][K]^T with both operands K-major in global
-// memory, loaded by TMA with 128-byte swizzle, the MMA accumulating in TMEM, and the
-// accumulator read back with tcgen05.ld.
+// Kernels: the operand preparation (k_tprep, k_gtable), the tensor-core ranking of every
+// candidate (k_tsearch) and a diagnostic contraction (k_tc_check) that checks the tcgen05
+// machinery: TMA loads with 128-byte swizzle into shared memory, tcgen05.mma accumulating
+// in TMEM, and tcgen05.ld read-back.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <cstdio>
 #include <mutex>
+
+#include <cuda_bf16.h>
+#include <climits>
 
 #include "pxst_common.cuh"
 #include "tc_ptx.cuh"
@@ -59,8 +62,9 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    volatile int *abortp = &abort_flag;
     if (tid == 0) {
-        abort_flag = 0;
+        *abortp = 0;
         tc::mbar_init(&bar_full, 1);
         tc::mbar_init(&bar_mma, 1);
         tc::fence_mbar_init();
@@ -78,13 +82,13 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
 
     const int nkb = (K + KB - 1) / KB;
     for (int kb = 0; kb < nkb; ++kb) {
-        if (tid == 0 && !abort_flag) {
+        if (tid == 0 && !*abortp) {
             const uint32_t ph = kb & 1;
             tc::mbar_expect_tx(&bar_full, (128 + 256) * 128);
             tc::tma_load_2d(As, &ta, &bar_full, kb * KB, 0);
             tc::tma_load_2d(Bs, &tb, &bar_full, kb * KB, 0);
-            if (!tc::mbar_wait(&bar_full, ph, &abort_flag)) {
-                abort_flag = 1;
+            if (!tc::mbar_wait(&bar_full, ph, abortp)) {
+                *abortp = 1;
             } else {
                 tc::tc_fence_after();
                 const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
@@ -93,14 +97,14 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
                     tc::mma<TF32>(tmem, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
                                   IDESC, (kb > 0 || k > 0) ? 1u : 0u);
                 tc::mma_commit(&bar_mma);
-                if (!tc::mbar_wait(&bar_mma, ph, &abort_flag)) abort_flag = 1;
+                if (!tc::mbar_wait(&bar_mma, ph, abortp)) *abortp = 1;
             }
         }
         __syncthreads();
-        if (abort_flag) break;
+        if (*abortp) break;
     }
     tc::tc_fence_after();
-    if (!abort_flag) {
+    if (!*abortp) {
         for (int c = 0; c < 256; c += 32) {
             float v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
@@ -116,7 +120,380 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// ==========================================================================================
+// Precision form of update_pixel_map.
+//
+// Centred operands: A~_n(x) = I_n(x)/W(x) - 1 and G~_n(c) = V_n(c) (R_n(c) - 1), so that for
+// a pixel whose candidates are all valid
+//     error(c) / var = 1 + (T~(c) - 2 C~(x, c)) / sum_n A~_n(x)^2,
+//     C~(x, c) = sum_n A~_n(x) G~_n(c),  T~(c) = sum_n G~_n(c)^2,
+// and the candidates of one pixel are ranked by q = T~(c) - 2 C~(x, c). C~ is a dense
+// contraction over frames for a tile of pixels against the union of their windows: it
+// runs on the tensor cores (BF16 or TF32 operands, FP32 accumulation in TMEM). The best
+// few candidates per pixel are then evaluated exactly in FP32 by the search kernel.
+// ==========================================================================================
+
+// A~ [ny][nx][Npad] (frames innermost, zero for masked pixels and padding frames):
+// a 32-frame x 32-pixel transpose through shared memory per block.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
+                                               const float *__restrict__ frames,
+                                               const float *__restrict__ W,
+                                               const uint8_t *__restrict__ mask, T *__restrict__ At) {
+    __shared__ float tile[32][33];
+    const size_t P = (size_t)ny * nx;
+    const size_t p0 = (size_t)blockIdx.x * 32;
+    const int n0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 8 rows of 32
+    for (int r = ty; r < 32; r += 8) {
+        const int n = n0 + r;
+        const size_t p = p0 + tx;
+        float v = 0.0f;
+        if (n < N && p < P && mask[p]) v = __ldg(frames + (size_t)n * P + p) / __ldg(W + p) - 1.0f;
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const size_t p = p0 + r;
+        const int n = n0 + tx;
+        if (p < P && n < Npad) At[p * Npad + n] = T(tile[tx][r]);
+    }
+}
+
+// G~ [Ry][Rx][Npad], T~ and n_valid per reference pixel; one warp per reference pixel.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
+                                                const float *__restrict__ Iref, const float *__restrict__ w,
+                                                const FrameShift *__restrict__ shifts, T *__restrict__ G,
+                                                float *__restrict__ Tt, int *__restrict__ nvalid) {
+    const int lane = threadIdx.x & 31;
+    const size_t R = (size_t)Ry * Rx;
+    for (size_t c = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; c < R;
+         c += ((size_t)gridDim.x * blockDim.x) >> 5) {
+        const int cy = (int)(c / Rx), cx = (int)(c % Rx);
+        float t = 0.0f;
+        int nv = 0;
+        for (int n = lane; n < Npad; n += 32) {
+            float g = 0.0f;
+            if (n < N) {
+                const FrameShift s = shifts[n];
+                float Rv;
+                if (gather_masked(Iref, w, Ry, Rx, cy + s.ky, cx + s.kx, s.fy, s.fx, Rv)) {
+                    const T gt = T(Rv - 1.0f);
+                    g = float(gt);
+                    t = fmaf(g, g, t);
+                    ++nv;
+                }
+            }
+            G[c * Npad + n] = T(g);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            t += __shfl_xor_sync(0xffffffffu, t, off);
+            nv += __shfl_xor_sync(0xffffffffu, nv, off);
+        }
+        if (lane == 0) {
+            Tt[c] = t;
+            nvalid[c] = nv;
+        }
+    }
+}
+
+constexpr int TS_TY = 8, TS_TX = 16;          // pixel tile: M = 128
+constexpr int TS_CR = 8, TS_CC = 32;          // candidate chunk: N = 256 (8 rows x 32 columns)
+constexpr int TS_STAGES = 4;
+constexpr int TS_THREADS = 192;               // producer, MMA, 4 epilogue warps
+constexpr int TS_A_BYTES = 128 * 128, TS_B_BYTES = 256 * 128;
+constexpr int TS_SMEM = TS_STAGES * (TS_A_BYTES + TS_B_BYTES) + 1024;
+
+struct TSearchArgs {
+    int N, Npad, ny, nx, Ry, Rx, Sy, Sx;
+    const uint8_t *mask;
+    const double *u;
+    const float *Tt;
+    const int *nvalid;
+    WsHeader *hdr;
+    int *cand;          // [P][4] window indices of the best candidates (-1: none)
+    uint8_t *edge;      // [P] 1: a candidate of the pixel reads an invalid reference pixel
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant__ CUtensorMap tA,
+                                                           const __grid_constant__ CUtensorMap tB,
+                                                           TSearchArgs a) {
+    constexpr int KB = TF32 ? 32 : 64;       // frames per 128-byte operand row
+    constexpr int KSTEP = TF32 ? 8 : 16;     // frames per MMA
+    constexpr uint32_t IDESC = tc::instr_desc(TF32 ? 2u : 1u, 128, 256);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bar_full[TS_STAGES], bar_empty[TS_STAGES], bar_tfull[2], bar_tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int s_box[4];
+    __shared__ int s_ci[128], s_cj[128], s_act[128];
+    __shared__ float s_T[256];
+    __shared__ int s_nv[256];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t P = (size_t)a.ny * a.nx;
+    const int x0 = blockIdx.x * TS_TX, y0 = blockIdx.y * TS_TY;
+    volatile int *abortp = &abort_flag;
+
+    if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
+    if (tid == 0) *abortp = 0;
+    __syncthreads();
+    if (tid < 128) {
+        const int x = x0 + (tid % TS_TX), y = y0 + (tid / TS_TX);
+        int act = 0, ci = 0, cj = 0;
+        if (x < a.nx && y < a.ny) {
+            const size_t pix = (size_t)y * a.nx + x;
+            const double u0 = a.u[pix], u1 = a.u[P + pix];
+            if (a.mask[pix] && isfinite(u0) && isfinite(u1) && fabs(u0) <= kMaxCoord && fabs(u1) <= kMaxCoord) {
+                ci = (int)floor(u0 + 0.5);
+                cj = (int)floor(u1 + 0.5);
+                act = 1;
+                atomicMin(&s_box[0], ci); atomicMax(&s_box[1], ci);
+                atomicMin(&s_box[2], cj); atomicMax(&s_box[3], cj);
+            }
+        }
+        s_act[tid] = act;
+        s_ci[tid] = ci;
+        s_cj[tid] = cj;
+    }
+    __syncthreads();
+    if (s_box[0] == INT_MAX) return;                  // nothing to do in this tile
+
+    const int ur0 = s_box[0] - a.Sy, uc0 = s_box[2] - a.Sx;
+    const int nrc = (s_box[1] - s_box[0] + 2 * a.Sy + TS_CR) / TS_CR;
+    const int ncc = (s_box[3] - s_box[2] + 2 * a.Sx + TS_CC) / TS_CC;
+    const int nchunks = nrc * ncc;
+    const int nkb = a.Npad / KB;
+
+    if (tid == 0) {
+        for (int i = 0; i < TS_STAGES; ++i) {
+            tc::mbar_init(&bar_full[i], 1);
+            tc::mbar_init(&bar_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&bar_tfull[i], 1);
+            tc::mbar_init(&bar_tempty[i], 4);
+        }
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&tA);
+        tc::prefetch_tmap(&tB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tmem_base, 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ---- TMA producer ---------------------------------------------------------------
+        if (lane == 0) {
+            int it = 0;
+            for (int j = 0; j < nchunks && !*abortp; ++j) {
+                const int row0 = ur0 + TS_CR * (j / ncc), col0 = uc0 + TS_CC * (j % ncc);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % TS_STAGES;
+                    if (!tc::mbar_wait(&bar_empty[s], ((it / TS_STAGES) & 1) ^ 1, abortp)) {
+                        *abortp = 1;
+                        break;
+                    }
+                    uint8_t *As = smem + s * (TS_A_BYTES + TS_B_BYTES);
+                    uint8_t *Bs = As + TS_A_BYTES;
+                    tc::mbar_expect_tx(&bar_full[s], TS_A_BYTES + TS_B_BYTES);
+                    tc::tma_load_3d(As, &tA, &bar_full[s], kb * KB, x0, y0);
+                    tc::tma_load_3d(Bs, &tB, &bar_full[s], kb * KB, col0, row0);
+                }
+            }
+            // let every copy this CTA issued land before the CTA can exit
+            for (int k = 0; k < TS_STAGES && k < it; ++k) {
+                const int i2 = it - 1 - k, s = i2 % TS_STAGES;
+                volatile int never = 0;
+                tc::mbar_wait(&bar_full[s], (i2 / TS_STAGES) & 1, &never);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer -------------------------------------------------------------------
+        if (lane == 0) {
+            int it = 0;
+            for (int j = 0; j < nchunks && !*abortp; ++j) {
+                const int buf = j & 1;
+                if (!tc::mbar_wait(&bar_tempty[buf], ((j >> 1) & 1) ^ 1, abortp)) {
+                    *abortp = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t d = tmem + buf * 256;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % TS_STAGES;
+                    if (!tc::mbar_wait(&bar_full[s], (it / TS_STAGES) & 1, abortp)) {
+                        *abortp = 1;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(smem + s * (TS_A_BYTES + TS_B_BYTES));
+                    const uint32_t b0 = a0 + TS_A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < KB / KSTEP; ++k)
+                        tc::mma<TF32>(d, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
+                                      IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                    tc::mma_commit(&bar_empty[s]);
+                }
+                if (*abortp) break;
+                tc::mma_commit(&bar_tfull[buf]);
+            }
+        }
+    } else {
+        // ---- epilogue: 4 warps, TMEM lane quarter = warp % 4 --------------------------------
+        const int q = warp & 3;
+        const int p = q * 32 + lane;                  // pixel of the tile = TMEM lane
+        const int et = tid - 64;                      // 0..127 among the epilogue threads
+        const bool act = s_act[p] != 0;
+        const int ci = s_ci[p], cj = s_cj[p];
+        const int wxn = 2 * a.Sx + 1;
+        float bq[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+        int bi[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+        bool edge = false;
+        for (int j = 0; j < nchunks; ++j) {
+            const int buf = j & 1;
+            const int row0 = ur0 + TS_CR * (j / ncc), col0 = uc0 + TS_CC * (j % ncc);
+            for (int k = et; k < 256; k += 128) {
+                const int gy = row0 + k / TS_CC, gx = col0 + k % TS_CC;
+                float t = 0.0f;
+                int nv = 0;
+                if (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) {
+                    t = a.Tt[(size_t)gy * a.Rx + gx];
+                    nv = a.nvalid[(size_t)gy * a.Rx + gx];
+                }
+                s_T[k] = t;
+                s_nv[k] = nv;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const bool ok = tc::mbar_wait(&bar_tfull[buf], (j >> 1) & 1, abortp);
+            if (!ok) *abortp = 1;
+            tc::tc_fence_after();
+            if (ok) {
+                for (int r = 0; r < TS_CR; ++r) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + buf * 256 + r * 32 + ((uint32_t)(q * 32) << 16), v);
+                    const int aa = row0 + r - ci;
+                    if (!act || aa < -a.Sy || aa > a.Sy) continue;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int b = col0 + i - cj;
+                        if (b < -a.Sx || b > a.Sx) continue;
+                        const int k = r * 32 + i;
+                        if (s_nv[k] != a.N) {
+                            edge = true;
+                            continue;
+                        }
+                        const float qv = s_T[k] - 2.0f * v[i];
+                        const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
+                        if (qv < bq[3] || (qv == bq[3] && idx < bi[3])) {
+                            int m = 3;
+                            while (m > 0 && (qv < bq[m - 1] || (qv == bq[m - 1] && idx < bi[m - 1]))) {
+                                bq[m] = bq[m - 1];
+                                bi[m] = bi[m - 1];
+                                --m;
+                            }
+                            bq[m] = qv;
+                            bi[m] = idx;
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (lane == 0) tc::mbar_arrive(&bar_tempty[buf]);
+            if (!ok) break;
+        }
+        if (act && !*abortp) {
+            const int x = x0 + (p % TS_TX), y = y0 + (p / TS_TX);
+            const size_t pix = (size_t)y * a.nx + x;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) a.cand[pix * 4 + m] = bi[m] == INT_MAX ? -1 : bi[m];
+            a.edge[pix] = edge ? 1 : 0;
+        }
+    }
+    if (tid == 0 && *abortp) atomicOr(&a.hdr->status, PXST_DEV_TIMEOUT);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
 }  // namespace
+
+// ---- host launchers for the precision form --------------------------------------------------
+
+cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
+                         const uint8_t *mask, void *At, cudaStream_t stream) {
+    const size_t P = (size_t)d.ny * d.nx;
+    dim3 grid((unsigned)((P + 31) / 32), (unsigned)((Npad + 31) / 32));
+    if (form == PXST_FORM_TF32)
+        k_tprep<float><<<grid, 256, 0, stream>>>(d.n_frames, Npad, d.ny, d.nx, frames, W, mask,
+                                                 static_cast<float *>(At));
+    else
+        k_tprep<__nv_bfloat16><<<grid, 256, 0, stream>>>(d.n_frames, Npad, d.ny, d.nx, frames, W, mask,
+                                                         static_cast<__nv_bfloat16 *>(At));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
+                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, cudaStream_t stream) {
+    const size_t R = (size_t)d.ref_ny * d.ref_nx;
+    size_t blocks = (R + 7) / 8;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (form == PXST_FORM_TF32)
+        k_gtable<float><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref, w,
+                                                               shifts, static_cast<float *>(G), Tt, nvalid);
+    else
+        k_gtable<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref,
+                                                                       w, shifts, static_cast<__nv_bfloat16 *>(G),
+                                                                       Tt, nvalid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *G,
+                           const uint8_t *mask, const double *u, const float *Tt, const int *nvalid,
+                           WsHeader *hdr, int *cand, uint8_t *edge, cudaStream_t stream) {
+    const bool tf32 = o.form == PXST_FORM_TF32;
+    const uint64_t es = tf32 ? 4 : 2;
+    const uint32_t kb = tf32 ? 32 : 64;
+    const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUtensorMap tA, tB;
+    const uint64_t dA[3] = {(uint64_t)Npad, (uint64_t)d.nx, (uint64_t)d.ny};
+    const uint64_t sA[2] = {(uint64_t)Npad * es, (uint64_t)Npad * es * d.nx};
+    const uint32_t bA[3] = {kb, TS_TX, TS_TY};
+    const uint64_t dB[3] = {(uint64_t)Npad, (uint64_t)d.ref_nx, (uint64_t)d.ref_ny};
+    const uint64_t sB[2] = {(uint64_t)Npad * es, (uint64_t)Npad * es * d.ref_nx};
+    const uint32_t bB[3] = {kb, TS_CC, TS_CR};
+    cudaError_t e = tmap_encode(&tA, dt, 3, const_cast<void *>(At), dA, sA, bA);
+    if (e != cudaSuccess) return e;
+    e = tmap_encode(&tB, dt, 3, const_cast<void *>(G), dB, sB, bB);
+    if (e != cudaSuccess) return e;
+    TSearchArgs a;
+    a.N = d.n_frames; a.Npad = Npad; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
+    a.Sy = o.win_y; a.Sx = o.win_x; a.mask = mask; a.u = u; a.Tt = Tt; a.nvalid = nvalid; a.hdr = hdr;
+    a.cand = cand; a.edge = edge;
+    dim3 grid((d.nx + TS_TX - 1) / TS_TX, (d.ny + TS_TY - 1) / TS_TY);
+    if (tf32) {
+        e = cudaFuncSetAttribute(k_tsearch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+        if (e == cudaSuccess) k_tsearch<true><<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
+    } else {
+        e = cudaFuncSetAttribute(k_tsearch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+        if (e == cudaSuccess) k_tsearch<false><<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 }  // namespace pxst
 
 using namespace pxst;

@@ -30,6 +30,10 @@ namespace {
 
 struct SearchArgs {
     int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ebuf, win_cap;
+    int mode;                 // 0: search every candidate; 1: evaluate the listed candidates
+    const int *cand;          // mode 1: [P][4] window indices (-1: none)
+    const uint8_t *sel;       // if set, only pixels with sel[pix] == sel_value are processed
+    int sel_value;
     const float *frames, *W;
     const uint8_t *mask;
     const float *Iref, *w;
@@ -367,7 +371,9 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         float Wv = 0.0f;
         if (x < a.nx && y < a.ny) {
             const size_t pix = (size_t)y * a.nx + x;
-            if (!a.mask[pix]) {
+            if (a.sel && a.sel[pix] != a.sel_value) {
+                // another pass owns this pixel
+            } else if (!a.mask[pix]) {
                 if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
             } else {
                 const double u0 = a.u[pix], u1 = a.u[P + pix];
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
 
     // ---- search: strips of the groups' window unions, 4 lanes per strip ----------------
     const int j = tid & (kSplit - 1);
-    const int units = s_goff[NG] * kSplit;
+    const int units = a.mode == 0 ? s_goff[NG] * kSplit : 0;
     for (int u0 = 0; u0 < units; u0 += NT) {
         const int t = u0 + tid;
         const bool valid = t < units;               // uniform over each strip's 4 lanes
@@ -604,6 +610,30 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         }
     }
     __syncthreads();
+
+    // ---- mode 1: the listed candidates of each pixel, evaluated exactly ------------------
+    if (a.mode == 1) {
+        for (int q = tid; q < TP * 4; q += NT) {
+            const int p = q >> 2;
+            if (!s_act[p]) continue;
+            const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
+            const int idx = a.cand[((size_t)y * a.nx + x) * 4 + (q & 3)];
+            if (idx < 0) continue;
+            const int na = idx / wxn, nb = idx % wxn;
+            const float *wn = win + (s_ci[p] + na - a.Sy - wy0) * WS + (s_cj[p] + nb - a.Sx - wx0);
+            float acc1[1];
+            eval_strip<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
+            const float var = s_var[p];
+            float ev = var > 0.0f ? acc1[0] / var : acc1[0];
+            if (isnan(ev)) {
+                eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                ev = acc1[0];
+                s_slow[p] = 1;
+            }
+            atomicMin(&s_key[p], pack_key(ev, idx));
+        }
+        __syncthreads();
+    }
 
     // ---- 3x3 about each pixel's minimum ---------------------------------------------------
     if (a.quadratic) {
@@ -841,6 +871,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
+                          int mode, const int *cand, const uint8_t *sel, int sel_value,
                           cudaStream_t stream) {
     Plan pl;
     const int wxn = 2 * o.win_x + 1;
@@ -862,7 +893,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     pl.TY = 1;
     pl.smem = 0;
     int best_ebuf = 0;
-    for (int ebuf = 1; ebuf >= 0; --ebuf)
+    for (int ebuf = mode == 0 ? 1 : 0; ebuf >= 0; --ebuf)
         for (int ty = 8; ty >= 1; ty >>= 1) {
             size_t st = 0;
             int cr = 1;
@@ -894,6 +925,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
     a.ebuf = best_ebuf; a.win_cap = pl.win_cap;
+    a.mode = mode; a.cand = cand; a.sel = sel; a.sel_value = sel_value;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.exact_list = exact_list; a.u = u; a.err_out = err_out;
     switch (pl.L) {

@@ -35,10 +35,10 @@ def gpu_make_object_map(frames, W, M, u, delta, ref_shape):
     return Iref.cpu().numpy(), w.cpu().numpy()
 
 
-def gpu_update(frames, W, M, Iref32, w32, delta, u, window, quadratic=True, return_exact=False):
+def gpu_update(frames, W, M, Iref32, w32, delta, u, window, quadratic=True, return_exact=False, form=0):
     t = torch()
     d = dims_of(frames, Iref32.shape)
-    o = px.Options(int(window[0]), int(window[1]), quadratic)
+    o = px.Options(int(window[0]), int(window[1]), quadratic, form)
     ud = dev(u, t.float64)
     err = t.full(M.shape, -7.0, dtype=t.float32, device="cuda")
     ws = px.workspace(d, o)
@@ -51,10 +51,10 @@ def gpu_update(frames, W, M, Iref32, w32, delta, u, window, quadratic=True, retu
     return out + (n_exact,) if return_exact else out
 
 
-def gpu_iterate(frames, W, M, delta, u, ref_shape, window, n_iter, quadratic=True):
+def gpu_iterate(frames, W, M, delta, u, ref_shape, window, n_iter, quadratic=True, form=0):
     t = torch()
     d = dims_of(frames, ref_shape)
-    o = px.Options(int(window[0]), int(window[1]), quadratic)
+    o = px.Options(int(window[0]), int(window[1]), quadratic, form)
     ud = dev(u, t.float64)
     Iref = t.empty(ref_shape, dtype=t.float32, device="cuda")
     w = t.empty(ref_shape, dtype=t.float32, device="cuda")
