@@ -70,8 +70,8 @@ typedef struct {
                               integers c = round(u) + (a, b), |a| <= S_y, |b| <= S_x */
     int32_t quadratic;     /* 1: 3x3 paraboloid sub-pixel refinement, 0: integer argmin */
     int32_t form;          /* PXST_FORM_* */
-    int32_t rescore_k;     /* tensor forms: candidates per pixel re-evaluated in FP32
-                              (0 = default = 4; only 4 is supported) */
+    int32_t rescore_k;     /* tensor forms: candidates per pixel re-evaluated in FP32:
+                              4 or 8 (0 = 8 below 128 frames, else 4) */
     int32_t reserved;
     int64_t timeout_ns;    /* reserved for device-side waits (0 = default) */
 } pxst_options;

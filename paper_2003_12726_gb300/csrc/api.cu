@@ -27,7 +27,7 @@ bool opts_ok(const pxst_options *o) {
     if ((long long)(2 * o->win_y + 1) * (2 * o->win_x + 1) >= (1LL << 30)) return false;
     if (o->quadratic != 0 && o->quadratic != 1) return false;
     if (o->form != PXST_FORM_FP32 && o->form != PXST_FORM_BF16 && o->form != PXST_FORM_TF32) return false;
-    if (o->rescore_k != 0 && o->rescore_k != 4) return false;     // the tensor forms keep 4
+    if (o->rescore_k != 0 && o->rescore_k != 4 && o->rescore_k != 8) return false;
     return true;
 }
 
@@ -197,7 +197,7 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
         if (o.form == PXST_FORM_FP32) {
             Timed t(PXST_K_SEARCH, s);
             PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr,
-                                   w.exact_list, u, err_out, sy, sx, 0, nullptr, nullptr, 0, s));
+                                   w.exact_list, u, err_out, sy, sx, 0, nullptr, 0, nullptr, 0, s));
         } else {
             // tensor-core ranking of every candidate, then exact FP32 evaluation of the best
             // four per pixel (and of every candidate of pixels touching invalid reference pixels)
@@ -214,14 +214,16 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
                 PXST_TRY(launch_tsearch(d, o, w.Npad, w.At, w.G, mask, u, w.Tt, w.nvalid, w.hdr, w.cand,
                                         w.edge, s));
             }
+            // few frames make the reduced-precision ranking noisier: rescore more of it
+            const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
             {
                 Timed t(PXST_K_RESCORE, s);
                 PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list, u,
-                                       err_out, sy, sx, 1, w.cand, w.edge, 0, s));
+                                       err_out, sy, sx, 1, w.cand, rk, w.edge, 0, s));
             }
             Timed t(PXST_K_SEARCH, s);
             PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list, u,
-                                   err_out, sy, sx, 0, nullptr, w.edge, 1, s));
+                                   err_out, sy, sx, 0, nullptr, 0, w.edge, 1, s));
         }
         Timed t(PXST_K_EXACT, s);
         PXST_TRY(launch_exact(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list,

@@ -64,7 +64,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
         L.G = off;      off += align256(es * R * L.Npad);
         L.Tt = off;     off += align256(sizeof(float) * R);
         L.nvalid = off; off += align256(sizeof(int) * R);
-        L.cand = off;   off += align256(sizeof(int) * 4 * P);
+        L.cand = off;   off += align256(sizeof(int) * kTopK * P);
         L.edge = off;   off += align256(P);
     }
     L.total = off;
@@ -86,6 +86,10 @@ __device__ __forceinline__ void split_neg_delta(double delta, int &k, float &f) 
 // |u| beyond this is rejected (status bit) so integer window arithmetic cannot overflow.
 constexpr double kMaxCoord = 1.0e8;
 
+// Candidates per pixel kept by the tensor-core ranking (the rescore evaluates the first
+// 4 or all 8 of them exactly).
+constexpr int kTopK = 8;
+
 // Launch-time configuration of the search kernel.
 constexpr int kSearchSmemBudget = 200 * 1024;   // dynamic shared memory per CTA (bytes)
 
@@ -103,7 +107,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
-                          int mode, const int *cand, const uint8_t *sel, int sel_value,
+                          int mode, const int *cand, int ncand, const uint8_t *sel, int sel_value,
                           cudaStream_t stream);
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,

@@ -213,7 +213,7 @@ struct TSearchArgs {
     const float *Tt;
     const int *nvalid;
     WsHeader *hdr;
-    int *cand;          // [P][4] window indices of the best candidates (-1: none)
+    int *cand;          // [P][8] window indices of the best candidates, best first (-1: none)
     uint8_t *edge;      // [P] 1: a candidate of the pixel reads an invalid reference pixel
 };
 
@@ -356,8 +356,13 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
         const bool act = s_act[p] != 0;
         const int ci = s_ci[p], cj = s_cj[p];
         const int wxn = 2 * a.Sx + 1;
-        float bq[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-        int bi[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+        float bq[kTopK];
+        int bi[kTopK];
+#pragma unroll
+        for (int m = 0; m < kTopK; ++m) {
+            bq[m] = INFINITY;
+            bi[m] = INT_MAX;
+        }
         bool edge = false;
         for (int j = 0; j < nchunks; ++j) {
             const int buf = j & 1;
@@ -394,8 +399,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                         }
                         const float qv = s_T[k] - 2.0f * v[i];
                         const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
-                        if (qv < bq[3] || (qv == bq[3] && idx < bi[3])) {
-                            int m = 3;
+                        if (qv < bq[kTopK - 1] || (qv == bq[kTopK - 1] && idx < bi[kTopK - 1])) {
+                            int m = kTopK - 1;
                             while (m > 0 && (qv < bq[m - 1] || (qv == bq[m - 1] && idx < bi[m - 1]))) {
                                 bq[m] = bq[m - 1];
                                 bi[m] = bi[m - 1];
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             const int x = x0 + (p % TS_TX), y = y0 + (p / TS_TX);
             const size_t pix = (size_t)y * a.nx + x;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) a.cand[pix * 4 + m] = bi[m] == INT_MAX ? -1 : bi[m];
+            for (int m = 0; m < kTopK; ++m) a.cand[pix * kTopK + m] = bi[m] == INT_MAX ? -1 : bi[m];
             a.edge[pix] = edge ? 1 : 0;
         }
     }

@@ -31,7 +31,8 @@ namespace {
 struct SearchArgs {
     int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ebuf, win_cap;
     int mode;                 // 0: search every candidate; 1: evaluate the listed candidates
-    const int *cand;          // mode 1: [P][4] window indices (-1: none)
+    const int *cand;          // mode 1: [P][kTopK] window indices (-1: none)
+    int ncand;                // mode 1: how many of them to evaluate (<= kTopK)
     const uint8_t *sel;       // if set, only pixels with sel[pix] == sel_value are processed
     int sel_value;
     const float *frames, *W;
@@ -613,11 +614,11 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
 
     // ---- mode 1: the listed candidates of each pixel, evaluated exactly ------------------
     if (a.mode == 1) {
-        for (int q = tid; q < TP * 4; q += NT) {
-            const int p = q >> 2;
+        for (int q = tid; q < TP * a.ncand; q += NT) {
+            const int p = q / a.ncand;
             if (!s_act[p]) continue;
             const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
-            const int idx = a.cand[((size_t)y * a.nx + x) * 4 + (q & 3)];
+            const int idx = a.cand[((size_t)y * a.nx + x) * kTopK + (q % a.ncand)];
             if (idx < 0) continue;
             const int na = idx / wxn, nb = idx % wxn;
             const float *wn = win + (s_ci[p] + na - a.Sy - wy0) * WS + (s_cj[p] + nb - a.Sx - wx0);
@@ -871,7 +872,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
-                          int mode, const int *cand, const uint8_t *sel, int sel_value,
+                          int mode, const int *cand, int ncand, const uint8_t *sel, int sel_value,
                           cudaStream_t stream) {
     Plan pl;
     const int wxn = 2 * o.win_x + 1;
@@ -925,7 +926,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
     a.ebuf = best_ebuf; a.win_cap = pl.win_cap;
-    a.mode = mode; a.cand = cand; a.sel = sel; a.sel_value = sel_value;
+    a.mode = mode; a.cand = cand; a.ncand = ncand; a.sel = sel; a.sel_value = sel_value;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.exact_list = exact_list; a.u = u; a.err_out = err_out;
     switch (pl.L) {
