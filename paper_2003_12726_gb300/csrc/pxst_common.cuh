@@ -29,6 +29,10 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 
+// Candidates per pixel kept by the tensor-core ranking (the rescore evaluates the first
+// 4 or all 8 of them exactly).
+constexpr int kTopK = 8;
+
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
     size_t header, shifts, exact_list, num, den;
@@ -85,10 +89,6 @@ __device__ __forceinline__ void split_neg_delta(double delta, int &k, float &f) 
 
 // |u| beyond this is rejected (status bit) so integer window arithmetic cannot overflow.
 constexpr double kMaxCoord = 1.0e8;
-
-// Candidates per pixel kept by the tensor-core ranking (the rescore evaluates the first
-// 4 or all 8 of them exactly).
-constexpr int kTopK = 8;
 
 // Launch-time configuration of the search kernel.
 constexpr int kSearchSmemBudget = 200 * 1024;   // dynamic shared memory per CTA (bytes)
