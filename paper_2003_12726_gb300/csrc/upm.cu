@@ -173,23 +173,32 @@ __device__ __forceinline__ void accum_strip_exact(const float *__restrict__ fr, 
         const float w10 = s.fy * (1.0f - s.fx), w11 = s.fy * s.fx;
 #pragma unroll
         for (int k = 0; k < L; ++k) {
-            float num = 0.0f, den = 0.0f;
             const float v00 = wp[k];
-            if (!isnan(v00)) { num = w00 * v00; den = w00; }
-            if (s.fx != 0.0f) {
-                const float v01 = wp[k + 1];
-                if (!isnan(v01)) { num = fmaf(w01, v01, num); den += w01; }
-            }
-            if (s.fy != 0.0f) {
-                const float v10 = wp[WS + k];
-                if (!isnan(v10)) { num = fmaf(w10, v10, num); den += w10; }
-                if (s.fx != 0.0f) {
-                    const float v11 = wp[WS + k + 1];
-                    if (!isnan(v11)) { num = fmaf(w11, v11, num); den += w11; }
+            const float v01 = s.fx != 0.0f ? wp[k + 1] : 0.0f;
+            const float v10 = s.fy != 0.0f ? wp[WS + k] : 0.0f;
+            const float v11 = (s.fx != 0.0f && s.fy != 0.0f) ? wp[WS + k + 1] : 0.0f;
+            float R;
+            bool valid;
+            if (!isnan(v00) && !isnan(v01) && !isnan(v10) && !isnan(v11)) {
+                // every corner counts: the read the fast path makes, bit for bit
+                if (s.fy == 0.0f) R = s.fx == 0.0f ? v00 : fmaf(s.fx, v01 - v00, v00);
+                else if (s.fx == 0.0f) R = fmaf(s.fy, v10 - v00, v00);
+                else {
+                    const float t0 = fmaf(s.fx, v01 - v00, v00), t1 = fmaf(s.fx, v11 - v10, v10);
+                    R = fmaf(s.fy, t1 - t0, t0);
                 }
+                valid = true;
+            } else {
+                float num = 0.0f, den = 0.0f;
+                if (!isnan(v00)) { num = w00 * v00; den = w00; }
+                if (s.fx != 0.0f && !isnan(v01)) { num = fmaf(w01, v01, num); den += w01; }
+                if (s.fy != 0.0f && !isnan(v10)) { num = fmaf(w10, v10, num); den += w10; }
+                if (s.fx != 0.0f && s.fy != 0.0f && !isnan(v11)) { num = fmaf(w11, v11, num); den += w11; }
+                valid = den > 0.0f;
+                R = valid ? num / den : 0.0f;
             }
-            if (den > 0.0f) {
-                const float d = fmaf(-Wv, num / den, I);
+            if (valid) {
+                const float d = fmaf(-Wv, R, I);
                 err[k] = fmaf(d, d, err[k]);
                 var[k] += t2;
                 nv[k] += 1.0f;
@@ -198,25 +207,41 @@ __device__ __forceinline__ void accum_strip_exact(const float *__restrict__ fr, 
     }
 }
 
+// e = err / var, with the pixel's own all-frame var (the fast path's value) wherever every
+// frame counted, so that a candidate gets the same value whichever path evaluated it.
 template <int L>
 __device__ __forceinline__ void finish_exact(const float (&err)[L], const float (&var)[L],
-                                             const float (&nv)[L], float (&e)[L]) {
+                                             const float (&nv)[L], int N, float var_all,
+                                             float (&e)[L]) {
 #pragma unroll
-    for (int k = 0; k < L; ++k)
-        e[k] = nv[k] == 0.0f ? INFINITY : (var[k] > 0.0f ? err[k] / var[k] : err[k]);
+    for (int k = 0; k < L; ++k) {
+        const float vk = nv[k] == (float)N ? var_all : var[k];
+        e[k] = nv[k] == 0.0f ? INFINITY : (vk > 0.0f ? err[k] / vk : err[k]);
+    }
 }
 
-// Whole-strip exact evaluation by one thread (over all frames).
+// Whole-strip exact evaluation by one thread, with the same frame partition (n mod 4) and
+// the same combination of the four partial sums as the strips evaluated by four lanes.
 template <int L>
 __device__ __noinline__ void eval_strip_exact(const float *__restrict__ fr, int pitch, int p,
                                               const FrameShift *__restrict__ sh, int N,
                                               const float *__restrict__ win, int WS, float Wv,
-                                              float (&e)[L]) {
-    float err[L], var[L], nv[L];
+                                              float var_all, float (&e)[L]) {
+    float err[4][L], var[4][L], nv[4][L];
 #pragma unroll
-    for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
-    accum_strip_exact<L>(fr, pitch, p, sh, 0, 1, N, win, WS, Wv, err, var, nv);
-    finish_exact<L>(err, var, nv, e);
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < L; ++k) err[j][k] = var[j][k] = nv[j][k] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accum_strip_exact<L>(fr, pitch, p, sh, j, 4, N, win, WS, Wv, err[j], var[j], nv[j]);
+    float E[L], V[L], C[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        E[k] = (err[0][k] + err[1][k]) + (err[2][k] + err[3][k]);
+        V[k] = (var[0][k] + var[1][k]) + (var[2][k] + var[3][k]);
+        C[k] = (nv[0][k] + nv[1][k]) + (nv[2][k] + nv[3][k]);
+    }
+    finish_exact<L>(E, V, C, N, var_all, e);
 }
 
 __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
@@ -525,7 +550,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
                 atomicOr(&s_xbits[bit >> 5], 1u << (bit & 31));
                 continue;
             }
-            eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], e);
+            eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], var, e);
         }
         float be = INFINITY;
         int bi = -1;
@@ -592,7 +617,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
                 if (!valid || j != 0) continue;
                 const int aa = r - s_ci[p], bofs = c - s_cj[p];
                 float e[L];
-                finish_exact<L>(err, var, nv, e);
+                finish_exact<L>(err, var, nv, a.N, s_var[p], e);
                 float be = INFINITY;
                 int bi = -1;
 #pragma unroll
@@ -627,7 +652,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
             const float var = s_var[p];
             float ev = var > 0.0f ? acc1[0] / var : acc1[0];
             if (isnan(ev)) {
-                eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], var, acc1);
                 ev = acc1[0];
                 s_slow[p] = 1;
             }
@@ -660,7 +685,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
                 const float var = s_var[p];
                 ev = var > 0.0f ? acc1[0] / var : acc1[0];
                 if (isnan(ev)) {
-                    eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
+                    eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], var, acc1);
                     ev = acc1[0];
                     s_slow[p] = 1;
                 }
