@@ -34,6 +34,7 @@ KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/
                   "paper_2003_12726_gb300/csrc/pxst_common.cuh"]
 
 
+FORMS = {"fp32": 0, "bf16": 1, "tf32": 2}
 WORKLOADS = {"lens1d": (gen.config_lens1d, 1), "small": (gen.config_small, 0),
              "precision2d": (gen.config_precision2d, 2)}
 
@@ -197,7 +198,8 @@ def pxst_arm(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     s = make_workload(args.workload, rank)
     ev_step = evals_per_step(s)
-    rec = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window)
+    form = FORMS[args.form]
+    rec = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, form=form)
     u0 = rec.u.clone()
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local_rank) if rank == 0 else None
@@ -270,7 +272,14 @@ def pxst_arm(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    if name in ("upm_search", "upm_exact"):
+    if name == "tensor_search":
+        flop = 2.0 * ev_step                                  # cross term: one multiply-add per evaluation
+        achieved = flop / (avg_ms * 1e-3) / 1e12
+        peak = float(pk["bf16_tflops"]) * (0.5 if form == 2 else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
+                "peak_basis": f"{basis} dense bf16 cuBLAS burst" + (" x 0.5 (nominal tf32/bf16 ratio)" if form == 2 else "")}
+    elif name in ("upm_search", "upm_exact"):
         flop = 4.0 * ev_step                                  # 2 FP32 FMA per evaluation
         achieved = flop / (avg_ms * 1e-3) / 1e12
         peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12            # FP32 lanes x FMA x clock
@@ -298,10 +307,10 @@ def pxst_arm(args, rank, world, local_rank):
                          f"update_pixel_map of the stripe, {sec:.1f} s"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form], "data": "synthetic",
             "config": {"workload": s.name, "frames": int(s.frames.shape[0]),
                        "detector": list(s.frames.shape[1:]), "window": list(s.window),
-                       "reference": list(s.ref_shape), "form": "fp32", "quadratic": True,
+                       "reference": list(s.ref_shape), "form": args.form, "quadratic": True,
                        "evals_per_step": ev_step, "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
             "roofline": roof, "cpu_baseline": cpu,
@@ -323,6 +332,8 @@ def main():
     ap.add_argument("--impl", default="pxst", choices=["pxst", "reference"])
     ap.add_argument("--workload", default="lens1d", choices=sorted(WORKLOADS),
                     help="lens1d (the benchmark workload) or a smaller/larger scan for profiling")
+    ap.add_argument("--form", default="fp32", choices=sorted(FORMS),
+                    help="arithmetic of the candidate search: fp32 (CUDA cores) or the tensor-core bf16/tf32")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")

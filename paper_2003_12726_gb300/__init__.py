@@ -280,11 +280,11 @@ class Reconstruction:
     and the error back, all on one stream.
     """
 
-    def __init__(self, frames, W, M, delta, u, ref_shape, window, quadratic=True, device="cuda"):
+    def __init__(self, frames, W, M, delta, u, ref_shape, window, quadratic=True, device="cuda", form=FORM_FP32):
         torch = _torch()
         self.dims = Dims(int(frames.shape[0]), int(frames.shape[1]), int(frames.shape[2]),
                          int(ref_shape[0]), int(ref_shape[1]))
-        self.opts = Options(int(window[0]), int(window[1]), bool(quadratic))
+        self.opts = Options(int(window[0]), int(window[1]), bool(quadratic), int(form))
         dev = torch.device(device)
         t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt).contiguous()
         self.frames = t(frames, torch.float32)

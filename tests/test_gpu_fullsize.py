@@ -24,19 +24,33 @@ def _sample(M, k, seed):
     return np.unique(np.concatenate([pick, edge[:: max(1, edge.size // 400)]]))
 
 
-@pytest.mark.parametrize("name,k", [("lens1d", 3000), ("precision2d", 600)])
-def test_full_size(name, k):
-    s = gen.CONFIGS[name]()
-    Ig, wg = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+_CACHE = {}
+
+
+def _scan(name):
+    if name not in _CACHE:
+        _CACHE.clear()
+        _CACHE[name] = gen.CONFIGS[name]()
+    return _CACHE[name]
+
+
+@pytest.mark.parametrize("name,k,form", [("lens1d", 3000, 0), ("precision2d", 600, 0), ("precision2d", 600, 1),
+                                         ("precision2d", 600, 2)], ids=["lens1d-fp32", "precision2d-fp32",
+                                                                        "precision2d-bf16", "precision2d-tf32"])
+def test_full_size(name, k, form):
+    s = _scan(name)
     Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
-    print(name, "make_object_map", parity.check_omap(Ig, wg, Io, wo))
+    if form == 0:
+        Ig, wg = gpu_make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+        print(name, "make_object_map", parity.check_omap(Ig, wg, Io, wo))
     I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
     inp = dict(frames=s.frames, W=s.W, M=s.M, Iref=I32.astype(np.float64), w=w32.astype(np.float64),
                delta=s.delta, u=s.u_init, window=s.window)
     ug_i, eg_i, n_exact = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window,
-                                     quadratic=False, return_exact=True)
-    ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True)
+                                     quadratic=False, return_exact=True, form=form)
+    ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True,
+                            form=form)
     pix = _sample(s.M, k, gen.BASE_SEED + 55)
     rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
                               ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
-    print(name, "update_pixel_map", rep, "exact-path pixels:", n_exact)
+    print(name, "form", form, "update_pixel_map", rep, "exact-rule pixels:", n_exact)
