@@ -36,14 +36,17 @@ KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/
 
 FORMS = {"fp32": 0, "bf16": 1, "tf32": 2}
 WORKLOADS = {"lens1d": (gen.config_lens1d, 1), "small": (gen.config_small, 0),
-             "precision2d": (gen.config_precision2d, 2)}
+             "precision2d": (gen.config_precision2d, 2), "precision2d-256": (gen.config_precision2d, 2)}
 
 
 def make_workload(name, rank):
     fn, idx = WORKLOADS[name]
+    seed = gen.BASE_SEED + idx + 1000 * rank
     if name == "small":
-        return gen.tiny2d(seed=gen.BASE_SEED + idx + 1000 * rank, name="2d-16x64x64-w4")
-    return fn(seed=gen.BASE_SEED + idx + 1000 * rank)
+        return gen.tiny2d(seed=seed, name="2d-16x64x64-w4")
+    if name == "precision2d-256":        # the 2-D precision scan on a 256 x 256 detector (profiling)
+        return fn(det=256, ref=400, seed=seed)
+    return fn(seed=seed)
 
 
 def evals_per_step(s):
