@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
 // few candidates per pixel are then evaluated exactly in FP32 by the search kernel.
 // ==========================================================================================
 
-// A~ [ny][nx][Npad] (frames innermost, zero for masked pixels and padding frames):
-// a 32-frame x 32-pixel transpose through shared memory per block.
+// A~ [Npad/KB][ny][nx][KB] (frame blocks of one 128-byte operand row, zero for masked
+// pixels and padding frames): a 32-frame x 32-pixel transpose through shared memory.
+// The frame-block-major layout makes each TMA box a few contiguous runs of pixels.
 template <typename T>
 __global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
                                                const float *__restrict__ frames,
@@ -153,19 +154,21 @@ __global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
         tile[r][tx] = v;
     }
     __syncthreads();
+    constexpr int KB = 128 / sizeof(T);
     for (int r = ty; r < 32; r += 8) {
         const size_t p = p0 + r;
         const int n = n0 + tx;
-        if (p < P && n < Npad) At[p * Npad + n] = T(tile[tx][r]);
+        if (p < P && n < Npad) At[((size_t)(n / KB) * P + p) * KB + (n % KB)] = T(tile[tx][r]);
     }
 }
 
-// G~ [Ry][Rx][Npad], T~ and n_valid per reference pixel; one warp per reference pixel.
+// G~ [Npad/KB][Ry][Rx][KB], T~ and n_valid per reference pixel; one warp per reference pixel.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                                                 const float *__restrict__ Iref, const float *__restrict__ w,
                                                 const FrameShift *__restrict__ shifts, T *__restrict__ G,
                                                 float *__restrict__ Tt, int *__restrict__ nvalid) {
+    constexpr int KB = 128 / sizeof(T);
     const int lane = threadIdx.x & 31;
     const size_t R = (size_t)Ry * Rx;
     for (size_t c = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; c < R;
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                     ++nv;
                 }
             }
-            G[c * Npad + n] = T(g);
+            G[((size_t)(n / KB) * R + c) * KB + (n % KB)] = T(g);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -306,8 +309,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                     uint8_t *As = smem + s * (TS_A_BYTES + TS_B_BYTES);
                     uint8_t *Bs = As + TS_A_BYTES;
                     tc::mbar_expect_tx(&bar_full[s], TS_A_BYTES + TS_B_BYTES);
-                    tc::tma_load_3d(As, &tA, &bar_full[s], kb * KB, x0, y0);
-                    tc::tma_load_3d(Bs, &tB, &bar_full[s], kb * KB, col0, row0);
+                    tc::tma_load_4d(As, &tA, &bar_full[s], 0, x0, y0, kb);
+                    tc::tma_load_4d(Bs, &tB, &bar_full[s], 0, col0, row0, kb);
                 }
             }
             // let every copy this CTA issued land before the CTA can exit
@@ -474,15 +477,16 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     const uint32_t kb = tf32 ? 32 : 64;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap tA, tB;
-    const uint64_t dA[3] = {(uint64_t)Npad, (uint64_t)d.nx, (uint64_t)d.ny};
-    const uint64_t sA[2] = {(uint64_t)Npad * es, (uint64_t)Npad * es * d.nx};
-    const uint32_t bA[3] = {kb, TS_TX, TS_TY};
-    const uint64_t dB[3] = {(uint64_t)Npad, (uint64_t)d.ref_nx, (uint64_t)d.ref_ny};
-    const uint64_t sB[2] = {(uint64_t)Npad * es, (uint64_t)Npad * es * d.ref_nx};
-    const uint32_t bB[3] = {kb, TS_CC, TS_CR};
-    cudaError_t e = tmap_encode(&tA, dt, 3, const_cast<void *>(At), dA, sA, bA);
+    const uint64_t nkb = (uint64_t)Npad / kb, row = (uint64_t)kb * es;     // 128-byte rows
+    const uint64_t dA[4] = {kb, (uint64_t)d.nx, (uint64_t)d.ny, nkb};
+    const uint64_t sA[3] = {row, row * d.nx, row * d.nx * d.ny};
+    const uint32_t bA[4] = {kb, TS_TX, TS_TY, 1};
+    const uint64_t dB[4] = {kb, (uint64_t)d.ref_nx, (uint64_t)d.ref_ny, nkb};
+    const uint64_t sB[3] = {row, row * d.ref_nx, row * d.ref_nx * d.ref_ny};
+    const uint32_t bB[4] = {kb, TS_CC, TS_CR, 1};
+    cudaError_t e = tmap_encode(&tA, dt, 4, const_cast<void *>(At), dA, sA, bA);
     if (e != cudaSuccess) return e;
-    e = tmap_encode(&tB, dt, 3, const_cast<void *>(G), dB, sB, bB);
+    e = tmap_encode(&tB, dt, 4, const_cast<void *>(G), dB, sB, bB);
     if (e != cudaSuccess) return e;
     TSearchArgs a;
     a.N = d.n_frames; a.Npad = Npad; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
