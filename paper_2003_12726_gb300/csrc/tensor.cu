@@ -390,27 +390,32 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                     float v[32];
                     tc::tmem_ld32(tmem + buf * 256 + r * 32 + ((uint32_t)(q * 32) << 16), v);
                     const int aa = row0 + r - ci;
-                    if (!act || aa < -a.Sy || aa > a.Sy) continue;
+                    // this pixel's window columns within the chunk row: i in [ilo, ihi]
+                    const int ilo = max(0, cj - a.Sx - col0), ihi = min(31, cj + a.Sx - col0);
+                    if (!act || aa < -a.Sy || aa > a.Sy || ilo > ihi) continue;
+                    const int rowbase = (aa + a.Sy) * wxn + (col0 - cj + a.Sx);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        const int b = col0 + i - cj;
-                        if (b < -a.Sx || b > a.Sx) continue;
                         const int k = r * 32 + i;
-                        if (s_nv[k] != a.N) {
-                            edge = true;
-                            continue;
-                        }
+                        const bool in = i >= ilo && i <= ihi;
+                        const bool inval = in && s_nv[k] != a.N;
+                        edge = edge || inval;
                         const float qv = s_T[k] - 2.0f * v[i];
-                        const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
-                        if (qv < bq[kTopK - 1] || (qv == bq[kTopK - 1] && idx < bi[kTopK - 1])) {
-                            int m = kTopK - 1;
-                            while (m > 0 && (qv < bq[m - 1] || (qv == bq[m - 1] && idx < bi[m - 1]))) {
-                                bq[m] = bq[m - 1];
-                                bi[m] = bi[m - 1];
-                                --m;
+                        const int idx = rowbase + i;
+                        if (in && !inval && (qv < bq[kTopK - 1] || (qv == bq[kTopK - 1] && idx < bi[kTopK - 1]))) {
+                            // insert into the sorted best list (registers only)
+                            float cq = qv;
+                            int cx = idx;
+#pragma unroll
+                            for (int m = 0; m < kTopK; ++m) {
+                                const bool lt = cq < bq[m] || (cq == bq[m] && cx < bi[m]);
+                                const float tq = lt ? bq[m] : cq;
+                                const int tx = lt ? bi[m] : cx;
+                                bq[m] = lt ? cq : bq[m];
+                                bi[m] = lt ? cx : bi[m];
+                                cq = tq;
+                                cx = tx;
                             }
-                            bq[m] = qv;
-                            bi[m] = idx;
                         }
                     }
                 }
