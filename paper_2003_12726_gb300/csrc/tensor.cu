@@ -205,9 +205,11 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
 constexpr int TS_TY = 8, TS_TX = 16;          // pixel tile: M = 128
 constexpr int TS_CR = 8, TS_CC = 32;          // candidate chunk: N = 256 (8 rows x 32 columns)
 constexpr int TS_STAGES = 4;
-constexpr int TS_THREADS = 192;               // producer, MMA, 4 epilogue warps
+constexpr int TS_EPI_WARPS = 8;               // two per TMEM lane quarter, splitting the chunk rows
+constexpr int TS_THREADS = 64 + 32 * TS_EPI_WARPS;   // producer, MMA, epilogue warps
 constexpr int TS_A_BYTES = 128 * 128, TS_B_BYTES = 256 * 128;
 constexpr int TS_SMEM = TS_STAGES * (TS_A_BYTES + TS_B_BYTES) + 1024;
+constexpr int TS_MAX_ORDER = 64;              // chunk rows / columns visited centre-first
 
 struct TSearchArgs {
     int N, Npad, ny, nx, Ry, Rx, Sy, Sx;
@@ -216,11 +218,62 @@ struct TSearchArgs {
     const float *Tt;
     const int *nvalid;
     WsHeader *hdr;
-    int *cand;          // [P][8] window indices of the best candidates, best first (-1: none)
+    int *cand;          // [P][kTopK] window indices of the best candidates, best first (-1: none)
     uint8_t *edge;      // [P] 1: a candidate of the pixel reads an invalid reference pixel
 };
 
-template <bool TF32>
+// Insert (qv, idx) into the ascending list bq/bi when it beats an entry (strict <, so of
+// equal keys the one seen first stays ahead). Every position is decided from the old list
+// in parallel, so the update is three dependent steps deep whatever the list length.
+template <int TK>
+__device__ __forceinline__ void topk_insert(float (&bq)[TK], int (&bi)[TK], float qv, int idx) {
+    bool lt[TK];
+#pragma unroll
+    for (int m = 0; m < TK; ++m) lt[m] = qv < bq[m];
+#pragma unroll
+    for (int m = TK - 1; m > 0; --m) {
+        bq[m] = lt[m] ? (lt[m - 1] ? bq[m - 1] : qv) : bq[m];
+        bi[m] = lt[m] ? (lt[m - 1] ? bi[m - 1] : idx) : bi[m];
+    }
+    bq[0] = lt[0] ? qv : bq[0];
+    bi[0] = lt[0] ? idx : bi[0];
+}
+
+// One chunk row of 32 candidates for the warp's 32 pixels: q = T~ - 2 C~, where sT holds
+// T~ (+inf for a candidate that is not valid in every frame). Lanes whose window does not
+// hold column i (bit i of inmask clear) skip it; the insertion runs only when some lane of
+// the warp improves its list.
+template <int TK, bool FULL>
+__device__ __forceinline__ void scan_row(const float (&v)[32], const float *__restrict__ sT, uint32_t inmask,
+                                         int rowbase, float (&bq)[TK], int (&bi)[TK]) {
+#pragma unroll
+    for (int i4 = 0; i4 < 32; i4 += 4) {
+        const float4 t4 = *reinterpret_cast<const float4 *>(sT + i4);
+        const float tt[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = i4 + e;
+            float qv = fmaf(-2.0f, v[i], tt[e]);
+            if (!FULL) qv = ((inmask >> i) & 1u) ? qv : INFINITY;
+            if (__any_sync(0xffffffffu, qv < bq[TK - 1])) topk_insert<TK>(bq, bi, qv, rowbase + i);
+        }
+    }
+}
+
+// Visit order of n chunk rows (or columns): the one holding the tile's centre first, then
+// alternately outwards, so that the best candidates are met early and later chunks rarely
+// change a pixel's list.
+__device__ inline void centre_first(int *ord, int n, int c) {
+    c = min(max(c, 0), n - 1);
+    int k = 0;
+    ord[k++] = c;
+    for (int d = 1; k < n; ++d) {
+        if (c + d < n) ord[k++] = c + d;
+        if (c - d >= 0 && k < n) ord[k++] = c - d;
+    }
+}
+
+template <bool TF32, int TK>
 __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant__ CUtensorMap tA,
                                                            const __grid_constant__ CUtensorMap tB,
                                                            TSearchArgs a) {
@@ -234,8 +287,12 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     __shared__ int abort_flag;
     __shared__ int s_box[4];
     __shared__ int s_ci[128], s_cj[128], s_act[128];
-    __shared__ float s_T[256];
-    __shared__ int s_nv[256];
+    __shared__ int s_rord[TS_MAX_ORDER], s_cord[TS_MAX_ORDER];
+    __shared__ __align__(16) float s_T[2][TS_CR * TS_CC];
+    __shared__ uint32_t s_vm[2][TS_CR];
+    __shared__ float s_mq[128][TK];
+    __shared__ int s_mi[128][TK];
+    __shared__ uint8_t s_medge[128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t P = (size_t)a.ny * a.nx;
@@ -271,6 +328,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     const int ncc = (s_box[3] - s_box[2] + 2 * a.Sx + TS_CC) / TS_CC;
     const int nchunks = nrc * ncc;
     const int nkb = a.Npad / KB;
+    const bool ordered = nrc <= TS_MAX_ORDER && ncc <= TS_MAX_ORDER;
 
     if (tid == 0) {
         for (int i = 0; i < TS_STAGES; ++i) {
@@ -279,11 +337,15 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&bar_tfull[i], 1);
-            tc::mbar_init(&bar_tempty[i], 4);
+            tc::mbar_init(&bar_tempty[i], TS_EPI_WARPS);
         }
         tc::fence_mbar_init();
         tc::prefetch_tmap(&tA);
         tc::prefetch_tmap(&tB);
+        if (ordered) {
+            centre_first(s_rord, nrc, ((s_box[0] + s_box[1]) / 2 - ur0) / TS_CR);
+            centre_first(s_cord, ncc, ((s_box[2] + s_box[3]) / 2 - uc0) / TS_CC);
+        }
     }
     if (warp == 1) {
         tc::tmem_alloc(&tmem_base, 512);
@@ -293,13 +355,20 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
+    // origin (reference row, column) of the j-th chunk visited
+    auto chunk_origin = [&](int j, int &row0, int &col0) {
+        const int jr = j / ncc, jc = j % ncc;
+        row0 = ur0 + TS_CR * (ordered ? s_rord[jr] : jr);
+        col0 = uc0 + TS_CC * (ordered ? s_cord[jc] : jc);
+    };
 
     if (warp == 0) {
         // ---- TMA producer ---------------------------------------------------------------
         if (lane == 0) {
             int it = 0;
             for (int j = 0; j < nchunks && !*abortp; ++j) {
-                const int row0 = ur0 + TS_CR * (j / ncc), col0 = uc0 + TS_CC * (j % ncc);
+                int row0, col0;
+                chunk_origin(j, row0, col0);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % TS_STAGES;
                     if (!tc::mbar_wait(&bar_empty[s], ((it / TS_STAGES) & 1) ^ 1, abortp)) {
@@ -352,85 +421,105 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             }
         }
     } else {
-        // ---- epilogue: 4 warps, TMEM lane quarter = warp % 4 --------------------------------
-        const int q = warp & 3;
+        // ---- epilogue: 8 warps; TMEM lane quarter q = warp % 4, chunk rows h, h + 2, ... ----
+        const int ew = warp - 2;                      // 0..7: also the chunk row this warp stages
+        const int q = warp & 3, h = ew >> 2;
         const int p = q * 32 + lane;                  // pixel of the tile = TMEM lane
-        const int et = tid - 64;                      // 0..127 among the epilogue threads
         const bool act = s_act[p] != 0;
         const int ci = s_ci[p], cj = s_cj[p];
         const int wxn = 2 * a.Sx + 1;
-        float bq[kTopK];
-        int bi[kTopK];
+        float bq[TK];
+        int bi[TK];
 #pragma unroll
-        for (int m = 0; m < kTopK; ++m) {
+        for (int m = 0; m < TK; ++m) {
             bq[m] = INFINITY;
-            bi[m] = INT_MAX;
+            bi[m] = -1;
         }
         bool edge = false;
+        // T~ and validity of chunk row `ew` of chunk j (+inf / clear bit: not valid in every frame)
+        auto fetch = [&](int j, float &t, bool &ok) {
+            int row0, col0;
+            chunk_origin(j, row0, col0);
+            const int gy = row0 + ew, gx = col0 + lane;
+            t = INFINITY;
+            ok = false;
+            if (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) {
+                const size_t c = (size_t)gy * a.Rx + gx;
+                ok = __ldg(a.nvalid + c) == a.N;
+                if (ok) t = __ldg(a.Tt + c);
+            }
+        };
+        {
+            float t;
+            bool ok;
+            fetch(0, t, ok);
+            s_T[0][ew * TS_CC + lane] = t;
+            const uint32_t vm = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) s_vm[0][ew] = vm;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
         for (int j = 0; j < nchunks; ++j) {
             const int buf = j & 1;
-            const int row0 = ur0 + TS_CR * (j / ncc), col0 = uc0 + TS_CC * (j % ncc);
-            for (int k = et; k < 256; k += 128) {
-                const int gy = row0 + k / TS_CC, gx = col0 + k % TS_CC;
-                float t = 0.0f;
-                int nv = 0;
-                if (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) {
-                    t = a.Tt[(size_t)gy * a.Rx + gx];
-                    nv = a.nvalid[(size_t)gy * a.Rx + gx];
-                }
-                s_T[k] = t;
-                s_nv[k] = nv;
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const bool ok = tc::mbar_wait(&bar_tfull[buf], (j >> 1) & 1, abortp);
+            int row0, col0;
+            chunk_origin(j, row0, col0);
+            float tn = INFINITY;
+            bool okn = false;
+            if (j + 1 < nchunks) fetch(j + 1, tn, okn);
+            // a wait that ran out stops every epilogue warp after the same barrier below
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], (j >> 1) & 1, abortp));
             if (!ok) *abortp = 1;
             tc::tc_fence_after();
             if (ok) {
-                for (int r = 0; r < TS_CR; ++r) {
+                // this pixel's window columns within a chunk row: [ilo, ihi]
+                const int ilo = max(0, cj - a.Sx - col0), ihi = min(TS_CC - 1, cj + a.Sx - col0);
+                const uint32_t colmask =
+                    ilo > ihi ? 0u : ((ihi == 31 ? 0xffffffffu : ((1u << (ihi + 1)) - 1u)) & ~((1u << ilo) - 1u));
+#pragma unroll 1
+                for (int r = h; r < TS_CR; r += 2) {
+                    const int aa = row0 + r - ci;
+                    const uint32_t inmask = (act && aa >= -a.Sy && aa <= a.Sy) ? colmask : 0u;
+                    if (__all_sync(0xffffffffu, inmask == 0u)) continue;
                     float v[32];
                     tc::tmem_ld32(tmem + buf * 256 + r * 32 + ((uint32_t)(q * 32) << 16), v);
-                    const int aa = row0 + r - ci;
-                    // this pixel's window columns within the chunk row: i in [ilo, ihi]
-                    const int ilo = max(0, cj - a.Sx - col0), ihi = min(31, cj + a.Sx - col0);
-                    if (!act || aa < -a.Sy || aa > a.Sy || ilo > ihi) continue;
+                    const uint32_t vm = s_vm[buf][r];
+                    edge = edge || (inmask & ~vm) != 0u;
+                    const uint32_t use = inmask & vm;
                     const int rowbase = (aa + a.Sy) * wxn + (col0 - cj + a.Sx);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int k = r * 32 + i;
-                        const bool in = i >= ilo && i <= ihi;
-                        const bool inval = in && s_nv[k] != a.N;
-                        edge = edge || inval;
-                        const float qv = s_T[k] - 2.0f * v[i];
-                        const int idx = rowbase + i;
-                        if (in && !inval && (qv < bq[kTopK - 1] || (qv == bq[kTopK - 1] && idx < bi[kTopK - 1]))) {
-                            // insert into the sorted best list (registers only)
-                            float cq = qv;
-                            int cx = idx;
-#pragma unroll
-                            for (int m = 0; m < kTopK; ++m) {
-                                const bool lt = cq < bq[m] || (cq == bq[m] && cx < bi[m]);
-                                const float tq = lt ? bq[m] : cq;
-                                const int tx = lt ? bi[m] : cx;
-                                bq[m] = lt ? cq : bq[m];
-                                bi[m] = lt ? cx : bi[m];
-                                cq = tq;
-                                cx = tx;
-                            }
-                        }
-                    }
+                    if (__all_sync(0xffffffffu, use == 0xffffffffu))
+                        scan_row<TK, true>(v, &s_T[buf][r * TS_CC], use, rowbase, bq, bi);
+                    else
+                        scan_row<TK, false>(v, &s_T[buf][r * TS_CC], use, rowbase, bq, bi);
                 }
             }
             tc::tc_fence_before();
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (j + 1 < nchunks) {
+                s_T[buf ^ 1][ew * TS_CC + lane] = tn;
+                const uint32_t vm = __ballot_sync(0xffffffffu, okn);
+                if (lane == 0) s_vm[buf ^ 1][ew] = vm;
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
             if (lane == 0) tc::mbar_arrive(&bar_tempty[buf]);
-            if (!ok) break;
+            if (*abortp) break;
         }
-        if (act && !*abortp) {
+        // merge the two lists of each pixel (rows of the two halves), write the result
+        if (h == 1) {
+#pragma unroll
+            for (int m = 0; m < TK; ++m) {
+                s_mq[p][m] = bq[m];
+                s_mi[p][m] = bi[m];
+            }
+            s_medge[p] = edge ? 1 : 0;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
+        if (h == 0 && act && !*abortp) {
+#pragma unroll
+            for (int m = 0; m < TK; ++m)
+                if (s_mq[p][m] < bq[TK - 1]) topk_insert<TK>(bq, bi, s_mq[p][m], s_mi[p][m]);
             const int x = x0 + (p % TS_TX), y = y0 + (p / TS_TX);
             const size_t pix = (size_t)y * a.nx + x;
 #pragma unroll
-            for (int m = 0; m < kTopK; ++m) a.cand[pix * kTopK + m] = bi[m] == INT_MAX ? -1 : bi[m];
-            a.edge[pix] = edge ? 1 : 0;
+            for (int m = 0; m < kTopK; ++m) a.cand[pix * kTopK + m] = m < TK ? bi[m] : -1;
+            a.edge[pix] = (edge || s_medge[p]) ? 1 : 0;
         }
     }
     if (tid == 0 && *abortp) atomicOr(&a.hdr->status, PXST_DEV_TIMEOUT);
@@ -498,13 +587,17 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     a.Sy = o.win_y; a.Sx = o.win_x; a.mask = mask; a.u = u; a.Tt = Tt; a.nvalid = nvalid; a.hdr = hdr;
     a.cand = cand; a.edge = edge;
     dim3 grid((d.nx + TS_TX - 1) / TS_TX, (d.ny + TS_TY - 1) / TS_TY);
-    if (tf32) {
-        e = cudaFuncSetAttribute(k_tsearch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
-        if (e == cudaSuccess) k_tsearch<true><<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
-    } else {
-        e = cudaFuncSetAttribute(k_tsearch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
-        if (e == cudaSuccess) k_tsearch<false><<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
-    }
+    // list length: the candidates the rescore reads (4 unless more are asked for)
+    const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
+    auto go = [&](auto kern) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+        if (r == cudaSuccess) kern<<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
+        return r;
+    };
+    if (tf32)
+        e = rk <= 4 ? go(k_tsearch<true, 4>) : go(k_tsearch<true, 8>);
+    else
+        e = rk <= 4 ? go(k_tsearch<false, 4>) : go(k_tsearch<false, 8>);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
