@@ -36,7 +36,8 @@ KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/
 
 FORMS = {"fp32": 0, "bf16": 1, "tf32": 2}
 WORKLOADS = {"lens1d": (gen.config_lens1d, 1), "small": (gen.config_small, 0),
-             "precision2d": (gen.config_precision2d, 2), "precision2d-256": (gen.config_precision2d, 2)}
+             "precision2d": (gen.config_precision2d, 2), "precision2d-256": (gen.config_precision2d, 2),
+             "precision2d-512": (gen.config_precision2d, 2)}
 
 
 def make_workload(name, rank):
@@ -46,6 +47,8 @@ def make_workload(name, rank):
         return gen.tiny2d(seed=seed, name="2d-16x64x64-w4")
     if name == "precision2d-256":        # the 2-D precision scan on a 256 x 256 detector (profiling)
         return fn(det=256, ref=400, seed=seed)
+    if name == "precision2d-512":        # 512 x 512: frames (420 MB) still larger than L2 (profiling)
+        return fn(det=512, ref=680, seed=seed)
     return fn(seed=seed)
 
 

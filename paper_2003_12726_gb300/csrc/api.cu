@@ -37,9 +37,10 @@ struct Ws {
     int *exact_list;
     double *num, *den;
     void *At, *G;
-    float *Tt;
+    float *Tt, *Rm;
     int *nvalid, *cand;
     uint8_t *edge;
+    unsigned long long *keys;
     int Npad;
 };
 
@@ -58,8 +59,10 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     w.G = b + L.G;
     w.Tt = reinterpret_cast<float *>(b + L.Tt);
     w.nvalid = reinterpret_cast<int *>(b + L.nvalid);
+    w.Rm = reinterpret_cast<float *>(b + L.Rm);
     w.cand = reinterpret_cast<int *>(b + L.cand);
     w.edge = reinterpret_cast<uint8_t *>(b + L.edge);
+    w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);
     w.Npad = L.Npad;
     return PXST_OK;
 }
@@ -191,39 +194,35 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
                        const double *delta, double *u, float *err_out, Ws &w, cudaStream_t s,
                        bool operands_ready = false) {
     PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, 2 * sizeof(int), s));   // n_exact, n_exact_cta
-    if (d.n_frames <= search_max_frames()) {
+    if (o.form != PXST_FORM_FP32) {
+        // tensor-core ranking of every candidate that is valid in every frame, then exact
+        // FP32 errors of the best few per pixel, of every candidate that is not, and of the
+        // 3x3 about the minimum
+        if (!operands_ready) {
+            Timed t(PXST_K_TPREP, s);
+            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, s));
+        }
+        {
+            Timed t(PXST_K_GTABLE, s);
+            PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.G, w.Tt, w.nvalid, w.Rm, s));
+        }
+        {
+            Timed t(PXST_K_TSEARCH, s);
+            PXST_TRY(launch_tsearch(d, o, w.Npad, w.At, w.G, mask, u, w.Tt, w.nvalid, w.hdr, w.cand,
+                                    w.edge, w.exact_list, s));
+        }
+        // few frames make the reduced-precision ranking noisier: rescore more of it
+        const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
+        Timed t(PXST_K_RESCORE, s);
+        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.nvalid, w.shifts, w.cand, w.edge,
+                                w.exact_list, w.keys, w.hdr, u, err_out, s));
+    } else if (d.n_frames <= search_max_frames()) {
         int sy, sx;
         shift_span(d, delta, s, sy, sx);
-        if (o.form == PXST_FORM_FP32) {
+        {
             Timed t(PXST_K_SEARCH, s);
             PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr,
-                                   w.exact_list, u, err_out, sy, sx, 0, nullptr, 0, nullptr, 0, s));
-        } else {
-            // tensor-core ranking of every candidate, then exact FP32 evaluation of the best
-            // four per pixel (and of every candidate of pixels touching invalid reference pixels)
-            if (!operands_ready) {
-                Timed t(PXST_K_TPREP, s);
-                PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, s));
-            }
-            {
-                Timed t(PXST_K_GTABLE, s);
-                PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.G, w.Tt, w.nvalid, s));
-            }
-            {
-                Timed t(PXST_K_TSEARCH, s);
-                PXST_TRY(launch_tsearch(d, o, w.Npad, w.At, w.G, mask, u, w.Tt, w.nvalid, w.hdr, w.cand,
-                                        w.edge, s));
-            }
-            // few frames make the reduced-precision ranking noisier: rescore more of it
-            const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
-            {
-                Timed t(PXST_K_RESCORE, s);
-                PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list, u,
-                                       err_out, sy, sx, 1, w.cand, rk, w.edge, 0, s));
-            }
-            Timed t(PXST_K_SEARCH, s);
-            PXST_TRY(launch_search(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list, u,
-                                   err_out, sy, sx, 0, nullptr, 0, w.edge, 1, s));
+                                   w.exact_list, u, err_out, sy, sx, s));
         }
         Timed t(PXST_K_EXACT, s);
         PXST_TRY(launch_exact(d, o, frames, W, mask, I_ref, wref, w.shifts, w.hdr, w.exact_list,

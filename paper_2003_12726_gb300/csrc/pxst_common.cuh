@@ -37,7 +37,7 @@ constexpr int kTopK = 8;
 struct WsLayout {
     size_t header, shifts, exact_list, num, den;
     // precision forms only (zero size otherwise)
-    size_t At, G, Tt, nvalid, cand, edge;
+    size_t At, G, Tt, nvalid, Rm, cand, edge, keys;
     int Npad;
     size_t total;
 };
@@ -60,7 +60,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.num = off;        off += align256(sizeof(double) * R);
     L.den = off;        off += align256(sizeof(double) * R);
     L.Npad = 0;
-    L.At = L.G = L.Tt = L.nvalid = L.cand = L.edge = off;
+    L.At = L.G = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.keys = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
         const size_t es = form == PXST_FORM_TF32 ? 4 : 2;
         L.Npad = tensor_npad(d.n_frames, form);
@@ -68,8 +68,10 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
         L.G = off;      off += align256(es * R * L.Npad);
         L.Tt = off;     off += align256(sizeof(float) * R);
         L.nvalid = off; off += align256(sizeof(int) * R);
+        L.Rm = off;     off += align256(sizeof(float) * R);
         L.cand = off;   off += align256(sizeof(int) * kTopK * P);
         L.edge = off;   off += align256(P);
+        L.keys = off;   off += align256(sizeof(unsigned long long) * P);
     }
     L.total = off;
     return L;
@@ -107,16 +109,21 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
-                          int mode, const int *cand, int ncand, const uint8_t *sel, int sel_value,
                           cudaStream_t stream);
+cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
+                           const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
+                           const FrameShift *shifts, const int *cand, const uint8_t *edge,
+                           const int *edge_list, unsigned long long *keys, WsHeader *hdr, double *u,
+                           float *err_out, cudaStream_t stream);
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
                          const uint8_t *mask, void *At, cudaStream_t stream);
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
-                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, cudaStream_t stream);
+                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, float *Rm,
+                          cudaStream_t stream);
 cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *G,
                            const uint8_t *mask, const double *u, const float *Tt, const int *nvalid,
-                           WsHeader *hdr, int *cand, uint8_t *edge, cudaStream_t stream);
+                           WsHeader *hdr, int *cand, uint8_t *edge, int *edge_list, cudaStream_t stream);
 cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float *frames,
                          const float *W, const uint8_t *mask, const float *I_ref,
                          const float *w, const FrameShift *shifts, WsHeader *hdr,

@@ -162,12 +162,14 @@ __global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
     }
 }
 
-// G~ [Npad/KB][Ry][Rx][KB], T~ and n_valid per reference pixel; one warp per reference pixel.
+// G~ [Npad/KB][Ry][Rx][KB], T~, n_valid and the NaN-masked reference per reference pixel;
+// one warp per reference pixel.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                                                 const float *__restrict__ Iref, const float *__restrict__ w,
                                                 const FrameShift *__restrict__ shifts, T *__restrict__ G,
-                                                float *__restrict__ Tt, int *__restrict__ nvalid) {
+                                                float *__restrict__ Tt, int *__restrict__ nvalid,
+                                                float *__restrict__ Rm) {
     constexpr int KB = 128 / sizeof(T);
     const int lane = threadIdx.x & 31;
     const size_t R = (size_t)Ry * Rx;
@@ -198,6 +200,8 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
         if (lane == 0) {
             Tt[c] = t;
             nvalid[c] = nv;
+            // the reference with uncovered pixels as NaN, for the exact rescore
+            Rm[c] = __ldg(w + c) > 0.0f ? __ldg(Iref + c) : __int_as_float(0x7fc00000);
         }
     }
 }
@@ -220,6 +224,7 @@ struct TSearchArgs {
     WsHeader *hdr;
     int *cand;          // [P][kTopK] window indices of the best candidates, best first (-1: none)
     uint8_t *edge;      // [P] 1: a candidate of the pixel reads an invalid reference pixel
+    int *edge_list;     // those pixels, hdr->n_exact of them (in no particular order)
 };
 
 // Insert (qv, idx) into the ascending list bq/bi when it beats an entry (strict <, so of
@@ -519,7 +524,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             const size_t pix = (size_t)y * a.nx + x;
 #pragma unroll
             for (int m = 0; m < kTopK; ++m) a.cand[pix * kTopK + m] = m < TK ? bi[m] : -1;
-            a.edge[pix] = (edge || s_medge[p]) ? 1 : 0;
+            const bool e = edge || s_medge[p];
+            a.edge[pix] = e ? 1 : 0;
+            if (e) a.edge_list[atomicAdd(&a.hdr->n_exact, 1)] = (int)pix;
         }
     }
     if (tid == 0 && *abortp) atomicOr(&a.hdr->status, PXST_DEV_TIMEOUT);
@@ -549,23 +556,24 @@ cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *fr
 }
 
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
-                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, cudaStream_t stream) {
+                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, float *Rm,
+                          cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
     size_t blocks = (R + 7) / 8;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (form == PXST_FORM_TF32)
         k_gtable<float><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref, w,
-                                                               shifts, static_cast<float *>(G), Tt, nvalid);
+                                                               shifts, static_cast<float *>(G), Tt, nvalid, Rm);
     else
         k_gtable<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref,
                                                                        w, shifts, static_cast<__nv_bfloat16 *>(G),
-                                                                       Tt, nvalid);
+                                                                       Tt, nvalid, Rm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *G,
                            const uint8_t *mask, const double *u, const float *Tt, const int *nvalid,
-                           WsHeader *hdr, int *cand, uint8_t *edge, cudaStream_t stream) {
+                           WsHeader *hdr, int *cand, uint8_t *edge, int *edge_list, cudaStream_t stream) {
     const bool tf32 = o.form == PXST_FORM_TF32;
     const uint64_t es = tf32 ? 4 : 2;
     const uint32_t kb = tf32 ? 32 : 64;
@@ -585,7 +593,7 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     TSearchArgs a;
     a.N = d.n_frames; a.Npad = Npad; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.mask = mask; a.u = u; a.Tt = Tt; a.nvalid = nvalid; a.hdr = hdr;
-    a.cand = cand; a.edge = edge;
+    a.cand = cand; a.edge = edge; a.edge_list = edge_list;
     dim3 grid((d.nx + TS_TX - 1) / TS_TX, (d.ny + TS_TY - 1) / TS_TY);
     // list length: the candidates the rescore reads (4 unless more are asked for)
     const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);

@@ -20,6 +20,7 @@
 // masked renormalised reads from global memory, lexicographic warp argmin, FP64 fit.
 // It serves tiles whose reference window does not fit in shared memory and scans with
 // too many frames to stage.
+// Rescore (k_rescore): the exact stage of the tensor-core forms, one thread per pixel.
 #include <climits>
 #include <cmath>
 
@@ -30,11 +31,6 @@ namespace {
 
 struct SearchArgs {
     int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ebuf, win_cap;
-    int mode;                 // 0: search every candidate; 1: evaluate the listed candidates
-    const int *cand;          // mode 1: [P][kTopK] window indices (-1: none)
-    int ncand;                // mode 1: how many of them to evaluate (<= kTopK)
-    const uint8_t *sel;       // if set, only pixels with sel[pix] == sel_value are processed
-    int sel_value;
     const float *frames, *W;
     const uint8_t *mask;
     const float *Iref, *w;
@@ -383,6 +379,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
     __shared__ float s_nb[9][TP];
     __shared__ int s_gr0[NG], s_gc0[NG], s_gns[NG], s_goff[NG + 1];
     __shared__ unsigned int s_xbits[kExactWords];    // bit 4*item + j: strip needs the exact phase
+    __shared__ int s_glob[TP];                       // 1: the pixel is left to the global path
 
     const int tid = threadIdx.x;
     const size_t P = (size_t)a.ny * a.nx;
@@ -397,9 +394,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         float Wv = 0.0f;
         if (x < a.nx && y < a.ny) {
             const size_t pix = (size_t)y * a.nx + x;
-            if (a.sel && a.sel[pix] != a.sel_value) {
-                // another pass owns this pixel
-            } else if (!a.mask[pix]) {
+            if (!a.mask[pix]) {
                 if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
             } else {
                 const double u0 = a.u[pix], u1 = a.u[P + pix];
@@ -420,6 +415,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         s_cj[p] = cj;
         s_W[p] = Wv;
         s_slow[p] = 0;
+        s_glob[p] = 0;
         s_key[p] = ~0ull;
     }
     // the tile's frames: [n][FP], coalesced 128-byte rows
@@ -501,7 +497,7 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
 
     // ---- search: strips of the groups' window unions, 4 lanes per strip ----------------
     const int j = tid & (kSplit - 1);
-    const int units = a.mode == 0 ? s_goff[NG] * kSplit : 0;
+    const int units = s_goff[NG] * kSplit;
     for (int u0 = 0; u0 < units; u0 += NT) {
         const int t = u0 + tid;
         const bool valid = t < units;               // uniform over each strip's 4 lanes
@@ -546,11 +542,11 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         if (nan_seen) {
             s_slow[p] = 1;
             const int bit = item * kSplit + j;
-            if (bit < kExactWords * 32) {            // evaluated by the whole CTA below
+            if (bit < kExactWords * 32)              // evaluated by the whole CTA below
                 atomicOr(&s_xbits[bit >> 5], 1u << (bit & 31));
-                continue;
-            }
-            eval_strip_exact<L>(fr, FP, p, sh, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p], var, e);
+            else
+                s_glob[p] = 1;                       // beyond the bitmask: the global path
+            continue;
         }
         float be = INFINITY;
         int bi = -1;
@@ -637,30 +633,6 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
     }
     __syncthreads();
 
-    // ---- mode 1: the listed candidates of each pixel, evaluated exactly ------------------
-    if (a.mode == 1) {
-        for (int q = tid; q < TP * a.ncand; q += NT) {
-            const int p = q / a.ncand;
-            if (!s_act[p]) continue;
-            const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
-            const int idx = a.cand[((size_t)y * a.nx + x) * kTopK + (q % a.ncand)];
-            if (idx < 0) continue;
-            const int na = idx / wxn, nb = idx % wxn;
-            const float *wn = win + (s_ci[p] + na - a.Sy - wy0) * WS + (s_cj[p] + nb - a.Sx - wx0);
-            float acc1[1];
-            eval_strip<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], acc1);
-            const float var = s_var[p];
-            float ev = var > 0.0f ? acc1[0] / var : acc1[0];
-            if (isnan(ev)) {
-                eval_strip_exact<1>(fr, FP, p, sh, a.N, wn, WS, s_W[p], var, acc1);
-                ev = acc1[0];
-                s_slow[p] = 1;
-            }
-            atomicMin(&s_key[p], pack_key(ev, idx));
-        }
-        __syncthreads();
-    }
-
     // ---- 3x3 about each pixel's minimum ---------------------------------------------------
     if (a.quadratic) {
         for (int q = tid; q < TP * 9; q += NT) {
@@ -699,6 +671,10 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         if (!s_act[p]) continue;
         const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
         const size_t pix = (size_t)y * a.nx + x;
+        if (s_glob[p]) {
+            a.exact_list[atomicAdd(&a.hdr->n_exact, 1)] = (int)pix;
+            continue;
+        }
         if (s_slow[p]) atomicAdd(&a.hdr->n_exact_cta, 1);
         const unsigned long long key = s_key[p];
         const float be = __uint_as_float((unsigned int)(key >> 32));
@@ -888,6 +864,536 @@ cudaError_t launch_L(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
     }
 }
 
+
+// ------------------------------------------------------------------------------------
+// Rescore of the tensor-core forms: exact FP32 errors of the candidates the reduced-
+// precision ranking kept, of every candidate of the pixel that is not valid in every frame
+// (the ranking leaves those out: their error is normalised by a variance over fewer
+// frames), and of the 3x3 about the best, then the FP64 fit.
+//   k_rescore_edge: one warp per listed pixel with such candidates; the lanes split the
+//     window (the listed candidates included) and reduce to the lexicographic minimum;
+//     the pixel's frames are staged in shared memory by all 32 lanes at once.
+//   k_rescore: one block per 128 consecutive pixels, one thread per pixel; the frames
+//     stream through a 4-stage cp.async pipeline in shared memory while each thread
+//     evaluates the 3x3 about its first candidate (or the warp's minimum) and the other
+//     listed candidates; the reference is read through the cache.
+struct RescoreArgs {
+    int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ncand;
+    const float *frames, *W;
+    const uint8_t *mask;
+    const float *Rm;          // I_ref where w > 0, NaN elsewhere
+    const int *nvalid;        // frames in which each reference pixel is a valid candidate
+    const FrameShift *shifts;
+    const int *cand;          // [P][kTopK] window indices, -1 = none
+    const uint8_t *edge;      // [P] 1: some candidate of the pixel is not valid in every frame
+    const int *edge_list;     // the pixels with edge = 1; hdr->n_exact of them
+    unsigned long long *keys; // [P] packed (e, window index) minimum of those pixels
+    WsHeader *hdr;
+    double *u;
+    float *err_out;
+};
+
+// The frames stream through once: their loads are marked streaming (evict first), so that
+// they do not displace the masked reference and the validity counts, which every pixel
+// re-reads.
+
+// R_n at (i0 + fy, j0 + fx) by the masked renormalised bilinear gather, read from the
+// NaN-masked reference (the same arithmetic as gather_masked); false: frame not valid.
+__device__ __forceinline__ bool gather_rm(const float *__restrict__ Rm, int Ry, int Rx, int i0, int j0,
+                                          float fy, float fx, float &R) {
+    if (fy == 0.0f && fx == 0.0f) {
+        if (i0 < 0 || i0 >= Ry || j0 < 0 || j0 >= Rx) return false;
+        R = __ldg(Rm + (size_t)i0 * Rx + j0);
+        return R == R;
+    }
+    const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx), fy * fx};
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
+        if (wt[k] == 0.0f || ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;
+        const float r = __ldg(Rm + (size_t)ii * Rx + jj);
+        if (r != r) continue;
+        num = fmaf(wt[k], r, num);
+        den += wt[k];
+    }
+    if (!(den > 0.0f)) return false;
+    R = num / den;
+    return true;
+}
+
+// Running sums of one candidate over the frames where it is valid.
+struct CandSums {
+    float err, var;
+    int nv;
+    __device__ __forceinline__ void zero() { err = var = 0.0f; nv = 0; }
+    // frame value I, t = I - W; R read for this frame (ok: valid)
+    __device__ __forceinline__ void add(bool ok, float R, float I, float t, float Wv) {
+        if (ok) {
+            const float d = fmaf(-Wv, R, I);
+            err = fmaf(d, d, err);
+            var = fmaf(t, t, var);
+            ++nv;
+        }
+    }
+    __device__ __forceinline__ float e() const { return nv == 0 ? INFINITY : (var > 0.0f ? err / var : err); }
+};
+
+// R for a whole-pixel shift (ky, kx) of candidate (cy, cx) with flat index base = cy Rx + cx
+// and off = ky Rx + kx: NaN when the read is off the grid (or uncovered). `safe`: every
+// shift keeps this candidate's reads on the grid, so no bounds test is needed.
+__device__ __forceinline__ float read_int(const RescoreArgs &a, int cy, int cx, int base, bool safe, int ky, int kx,
+                                          int off) {
+    const bool inb = safe || ((unsigned)(cy + ky) < (unsigned)a.Ry && (unsigned)(cx + kx) < (unsigned)a.Rx);
+    return inb ? __ldg(a.Rm + (base + off)) : __int_as_float(0x7fc00000);
+}
+
+// R_n of candidate (cy, cx) for any shift: whole shifts by one load, else the general gather
+__device__ __forceinline__ bool read_any(const RescoreArgs &a, int cy, int cx, int base, bool safe,
+                                         const FrameShift &s, float &R) {
+    if (s.fy == 0.0f && s.fx == 0.0f) {
+        R = read_int(a, cy, cx, base, safe, s.ky, s.kx, s.ky * a.Rx + s.kx);
+        return R == R;
+    }
+    return gather_rm(a.Rm, a.Ry, a.Rx, cy + s.ky, cx + s.kx, s.fy, s.fx, R);
+}
+
+// every shift's reads of candidate rows [y0, y1] and columns [x0, x1] stay on the grid
+__device__ __forceinline__ bool span_safe(const RescoreArgs &a, int y0, int y1, int x0, int x1) {
+    const WsHeader &h = *a.hdr;
+    return y0 + h.kmin_y >= 0 && y1 + h.kmax_y + 1 < a.Ry && x0 + h.kmin_x >= 0 && x1 + h.kmax_x + 1 < a.Rx;
+}
+
+// Errors of up to B candidates (cy[k], cx[k]), k < nb, of pixel `pix`, frames read from
+// global memory (the rare second 3x3).
+template <int B>
+__device__ void eval_batch(const RescoreArgs &a, size_t pix, float Wv, const int (&cy)[B], const int (&cx)[B],
+                           int nb, float (&e)[B]) {
+    const size_t P = (size_t)a.ny * a.nx;
+    CandSums cs[B];
+    int base[B];
+    bool safe[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        cs[k].zero();
+        base[k] = cy[k] * a.Rx + cx[k];
+        safe[k] = span_safe(a, cy[k], cy[k], cx[k], cx[k]);
+    }
+    for (int n = 0; n < a.N; ++n) {
+        const FrameShift s = a.shifts[n];
+        const float I = __ldcs(a.frames + (size_t)n * P + pix);
+        const float t = I - Wv;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            if (k >= nb) continue;
+            float R;
+            const bool ok = read_any(a, cy[k], cx[k], base[k], safe[k], s, R);
+            cs[k].add(ok, R, I, t, Wv);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) e[k] = cs[k].e();
+}
+
+constexpr int RE_F = 512;     // frames staged per warp, and shifts per block
+constexpr int RE_B = 4;       // candidates per lane per pass over the frames
+constexpr int RE_L = 512;     // listed candidates held per warp (static smem <= 48 KB)
+
+// One pass over the frames for up to 32 x RE_B listed candidates of one pixel (lane l takes
+// entries l, l + 32, ...; neighbouring lanes hold neighbouring window positions).
+__device__ __forceinline__ void edge_batch(const RescoreArgs &a, const int *list, int b0, int cnt, int lane,
+                                           float *sIw, const int4 *sS, size_t pix, int ci, int cj, float Wv,
+                                           int wxn, unsigned long long &key) {
+    const size_t P = (size_t)a.ny * a.nx;
+    int cy[RE_B], cx[RE_B], id[RE_B], base[RE_B];
+    bool on[RE_B], safe[RE_B];
+    CandSums cs[RE_B];
+    bool all_safe = true;
+#pragma unroll
+    for (int k = 0; k < RE_B; ++k) {
+        const int e = b0 + 32 * k + lane;
+        on[k] = e < cnt;
+        id[k] = on[k] ? list[e] : 0;
+        cy[k] = on[k] ? ci + id[k] / wxn - a.Sy : 0;
+        cx[k] = on[k] ? cj + id[k] % wxn - a.Sx : 0;
+        base[k] = cy[k] * a.Rx + cx[k];
+        safe[k] = on[k] && span_safe(a, cy[k], cy[k], cx[k], cx[k]);
+        all_safe = all_safe && (!on[k] || safe[k]);
+        cs[k].zero();
+    }
+    all_safe = __all_sync(0xffffffffu, all_safe);
+    for (int f0 = 0; f0 < a.N; f0 += RE_F) {
+        const int nf = min(RE_F, a.N - f0);
+        if (a.N > RE_F) {
+            // more frames than one staged slice: stage this one (one slice is staged per pixel)
+            __syncwarp();
+            for (int l = lane; l < nf; l += 32) sIw[l] = __ldcs(a.frames + (size_t)(f0 + l) * P + pix);
+            __syncwarp();
+        }
+        for (int f = 0; f < nf; ++f) {
+            const float I = sIw[f];
+            const float t = I - Wv;
+            int4 q4;
+            if (f0 == 0) {
+                q4 = sS[f];
+            } else {
+                const FrameShift s = a.shifts[f0 + f];
+                q4 = make_int4(s.ky, s.kx, s.ky * a.Rx + s.kx, (s.fy == 0.0f && s.fx == 0.0f) ? 1 : 0);
+            }
+            if (q4.w && all_safe) {                    // the same for every lane
+#pragma unroll
+                for (int k = 0; k < RE_B; ++k) {
+                    if (!on[k]) continue;
+                    const float R = __ldg(a.Rm + (base[k] + q4.z));
+                    cs[k].add(R == R, R, I, t, Wv);
+                }
+            } else if (q4.w) {
+#pragma unroll
+                for (int k = 0; k < RE_B; ++k) {
+                    if (!on[k]) continue;
+                    const float R = read_int(a, cy[k], cx[k], base[k], safe[k], q4.x, q4.y, q4.z);
+                    cs[k].add(R == R, R, I, t, Wv);
+                }
+            } else {
+                const FrameShift s = a.shifts[f0 + f];
+#pragma unroll
+                for (int k = 0; k < RE_B; ++k) {
+                    if (!on[k]) continue;
+                    float R;
+                    const bool ok = gather_rm(a.Rm, a.Ry, a.Rx, cy[k] + s.ky, cx[k] + s.kx, s.fy, s.fx, R);
+                    cs[k].add(ok, R, I, t, Wv);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RE_B; ++k)
+        if (on[k]) key = min(key, pack_key(cs[k].e(), id[k]));
+}
+
+__global__ void __launch_bounds__(256, 3) k_rescore_edge(RescoreArgs a) {
+    __shared__ float sI[8][RE_F];
+    __shared__ int sL[8][RE_L];
+    __shared__ int4 sS[RE_F];                         // (ky, kx, ky Rx + kx, whole shift)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // the shifts of the first RE_F frames, once per block (later frames: global memory)
+    for (int n = threadIdx.x; n < min(a.N, RE_F); n += blockDim.x) {
+        const FrameShift s = a.shifts[n];
+        sS[n] = make_int4(s.ky, s.kx, s.ky * a.Rx + s.kx, (s.fy == 0.0f && s.fx == 0.0f) ? 1 : 0);
+    }
+    __syncthreads();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const size_t P = (size_t)a.ny * a.nx;
+    const int count = min(a.hdr->n_exact, (int)min(P, (size_t)INT_MAX));
+    const int wxn = 2 * a.Sx + 1, nwin = (2 * a.Sy + 1) * wxn;
+    int *list = sL[wib];
+    float *sIw = sI[wib];
+    for (int it = warp; it < count; it += nwarps) {
+        const size_t pix = (size_t)a.edge_list[it];
+        // listed by the ranking kernel, so M = 1 and u is finite and in range
+        const int ci = (int)floor(a.u[pix] + 0.5), cj = (int)floor(a.u[P + pix] + 0.5);
+        const float Wv = a.W[pix];
+        unsigned long long key = ~0ull;
+        __syncwarp();
+        if (a.N <= RE_F)
+            for (int l = lane; l < a.N; l += 32) sIw[l] = __ldcs(a.frames + (size_t)l * P + pix);
+        // the list: the ranking's candidates, then every window position that is not valid in
+        // every frame, in row-major order; whole batches are evaluated as the list fills and
+        // the remainder is carried to the front
+        int cnt;
+        {
+            const int idx = lane < a.ncand ? a.cand[pix * kTopK + lane] : -1;
+            const unsigned m = __ballot_sync(0xffffffffu, idx >= 0);
+            if (idx >= 0) list[__popc(m & ((1u << lane) - 1u))] = idx;
+            cnt = __popc(m);
+        }
+        int pos0 = 0;
+        while (true) {
+            for (; pos0 < nwin && cnt + 32 <= RE_L; pos0 += 32) {
+                const int pos = pos0 + lane;
+                bool inv = false;
+                if (pos < nwin) {
+                    const int y = ci + pos / wxn - a.Sy, x = cj + pos % wxn - a.Sx;
+                    inv = !(y >= 0 && y < a.Ry && x >= 0 && x < a.Rx) ||
+                          __ldg(a.nvalid + (size_t)y * a.Rx + x) != a.N;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, inv);
+                if (inv) list[cnt + __popc(m & ((1u << lane) - 1u))] = pos;
+                cnt += __popc(m);
+            }
+            const bool last = pos0 >= nwin;
+            const int nproc = last ? cnt : (cnt / (32 * RE_B)) * (32 * RE_B);
+            __syncwarp();
+            for (int b0 = 0; b0 < nproc; b0 += 32 * RE_B)
+                edge_batch(a, list, b0, cnt, lane, sIw, sS, pix, ci, cj, Wv, wxn, key);
+            if (last) break;
+            // carry the remainder (fewer than one batch, after at least one whole batch)
+            __syncwarp();
+            const int rem = cnt - nproc;
+            int v = lane < rem ? list[nproc + lane] : 0;
+            int v2 = lane + 32 < rem ? list[nproc + lane + 32] : 0;
+            int v3 = lane + 64 < rem ? list[nproc + lane + 64] : 0;
+            int v4 = lane + 96 < rem ? list[nproc + lane + 96] : 0;
+            __syncwarp();
+            if (lane < rem) list[lane] = v;
+            if (lane + 32 < rem) list[lane + 32] = v2;
+            if (lane + 64 < rem) list[lane + 64] = v3;
+            if (lane + 96 < rem) list[lane + 96] = v4;
+            cnt = rem;
+            __syncwarp();
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+            key = min(key, o);
+        }
+        if (lane == 0) a.keys[pix] = key;
+    }
+}
+
+constexpr int RS_T = 128;     // pixels per block
+constexpr int RS_F = 16;      // frames per pipeline stage
+constexpr int RS_S = 4;       // pipeline stages
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+// XK: listed candidates beyond the first that may lie outside its 3x3 (rescore length - 1)
+template <int XK>
+__global__ void __launch_bounds__(RS_T) k_rescore(RescoreArgs a) {
+    __shared__ __align__(16) float sfr[RS_S][RS_F][RS_T];
+    __shared__ __align__(16) FrameShift ssh[RS_S][RS_F];
+    const size_t P = (size_t)a.ny * a.nx;
+    const size_t p0 = (size_t)blockIdx.x * RS_T;
+    const int t = threadIdx.x;
+    const size_t pix = p0 + t;
+    const int wxn = 2 * a.Sx + 1;
+
+    // ---- this thread's pixel and its candidates --------------------------------------------
+    bool act = false;
+    int ci = 0, cj = 0;
+    float Wv = 0.0f;
+    if (pix < P) {
+        if (!a.mask[pix]) {
+            if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
+        } else {
+            const double u0 = a.u[pix], u1 = a.u[P + pix];
+            if (!isfinite(u0) || !isfinite(u1)) {
+                atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
+            } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
+                atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
+            } else {
+                ci = (int)floor(u0 + 0.5);
+                cj = (int)floor(u1 + 0.5);
+                Wv = a.W[pix];
+                act = true;
+            }
+        }
+    }
+    unsigned long long key = ~0ull;
+    int c0 = -1;                                      // window index the 3x3 is centred on
+    int xid[XK > 0 ? XK : 1];                         // listed candidates outside that 3x3
+    int nxk = 0;
+    if (act) {
+        if (a.edge[pix]) {
+            key = a.keys[pix];                        // minimum over the whole window
+            if (__uint_as_float((unsigned int)(key >> 32)) < INFINITY) c0 = (int)(key & 0xffffffffu);
+        } else {
+            c0 = a.cand[pix * kTopK];
+#pragma unroll
+            for (int m = 1; m <= XK; ++m) {
+                const int idx = m < a.ncand ? a.cand[pix * kTopK + m] : -1;
+                const bool far = idx >= 0 && c0 >= 0 && (abs(idx / wxn - c0 / wxn) > 1 || abs(idx % wxn - c0 % wxn) > 1);
+#pragma unroll
+                for (int q = 0; q < XK; ++q)
+                    if (q == nxk && far) xid[q] = idx;
+                nxk += far ? 1 : 0;
+            }
+        }
+    }
+    const bool run = act && c0 >= 0;
+    const int a0 = run ? c0 / wxn : 0, b0 = run ? c0 % wxn : 0;
+    const int y0 = ci + a0 - a.Sy, x0 = cj + b0 - a.Sx;             // reference pixel of c0
+    const int base0 = y0 * a.Rx + x0;
+    const bool safe9 = run && span_safe(a, y0 - 1, y0 + 1, x0 - 1, x0 + 1);
+    bool in9[9];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) {
+        const int na = a0 + jn / 3 - 1, nb = b0 + jn % 3 - 1;
+        in9[jn] = run && na >= 0 && na <= 2 * a.Sy && nb >= 0 && nb < wxn;
+    }
+    int xy[XK > 0 ? XK : 1], xx[XK > 0 ? XK : 1], xbase[XK > 0 ? XK : 1];
+    bool xsafe[XK > 0 ? XK : 1];
+#pragma unroll
+    for (int q = 0; q < XK; ++q) {
+        const bool on = run && q < nxk;
+        xy[q] = on ? ci + xid[q] / wxn - a.Sy : 0;
+        xx[q] = on ? cj + xid[q] % wxn - a.Sx : 0;
+        xbase[q] = xy[q] * a.Rx + xx[q];
+        xsafe[q] = on && span_safe(a, xy[q], xy[q], xx[q], xx[q]);
+    }
+    // lean: no pixel of the warp has a candidate that is not valid in every frame, and every
+    // read stays on the grid; only the errors are summed (the variance is the pixel's own)
+    bool ok_lean = !run || (!a.edge[pix] && safe9);
+#pragma unroll
+    for (int q = 0; q < XK; ++q) ok_lean = ok_lean && (q >= nxk || xsafe[q]);
+    const bool lean = __all_sync(0xffffffffu, ok_lean);
+    float var_all = 0.0f;
+    CandSums s9[9], sx[XK > 0 ? XK : 1];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) s9[jn].zero();
+#pragma unroll
+    for (int q = 0; q < XK; ++q) sx[q].zero();
+
+    // ---- frames through the cp.async pipeline -----------------------------------------------
+    const int nst = (a.N + RS_F - 1) / RS_F;
+    const bool vec = (P % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.frames) & 15) == 0) && p0 + RS_T <= P;
+    auto issue = [&](int st) {
+        if (st < nst) {
+            const int buf = st % RS_S;
+            if (vec) {
+                // 16 frames x 32 chunks of 4 pixels: 4 per thread
+#pragma unroll
+                for (int r = 0; r < (RS_F * RS_T / 4) / RS_T; ++r) {
+                    const int q = r * RS_T + t, f = q / (RS_T / 4), x4 = (q % (RS_T / 4)) * 4;
+                    const int n = st * RS_F + f;
+                    if (n < a.N) cp_async16(&sfr[buf][f][x4], a.frames + (size_t)n * P + p0 + x4);
+                }
+            } else {
+#pragma unroll 4
+                for (int f = 0; f < RS_F; ++f) {
+                    const int n = st * RS_F + f;
+                    if (n < a.N && pix < P) cp_async4(&sfr[buf][f][t], a.frames + (size_t)n * P + pix);
+                }
+            }
+            if (t < RS_F && st * RS_F + t < a.N) cp_async16(&ssh[buf][t], a.shifts + st * RS_F + t);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < RS_S - 1; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + RS_S - 1);
+        cp_async_wait<RS_S - 1>();
+        __syncthreads();
+        const int buf = st % RS_S;
+        if (run) {
+            const int nf = min(RS_F, a.N - st * RS_F);
+            for (int f = 0; f < nf; ++f) {
+                const FrameShift s = ssh[buf][f];
+                const float I = sfr[buf][f][t];
+                const float tt = I - Wv;
+                if (lean && s.fy == 0.0f && s.fx == 0.0f) {      // the same for every lane
+                    const int off = s.ky * a.Rx + s.kx;
+                    var_all = fmaf(tt, tt, var_all);
+#pragma unroll
+                    for (int jn = 0; jn < 9; ++jn) {
+                        if (!in9[jn]) continue;
+                        const float R = __ldg(a.Rm + (base0 + (jn / 3 - 1) * a.Rx + (jn % 3 - 1) + off));
+                        const float d = fmaf(-Wv, R, I);
+                        s9[jn].err = fmaf(d, d, s9[jn].err);
+                    }
+#pragma unroll
+                    for (int q = 0; q < XK; ++q) {
+                        if (q >= nxk) continue;
+                        const float R = __ldg(a.Rm + (xbase[q] + off));
+                        const float d = fmaf(-Wv, R, I);
+                        sx[q].err = fmaf(d, d, sx[q].err);
+                    }
+                } else {
+                    var_all = fmaf(tt, tt, var_all);
+#pragma unroll
+                    for (int jn = 0; jn < 9; ++jn) {
+                        if (!in9[jn]) continue;
+                        const int dy = jn / 3 - 1, dx = jn % 3 - 1;
+                        float R;
+                        const bool ok = read_any(a, y0 + dy, x0 + dx, base0 + dy * a.Rx + dx, safe9, s, R);
+                        s9[jn].add(ok, R, I, tt, Wv);
+                    }
+#pragma unroll
+                    for (int q = 0; q < XK; ++q) {
+                        if (q >= nxk) continue;
+                        float R;
+                        const bool ok = read_any(a, xy[q], xx[q], xbase[q], xsafe[q], s, R);
+                        sx[q].add(ok, R, I, tt, Wv);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    if (!act) return;
+
+    // ---- minimum, 3x3, fit ----------------------------------------------------------------------
+    if (lean) {
+        // every frame was valid for every candidate (the general branch above, taken for
+        // frames with a fractional shift, summed var and the count the same way)
+#pragma unroll
+        for (int jn = 0; jn < 9; ++jn) {
+            s9[jn].var = var_all;
+            s9[jn].nv = a.N;
+        }
+#pragma unroll
+        for (int q = 0; q < XK; ++q) {
+            sx[q].var = var_all;
+            sx[q].nv = a.N;
+        }
+    }
+    float f9[9];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) {
+        f9[jn] = in9[jn] ? s9[jn].e() : INFINITY;
+        if (in9[jn]) key = min(key, pack_key(f9[jn], c0 + (jn / 3 - 1) * wxn + (jn % 3 - 1)));
+    }
+#pragma unroll
+    for (int q = 0; q < XK; ++q)
+        if (q < nxk) key = min(key, pack_key(sx[q].e(), xid[q]));
+    const float be = __uint_as_float((unsigned int)(key >> 32));
+    if (!(be < INFINITY)) {
+        if (a.err_out) a.err_out[pix] = INFINITY;
+        return;
+    }
+    const int bi = (int)(key & 0xffffffffu);
+    const int ia = bi / wxn, ib = bi % wxn;
+    double da = 0.0, db = 0.0;
+    if (a.quadratic) {
+        if (bi != c0) {
+            // the minimum moved off the evaluated 3x3: evaluate the one about it
+            int cy[8], cx[8];
+            float e8[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int jn = m < 4 ? m : m + 1;
+                cy[m] = ci + ia + jn / 3 - 1 - a.Sy;
+                cx[m] = cj + ib + jn % 3 - 1 - a.Sx;
+            }
+            eval_batch<8>(a, pix, Wv, cy, cx, 8, e8);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int jn = m < 4 ? m : m + 1;
+                const int na = ia + jn / 3 - 1, nb = ib + jn % 3 - 1;
+                f9[jn] = (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) ? INFINITY : e8[m];
+            }
+            f9[4] = be;
+        }
+        refine3x3(f9, da, db);
+    }
+    a.u[pix] = (double)(ci + ia - a.Sy) + da;
+    a.u[P + pix] = (double)(cj + ib - a.Sx) + db;
+    if (a.err_out) a.err_out[pix] = be;
+}
+
 }  // namespace
 
 // Largest frame count the fast path can stage (a 1 x 32 tile in shared memory).
@@ -897,7 +1403,6 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           const float *W, const uint8_t *mask, const float *I_ref,
                           const float *w, const FrameShift *shifts, WsHeader *hdr,
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
-                          int mode, const int *cand, int ncand, const uint8_t *sel, int sel_value,
                           cudaStream_t stream) {
     Plan pl;
     const int wxn = 2 * o.win_x + 1;
@@ -919,7 +1424,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     pl.TY = 1;
     pl.smem = 0;
     int best_ebuf = 0;
-    for (int ebuf = mode == 0 ? 1 : 0; ebuf >= 0; --ebuf)
+    for (int ebuf = 1; ebuf >= 0; --ebuf)
         for (int ty = 8; ty >= 1; ty >>= 1) {
             size_t st = 0;
             int cr = 1;
@@ -951,7 +1456,6 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
     a.ebuf = best_ebuf; a.win_cap = pl.win_cap;
-    a.mode = mode; a.cand = cand; a.ncand = ncand; a.sel = sel; a.sel_value = sel_value;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.exact_list = exact_list; a.u = u; a.err_out = err_out;
     switch (pl.L) {
@@ -972,6 +1476,27 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.list = exact_list; a.u = u; a.err_out = err_out;
     k_exact<<<152 * 4, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
+                           const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
+                           const FrameShift *shifts, const int *cand, const uint8_t *edge,
+                           const int *edge_list, unsigned long long *keys, WsHeader *hdr, double *u,
+                           float *err_out, cudaStream_t stream) {
+    RescoreArgs a;
+    a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
+    a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0; a.ncand = ncand;
+    a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.nvalid = nvalid; a.shifts = shifts;
+    a.cand = cand; a.edge = edge; a.edge_list = edge_list; a.keys = keys;
+    a.hdr = hdr; a.u = u; a.err_out = err_out;
+    k_rescore_edge<<<152 * 8, 256, 0, stream>>>(a);
+    const size_t P = (size_t)d.ny * d.nx;
+    const unsigned blocks = (unsigned)((P + RS_T - 1) / RS_T);
+    if (ncand <= 4)
+        k_rescore<3><<<blocks, RS_T, 0, stream>>>(a);
+    else
+        k_rescore<7><<<blocks, RS_T, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -31,12 +31,22 @@ def test_tensor_contraction(form, K):
         assert np.max(np.abs(D - ref)) < 1e-5 * np.sqrt(K) + 1e-5
 
 
+def _ragged2d():
+    from test_gpu_parity import ragged2d
+    return ragged2d()
+
+
 SCANS = {
     "small": lambda: __import__("gen").config_small(),
+    "ragged2d": _ragged2d,
     "lens1d-48x768": lambda: __import__("gen").config_lens1d(ny=48, nx=768),
     "2d-100x96": lambda: __import__("gen").tiny2d(n_side=10, det=96, step=4, ref=200, sigma=1.5, mag=1.02,
                                                   offset=50.0, aberr=3.0, window=8,
                                                   seed=__import__("gen").BASE_SEED + 61),
+    # more frames than the rescore stages per slice (512)
+    "2d-625x40": lambda: __import__("gen").tiny2d(n_side=25, det=40, step=2, ref=160, sigma=1.5, mag=1.02,
+                                                  offset=60.0, aberr=2.0, window=5,
+                                                  seed=__import__("gen").BASE_SEED + 62),
 }
 
 
@@ -45,22 +55,53 @@ def tscan(request):
     return SCANS[request.param]()
 
 
-@pytest.mark.parametrize("form", [1, 2], ids=["bf16", "tf32"])
-def test_tensor_form_parity(tscan, form):
-    """BF16 / TF32 ranking on the tensor cores + exact FP32 evaluation of the best 4 (and of
-    every candidate of pixels touching invalid reference pixels) against the FP64 oracle,
-    with the same tolerances as the FP32 form."""
+def _inputs(s, hole):
     import oracle
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    if hole:
+        # an uncovered patch inside the reference: candidates reading it lose frames and are
+        # evaluated by the masked rule instead of being ranked on the tensor cores
+        Ry, Rx = s.ref_shape
+        w32[Ry // 2 - 3:Ry // 2 + 3, Rx // 2 - 4:Rx // 2 + 4] = 0.0
+        I32[w32 == 0] = 0.0
+    inp = dict(frames=s.frames, W=s.W, M=s.M, Iref=I32.astype(np.float64), w=w32.astype(np.float64),
+               delta=s.delta, u=s.u_init, window=s.window)
+    return inp, I32, w32
+
+
+@pytest.mark.parametrize("hole", [False, True], ids=["covered", "hole"])
+@pytest.mark.parametrize("form", [1, 2], ids=["bf16", "tf32"])
+def test_tensor_form_parity(tscan, form, hole):
+    """BF16 / TF32 ranking on the tensor cores + exact FP32 evaluation of the best few (and of
+    every candidate that is not valid in every frame) against the FP64 oracle, with the same
+    tolerances as the FP32 form."""
     import parity
     from gpu_util import gpu_update
     s = tscan
-    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
-    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
-    inp = dict(frames=s.frames, W=s.W, M=s.M, Iref=I32.astype(np.float64), w=w32.astype(np.float64),
-               delta=s.delta, u=s.u_init, window=s.window)
-    ug_i, eg_i = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=False, form=form)
+    inp, I32, w32 = _inputs(s, hole)
+    ug_i, eg_i, n_slow = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=False,
+                                    return_exact=True, form=form)
     ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True, form=form)
     pix = np.flatnonzero(s.M.ravel())
     rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
                               ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
-    print(s.name, "form", form, rep)
+    off = s.M == 0
+    assert np.array_equal(ug_q[:, off], s.u_init[:, off])
+    assert np.all(np.isnan(eg_q[off]))
+    if hole:
+        assert n_slow > 0
+    print(s.name, "form", form, "hole" if hole else "", rep, "masked-rule pixels:", n_slow)
+
+
+@pytest.mark.parametrize("form", [1, 2], ids=["bf16", "tf32"])
+def test_tensor_form_deterministic(tscan, form):
+    """Repeated calls of a tensor form give bit-identical maps and errors."""
+    from gpu_util import gpu_update
+    s = tscan
+    _, I32, w32 = _inputs(s, True)
+    runs = [gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True, form=form)
+            for _ in range(3)]
+    for k in (1, 2):
+        assert np.array_equal(runs[0][0], runs[k][0])
+        assert np.array_equal(runs[0][1], runs[k][1], equal_nan=True)
