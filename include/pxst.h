@@ -72,7 +72,11 @@ typedef struct {
     int32_t form;          /* PXST_FORM_* */
     int32_t rescore_k;     /* tensor forms: candidates per pixel re-evaluated in FP32:
                               4 or 8 (0 = 8 below 128 frames, else 4) */
-    int32_t reserved;
+    int32_t tile;          /* tile shape (0 = automatic). FP32 form: tile height in rows of 32
+                              pixels, 1, 2, 4 or 8 (a height whose staging does not fit falls
+                              back to the automatic choice). Tensor forms: 0 = 8 x 16 pixels
+                              against 8 x 32 candidates, 1 = 4 x 32 / 4 x 64, 2 = 2 x 64 /
+                              2 x 128. Any other value is PXST_ERR_ARG. */
     int64_t timeout_ns;    /* reserved for device-side waits (0 = default) */
 } pxst_options;
 
@@ -196,6 +200,54 @@ const char *pxst_kernel_name(int32_t k);
  * int) gets PXST_DEV_TIMEOUT if a wait ran out. Not part of the method: a self-check. */
 pxst_status pxst_tensor_check(int32_t form, int32_t K, const void *A, const void *B, float *D,
                               int32_t *status, void *stream);
+
+/* ---- Batched form ------------------------------------------------------------------------
+ * Many independent scans of uneven frame count, detector size and window, iterated by one
+ * graph launch. A pxst_scan names one scan's device arrays exactly as pxst_iterate takes
+ * them (all device pointers, owned by the caller, alive and unmoved for the batch's life;
+ * err_out may be NULL) and its own workspace of pxst_workspace_size(&dims, &opts) bytes.
+ * Scans in one batch must not share any output array or workspace. */
+typedef struct {
+    pxst_dims dims;
+    pxst_options opts;
+    const float *frames;      /* [N][ny][nx] */
+    const float *W;           /* [ny][nx] */
+    const uint8_t *mask;      /* [ny][nx] */
+    const double *delta;      /* [N][2] */
+    double *u;                /* [2][ny][nx], updated in place */
+    float *I_ref, *w;         /* [ref_ny][ref_nx] */
+    float *err_out;           /* [ny][nx] or NULL */
+    void *workspace;
+    size_t ws_bytes;
+} pxst_scan;
+
+typedef struct pxst_batch_s *pxst_batch;
+
+/* Plan a batch: validate every scan, optionally pick each scan's tile shape by measurement
+ * (autotune = 1: pxst_autotune per shape class, which runs update_pixel_map on the scan's own
+ * data and restores its map), spread the scans over n_branches parallel graph branches
+ * (1..64; largest estimated work first, each to the least loaded branch) and capture n_iter
+ * iterations of every scan (the pxst_iterate sequence: make_object_map, update_pixel_map)
+ * into one CUDA graph. Synchronises `stream` (plan-time work runs on it). *out receives the
+ * batch, to be released with pxst_batch_destroy. Errors: those of pxst_iterate for the
+ * first scan that fails, PXST_ERR_ARG for bad counts, PXST_ERR_CUDA if capture fails. */
+pxst_status pxst_batch_plan(const pxst_scan *scans, int32_t n_scans, int32_t n_iter, int32_t n_branches,
+                            int32_t autotune, void *stream, pxst_batch *out);
+/* Run the planned iterations of every scan: one cudaGraphLaunch on `stream` (asynchronous).
+ * Device-side status goes to each scan's workspace as for pxst_iterate. */
+pxst_status pxst_batch_run(pxst_batch batch, void *stream);
+/* The branch a scan was placed on (-1 for a bad index). */
+int32_t pxst_batch_branch(pxst_batch batch, int32_t scan);
+void pxst_batch_destroy(pxst_batch batch);
+
+/* Autotuner: time update_pixel_map on this scan for every tile shape its form allows
+ * (pxst_options.tile), `trials` timed runs each after one warm-up, and return the shape with
+ * the smallest median time (and that time in ms if best_ms is not NULL). The scan's map u is
+ * saved in its workspace and restored after every run; err_out receives the last run's
+ * errors. Results are cached per shape class (dims, window, form, rescore_k) for the
+ * process. Synchronises `stream`; PXST_ERR_ARG on a capturing stream. */
+pxst_status pxst_autotune(const pxst_scan *scan, int32_t trials, void *stream, int32_t *best_tile,
+                          float *best_ms);
 
 /* Human-readable text for a status code. */
 const char *pxst_status_string(pxst_status s);

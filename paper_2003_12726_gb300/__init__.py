@@ -41,8 +41,15 @@ class _Dims(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("win_y", C.c_int32), ("win_x", C.c_int32), ("quadratic", C.c_int32),
-                ("form", C.c_int32), ("rescore_k", C.c_int32), ("reserved", C.c_int32),
+                ("form", C.c_int32), ("rescore_k", C.c_int32), ("tile", C.c_int32),
                 ("timeout_ns", C.c_int64)]
+
+
+class _Scan(C.Structure):
+    _fields_ = [("dims", _Dims), ("opts", _Opts), ("frames", C.c_void_p), ("W", C.c_void_p),
+                ("mask", C.c_void_p), ("delta", C.c_void_p), ("u", C.c_void_p), ("I_ref", C.c_void_p),
+                ("w", C.c_void_p), ("err_out", C.c_void_p), ("workspace", C.c_void_p),
+                ("ws_bytes", C.c_size_t)]
 
 
 _lib = None
@@ -89,6 +96,17 @@ def lib():
         L.pxst_version.restype = C.c_char_p
         L.pxst_tensor_check.argtypes = [i32, i32, P, P, P, P, P]
         L.pxst_tensor_check.restype = i32
+        S = C.POINTER(_Scan)
+        L.pxst_batch_plan.argtypes = [S, i32, i32, i32, i32, P, C.POINTER(P)]
+        L.pxst_batch_plan.restype = i32
+        L.pxst_batch_run.argtypes = [P, P]
+        L.pxst_batch_run.restype = i32
+        L.pxst_batch_branch.argtypes = [P, i32]
+        L.pxst_batch_branch.restype = i32
+        L.pxst_batch_destroy.argtypes = [P]
+        L.pxst_batch_destroy.restype = None
+        L.pxst_autotune.argtypes = [S, i32, P, C.POINTER(i32), C.POINTER(C.c_float)]
+        L.pxst_autotune.restype = i32
         _lib = L
     return _lib
 
@@ -97,7 +115,8 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_update_pixel_map",
             "pxst_iterate", "pxst_reference_terms", "pxst_get_status", "pxst_last_exact_count",
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
-            "pxst_version", "pxst_tensor_check"]
+            "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
+            "pxst_batch_destroy", "pxst_autotune"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -149,9 +168,11 @@ class Options:
     win_x: int
     quadratic: bool = True
     form: int = FORM_FP32
+    rescore_k: int = 0      # tensor forms: 4 or 8 (0: 8 below 128 frames, else 4)
+    tile: int = 0           # tile shape (0: automatic); see pxst_options.tile
 
     def c(self):
-        return _Opts(self.win_y, self.win_x, 1 if self.quadratic else 0, self.form, 0, 0, 0)
+        return _Opts(self.win_y, self.win_x, 1 if self.quadratic else 0, self.form, self.rescore_k, self.tile, 0)
 
 
 def workspace_size(dims: Dims, opts: Options | None = None):
@@ -343,3 +364,52 @@ def tensor_check(form, A, B, stream=None):
     _raise(lib().pxst_tensor_check(int(form), K, a, b, C.c_void_p(D.data_ptr()), C.c_void_p(st.data_ptr()),
                                    _stream(stream)), "tensor_check")
     return D, int(st.item())
+
+
+def _scan_struct(rec):
+    """pxst_scan for a Reconstruction's device-resident state."""
+    p = lambda t: C.c_void_p(t.data_ptr())
+    return _Scan(rec.dims.c(), rec.opts.c(), p(rec.frames), p(rec.W), p(rec.M), p(rec.delta), p(rec.u),
+                 p(rec.I_ref), p(rec.w), p(rec.err), p(rec.ws), rec.ws.numel())
+
+
+def autotune(rec, trials=3, stream=None):
+    """pxst_autotune on a Reconstruction: (best tile, its median update time in ms). The
+    scan's map is restored; rec.opts.tile is set to the choice."""
+    sc = _scan_struct(rec)
+    tile, ms = C.c_int32(0), C.c_float(0.0)
+    _raise(lib().pxst_autotune(C.byref(sc), int(trials), _stream(stream), C.byref(tile), C.byref(ms)),
+           "autotune")
+    rec.opts.tile = int(tile.value)
+    return int(tile.value), float(ms.value)
+
+
+class Batch:
+    """Many scans (Reconstruction objects, each with its own device state) iterated by one
+    CUDA graph launch: pxst_batch_plan / pxst_batch_run. The scans' arrays must stay alive
+    and in place while the batch exists."""
+
+    def __init__(self, recs, n_iter, n_branches=8, autotune=False, stream=None):
+        self.recs = list(recs)
+        arr = (_Scan * len(self.recs))(*[_scan_struct(r) for r in self.recs])
+        h = C.c_void_p()
+        _raise(lib().pxst_batch_plan(arr, len(self.recs), int(n_iter), int(n_branches), 1 if autotune else 0,
+                                     _stream(stream), C.byref(h)), "batch_plan")
+        self._h = h
+
+    def run(self, stream=None):
+        _raise(lib().pxst_batch_run(self._h, _stream(stream)), "batch_run")
+
+    def branch(self, i):
+        return int(lib().pxst_batch_branch(self._h, int(i)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().pxst_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,6 +28,9 @@ bool opts_ok(const pxst_options *o) {
     if (o->quadratic != 0 && o->quadratic != 1) return false;
     if (o->form != PXST_FORM_FP32 && o->form != PXST_FORM_BF16 && o->form != PXST_FORM_TF32) return false;
     if (o->rescore_k != 0 && o->rescore_k != 4 && o->rescore_k != 8) return false;
+    if (o->form == PXST_FORM_FP32 ? (o->tile != 0 && o->tile != 1 && o->tile != 2 && o->tile != 4 && o->tile != 8)
+                                  : (o->tile < 0 || o->tile > 2))
+        return false;
     return true;
 }
 
@@ -96,6 +99,9 @@ struct Timed {
     Timed(int kernel, cudaStream_t st) : k(kernel), s(st) {
         std::lock_guard<std::mutex> g(g_tmu);
         if (g_timing && g_recs.size() < kMaxRecs) {
+            // a stream being captured into a graph records no timing events
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
             a = take_event();
             b = take_event();
             cudaEventRecord(a, s);
@@ -237,6 +243,11 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
 }
 
 }  // namespace
+
+void pxst::prime_shift_span(const pxst_dims &d, const double *delta, cudaStream_t s) {
+    int sy, sx;
+    shift_span(d, delta, s, sy, sx);
+}
 
 extern "C" {
 

@@ -35,7 +35,7 @@ constexpr int kTopK = 8;
 
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
-    size_t header, shifts, exact_list, num, den;
+    size_t header, shifts, exact_list, num, den, u_save;
     // precision forms only (zero size otherwise)
     size_t At, G, Tt, nvalid, Rm, cand, edge, keys;
     int Npad;
@@ -59,6 +59,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.exact_list = off; off += align256(sizeof(int) * P);
     L.num = off;        off += align256(sizeof(double) * R);
     L.den = off;        off += align256(sizeof(double) * R);
+    L.u_save = off;     off += align256(sizeof(double) * 2 * P);   // the autotuner's copy of u
     L.Npad = 0;
     L.At = L.G = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.keys = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
@@ -129,6 +130,8 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
                          const float *w, const FrameShift *shifts, WsHeader *hdr,
                          const int *exact_list, double *u, float *err_out, cudaStream_t stream);
 int search_max_frames();
+// learn (and cache) the integer shift span of a translation array outside any capture
+void prime_shift_span(const pxst_dims &d, const double *delta, cudaStream_t s);
 cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float *w,
                             const FrameShift *shifts, float *T, int32_t *n_valid,
                             cudaStream_t stream);

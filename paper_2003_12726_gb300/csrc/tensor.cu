@@ -12,6 +12,7 @@
 
 #include <cuda_bf16.h>
 #include <climits>
+#include <type_traits>
 
 #include "pxst_common.cuh"
 #include "tc_ptx.cuh"
@@ -206,8 +207,9 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
     }
 }
 
-constexpr int TS_TY = 8, TS_TX = 16;          // pixel tile: M = 128
-constexpr int TS_CR = 8, TS_CC = 32;          // candidate chunk: N = 256 (8 rows x 32 columns)
+// Tile shapes (template parameters PTY, CCW): a pixel tile of PTY x (128 / PTY) pixels
+// (M = 128) against candidate chunks of (256 / CCW) x CCW reference pixels (N = 256).
+// Shape 0: 8 x 16 pixels, 8 x 32 candidates; 1: 4 x 32, 4 x 64; 2: 2 x 64, 2 x 128.
 constexpr int TS_STAGES = 4;
 constexpr int TS_EPI_WARPS = 8;               // two per TMEM lane quarter, splitting the chunk rows
 constexpr int TS_THREADS = 64 + 32 * TS_EPI_WARPS;   // producer, MMA, epilogue warps
@@ -278,10 +280,14 @@ __device__ inline void centre_first(int *ord, int n, int c) {
     }
 }
 
-template <bool TF32, int TK>
+template <bool TF32, int TK, int PTY, int CCW>
 __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant__ CUtensorMap tA,
                                                            const __grid_constant__ CUtensorMap tB,
                                                            TSearchArgs a) {
+    constexpr int TS_TY = PTY, TS_TX = 128 / PTY;  // pixel tile
+    constexpr int TS_CR = 256 / CCW, TS_CC = CCW;  // candidate chunk
+    constexpr int SPR = CCW / 32;                  // 32-candidate segments per chunk row
+    static_assert(TS_TY * TS_TX == 128 && TS_CR * TS_CC == 256 && SPR >= 1, "tile shape");
     constexpr int KB = TF32 ? 32 : 64;       // frames per 128-byte operand row
     constexpr int KSTEP = TF32 ? 8 : 16;     // frames per MMA
     constexpr uint32_t IDESC = tc::instr_desc(TF32 ? 2u : 1u, 128, 256);
@@ -293,8 +299,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     __shared__ int s_box[4];
     __shared__ int s_ci[128], s_cj[128], s_act[128];
     __shared__ int s_rord[TS_MAX_ORDER], s_cord[TS_MAX_ORDER];
-    __shared__ __align__(16) float s_T[2][TS_CR * TS_CC];
-    __shared__ uint32_t s_vm[2][TS_CR];
+    __shared__ __align__(16) float s_T[2][256];
+    __shared__ uint32_t s_vm[2][8];
     __shared__ float s_mq[128][TK];
     __shared__ int s_mi[128][TK];
     __shared__ uint8_t s_medge[128];
@@ -426,8 +432,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             }
         }
     } else {
-        // ---- epilogue: 8 warps; TMEM lane quarter q = warp % 4, chunk rows h, h + 2, ... ----
-        const int ew = warp - 2;                      // 0..7: also the chunk row this warp stages
+        // ---- epilogue: 8 warps; TMEM lane quarter q = warp % 4; the chunk's 8 segments of 32
+        //      candidates (TMEM columns 32 g ..) are split h, h + 2, ... --------------------------
+        const int ew = warp - 2;                      // 0..7: also the segment this warp stages
         const int q = warp & 3, h = ew >> 2;
         const int p = q * 32 + lane;                  // pixel of the tile = TMEM lane
         const bool act = s_act[p] != 0;
@@ -441,11 +448,11 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             bi[m] = -1;
         }
         bool edge = false;
-        // T~ and validity of chunk row `ew` of chunk j (+inf / clear bit: not valid in every frame)
+        // T~ and validity of segment `ew` of chunk j (+inf / clear bit: not valid in every frame)
         auto fetch = [&](int j, float &t, bool &ok) {
             int row0, col0;
             chunk_origin(j, row0, col0);
-            const int gy = row0 + ew, gx = col0 + lane;
+            const int gy = row0 + ew / SPR, gx = col0 + (ew % SPR) * 32 + lane;
             t = INFINITY;
             ok = false;
             if (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) {
@@ -458,7 +465,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             float t;
             bool ok;
             fetch(0, t, ok);
-            s_T[0][ew * TS_CC + lane] = t;
+            s_T[0][ew * 32 + lane] = t;
             const uint32_t vm = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) s_vm[0][ew] = vm;
         }
@@ -475,30 +482,31 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             if (!ok) *abortp = 1;
             tc::tc_fence_after();
             if (ok) {
-                // this pixel's window columns within a chunk row: [ilo, ihi]
-                const int ilo = max(0, cj - a.Sx - col0), ihi = min(TS_CC - 1, cj + a.Sx - col0);
-                const uint32_t colmask =
-                    ilo > ihi ? 0u : ((ihi == 31 ? 0xffffffffu : ((1u << (ihi + 1)) - 1u)) & ~((1u << ilo) - 1u));
 #pragma unroll 1
-                for (int r = h; r < TS_CR; r += 2) {
+                for (int g = h; g < 8; g += 2) {
+                    const int r = g / SPR, c0 = col0 + (g % SPR) * 32;
                     const int aa = row0 + r - ci;
+                    // this pixel's window columns within the segment: [ilo, ihi]
+                    const int ilo = max(0, cj - a.Sx - c0), ihi = min(31, cj + a.Sx - c0);
+                    const uint32_t colmask =
+                        ilo > ihi ? 0u : ((ihi == 31 ? 0xffffffffu : ((1u << (ihi + 1)) - 1u)) & ~((1u << ilo) - 1u));
                     const uint32_t inmask = (act && aa >= -a.Sy && aa <= a.Sy) ? colmask : 0u;
                     if (__all_sync(0xffffffffu, inmask == 0u)) continue;
                     float v[32];
-                    tc::tmem_ld32(tmem + buf * 256 + r * 32 + ((uint32_t)(q * 32) << 16), v);
-                    const uint32_t vm = s_vm[buf][r];
+                    tc::tmem_ld32(tmem + buf * 256 + g * 32 + ((uint32_t)(q * 32) << 16), v);
+                    const uint32_t vm = s_vm[buf][g];
                     edge = edge || (inmask & ~vm) != 0u;
                     const uint32_t use = inmask & vm;
-                    const int rowbase = (aa + a.Sy) * wxn + (col0 - cj + a.Sx);
+                    const int rowbase = (aa + a.Sy) * wxn + (c0 - cj + a.Sx);
                     if (__all_sync(0xffffffffu, use == 0xffffffffu))
-                        scan_row<TK, true>(v, &s_T[buf][r * TS_CC], use, rowbase, bq, bi);
+                        scan_row<TK, true>(v, &s_T[buf][g * 32], use, rowbase, bq, bi);
                     else
-                        scan_row<TK, false>(v, &s_T[buf][r * TS_CC], use, rowbase, bq, bi);
+                        scan_row<TK, false>(v, &s_T[buf][g * 32], use, rowbase, bq, bi);
                 }
             }
             tc::tc_fence_before();
             if (j + 1 < nchunks) {
-                s_T[buf ^ 1][ew * TS_CC + lane] = tn;
+                s_T[buf ^ 1][ew * 32 + lane] = tn;
                 const uint32_t vm = __ballot_sync(0xffffffffu, okn);
                 if (lane == 0) s_vm[buf ^ 1][ew] = vm;
             }
@@ -582,10 +590,13 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     const uint64_t nkb = (uint64_t)Npad / kb, row = (uint64_t)kb * es;     // 128-byte rows
     const uint64_t dA[4] = {kb, (uint64_t)d.nx, (uint64_t)d.ny, nkb};
     const uint64_t sA[3] = {row, row * d.nx, row * d.nx * d.ny};
-    const uint32_t bA[4] = {kb, TS_TX, TS_TY, 1};
+    // tile shape: pixel tile rows and candidate chunk columns
+    const int shape = (o.tile >= 0 && o.tile <= 2) ? o.tile : 0;
+    const uint32_t pty = 8u >> shape, ccw = 32u << shape;
+    const uint32_t bA[4] = {kb, 128 / pty, pty, 1};
     const uint64_t dB[4] = {kb, (uint64_t)d.ref_nx, (uint64_t)d.ref_ny, nkb};
     const uint64_t sB[3] = {row, row * d.ref_nx, row * d.ref_nx * d.ref_ny};
-    const uint32_t bB[4] = {kb, TS_CC, TS_CR, 1};
+    const uint32_t bB[4] = {kb, ccw, 256 / ccw, 1};
     cudaError_t e = tmap_encode(&tA, dt, 4, const_cast<void *>(At), dA, sA, bA);
     if (e != cudaSuccess) return e;
     e = tmap_encode(&tB, dt, 4, const_cast<void *>(G), dB, sB, bB);
@@ -594,7 +605,7 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     a.N = d.n_frames; a.Npad = Npad; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.mask = mask; a.u = u; a.Tt = Tt; a.nvalid = nvalid; a.hdr = hdr;
     a.cand = cand; a.edge = edge; a.edge_list = edge_list;
-    dim3 grid((d.nx + TS_TX - 1) / TS_TX, (d.ny + TS_TY - 1) / TS_TY);
+    dim3 grid((d.nx + 128 / pty - 1) / (128 / pty), (d.ny + pty - 1) / pty);
     // list length: the candidates the rescore reads (4 unless more are asked for)
     const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
     auto go = [&](auto kern) {
@@ -602,10 +613,21 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
         if (r == cudaSuccess) kern<<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
         return r;
     };
+    auto by_shape = [&](auto tf32_tag, auto tk_tag) {
+        constexpr bool T = decltype(tf32_tag)::value;
+        constexpr int K = decltype(tk_tag)::value;
+        switch (shape) {
+            case 1: return go(k_tsearch<T, K, 4, 64>);
+            case 2: return go(k_tsearch<T, K, 2, 128>);
+            default: return go(k_tsearch<T, K, 8, 32>);
+        }
+    };
+    using t_ = std::true_type;
+    using f_ = std::false_type;
     if (tf32)
-        e = rk <= 4 ? go(k_tsearch<true, 4>) : go(k_tsearch<true, 8>);
+        e = rk <= 4 ? by_shape(t_{}, std::integral_constant<int, 4>{}) : by_shape(t_{}, std::integral_constant<int, 8>{});
     else
-        e = rk <= 4 ? go(k_tsearch<false, 4>) : go(k_tsearch<false, 8>);
+        e = rk <= 4 ? by_shape(f_{}, std::integral_constant<int, 4>{}) : by_shape(f_{}, std::integral_constant<int, 8>{});
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

@@ -1426,6 +1426,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     int best_ebuf = 0;
     for (int ebuf = 1; ebuf >= 0; --ebuf)
         for (int ty = 8; ty >= 1; ty >>= 1) {
+            if (o.tile > 0 && ty != o.tile) continue;          // a requested tile height
             size_t st = 0;
             int cr = 1;
             cudaError_t e = variant_info_any(pl.L, ty, st, cr);
@@ -1448,6 +1449,13 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                 break;
             }
         }
+    if (best_score < 0 && o.tile > 0) {
+        // the requested height does not fit: the automatic choice
+        pxst_options o2 = o;
+        o2.tile = 0;
+        return launch_search(d, o2, frames, W, mask, I_ref, w, shifts, hdr, exact_list, u, err_out, span_y, span_x,
+                             stream);
+    }
     if (best_score < 0) return cudaErrorInvalidConfiguration;   // callers check frame count first
     const size_t fixed = shifts_b + N * (32 * pl.TY + 4) * 4 + (best_ebuf ? (size_t)32 * pl.TY * nwin * 4 : 0);
     pl.win_cap = (int)((pl.smem - fixed) / 4);

@@ -35,10 +35,10 @@ def gpu_make_object_map(frames, W, M, u, delta, ref_shape):
     return Iref.cpu().numpy(), w.cpu().numpy()
 
 
-def gpu_update(frames, W, M, Iref32, w32, delta, u, window, quadratic=True, return_exact=False, form=0):
+def gpu_update(frames, W, M, Iref32, w32, delta, u, window, quadratic=True, return_exact=False, form=0, tile=0):
     t = torch()
     d = dims_of(frames, Iref32.shape)
-    o = px.Options(int(window[0]), int(window[1]), quadratic, form)
+    o = px.Options(int(window[0]), int(window[1]), quadratic, form, tile=tile)
     ud = dev(u, t.float64)
     err = t.full(M.shape, -7.0, dtype=t.float32, device="cuda")
     ws = px.workspace(d, o)

@@ -1,0 +1,108 @@
+"""The batched form (pxst_batch_plan / pxst_batch_run): scans of uneven frame count,
+detector size, window and form iterated by one graph launch give the same result as each
+scan iterated alone, and match the oracle; the autotuner returns a legal tile shape,
+restores the map, and the tuned shape keeps parity."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _scans():
+    B = gen.BASE_SEED
+    return [
+        (gen.tiny2d(n_side=4, det=48, step=6, ref=130, window=4, seed=B + 71), 0),
+        (gen.tiny2d(n_side=5, det=64, step=4, ref=150, window=6, sigma=1.5, mag=1.2, seed=B + 72), 1),
+        (gen.tiny2d(n_side=3, det=40, step=5, ref=110, window=3, seed=B + 73), 0),
+        (gen.config_lens1d(n_frames=24, ny=16, nx=256), 0),
+        (gen.tiny2d(n_side=6, det=56, step=3, ref=140, window=5, sigma=1.5, mag=1.1, seed=B + 74), 2),
+        (gen.tiny2d(n_side=4, det=72, step=6, ref=180, window=8, sigma=1.5, mag=1.3, seed=B + 75), 1),
+    ]
+
+
+def _rec(s, form):
+    import paper_2003_12726_gb300 as px
+    return px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, form=form)
+
+
+def _same(ra, rb, M):
+    ua, ub = ra.u.cpu().numpy(), rb.u.cpu().numpy()
+    good = M > 0
+    agree = np.all(np.abs(ua - ub) <= parity.U_TOL, axis=0)[good].mean()
+    Ia, Ib = ra.I_ref.cpu().numpy().astype(np.float64), rb.I_ref.cpu().numpy().astype(np.float64)
+    return agree, parity.rel_l2(Ib, Ia)
+
+
+def test_batch_matches_each_scan_alone():
+    import torch
+    import paper_2003_12726_gb300 as px
+    scans = _scans()
+    alone = []
+    for s, f in scans:
+        r = _rec(s, f)
+        r.run(2)
+        alone.append(r)
+    recs = [_rec(s, f) for s, f in scans]
+    b = px.Batch(recs, n_iter=2, n_branches=3)
+    assert sorted({b.branch(i) for i in range(len(recs))}) == [0, 1, 2]
+    b.run()
+    torch.cuda.synchronize()
+    for (s, f), ra, rb in zip(scans, alone, recs):
+        agree, rl2 = _same(ra, rb, s.M)
+        print(s.name, "form", f, "u agreement", agree, "I_ref rel L2", rl2)
+        # the reference image sums FP64 atomics: equal to rounding, so a near-tie may flip
+        assert agree >= 0.999 and rl2 < 1e-6
+    # the graph replays: two more iterations of every scan
+    b.run()
+    torch.cuda.synchronize()
+    for (s, f), ra in zip(scans, alone):
+        ra.run(2)
+    torch.cuda.synchronize()
+    for (s, f), ra, rb in zip(scans, alone, recs):
+        agree, rl2 = _same(ra, rb, s.M)
+        assert agree >= 0.995 and rl2 < 1e-5, (s.name, agree, rl2)
+    b.close()
+
+
+def test_batch_against_oracle():
+    """One iteration of every scan in one batch; scan 0 (FP32) and scan 1 (BF16) against the
+    oracle's iteration."""
+    import torch
+    import paper_2003_12726_gb300 as px
+    scans = _scans()
+    recs = [_rec(s, f) for s, f in scans]
+    b = px.Batch(recs, n_iter=1, n_branches=4)
+    b.run()
+    torch.cuda.synchronize()
+    for k in (0, 1):
+        s = scans[k][0]
+        uo, Io, wo, eo = oracle.iterate(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, 1)
+        parity.check_omap(recs[k].I_ref.cpu().numpy(), recs[k].w.cpu().numpy(), Io, wo)
+        ug = recs[k].u.cpu().numpy()
+        same = np.all(np.abs(ug - uo) <= parity.U_TOL, axis=0)[s.M > 0]
+        assert same.mean() >= parity.ARGMIN_AGREE - 0.004, (k, same.mean())
+    b.close()
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["fp32", "bf16"])
+def test_autotune(form):
+    import torch
+    import paper_2003_12726_gb300 as px
+    s = gen.tiny2d(n_side=5, det=64, step=4, ref=150, window=6, sigma=1.5, mag=1.2, seed=gen.BASE_SEED + 76)
+    r = _rec(s, form)
+    r.run(1)                                  # a reference image to search against
+    u0 = r.u.clone()
+    tile, ms = px.autotune(r, trials=2)
+    assert tile in ((0, 1, 2, 4, 8) if form == 0 else (0, 1, 2)) and ms > 0
+    assert torch.equal(r.u, u0)               # the map is restored
+    # the tuned shape keeps parity: one iteration from the restored state vs the oracle's
+    u_start = u0.cpu().numpy()
+    r.run(1)
+    uo, *_ = oracle.iterate(s.frames, s.W, s.M, s.delta, u_start, s.ref_shape, s.window, 1)
+    same = np.all(np.abs(r.u.cpu().numpy() - uo) <= parity.U_TOL, axis=0)[s.M > 0]
+    assert same.mean() >= parity.ARGMIN_AGREE - 0.004, same.mean()
+    print("form", form, "tuned tile", tile, "ms", ms)

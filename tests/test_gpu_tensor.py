@@ -105,3 +105,21 @@ def test_tensor_form_deterministic(tscan, form):
     for k in (1, 2):
         assert np.array_equal(runs[0][0], runs[k][0])
         assert np.array_equal(runs[0][1], runs[k][1], equal_nan=True)
+
+
+@pytest.mark.parametrize("tile", [1, 2], ids=["4x32-4x64", "2x64-2x128"])
+def test_tensor_tile_shapes(tscan, tile):
+    """The other pixel-tile / candidate-chunk shapes of the tensor search (BF16) against the
+    oracle, on the scans with uncovered reference pixels."""
+    import parity
+    from gpu_util import gpu_update
+    s = tscan
+    inp, I32, w32 = _inputs(s, True)
+    ug_i, eg_i = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=False, form=1,
+                            tile=tile)
+    ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True, form=1,
+                            tile=tile)
+    pix = np.flatnonzero(s.M.ravel())
+    rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
+                              ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
+    print(s.name, "tile", tile, rep)
