@@ -37,7 +37,7 @@ KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/
 FORMS = {"fp32": 0, "bf16": 1, "tf32": 2}
 WORKLOADS = {"lens1d": (gen.config_lens1d, 1), "small": (gen.config_small, 0),
              "precision2d": (gen.config_precision2d, 2), "precision2d-256": (gen.config_precision2d, 2),
-             "precision2d-512": (gen.config_precision2d, 2)}
+             "precision2d-512": (gen.config_precision2d, 2), "batch64": (None, 3), "serve": (None, 4)}
 
 
 def make_workload(name, rank):
@@ -330,6 +330,121 @@ def pxst_arm(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def _host_scan(sc):
+    """A GPU-rendered scan as host arrays (for the oracle's timed sample)."""
+    from types import SimpleNamespace
+    return SimpleNamespace(name=sc.name, frames=sc.frames.cpu().numpy(), W=sc.W.cpu().numpy(), M=sc.M.cpu().numpy(),
+                           u_init=sc.u_init.cpu().numpy(), delta=sc.delta.cpu().numpy(), ref_shape=sc.ref_shape,
+                           window=sc.window)
+
+
+def batch_arm(args):
+    """The batched workload: 64 scans of uneven size (frames U[16, 400], sides U[128, 1024],
+    windows U{4..16}) iterated together; a step is one iteration of every scan, one graph
+    launch of pxst_batch_run. Tile shapes come from the autotuner."""
+    import torch
+    import gen.gpu as gg
+    import paper_2003_12726_gb300 as px
+    form = FORMS[args.form]
+    specs = gg.batch_specs(64)
+    scans = [gg.render(sp) for sp in specs]
+    torch.cuda.synchronize()
+    recs = [px.Reconstruction.from_device(sc.frames, sc.W, sc.M, sc.delta, sc.u_init, sc.ref_shape, sc.window,
+                                          form=form) for sc in scans]
+    ev_step = sum(sc.evals for sc in scans)
+    t_plan = time.time()
+    b = px.Batch(recs, n_iter=1, n_branches=args.branches, autotune=True)
+    t_plan = time.time() - t_plan
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    for r in recs:
+        code, bits = px.get_status(r.ws)
+        if code != 0:
+            raise RuntimeError(f"device status {code} bits {bits}")
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    ms = e0.elapsed_time(e1)
+    sampler.stop()
+    tiles = {}
+    for r in recs:
+        tiles[r.opts.tile] = tiles.get(r.opts.tile, 0) + 1
+    cpu = None
+    if not args.no_cpu_baseline:
+        small = min(range(len(scans)), key=lambda k: scans[k].evals)
+        rate, rows, sec, threads = cpu_sample(_host_scan(scans[small]), target_s=args.cpu_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{rows} detector rows of scan {scans[small].name}: make_object_map + update_pixel_map "
+                         f"of the stripe, {sec:.1f} s"}
+    line = {"metric": METRIC, "value": ev_step / (ms / 1e3) * args.steps, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form],
+            "data": "synthetic (rendered on the GPU)",
+            "config": {"workload": "batch-64-scans", "scans": len(scans),
+                       "frames_range": [min(s.frames.shape[0] for s in scans), max(s.frames.shape[0] for s in scans)],
+                       "side_range": [min(s.frames.shape[1] for s in scans), max(s.frames.shape[1] for s in scans)],
+                       "window_range": [min(s.window[0] for s in scans), max(s.window[0] for s in scans)],
+                       "form": args.form, "evals_per_step": ev_step, "branches": args.branches,
+                       "tiles_chosen": {str(k): v for k, v in sorted(tiles.items())}, "plan_s": t_plan,
+                       "parallelism": "one graph launch per step",
+                       "l2": f"inputs larger than L2 (frames {sum(s.frames.numel() for s in scans) * 4 / 1e9:.1f} GB)"},
+            "scan_iterations_per_s": len(scans) * args.steps / (ms / 1e3),
+            "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps,
+            "clocks": sampler.summary(t_wall0 - 0.2, t_wall1 + 0.2)}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+def serve_arm(args):
+    """The served workload: a Poisson stream of scans (sizes log-uniform between the small
+    configuration and the 2-D precision scan, 1-D or 2-D), 10 iterations each, through the
+    continuous-batching server with admission by device memory."""
+    import torch
+    import gen.gpu as gg
+    import paper_2003_12726_gb300 as px
+    from paper_2003_12726_gb300.serve import Request, Server, estimate_bytes, poisson_arrivals
+    form = FORMS[args.form]
+    specs = gg.serve_specs(args.requests)
+    arr = poisson_arrivals(len(specs), args.rate, seed=gen.BASE_SEED + 44)
+
+    def reqs(sp_list, times):
+        out = []
+        for k, (sp, t) in enumerate(zip(sp_list, times)):
+            dims, wnd = gg.spec_dims(sp)
+            out.append(Request(rid=k, arrival=float(t), make=(lambda sp=sp: gg.render(sp)),
+                               est_bytes=estimate_bytes(dims, wnd, form), n_iter=10, form=form))
+        return out
+    server = Server(mem_budget=int(args.mem_gb * (1 << 30)), n_streams=8, max_active=32)
+    server.run(reqs(specs[:8], [0.0] * 8), realtime=False)          # warm-up
+    sampler = ClockSampler(0)
+    t_wall0 = time.time()
+    R = reqs(specs, arr)
+    st = server.run(R, realtime=True)
+    t_wall1 = time.time()
+    sampler.stop()
+    line = {"metric": METRIC, "value": st["scans_per_s"], "unit": "scans/s", "n_gpus": 1, "steps": len(R),
+            "warmup": 8, "ms_per_step": 1e3 / st["scans_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form],
+            "data": "synthetic (rendered on the GPU at admission)",
+            "config": {"workload": f"serve-{len(R)}-scans", "rate_per_s": args.rate, "iterations": 10,
+                       "form": args.form, "mem_budget_gb": args.mem_gb, "streams": 8, "max_active": 32,
+                       "parallelism": "continuous batching over streams"},
+            "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},
+            "evals_per_s": st["evals_per_s"], "span_s": st["span_s"], "peak_active": st["peak_active"],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "clocks": sampler.summary(t_wall0, t_wall1)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,13 +458,23 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")
+    ap.add_argument("--requests", type=int, default=500, help="serve: number of scans")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--mem-gb", type=float, default=96.0, help="serve: device memory budget")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference" and args.workload in ("batch64", "serve"):
+        ap.error("the reference arm times the oracle on the single-scan workloads")
     if args.impl == "reference":
         reference_arm(args, rank, world)
+    elif args.workload == "batch64":
+        batch_arm(args)
+    elif args.workload == "serve":
+        serve_arm(args)
     else:
         pxst_arm(args, rank, world, local_rank)
 

@@ -320,6 +320,34 @@ class Reconstruction:
         self.ws = workspace(self.dims, self.opts, dev)
         self._pinned = None
 
+    @classmethod
+    def from_device(cls, frames, W, M, delta, u, ref_shape, window, quadratic=True, form=FORM_FP32, tile=0):
+        """State around inputs already on the device (the tensors are used as they are; u is
+        cloned, so the caller's initial map is kept)."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        n, ny, nx = (int(v) for v in frames.shape)
+        self.dims = Dims(n, ny, nx, int(ref_shape[0]), int(ref_shape[1]))
+        self.opts = Options(int(window[0]), int(window[1]), bool(quadratic), int(form), tile=int(tile))
+        dev = frames.device
+        _check(frames, torch.float32, (n, ny, nx), "frames")
+        _check(W, torch.float32, (ny, nx), "W")
+        _check(M, torch.uint8, (ny, nx), "M")
+        _check(delta, torch.float64, (n, 2), "delta")
+        _check(u, torch.float64, (2, ny, nx), "u")
+        self.frames, self.W, self.M, self.delta, self.u = frames, W, M, delta, u.clone()
+        self.I_ref = torch.zeros(tuple(int(v) for v in ref_shape), dtype=torch.float32, device=dev)
+        self.w = torch.zeros_like(self.I_ref)
+        self.err = torch.zeros((ny, nx), dtype=torch.float32, device=dev)
+        self.ws = workspace(self.dims, self.opts, dev)
+        self._pinned = None
+        return self
+
+    def device_bytes(self):
+        """Bytes of device memory this scan holds (inputs, state and workspace)."""
+        ts = (self.frames, self.W, self.M, self.delta, self.u, self.I_ref, self.w, self.err, self.ws)
+        return sum(t.numel() * t.element_size() for t in ts)
+
     def run(self, n_iter, stream=None):
         iterate(self.dims, self.opts, n_iter, self.frames, self.W, self.M, self.delta, self.u,
                 self.I_ref, self.w, self.err, self.ws, stream)
