@@ -37,7 +37,8 @@ KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/
 FORMS = {"fp32": 0, "bf16": 1, "tf32": 2}
 WORKLOADS = {"lens1d": (gen.config_lens1d, 1), "small": (gen.config_small, 0),
              "precision2d": (gen.config_precision2d, 2), "precision2d-256": (gen.config_precision2d, 2),
-             "precision2d-512": (gen.config_precision2d, 2), "batch64": (None, 3), "serve": (None, 4)}
+             "precision2d-512": (gen.config_precision2d, 2), "lens1d-256": (gen.config_lens1d, 1),
+             "batch64": (None, 3), "serve": (None, 4)}
 
 
 def make_workload(name, rank):
@@ -49,6 +50,8 @@ def make_workload(name, rank):
         return fn(det=256, ref=400, seed=seed)
     if name == "precision2d-512":        # 512 x 512: frames (420 MB) still larger than L2 (profiling)
         return fn(det=512, ref=680, seed=seed)
+    if name == "lens1d-256":             # 256 rows of the lens scan: frames (190 MB) larger than L2 (profiling)
+        return fn(ny=256, seed=seed)
     return fn(seed=seed)
 
 
@@ -208,6 +211,14 @@ def pxst_arm(args, rank, world, local_rank):
     rec = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, form=form)
     u0 = rec.u.clone()
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_autotune:
+        # the tile shape the autotuner picks on this scan (one iteration first, so that the
+        # search runs against a reference image); the map is restored afterwards
+        rec.run(1)
+        tile, tms = px.autotune(rec, trials=3)
+        rec.u.copy_(u0)
+        tuned = {"tile": tile, "update_ms": tms}
     sampler = ClockSampler(local_rank) if rank == 0 else None
     for _ in range(args.warmup):
         rec.run(1)
@@ -317,7 +328,7 @@ def pxst_arm(args, rank, world, local_rank):
             "config": {"workload": s.name, "frames": int(s.frames.shape[0]),
                        "detector": list(s.frames.shape[1:]), "window": list(s.window),
                        "reference": list(s.ref_shape), "form": args.form, "quadratic": True,
-                       "evals_per_step": ev_step, "parallelism": f"replicas{world}",
+                       "evals_per_step": ev_step, "parallelism": f"replicas{world}", "autotuned": tuned,
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -459,6 +470,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the automatic tile shape")
     ap.add_argument("--requests", type=int, default=500, help="serve: number of scans")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--mem-gb", type=float, default=96.0, help="serve: device memory budget")
