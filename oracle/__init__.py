@@ -54,6 +54,9 @@ def _bind(L):
     L.pxst_oracle_update_pixels.argtypes = [i32] * 8 + [P] * 7 + [P, i64, P, P, i32]
     L.pxst_oracle_iterate.argtypes = [i32] * 9 + [P] * 7 + [P, i32]
     L.pxst_oracle_reference_terms.argtypes = [i32] * 3 + [P] * 5 + [i32]
+    L.pxst_oracle_calc_error.argtypes = [i32] * 5 + [P] * 11
+    L.pxst_oracle_frame_window.argtypes = [i32] * 7 + [P] * 7 + [i32, P]
+    L.pxst_oracle_update_translations.argtypes = [i32] * 8 + [P] * 9
     return L
 
 
@@ -198,3 +201,46 @@ def reference_terms(Iref, w, delta, threads=None, L=None):
     (L or lib()).pxst_oracle_reference_terms(delta.shape[0], Ry, Rx, _p(Iref), _p(w), _p(delta),
                                              _p(T), _p(nv), int(threads or default_threads()))
     return T, nv
+
+
+def calc_error(frames, W, M, Iref, w, u, delta, L=None):
+    """Figures of merit (section "Calculate figures of merit"): (pixel error [ny][nx] (NaN
+    where M = 0), frame error [N], total error, reference-plane error [Ry][Rx])."""
+    frames, W, M, Iref, w, u, delta = (_f32(frames), _f32(W), _u8(M), _f64(Iref), _f64(w), _f64(u),
+                                       _f64(delta))
+    N, ny, nx = frames.shape
+    Ry, Rx = Iref.shape
+    pe = np.empty((ny, nx))
+    fe = np.empty(N)
+    tot = np.zeros(1)
+    re = np.empty((Ry, Rx))
+    (L or lib()).pxst_oracle_calc_error(N, ny, nx, Ry, Rx, _p(frames), _p(W), _p(M), _p(Iref), _p(w), _p(u),
+                                        _p(delta), _p(pe), _p(fe), _p(tot), _p(re))
+    return pe, fe, float(tot[0]), re
+
+
+def frame_window(frames, W, M, Iref, w, u, delta, twindow, n, L=None):
+    """Error of frame n over the window of integer shifts of its translation."""
+    frames, W, M, Iref, w, u, delta = (_f32(frames), _f32(W), _u8(M), _f64(Iref), _f64(w), _f64(u),
+                                       _f64(delta))
+    N, ny, nx = frames.shape
+    Ty, Tx = twindow
+    e = np.empty((2 * Ty + 1, 2 * Tx + 1))
+    (L or lib()).pxst_oracle_frame_window(N, ny, nx, Iref.shape[0], Iref.shape[1], Ty, Tx, _p(frames), _p(W),
+                                          _p(M), _p(Iref), _p(w), _p(u), _p(delta), int(n), _p(e))
+    return e
+
+
+def update_translations(frames, W, M, Iref, w, u, delta, twindow, quadratic=True, L=None):
+    """Section "Update translations": (new translations [N][2], each frame's error at its
+    argmin [N])."""
+    frames, W, M, Iref, w, u, delta = (_f32(frames), _f32(W), _u8(M), _f64(Iref), _f64(w), _f64(u),
+                                       _f64(delta))
+    N, ny, nx = frames.shape
+    Ty, Tx = twindow
+    d_out = np.empty((N, 2))
+    err = np.empty(N)
+    (L or lib()).pxst_oracle_update_translations(N, ny, nx, Iref.shape[0], Iref.shape[1], Ty, Tx,
+                                                 int(bool(quadratic)), _p(frames), _p(W), _p(M), _p(Iref),
+                                                 _p(w), _p(u), _p(delta), _p(d_out), _p(err))
+    return d_out, err

@@ -15,7 +15,13 @@
  *   - update_pixel_map, the "Update pixel mapping" pseudo code: brute-force search of
  *     error/var over an integer window centred on the current u, argmin, and the
  *     optional 3x3 paraboloid ("quadratic_refinement") for sub-pixel precision;
- *   - iterate: steps (i) and (ii) of the main loop, repeated.
+ *   - iterate: steps (i) and (ii) of the main loop, repeated;
+ *   - calc_error, section "Calculate figures of merit": the per-pixel, per-frame error
+ *     term of Eq. 1 and its sums over frames (pixel error), pixels (frame error), both
+ *     (total error) and its map onto the reference plane;
+ *   - update_translations, section "Update translations": the error of Eq. 1 summed over
+ *     pixels for integer shifts of one frame's translation, argmin and the same 3x3
+ *     paraboloid.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   R1  the bilinear weight multiplies both the M*W*I term and the M*W^2 term;
@@ -36,6 +42,21 @@
  *       edge or +inf) or the Hessian is not positive definite, each axis is fitted alone
  *       by a 3-point parabola (0 shift if a point is missing or the curvature is <= 0);
  *       a shift larger than 1 on an axis is set to 0 on that axis.
+ *   R11 figures of merit: eps[n,x] = (I_n(x) - W(x) R_n)^2 / var(x), R_n read at
+ *       u(x) - Delta_n by the gather of R6 (u fractional); var(x) = sum over the frames
+ *       valid at x of (I_n(x) - W(x))^2 (Eq. 1's sigma^2 read as in R5-R7, at the pixel's
+ *       own map); frames invalid at x add nothing; var == 0 => eps = the squared residual;
+ *       M = 0 pixels add nothing and their pixel error is NaN. Pixel error = sum over n,
+ *       frame error = sum over x, total = sum over both.
+ *   R12 reference-plane error: eps[n,x] scattered to u(x) - Delta_n with the bilinear
+ *       weights of make_object_map (corners off the grid dropped), divided by the sum of
+ *       the weights that landed; 0 where none did.
+ *   R13 update_translations: candidates Delta_n + (a, b), a in [-Ty, Ty], b in [-Tx, Tx]
+ *       (integer shifts of the image); e_n(a, b) = the mean, over the pixels with M = 1,
+ *       var(x) > 0 (var of R11 with the current translations) and a valid read at
+ *       u(x) - Delta_n - (a, b), of (I_n(x) - W(x) R)^2 / var(x) (a mean, not a sum, so
+ *       that shifting pixels off the reference is not rewarded); +inf with no such pixel;
+ *       argmin as R8, the fit as R10; Delta_n <- Delta_n + (a*, b*) + fit.
  *
  * Array conventions: frames float32 [N][ny][nx]; W float32 [ny][nx]; M uint8 [ny][nx];
  * u float64 [2][ny][nx] (u[0] rows, u[1] columns, reference-pixel units);
@@ -382,4 +403,157 @@ void pxst_oracle_iterate(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx, 
                                      w, delta, u_inout, u_inout, err_out, 0, ny, nthreads);
     }
     /* I_ref and w are those built in the last iteration's step (i) */
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* figures of merit (section "Calculate figures of merit")                           */
+/* ---------------------------------------------------------------------------------- */
+
+/* var(x) of R11 for pixel p at its own map with translations delta (-1 if M = 0). */
+static double pixel_var(int N, int64_t P, int Ry, int Rx, const float *frames, const float *W,
+                        const uint8_t *M, const double *Iref, const double *w, const double *u,
+                        const double *delta, int64_t p)
+{
+    if (!M[p]) return -1.0;
+    const double Wv = (double)W[p];
+    double s2 = 0.0;
+    for (int n = 0; n < N; ++n) {
+        double R;
+        if (!pxst_oracle_gather(Iref, w, Ry, Rx, u[p] - delta[2 * n], u[P + p] - delta[2 * n + 1], &R)) continue;
+        const double v = (double)frames[(int64_t)n * P + p] - Wv;
+        s2 += v * v;
+    }
+    return s2;
+}
+
+/* pixel_err [ny][nx], frame_err [N], *total and ref_err [Ry][Rx] (R11, R12). Serial: the
+ * sums run in pixel order, frame order inside. */
+void pxst_oracle_calc_error(int N, int ny, int nx, int Ry, int Rx, const float *frames, const float *W,
+                            const uint8_t *M, const double *Iref, const double *w, const double *u,
+                            const double *delta, double *pixel_err, double *frame_err, double *total,
+                            double *ref_err)
+{
+    const int64_t P = (int64_t)ny * nx, R = (int64_t)Ry * Rx;
+    double *num = (double *)calloc((size_t)R, sizeof(double));
+    double *den = (double *)calloc((size_t)R, sizeof(double));
+    for (int n = 0; n < N; ++n) frame_err[n] = 0.0;
+    double tot = 0.0;
+    for (int64_t p = 0; p < P; ++p) {
+        const double var = pixel_var(N, P, Ry, Rx, frames, W, M, Iref, w, u, delta, p);
+        if (var < 0.0) {
+            pixel_err[p] = NAN;
+            continue;
+        }
+        const double Wv = (double)W[p];
+        double pe = 0.0;
+        for (int n = 0; n < N; ++n) {
+            const double q0 = u[p] - delta[2 * n], q1 = u[P + p] - delta[2 * n + 1];
+            double Rv;
+            if (!pxst_oracle_gather(Iref, w, Ry, Rx, q0, q1, &Rv)) continue;
+            const double d = (double)frames[(int64_t)n * P + p] - Wv * Rv;
+            const double eps = var > 0.0 ? d * d / var : d * d;
+            pe += eps;
+            frame_err[n] += eps;
+            int64_t i0, j0;
+            double wt[4];
+            pxst_oracle_bilinear(q0, q1, &i0, &j0, wt);
+            for (int k = 0; k < 4; ++k) {
+                const int64_t ii = i0 + (k >> 1), jj = j0 + (k & 1);
+                if (ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;
+                num[ii * Rx + jj] += wt[k] * eps;
+                den[ii * Rx + jj] += wt[k];
+            }
+        }
+        pixel_err[p] = pe;
+        tot += pe;
+    }
+    *total = tot;
+    for (int64_t c = 0; c < R; ++c) ref_err[c] = den[c] > 0.0 ? num[c] / den[c] : 0.0;
+    free(num);
+    free(den);
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* update_translations (section "Update translations")                               */
+/* ---------------------------------------------------------------------------------- */
+
+/* The error window of frame n: e[(a+Ty)*(2Tx+1) + (b+Tx)] (R13), given var[p]. */
+static void frame_window(int N, int ny, int nx, int Ry, int Rx, int Ty, int Tx, const float *frames,
+                         const float *W, const uint8_t *M, const double *Iref, const double *w,
+                         const double *u, const double *delta, const double *var, int n, double *e)
+{
+    const int64_t P = (int64_t)ny * nx;
+    const int wx = 2 * Tx + 1;
+    (void)N;
+    for (int a = -Ty; a <= Ty; ++a) {
+        for (int b = -Tx; b <= Tx; ++b) {
+            double sum = 0.0;
+            int64_t cnt = 0;
+            for (int64_t p = 0; p < P; ++p) {
+                if (!M[p] || !(var[p] > 0.0)) continue;
+                double Rv;
+                const double q0 = u[p] - (delta[2 * n] + a), q1 = u[P + p] - (delta[2 * n + 1] + b);
+                if (!pxst_oracle_gather(Iref, w, Ry, Rx, q0, q1, &Rv)) continue;
+                const double d = (double)frames[(int64_t)n * P + p] - (double)W[p] * Rv;
+                sum += d * d / var[p];
+                cnt += 1;
+            }
+            e[(a + Ty) * wx + (b + Tx)] = cnt > 0 ? sum / (double)cnt : INFINITY;
+        }
+    }
+}
+
+/* Error window of one frame (for tests): e has (2Ty+1)(2Tx+1) entries. */
+void pxst_oracle_frame_window(int N, int ny, int nx, int Ry, int Rx, int Ty, int Tx, const float *frames,
+                              const float *W, const uint8_t *M, const double *Iref, const double *w,
+                              const double *u, const double *delta, int n, double *e)
+{
+    const int64_t P = (int64_t)ny * nx;
+    double *var = (double *)malloc(sizeof(double) * (size_t)P);
+    for (int64_t p = 0; p < P; ++p) var[p] = pixel_var(N, P, Ry, Rx, frames, W, M, Iref, w, u, delta, p);
+    frame_window(N, ny, nx, Ry, Rx, Ty, Tx, frames, W, M, Iref, w, u, delta, var, n, e);
+    free(var);
+}
+
+/* New translations delta_out [N][2] and each frame's error at its argmin err_out [N]. */
+void pxst_oracle_update_translations(int N, int ny, int nx, int Ry, int Rx, int Ty, int Tx, int quadratic,
+                                     const float *frames, const float *W, const uint8_t *M, const double *Iref,
+                                     const double *w, const double *u, const double *delta_in,
+                                     double *delta_out, double *err_out)
+{
+    const int64_t P = (int64_t)ny * nx;
+    const int wy = 2 * Ty + 1, wx = 2 * Tx + 1;
+    double *var = (double *)malloc(sizeof(double) * (size_t)P);
+    for (int64_t p = 0; p < P; ++p) var[p] = pixel_var(N, P, Ry, Rx, frames, W, M, Iref, w, u, delta_in, p);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int n = 0; n < N; ++n) {
+        double *e = (double *)malloc(sizeof(double) * (size_t)(wy * wx));
+        frame_window(N, ny, nx, Ry, Rx, Ty, Tx, frames, W, M, Iref, w, u, delta_in, var, n, e);
+        int best = -1;
+        double be = INFINITY;
+        for (int k = 0; k < wy * wx; ++k)
+            if (e[k] < be) {                                  /* R8: strict <, first minimum */
+                be = e[k];
+                best = k;
+            }
+        delta_out[2 * n] = delta_in[2 * n];
+        delta_out[2 * n + 1] = delta_in[2 * n + 1];
+        err_out[n] = be;
+        if (best >= 0) {
+            const int ia = best / wx, ib = best % wx;
+            double da = 0.0, db = 0.0;
+            if (quadratic) {
+                double f[9];
+                for (int q = 0; q < 9; ++q) {
+                    const int a2 = ia + q / 3 - 1, b2 = ib + q % 3 - 1;
+                    f[q] = (a2 < 0 || a2 >= wy || b2 < 0 || b2 >= wx) ? INFINITY : e[a2 * wx + b2];
+                }
+                pxst_oracle_quadratic_fit(f, &da, &db);
+            }
+            delta_out[2 * n] = delta_in[2 * n] + (double)(ia - Ty) + da;
+            delta_out[2 * n + 1] = delta_in[2 * n + 1] + (double)(ib - Tx) + db;
+        }
+        free(e);
+    }
+    free(var);
 }

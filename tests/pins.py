@@ -354,4 +354,124 @@ def pin_truth_recovery(L):
     assert float(np.abs(d).max()) < 0.05, np.abs(d).max()
 
 
+# ---------------------------------------------------------------------------------------
+# figures of merit (section "Calculate figures of merit")
+# ---------------------------------------------------------------------------------------
+
+def pin_error_exact_zero(L):
+    """Integer map and translations with frames W * I_ref exactly: every error term is 0,
+    so the pixel, frame, total and reference-plane errors are exactly 0 (M = 0: NaN)."""
+    rng = np.random.default_rng(31)
+    frames, W, M, u, delta, Iref = _integer_scan(rng)
+    pe, fe, tot, re = oracle.calc_error(frames, W, M, Iref, np.ones(Iref.shape), u, delta, L=L)
+    assert np.all(pe[M > 0] == 0.0) and np.all(np.isnan(pe[M == 0]))
+    assert np.all(fe == 0.0) and tot == 0.0 and np.all(re == 0.0)
+
+
+def pin_error_matches_search_error(L):
+    """At an integer map the pixel error is the update step's normalised error of the
+    candidate at the window centre (pinned separately), and the sums agree: sum of pixel
+    errors = sum of frame errors = total."""
+    rng = np.random.default_rng(32)
+    frames, W, M, u, delta, Iref = _integer_scan(rng)
+    frames = frames * np.float32(1.0) + rng.uniform(-0.2, 0.2, frames.shape).astype(np.float32)
+    w = np.ones(Iref.shape)
+    w[18:22, 20:25] = 0.0                                    # a hole: some frames invalid
+    pe, fe, tot, re = oracle.calc_error(frames, W, M, Iref, w, u, delta, L=L)
+    ny, nx = M.shape
+    checked = 0
+    for p in range(ny * nx):
+        if not M.flat[p]:
+            continue
+        e, _ = oracle.pixel_window(frames, W, M, Iref, w, delta, u, (0, 0), p, L=L)
+        if np.isfinite(e[0, 0]):
+            np.testing.assert_allclose(pe.flat[p], e[0, 0], rtol=1e-12, atol=1e-15)
+            checked += 1
+    assert checked > 50
+    np.testing.assert_allclose(np.nansum(pe), tot, rtol=1e-12)
+    np.testing.assert_allclose(fe.sum(), tot, rtol=1e-12)
+
+
+def pin_error_reference_plane_weights(L):
+    """Fully covered reference, all reads inside the grid: every frame of every pixel is
+    valid, so the weights landing on each reference pixel are make_object_map's w for unit
+    frames and whitefield (pinned separately); the reference-plane error weighted by them
+    sums to the total error."""
+    rng = np.random.default_rng(33)
+    frames, W, M, u, delta, R = _fractional_scan(rng)
+    Iref = rng.uniform(0.5, 1.5, R)
+    w = np.ones(R)
+    pe, fe, tot, re = oracle.calc_error(frames, W, M, Iref, w, u, delta, L=L)
+    ones = np.ones_like(frames)
+    _, den = oracle.make_object_map(ones, np.ones_like(W), M, u, delta, R, L=L)
+    np.testing.assert_allclose((re * den).sum(), tot, rtol=1e-11)
+    assert np.all(re[den == 0] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------
+# update_translations (section "Update translations")
+# ---------------------------------------------------------------------------------------
+
+def pin_translations_exact_integer(L):
+    """Frames W * I_ref(u - Delta) exactly, integer everything, I_ref random: the error is 0
+    at the true translation and positive elsewhere, so starting from integer offsets inside
+    the window every translation is recovered exactly (no fit)."""
+    rng = np.random.default_rng(34)
+    frames, W, M, u, delta, Iref = _integer_scan(rng, N=6)
+    start = delta + rng.integers(-2, 3, size=delta.shape)
+    got, err = oracle.update_translations(frames, W, M, Iref, np.ones(Iref.shape), u, start, (3, 3),
+                                          quadratic=False, L=L)
+    np.testing.assert_array_equal(got, delta)
+    assert np.all(err == 0.0)
+
+
+def pin_translations_window_by_indexing(L):
+    """A frame's error window for integer shifts, computed by plain array indexing: the mean
+    over good pixels of (I - W I_ref[u - Delta - t])^2 / var, var over the frames at the
+    current translations."""
+    rng = np.random.default_rng(35)
+    frames, W, M, u, delta, Iref = _integer_scan(rng, N=5)
+    frames = frames + rng.uniform(-0.3, 0.3, frames.shape).astype(np.float32)
+    Ry, Rx = Iref.shape
+    ui, uj = u[0].astype(int), u[1].astype(int)
+    F, Wd = frames.astype(np.float64), W.astype(np.float64)
+    var = np.zeros(M.shape)
+    for n in range(frames.shape[0]):
+        var += (F[n] - Wd) ** 2                           # every read is on the grid here
+    T = 2
+    for n in (0, 3):
+        e = oracle.frame_window(frames, W, M, Iref, np.ones(Iref.shape), u, delta, (T, T), n, L=L)
+        for a in range(-T, T + 1):
+            for b in range(-T, T + 1):
+                qi, qj = ui - int(delta[n, 0]) - a, uj - int(delta[n, 1]) - b
+                ok = (M > 0) & (qi >= 0) & (qi < Ry) & (qj >= 0) & (qj < Rx) & (var > 0)
+                R = Iref[np.clip(qi, 0, Ry - 1), np.clip(qj, 0, Rx - 1)]
+                want = (((F[n] - Wd * R) ** 2) / np.where(var > 0, var, 1.0))[ok].mean()
+                np.testing.assert_allclose(e[a + T, b + T], want, rtol=1e-12)
+
+
+def pin_translations_linear_field_exact(L):
+    """Reference linear along the columns and translations along the columns only: a
+    frame's error is exactly quadratic in the column shift, so the refined translation
+    equals the truth from a fractional start."""
+    rng = np.random.default_rng(36)
+    N, ny, nx, R = 5, 6, 9, (30, 70)
+    alpha, beta = 0.4, 0.011
+    Iref = alpha + beta * np.broadcast_to(np.arange(R[1], dtype=np.float64), R)
+    u = np.empty((2, ny, nx))
+    u[0] = 10 + np.arange(ny)[:, None]
+    u[1] = 20 + 1.3 * np.arange(nx)[None, :] + rng.uniform(-0.45, 0.45, (ny, nx))
+    delta = np.stack([np.zeros(N), rng.uniform(0, 9, N)], axis=1)
+    W = rng.uniform(50, 150, (ny, nx))
+    frames = np.stack([W * (alpha + beta * (u[1] - delta[n, 1])) for n in range(N)]).astype(np.float64)
+    M = np.ones((ny, nx), np.uint8)
+    start = delta.copy()
+    start[:, 1] += rng.uniform(-1.4, 1.4, N)
+    # float32 frames: the truth of the rounded data differs from delta by ~1e-6
+    got, err = oracle.update_translations(frames.astype(np.float32), W.astype(np.float32), M, Iref, np.ones(R), u,
+                                          start, (0, 3), quadratic=True, L=L)
+    np.testing.assert_array_equal(got[:, 0], delta[:, 0])
+    np.testing.assert_allclose(got[:, 1], delta[:, 1], atol=5e-5)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

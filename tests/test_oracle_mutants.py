@@ -44,6 +44,18 @@ MUTANTS = {
     "refterms_not_squared": ("t += R * R;", "t += R;"),
     "invalid_frame_counted": ("if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) continue;",
                               "if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) R = 0.0;"),
+    "pixel_var_dropped": ("s2 += v * v;", "s2 += 1.0;"),
+    "error_not_normalised": ("const double eps = var > 0.0 ? d * d / var : d * d;", "const double eps = d * d;"),
+    "error_plane_unnormalised": ("ref_err[c] = den[c] > 0.0 ? num[c] / den[c] : 0.0;",
+                                 "ref_err[c] = den[c] > 0.0 ? num[c] : 0.0;"),
+    "error_plane_adds_delta": ("const double q0 = u[p] - delta[2 * n], q1 = u[P + p] - delta[2 * n + 1];",
+                               "const double q0 = u[p] + delta[2 * n], q1 = u[P + p] - delta[2 * n + 1];"),
+    "translation_shift_sign": ("const double q0 = u[p] - (delta[2 * n] + a), q1 = u[P + p] - (delta[2 * n + 1] + b);",
+                               "const double q0 = u[p] - (delta[2 * n] - a), q1 = u[P + p] - (delta[2 * n + 1] + b);"),
+    "translation_sum_not_mean": ("e[(a + Ty) * wx + (b + Tx)] = cnt > 0 ? sum / (double)cnt : INFINITY;",
+                                 "e[(a + Ty) * wx + (b + Tx)] = cnt > 0 ? sum : INFINITY;"),
+    "translation_update_sign": ("delta_out[2 * n + 1] = delta_in[2 * n + 1] + (double)(ib - Tx) + db;",
+                                "delta_out[2 * n + 1] = delta_in[2 * n + 1] - (double)(ib - Tx) + db;"),
 }
 
 
