@@ -227,6 +227,29 @@ def pxst_arm(args, rank, world, local_rank):
     if code != 0:
         raise RuntimeError(f"device status {code} bits {bits}")
 
+    # the paper's full iteration: + update translations (iii) and figures of merit (iv)
+    full = args.loop == "full"
+    if full:
+        tw = (0, 2) if s.window[0] <= 1 else (1, 1)
+        delta0 = rec.delta.clone()
+        pe_t = torch.empty((rec.dims.ny, rec.dims.nx), dtype=torch.float32, device="cuda")
+        fe_t = torch.empty(rec.dims.n_frames, dtype=torch.float64, device="cuda")
+        tot_t = torch.empty(1, dtype=torch.float64, device="cuda")
+        re_t = torch.empty(tuple(s.ref_shape), dtype=torch.float32, device="cuda")
+
+    def step():
+        rec.run(1)
+        if full:
+            px.update_translations(rec.dims, tw, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta,
+                                   rec.ws, fe_t)
+            px.calc_error(rec.dims, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta, rec.ws, pe_t,
+                          fe_t, tot_t, re_t)
+    if full:
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        rec.delta.copy_(delta0)
+
     # ---- device-resident timed region -------------------------------------------------
     rec.u.copy_(u0)
     px.timing_enable(True)
@@ -237,12 +260,14 @@ def pxst_arm(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        rec.run(1)
+        step()
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t_wall1 = time.time()
+    if full:
+        rec.delta.copy_(delta0)
     ms = e0.elapsed_time(e1)
     ktimes = px.timing_read()
     px.timing_enable(False)
@@ -303,10 +328,22 @@ def pxst_arm(args, rank, world, local_rank):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
+    elif name == "update_translations":
+        # per pixel, frame and shift: the masked bilinear read (8 flop), d = I - W R (2),
+        # d^2 / var (2): 12 flop; plus the per-pixel variance pass (one read per frame)
+        ntr = (2 * tw[0] + 1) * (2 * tw[1] + 1)
+        flop = 12.0 * int(s.M.sum()) * s.frames.shape[0] * ntr
+        achieved = flop / (avg_ms * 1e-3) / 1e12
+        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
     else:
         P = s.frames.shape[1] * s.frames.shape[2]
         R = s.ref_shape[0] * s.ref_shape[1]
         nbytes = 4.0 * s.frames.shape[0] * P + 21.0 * P + 32.0 * R
+        if name == "calc_error":              # frames read twice (variance, then the error terms)
+            nbytes = 8.0 * s.frames.shape[0] * P + 21.0 * P + 4.0 * P + 8.0 * s.frames.shape[0] + 20.0 * R
         achieved = nbytes / (avg_ms * 1e-3) / 1e9
         peak = float(pk["hbm_gbs"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -329,6 +366,8 @@ def pxst_arm(args, rank, world, local_rank):
                        "detector": list(s.frames.shape[1:]), "window": list(s.window),
                        "reference": list(s.ref_shape), "form": args.form, "quadratic": True,
                        "evals_per_step": ev_step, "parallelism": f"replicas{world}", "autotuned": tuned,
+                       "loop": "full: reference image, pixel map, translations (window "
+                               f"{list(tw)}), figures of merit" if full else "reference image, pixel map",
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -471,6 +510,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic tile shape")
+    ap.add_argument("--loop", default="main", choices=["main", "full"],
+                    help="main: steps (i)+(ii) of the main loop; full: + translations and figures of merit")
     ap.add_argument("--requests", type=int, default=500, help="serve: number of scans")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--mem-gb", type=float, default=96.0, help="serve: device memory budget")

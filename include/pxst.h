@@ -187,7 +187,9 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 #define PXST_K_GTABLE     7   /* tensor forms: shifted reference per frame, T~ and n_valid */
 #define PXST_K_TSEARCH    8   /* tensor forms: tensor-core ranking of every candidate */
 #define PXST_K_RESCORE    9   /* tensor forms: exact FP32 evaluation of the best candidates */
-#define PXST_K_COUNT      10
+#define PXST_K_ERROR      10  /* calc_error (with the per-pixel variance) */
+#define PXST_K_TRANS      11  /* update_translations (with the per-pixel variance) */
+#define PXST_K_COUNT      12
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);
@@ -200,6 +202,34 @@ const char *pxst_kernel_name(int32_t k);
  * int) gets PXST_DEV_TIMEOUT if a wait ran out. Not part of the method: a self-check. */
 pxst_status pxst_tensor_check(int32_t form, int32_t K, const void *A, const void *B, float *D,
                               int32_t *status, void *stream);
+
+/* ---- Figures of merit and the translation update ------------------------------------------
+ * pxst_calc_error (section "Calculate figures of merit"): the error term of Eq. 1 at each pixel
+ * x and frame n, eps[n,x] = (I_n(x) - W(x) R_n)^2 / var(x), with R_n the masked renormalised
+ * bilinear read of I_ref at u(x) - Delta_n (u fractional), var(x) = sum over the frames valid
+ * at x of (I_n(x) - W(x))^2, frames invalid at x left out, eps = the squared residual where
+ * var = 0, pixels with M = 0 (or a non-finite map) left out. Outputs (device pointers, each
+ * may be NULL): pixel_err float [ny][nx] = sum over n (NaN where left out); frame_err double
+ * [N] = sum over x; total_err double [1] = sum over both; ref_err float [ref_ny][ref_nx] = eps
+ * scattered to u(x) - Delta_n with make_object_map's bilinear weights (corners off the grid
+ * dropped) divided by the weights that landed (0 where none). Sums are FP64 atomics:
+ * equal to rounding, not bitwise, from run to run. */
+pxst_status pxst_calc_error(const pxst_dims *dims, const float *frames, const float *W, const uint8_t *mask,
+                            const float *I_ref, const float *w, const double *u, const double *delta,
+                            float *pixel_err, double *frame_err, double *total_err, float *ref_err,
+                            void *workspace, size_t ws_bytes, void *stream);
+
+/* pxst_update_translations (section "Update translations"): for every frame n and integer
+ * shift (a, b), |a| <= win_y, |b| <= win_x (each at most 8, else PXST_ERR_ARG), the mean over
+ * the pixels with M = 1, var(x) > 0 (var as above, at the current translations) and a valid
+ * read at u(x) - Delta_n - (a, b) of (I_n(x) - W(x) R)^2 / var(x); the first minimum in
+ * row-major order; with quadratic = 1 the 3x3 paraboloid of update_pixel_map about it;
+ * delta_inout[n] += (a*, b*) + fit. frame_err (double [N], may be NULL) receives each frame's
+ * mean error at its minimum (+inf if no pixel was valid: the translation is kept). */
+pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32_t win_x, int32_t quadratic,
+                                     const float *frames, const float *W, const uint8_t *mask,
+                                     const float *I_ref, const float *w, const double *u, double *delta_inout,
+                                     double *frame_err, void *workspace, size_t ws_bytes, void *stream);
 
 /* ---- Batched form ------------------------------------------------------------------------
  * Many independent scans of uneven frame count, detector size and window, iterated by one

@@ -25,7 +25,8 @@ FORM_FP32 = 0
 FORM_BF16 = 1
 FORM_TF32 = 2
 KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms",
-           "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore"]
+           "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore", "calc_error",
+           "update_translations"]
 
 
 class PxstError(RuntimeError):
@@ -107,6 +108,10 @@ def lib():
         L.pxst_batch_destroy.restype = None
         L.pxst_autotune.argtypes = [S, i32, P, C.POINTER(i32), C.POINTER(C.c_float)]
         L.pxst_autotune.restype = i32
+        L.pxst_calc_error.argtypes = [D] + [P] * 12 + [sz, P]
+        L.pxst_calc_error.restype = i32
+        L.pxst_update_translations.argtypes = [D, i32, i32, i32] + [P] * 9 + [sz, P]
+        L.pxst_update_translations.restype = i32
         _lib = L
     return _lib
 
@@ -116,7 +121,7 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_iterate", "pxst_reference_terms", "pxst_get_status", "pxst_last_exact_count",
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
-            "pxst_batch_destroy", "pxst_autotune"]
+            "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -441,3 +446,44 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def calc_error(dims: Dims, frames, W, M, I_ref, w, u, delta, ws, pixel_err=None, frame_err=None, total=None,
+               ref_err=None, stream=None):
+    """pxst_calc_error (section "Calculate figures of merit"); the outputs that are given
+    (CUDA tensors: pixel_err float32 [ny][nx], frame_err float64 [N], total float64 [1],
+    ref_err float32 [Ry][Rx]) are filled."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    opt = lambda t, dt, shape, name: _check(t, dt, shape, name) if t is not None else None
+    _raise(lib().pxst_calc_error(C.byref(dims.c()), _check(frames, torch.float32, (N, ny, nx), "frames"),
+                                 _check(W, torch.float32, (ny, nx), "W"), _check(M, torch.uint8, (ny, nx), "M"),
+                                 _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+                                 _check(w, torch.float32, (Ry, Rx), "w"), _check(u, torch.float64, (2, ny, nx), "u"),
+                                 _check(delta, torch.float64, (N, 2), "delta"),
+                                 opt(pixel_err, torch.float32, (ny, nx), "pixel_err"),
+                                 opt(frame_err, torch.float64, (N,), "frame_err"),
+                                 opt(total, torch.float64, (1,), "total"),
+                                 opt(ref_err, torch.float32, (Ry, Rx), "ref_err"),
+                                 C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)), "calc_error")
+
+
+def update_translations(dims: Dims, twindow, frames, W, M, I_ref, w, u, delta, ws, frame_err=None,
+                        quadratic=True, stream=None):
+    """pxst_update_translations (section "Update translations"): delta (float64 [N][2], CUDA)
+    is updated in place; frame_err (float64 [N]) receives each frame's error at its minimum."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    _raise(lib().pxst_update_translations(C.byref(dims.c()), int(twindow[0]), int(twindow[1]),
+                                          1 if quadratic else 0,
+                                          _check(frames, torch.float32, (N, ny, nx), "frames"),
+                                          _check(W, torch.float32, (ny, nx), "W"),
+                                          _check(M, torch.uint8, (ny, nx), "M"),
+                                          _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+                                          _check(w, torch.float32, (Ry, Rx), "w"),
+                                          _check(u, torch.float64, (2, ny, nx), "u"),
+                                          _check(delta, torch.float64, (N, 2), "delta"),
+                                          _check(frame_err, torch.float64, (N,), "frame_err")
+                                          if frame_err is not None else None,
+                                          C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
+           "update_translations")

@@ -36,6 +36,9 @@ bool opts_ok(const pxst_options *o) {
 
 struct Ws {
     WsHeader *hdr;
+    float *var_px;
+    double *tacc_sum, *delta_tmp;
+    unsigned long long *tacc_cnt;
     FrameShift *shifts;
     int *exact_list;
     double *num, *den;
@@ -54,6 +57,10 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     if (ws_bytes < L.total) return PXST_ERR_NOMEM;
     char *b = static_cast<char *>(workspace);
     w.hdr = reinterpret_cast<WsHeader *>(b + L.header);
+    w.var_px = reinterpret_cast<float *>(b + L.var_px);
+    w.tacc_sum = reinterpret_cast<double *>(b + L.tacc_sum);
+    w.tacc_cnt = reinterpret_cast<unsigned long long *>(b + L.tacc_cnt);
+    w.delta_tmp = reinterpret_cast<double *>(b + L.delta_tmp);
     w.shifts = reinterpret_cast<FrameShift *>(b + L.shifts);
     w.exact_list = reinterpret_cast<int *>(b + L.exact_list);
     w.num = reinterpret_cast<double *>(b + L.num);
@@ -314,6 +321,49 @@ pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_
     return PXST_OK;
 }
 
+pxst_status pxst_calc_error(const pxst_dims *dims, const float *frames, const float *W, const uint8_t *mask,
+                            const float *I_ref, const float *w, const double *u, const double *delta,
+                            float *pixel_err, double *frame_err, double *total_err, float *ref_err,
+                            void *workspace, size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!frames || !W || !mask || !I_ref || !w || !u || !delta) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, PXST_FORM_FP32, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    Timed t(PXST_K_ERROR, s);
+    PXST_TRY(launch_pixvar(*dims, frames, W, mask, I_ref, w, u, delta, ws.shifts, ws.var_px, ws.hdr, s));
+    PXST_TRY(launch_calc_error(*dims, frames, W, mask, I_ref, w, u, delta, ws.shifts, ws.var_px, ws.hdr, pixel_err,
+                               frame_err, total_err, ref_err, ws.num, ws.den, s));
+    return PXST_OK;
+}
+
+pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32_t win_x, int32_t quadratic,
+                                     const float *frames, const float *W, const uint8_t *mask,
+                                     const float *I_ref, const float *w, const double *u, double *delta_inout,
+                                     double *frame_err, void *workspace, size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (win_y < 0 || win_x < 0 || win_y > 8 || win_x > 8 || (quadratic != 0 && quadratic != 1)) return PXST_ERR_ARG;
+    if (!frames || !W || !mask || !I_ref || !w || !u || !delta_inout) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, PXST_FORM_FP32, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta_inout, ws, s);
+    if (st != PXST_OK) return st;
+    Timed t(PXST_K_TRANS, s);
+    PXST_TRY(launch_pixvar(*dims, frames, W, mask, I_ref, w, u, delta_inout, ws.shifts, ws.var_px, ws.hdr, s));
+    // every frame's shifts are scored against the translations as they were on entry
+    PXST_TRY(launch_update_translations(*dims, win_y, win_x, quadratic, frames, W, mask, I_ref, w, u, delta_inout,
+                                        ws.shifts, ws.var_px, ws.hdr, ws.tacc_sum, ws.tacc_cnt, ws.delta_tmp,
+                                        frame_err, s));
+    PXST_TRY(cudaMemcpyAsync(delta_inout, ws.delta_tmp, sizeof(double) * 2 * dims->n_frames,
+                             cudaMemcpyDeviceToDevice, s));
+    return PXST_OK;
+}
+
 pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, const float *w,
                                  const double *delta, float *T, int32_t *n_valid,
                                  void *workspace, size_t ws_bytes, void *stream) {
@@ -399,6 +449,8 @@ const char *pxst_kernel_name(int32_t k) {
         case PXST_K_GTABLE: return "tensor_gtable";
         case PXST_K_TSEARCH: return "tensor_search";
         case PXST_K_RESCORE: return "upm_rescore";
+        case PXST_K_ERROR: return "calc_error";
+        case PXST_K_TRANS: return "update_translations";
         default: return "?";
     }
 }

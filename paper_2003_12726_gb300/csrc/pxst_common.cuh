@@ -32,10 +32,11 @@ static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 // Candidates per pixel kept by the tensor-core ranking (the rescore evaluates the first
 // 4 or all 8 of them exactly).
 constexpr int kTopK = 8;
+constexpr int kTransMax = 17 * 17;     // translation update: shifts within +-8 on each axis
 
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
-    size_t header, shifts, exact_list, num, den, u_save;
+    size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp;
     // precision forms only (zero size otherwise)
     size_t At, G, Tt, nvalid, Rm, cand, edge, keys;
     int Npad;
@@ -60,6 +61,10 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.num = off;        off += align256(sizeof(double) * R);
     L.den = off;        off += align256(sizeof(double) * R);
     L.u_save = off;     off += align256(sizeof(double) * 2 * P);   // the autotuner's copy of u
+    L.var_px = off;     off += align256(sizeof(float) * P);        // figures of merit: var(x)
+    L.tacc_sum = off;   off += align256(sizeof(double) * kTransMax * (size_t)d.n_frames);
+    L.tacc_cnt = off;   off += align256(sizeof(unsigned long long) * kTransMax * (size_t)d.n_frames);
+    L.delta_tmp = off;  off += align256(sizeof(double) * 2 * (size_t)d.n_frames);
     L.Npad = 0;
     L.At = L.G = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.keys = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
@@ -130,6 +135,21 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
                          const float *w, const FrameShift *shifts, WsHeader *hdr,
                          const int *exact_list, double *u, float *err_out, cudaStream_t stream);
 int search_max_frames();
+// figures of merit and the translation update (frames.cu)
+cudaError_t launch_pixvar(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
+                          const float *I_ref, const float *w, const double *u, const double *delta,
+                          const FrameShift *shifts, float *var, WsHeader *hdr, cudaStream_t s);
+cudaError_t launch_calc_error(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
+                              const float *I_ref, const float *w, const double *u, const double *delta,
+                              const FrameShift *shifts, const float *var, WsHeader *hdr, float *pixel_err,
+                              double *frame_err, double *total, float *ref_err, double *num, double *den,
+                              cudaStream_t s);
+cudaError_t launch_update_translations(const pxst_dims &d, int Ty, int Tx, int quadratic, const float *frames,
+                                       const float *W, const uint8_t *mask, const float *I_ref, const float *w,
+                                       const double *u, const double *delta_in, const FrameShift *shifts,
+                                       const float *var, WsHeader *hdr, double *acc_sum,
+                                       unsigned long long *acc_cnt, double *delta_out, double *err_out,
+                                       cudaStream_t s);
 // learn (and cache) the integer shift span of a translation array outside any capture
 void prime_shift_span(const pxst_dims &d, const double *delta, cudaStream_t s);
 cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float *w,
@@ -161,6 +181,60 @@ __device__ __forceinline__ bool gather_masked(const float *__restrict__ Iref,
     if (!(den > 0.0f)) return false;
     R = num / den;
     return true;
+}
+
+// ------------------------------------------------------------------------------------
+// 3x3 paraboloid refinement (end of section "Update pixel mapping"): least-squares fit
+// of c0 + c1 a + c2 b + c3 a^2 + c4 ab + c5 b^2 at a, b in {-1, 0, 1}; stationary point
+// of the fit if it is a convex bowl, otherwise a parabola per axis; shifts beyond one
+// pixel are discarded per axis. f[3*(da+1) + (db+1)]; +inf marks a missing point.
+__device__ inline void refine3x3(const float *f, double &da_out, double &db_out) {
+    double v[9];
+    bool complete = true;
+    for (int k = 0; k < 9; ++k) {
+        v[k] = (double)f[k];
+        complete = complete && isfinite(v[k]);
+    }
+    double da = 0.0, db = 0.0;
+    bool done = false;
+    if (complete) {
+        double s = 0, sa = 0, sb = 0, sab = 0, ra = 0, rb = 0;
+        for (int ia = -1; ia <= 1; ++ia)
+            for (int ib = -1; ib <= 1; ++ib) {
+                const double t = v[(ia + 1) * 3 + (ib + 1)];
+                s += t;
+                sa += ia * t;
+                sb += ib * t;
+                sab += ia * ib * t;
+                if (ia) ra += t;
+                if (ib) rb += t;
+            }
+        const double g1 = sa / 6.0, g2 = sb / 6.0, h12 = sab / 4.0;
+        const double h11 = (ra - 2.0 * (s - ra)) / 6.0, h22 = (rb - 2.0 * (s - rb)) / 6.0;
+        const double det = 4.0 * h11 * h22 - h12 * h12;
+        if (h11 > 0.0 && det > 0.0) {
+            da = (h12 * g2 - 2.0 * h22 * g1) / det;
+            db = (h12 * g1 - 2.0 * h11 * g2) / det;
+            done = true;
+        }
+    }
+    if (!done) {
+        const double c = v[4];
+        da = 0.0;
+        if (isfinite(v[1]) && isfinite(v[7]) && isfinite(c)) {
+            const double k = v[1] - 2.0 * c + v[7];
+            if (k > 0.0) da = (v[1] - v[7]) / (2.0 * k);
+        }
+        db = 0.0;
+        if (isfinite(v[3]) && isfinite(v[5]) && isfinite(c)) {
+            const double k = v[3] - 2.0 * c + v[5];
+            if (k > 0.0) db = (v[3] - v[5]) / (2.0 * k);
+        }
+    }
+    if (!(fabs(da) <= 1.0)) da = 0.0;
+    if (!(fabs(db) <= 1.0)) db = 0.0;
+    da_out = da;
+    db_out = db;
 }
 
 }  // namespace pxst

@@ -41,59 +41,6 @@ struct SearchArgs {
     float *err_out;
 };
 
-// ------------------------------------------------------------------------------------
-// 3x3 paraboloid refinement (end of section "Update pixel mapping"): least-squares fit
-// of c0 + c1 a + c2 b + c3 a^2 + c4 ab + c5 b^2 at a, b in {-1, 0, 1}; stationary point
-// of the fit if it is a convex bowl, otherwise a parabola per axis; shifts beyond one
-// pixel are discarded per axis. f[3*(da+1) + (db+1)]; +inf marks a missing point.
-__device__ void refine3x3(const float *f, double &da_out, double &db_out) {
-    double v[9];
-    bool complete = true;
-    for (int k = 0; k < 9; ++k) {
-        v[k] = (double)f[k];
-        complete = complete && isfinite(v[k]);
-    }
-    double da = 0.0, db = 0.0;
-    bool done = false;
-    if (complete) {
-        double s = 0, sa = 0, sb = 0, sab = 0, ra = 0, rb = 0;
-        for (int ia = -1; ia <= 1; ++ia)
-            for (int ib = -1; ib <= 1; ++ib) {
-                const double t = v[(ia + 1) * 3 + (ib + 1)];
-                s += t;
-                sa += ia * t;
-                sb += ib * t;
-                sab += ia * ib * t;
-                if (ia) ra += t;
-                if (ib) rb += t;
-            }
-        const double g1 = sa / 6.0, g2 = sb / 6.0, h12 = sab / 4.0;
-        const double h11 = (ra - 2.0 * (s - ra)) / 6.0, h22 = (rb - 2.0 * (s - rb)) / 6.0;
-        const double det = 4.0 * h11 * h22 - h12 * h12;
-        if (h11 > 0.0 && det > 0.0) {
-            da = (h12 * g2 - 2.0 * h22 * g1) / det;
-            db = (h12 * g1 - 2.0 * h11 * g2) / det;
-            done = true;
-        }
-    }
-    if (!done) {
-        const double c = v[4];
-        da = 0.0;
-        if (isfinite(v[1]) && isfinite(v[7]) && isfinite(c)) {
-            const double k = v[1] - 2.0 * c + v[7];
-            if (k > 0.0) da = (v[1] - v[7]) / (2.0 * k);
-        }
-        db = 0.0;
-        if (isfinite(v[3]) && isfinite(v[5]) && isfinite(c)) {
-            const double k = v[3] - 2.0 * c + v[5];
-            if (k > 0.0) db = (v[3] - v[5]) / (2.0 * k);
-        }
-    }
-    if (!(fabs(da) <= 1.0)) da = 0.0;
-    if (!(fabs(db) <= 1.0)) db = 0.0;
-    da_out = da;
-    db_out = db;
-}
 
 // ------------------------------------------------------------------------------------
 // One strip of L candidates (same row, consecutive columns) over all frames.

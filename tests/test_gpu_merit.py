@@ -1,0 +1,117 @@
+"""calc_error and update_translations (sections "Calculate figures of merit" and "Update
+translations") through the C ABI against the FP64 oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import parity
+import pins
+from test_gpu_parity import ragged2d
+
+pytestmark = pytest.mark.gpu
+
+SCANS = {
+    "small": lambda: gen.config_small(),
+    "ragged2d": ragged2d,
+    "lens1d-48x768": lambda: gen.config_lens1d(ny=48, nx=768),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(SCANS))
+def scan(request):
+    return SCANS[request.param]()
+
+
+def _dev(s_frames, s_W, s_M, I32, w32, u, delta):
+    import torch
+    from gpu_util import dev
+    return (dev(s_frames, torch.float32), dev(s_W, torch.float32), dev(s_M, torch.uint8), dev(I32, torch.float32),
+            dev(w32, torch.float32), dev(u, torch.float64), dev(delta, torch.float64))
+
+
+def _gpu_calc_error(frames, W, M, I32, w32, u, delta):
+    import torch
+    import paper_2003_12726_gb300 as px
+    from gpu_util import dims_of
+    d = dims_of(frames, I32.shape)
+    t = _dev(frames, W, M, I32, w32, u, delta)
+    ws = px.workspace(d)
+    pe = torch.empty(M.shape, dtype=torch.float32, device="cuda")
+    fe = torch.empty(frames.shape[0], dtype=torch.float64, device="cuda")
+    tot = torch.empty(1, dtype=torch.float64, device="cuda")
+    re = torch.empty(I32.shape, dtype=torch.float32, device="cuda")
+    px.calc_error(d, *t, ws, pe, fe, tot, re)
+    code, bits = px.get_status(ws)
+    assert code == 0, (code, bits)
+    return pe.cpu().numpy(), fe.cpu().numpy(), float(tot.item()), re.cpu().numpy()
+
+
+def test_calc_error_parity(scan):
+    s = scan
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    pe_o, fe_o, tot_o, re_o = oracle.calc_error(s.frames, s.W, s.M, I32.astype(np.float64), w32.astype(np.float64),
+                                                s.u_init, s.delta)
+    pe, fe, tot, re = _gpu_calc_error(s.frames, s.W, s.M, I32, w32, s.u_init, s.delta)
+    good = s.M > 0
+    assert np.array_equal(np.isnan(pe), np.isnan(pe_o))
+    np.testing.assert_allclose(pe[good], pe_o[good], rtol=1e-4, atol=1e-6 * np.nanmax(pe_o))
+    np.testing.assert_allclose(fe, fe_o, rtol=1e-5)
+    np.testing.assert_allclose(tot, tot_o, rtol=1e-6)
+    cov = re_o != 0
+    assert parity.rel_l2(re[cov].astype(np.float64), re_o[cov]) < 1e-5
+    print(s.name, "total", tot, "oracle", tot_o)
+
+
+def test_calc_error_exact_zero():
+    rng = np.random.default_rng(31)
+    frames, W, M, u, delta, Iref = pins._integer_scan(rng)
+    pe, fe, tot, re = _gpu_calc_error(frames, W, M, Iref.astype(np.float32), np.ones(Iref.shape, np.float32), u, delta)
+    assert np.all(pe[M > 0] == 0.0) and np.all(np.isnan(pe[M == 0]))
+    assert np.all(fe == 0.0) and tot == 0.0 and np.all(re == 0.0)
+
+
+def _gpu_update_translations(frames, W, M, I32, w32, u, delta, twindow, quadratic=True):
+    import torch
+    import paper_2003_12726_gb300 as px
+    from gpu_util import dims_of
+    d = dims_of(frames, I32.shape)
+    t = _dev(frames, W, M, I32, w32, u, delta)
+    ws = px.workspace(d)
+    fe = torch.empty(frames.shape[0], dtype=torch.float64, device="cuda")
+    px.update_translations(d, twindow, *t, ws, fe, quadratic=quadratic)
+    code, bits = px.get_status(ws)
+    assert code == 0, (code, bits)
+    return t[6].cpu().numpy(), fe.cpu().numpy()
+
+
+@pytest.mark.parametrize("quadratic", [False, True])
+def test_update_translations_parity(scan, quadratic):
+    s = scan
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    rng = np.random.default_rng(gen.BASE_SEED + 81)
+    start = s.delta + rng.uniform(-0.7, 0.7, s.delta.shape)
+    tw = (1, 2) if s.window[0] >= 2 else (0, 3)
+    d_o, e_o = oracle.update_translations(s.frames, s.W, s.M, I32.astype(np.float64), w32.astype(np.float64),
+                                          s.u_init, start, tw, quadratic=quadratic)
+    d_g, e_g = _gpu_update_translations(s.frames, s.W, s.M, I32, w32, s.u_init, start, tw, quadratic=quadratic)
+    same = np.all(np.abs(np.round(d_g - start) - np.round(d_o - start)) < 0.5, axis=1) if not quadratic else None
+    if quadratic:
+        np.testing.assert_allclose(d_g, d_o, atol=1e-3)
+    else:
+        assert same.all()
+        np.testing.assert_array_equal(d_g, d_o)
+    np.testing.assert_allclose(e_g, e_o, rtol=1e-4)
+    print(s.name, "quadratic", quadratic, "max |d_gpu - d_oracle|", np.abs(d_g - d_o).max())
+
+
+def test_update_translations_exact_integer():
+    rng = np.random.default_rng(34)
+    frames, W, M, u, delta, Iref = pins._integer_scan(rng, N=6)
+    start = delta + rng.integers(-2, 3, size=delta.shape)
+    d_g, e_g = _gpu_update_translations(frames, W, M, Iref.astype(np.float32), np.ones(Iref.shape, np.float32), u,
+                                        start, (3, 3), quadratic=False)
+    np.testing.assert_array_equal(d_g, delta)
+    assert np.all(e_g == 0.0)
