@@ -57,6 +57,7 @@ def _bind(L):
     L.pxst_oracle_calc_error.argtypes = [i32] * 5 + [P] * 11
     L.pxst_oracle_frame_window.argtypes = [i32] * 7 + [P] * 7 + [i32, P]
     L.pxst_oracle_update_translations.argtypes = [i32] * 8 + [P] * 9
+    L.pxst_oracle_filter_map.argtypes = [i32, i32, dbl, P, P, P]
     return L
 
 
@@ -244,3 +245,13 @@ def update_translations(frames, W, M, Iref, w, u, delta, twindow, quadratic=True
                                                  int(bool(quadratic)), _p(frames), _p(W), _p(M), _p(Iref),
                                                  _p(w), _p(u), _p(delta), _p(d_out), _p(err))
     return d_out, err
+
+
+def filter_map(M, u, sigma, L=None):
+    """The "sigma" regularisation of the pixel map: Gaussian filter normalised over the good
+    pixels (M = 0 pixels keep u)."""
+    M, u = _u8(M), _f64(u)
+    ny, nx = M.shape
+    out = np.empty_like(u)
+    (L or lib()).pxst_oracle_filter_map(ny, nx, float(sigma), _p(M), _p(u), _p(out))
+    return out

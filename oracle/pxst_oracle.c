@@ -21,7 +21,9 @@
  *     (total error) and its map onto the reference plane;
  *   - update_translations, section "Update translations": the error of Eq. 1 summed over
  *     pixels for integer shifts of one frame's translation, argmin and the same 3x3
- *     paraboloid.
+ *     paraboloid;
+ *   - filter_map, the "sigma" regularisation of the pixel map (end of section "Update pixel
+ *     mapping"): a Gaussian filter of the map.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   R1  the bilinear weight multiplies both the M*W*I term and the M*W^2 term;
@@ -403,6 +405,46 @@ void pxst_oracle_iterate(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx, 
                                      w, delta, u_inout, u_inout, err_out, 0, ny, nthreads);
     }
     /* I_ref and w are those built in the last iteration's step (i) */
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* regularisation of the pixel map (the "sigma" option of the update)                 */
+/* ---------------------------------------------------------------------------------- */
+
+/* R14 u_f(x) = sum_y g(x - y) M(y) u(y) / sum_y g(x - y) M(y) for M(x) = 1, with
+ *     g(d) = exp(-|d|^2 / (2 sigma^2)) for |d_i|, |d_j| <= r = floor(4 sigma + 1/2) (a square
+ *     support, so the 2-D kernel is the product of two 1-D ones); M = 0 pixels keep u;
+ *     sigma <= 0 leaves u unchanged. Direct 2-D sum per pixel. */
+void pxst_oracle_filter_map(int ny, int nx, double sigma, const uint8_t *M, const double *u_in, double *u_out)
+{
+    const int64_t P = (int64_t)ny * nx;
+    memcpy(u_out, u_in, sizeof(double) * 2 * (size_t)P);
+    if (!(sigma > 0.0)) return;
+    const int r = (int)floor(4.0 * sigma + 0.5);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < ny; ++i) {
+        for (int j = 0; j < nx; ++j) {
+            const int64_t p = (int64_t)i * nx + j;
+            if (!M[p]) continue;
+            double num0 = 0.0, num1 = 0.0, den = 0.0;
+            for (int a = -r; a <= r; ++a) {
+                const int ii = i + a;
+                if (ii < 0 || ii >= ny) continue;
+                for (int b = -r; b <= r; ++b) {
+                    const int jj = j + b;
+                    if (jj < 0 || jj >= nx) continue;
+                    const int64_t q = (int64_t)ii * nx + jj;
+                    if (!M[q]) continue;
+                    const double g = exp(-(double)(a * a + b * b) / (2.0 * sigma * sigma));
+                    num0 += g * u_in[q];
+                    num1 += g * u_in[P + q];
+                    den += g;
+                }
+            }
+            u_out[p] = num0 / den;
+            u_out[P + p] = num1 / den;
+        }
+    }
 }
 
 /* ---------------------------------------------------------------------------------- */

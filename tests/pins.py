@@ -474,4 +474,44 @@ def pin_translations_linear_field_exact(L):
     np.testing.assert_allclose(got[:, 1], delta[:, 1], atol=5e-5)
 
 
+# ---------------------------------------------------------------------------------------
+# regularisation of the pixel map (the "sigma" option of the update)
+# ---------------------------------------------------------------------------------------
+
+def pin_filter_scipy(L):
+    """The normalised Gaussian filter equals scipy's separable gaussian_filter of M u and of M
+    (zero outside the detector, the same 4-sigma truncation), divided."""
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(41)
+    ny, nx, sigma = 23, 31, 1.7
+    M = (rng.random((ny, nx)) > 0.2).astype(np.uint8)
+    u = np.stack([100 + rng.normal(0, 3, (ny, nx)), 50 + rng.normal(0, 3, (ny, nx))])
+    got = oracle.filter_map(M, u, sigma, L=L)
+    m = M.astype(np.float64)
+    kw = dict(sigma=sigma, mode="constant", cval=0.0, truncate=4.0)
+    den = ndi.gaussian_filter(m, **kw)
+    for c in range(2):
+        want = ndi.gaussian_filter(m * u[c], **kw) / den
+        np.testing.assert_allclose(got[c][M > 0], want[M > 0], rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(got[c][M == 0], u[c][M == 0])
+
+
+def pin_filter_preserves_linear_and_constant(L):
+    """A constant map is unchanged; a linear map is unchanged at pixels whose whole kernel
+    support is inside the detector and unmasked (a symmetric kernel averages a linear
+    function to its centre); sigma = 0 is the identity."""
+    ny, nx, sigma = 30, 40, 2.0
+    M = np.ones((ny, nx), np.uint8)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    u = np.stack([7.0 + 1.3 * y + 0.2 * x, -3.0 + 0.7 * x - 0.1 * y])
+    got = oracle.filter_map(M, u, sigma, L=L)
+    r = int(np.floor(4 * sigma + 0.5))
+    inner = (slice(r, ny - r), slice(r, nx - r))
+    np.testing.assert_allclose(got[0][inner], u[0][inner], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(got[1][inner], u[1][inner], rtol=0, atol=1e-11)
+    c = np.full((2, ny, nx), 123.456)
+    np.testing.assert_allclose(oracle.filter_map(M, c, sigma, L=L), c, rtol=1e-14)
+    np.testing.assert_array_equal(oracle.filter_map(M, u, 0.0, L=L), u)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

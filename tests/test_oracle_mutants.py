@@ -45,6 +45,10 @@ MUTANTS = {
     "invalid_frame_counted": ("if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) continue;",
                               "if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) R = 0.0;"),
     "pixel_var_dropped": ("s2 += v * v;", "s2 += 1.0;"),
+    "filter_unnormalised": ("u_out[p] = num0 / den;", "u_out[p] = num0;"),
+    "filter_ignores_mask": ("if (!M[q]) continue;", "(void)q;"),
+    "filter_width_halved": ("const double g = exp(-(double)(a * a + b * b) / (2.0 * sigma * sigma));",
+                            "const double g = exp(-(double)(a * a + b * b) / (sigma * sigma));"),
     "error_not_normalised": ("const double eps = var > 0.0 ? d * d / var : d * d;", "const double eps = d * d;"),
     "error_plane_unnormalised": ("ref_err[c] = den[c] > 0.0 ? num[c] / den[c] : 0.0;",
                                  "ref_err[c] = den[c] > 0.0 ? num[c] : 0.0;"),
