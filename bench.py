@@ -240,6 +240,7 @@ def pxst_arm(args, rank, world, local_rank):
     def step():
         rec.run(1)
         if full:
+            px.filter_map(rec.dims, 1.0, rec.M, rec.u, rec.ws)
             px.update_translations(rec.dims, tw, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta,
                                    rec.ws, fe_t)
             px.calc_error(rec.dims, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta, rec.ws, pe_t,
@@ -366,7 +367,7 @@ def pxst_arm(args, rank, world, local_rank):
                        "detector": list(s.frames.shape[1:]), "window": list(s.window),
                        "reference": list(s.ref_shape), "form": args.form, "quadratic": True,
                        "evals_per_step": ev_step, "parallelism": f"replicas{world}", "autotuned": tuned,
-                       "loop": "full: reference image, pixel map, translations (window "
+                       "loop": "full: reference image, pixel map, map filter (sigma 1), translations (window "
                                f"{list(tw)}), figures of merit" if full else "reference image, pixel map",
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
             "roofline": roof, "cpu_baseline": cpu,

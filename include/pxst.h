@@ -189,7 +189,8 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 #define PXST_K_RESCORE    9   /* tensor forms: exact FP32 evaluation of the best candidates */
 #define PXST_K_ERROR      10  /* calc_error (with the per-pixel variance) */
 #define PXST_K_TRANS      11  /* update_translations (with the per-pixel variance) */
-#define PXST_K_COUNT      12
+#define PXST_K_FILTER     12  /* filter_map */
+#define PXST_K_COUNT      13
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);
@@ -230,6 +231,14 @@ pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32
                                      const float *frames, const float *W, const uint8_t *mask,
                                      const float *I_ref, const float *w, const double *u, double *delta_inout,
                                      double *frame_err, void *workspace, size_t ws_bytes, void *stream);
+
+/* pxst_filter_map: the "sigma" regularisation of the pixel map named at the end of section
+ * "Update pixel mapping": u(x) <- sum_y g(x - y) M(y) u(y) / sum_y g(x - y) M(y) for pixels
+ * with M = 1, g(d) = exp(-|d|^2 / (2 sigma^2)) on a square support of radius floor(4 sigma +
+ * 1/2) pixels per axis, zero outside the detector; M = 0 pixels keep their map; sigma = 0
+ * leaves u unchanged. FP64, two separable passes. sigma must be in [0, 1024]. */
+pxst_status pxst_filter_map(const pxst_dims *dims, double sigma, const uint8_t *mask, double *u_inout,
+                            void *workspace, size_t ws_bytes, void *stream);
 
 /* ---- Batched form ------------------------------------------------------------------------
  * Many independent scans of uneven frame count, detector size and window, iterated by one

@@ -26,7 +26,7 @@ FORM_BF16 = 1
 FORM_TF32 = 2
 KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms",
            "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore", "calc_error",
-           "update_translations"]
+           "update_translations", "filter_map"]
 
 
 class PxstError(RuntimeError):
@@ -112,6 +112,8 @@ def lib():
         L.pxst_calc_error.restype = i32
         L.pxst_update_translations.argtypes = [D, i32, i32, i32] + [P] * 9 + [sz, P]
         L.pxst_update_translations.restype = i32
+        L.pxst_filter_map.argtypes = [D, C.c_double, P, P, P, sz, P]
+        L.pxst_filter_map.restype = i32
         _lib = L
     return _lib
 
@@ -121,7 +123,8 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_iterate", "pxst_reference_terms", "pxst_get_status", "pxst_last_exact_count",
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
-            "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations"]
+            "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations",
+            "pxst_filter_map"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -487,3 +490,12 @@ def update_translations(dims: Dims, twindow, frames, W, M, I_ref, w, u, delta, w
                                           if frame_err is not None else None,
                                           C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
            "update_translations")
+
+
+def filter_map(dims: Dims, sigma, M, u, ws, stream=None):
+    """pxst_filter_map: the "sigma" regularisation of the pixel map u (float64 [2][ny][nx],
+    CUDA, in place)."""
+    torch = _torch()
+    _raise(lib().pxst_filter_map(C.byref(dims.c()), float(sigma), _check(M, torch.uint8, (dims.ny, dims.nx), "M"),
+                                 _check(u, torch.float64, (2, dims.ny, dims.nx), "u"), C.c_void_p(ws.data_ptr()),
+                                 ws.numel(), _stream(stream)), "filter_map")

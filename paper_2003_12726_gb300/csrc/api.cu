@@ -37,6 +37,7 @@ bool opts_ok(const pxst_options *o) {
 struct Ws {
     WsHeader *hdr;
     float *var_px;
+    double *u_save, *filt_den;
     double *tacc_sum, *delta_tmp;
     unsigned long long *tacc_cnt;
     FrameShift *shifts;
@@ -58,6 +59,8 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     char *b = static_cast<char *>(workspace);
     w.hdr = reinterpret_cast<WsHeader *>(b + L.header);
     w.var_px = reinterpret_cast<float *>(b + L.var_px);
+    w.u_save = reinterpret_cast<double *>(b + L.u_save);
+    w.filt_den = reinterpret_cast<double *>(b + L.filt_den);
     w.tacc_sum = reinterpret_cast<double *>(b + L.tacc_sum);
     w.tacc_cnt = reinterpret_cast<unsigned long long *>(b + L.tacc_cnt);
     w.delta_tmp = reinterpret_cast<double *>(b + L.delta_tmp);
@@ -364,6 +367,19 @@ pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32
     return PXST_OK;
 }
 
+pxst_status pxst_filter_map(const pxst_dims *dims, double sigma, const uint8_t *mask, double *u_inout,
+                            void *workspace, size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!mask || !u_inout || !(sigma >= 0.0) || sigma > 1024.0) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, PXST_FORM_FP32, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Timed t(PXST_K_FILTER, s);
+    PXST_TRY(launch_filter_map(*dims, sigma, mask, u_inout, ws.u_save, ws.filt_den, s));
+    return PXST_OK;
+}
+
 pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, const float *w,
                                  const double *delta, float *T, int32_t *n_valid,
                                  void *workspace, size_t ws_bytes, void *stream) {
@@ -451,6 +467,7 @@ const char *pxst_kernel_name(int32_t k) {
         case PXST_K_RESCORE: return "upm_rescore";
         case PXST_K_ERROR: return "calc_error";
         case PXST_K_TRANS: return "update_translations";
+        case PXST_K_FILTER: return "filter_map";
         default: return "?";
     }
 }

@@ -308,7 +308,98 @@ MeritArgs merit_args(const pxst_dims &d, const float *frames, const float *W, co
     return a;
 }
 
+// ---- regularisation of the pixel map (the "sigma" option of the update) --------------------
+// u_f = G * (M u) / G * M over the good pixels, the Gaussian truncated at r = floor(4 sigma + 1/2)
+// on each axis; separable: a pass along the rows into (num0, num1, den), then along the
+// columns. FP64: the map's coordinates (up to thousands of pixels) need 1e-9 relative.
+struct FilterArgs {
+    int ny, nx, r;
+    double inv2s2;                 // 1 / (2 sigma^2)
+    const uint8_t *mask;
+    double *u;                     // [2][ny][nx] in: the map; out: the filtered map
+    double *num;                   // [2][ny][nx] row-pass numerators
+    double *den;                   // [ny][nx] row-pass denominators
+};
+
+// the 1-D taps g(k), k = 0..r, once per block (FP64 exp is slow on this GPU)
+__device__ __forceinline__ void filter_taps(const FilterArgs &f, double *g) {
+    for (int k = threadIdx.x; k <= f.r; k += blockDim.x) g[k] = exp(-(double)k * (double)k * f.inv2s2);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_filter_rows(FilterArgs f) {
+    extern __shared__ double g[];
+    filter_taps(f, g);
+    const size_t P = (size_t)f.ny * f.nx;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p / f.nx), j = (int)(p % f.nx);
+        double n0 = 0.0, n1 = 0.0, dn = 0.0;
+        for (int b = -f.r; b <= f.r; ++b) {
+            const int jj = j + b;
+            if (jj < 0 || jj >= f.nx) continue;
+            const size_t q = (size_t)i * f.nx + jj;
+            if (!f.mask[q]) continue;
+            const double gk = g[b < 0 ? -b : b];
+            n0 = fma(gk, f.u[q], n0);
+            n1 = fma(gk, f.u[P + q], n1);
+            dn += gk;
+        }
+        f.num[p] = n0;
+        f.num[P + p] = n1;
+        f.den[p] = dn;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_filter_cols(FilterArgs f) {
+    extern __shared__ double g[];
+    filter_taps(f, g);
+    const size_t P = (size_t)f.ny * f.nx;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        if (!f.mask[p]) continue;                  // M = 0 keeps its map
+        const int i = (int)(p / f.nx), j = (int)(p % f.nx);
+        double n0 = 0.0, n1 = 0.0, dn = 0.0;
+        for (int a = -f.r; a <= f.r; ++a) {
+            const int ii = i + a;
+            if (ii < 0 || ii >= f.ny) continue;
+            const size_t q = (size_t)ii * f.nx + j;
+            const double gk = g[a < 0 ? -a : a];
+            n0 = fma(gk, f.num[q], n0);
+            n1 = fma(gk, f.num[P + q], n1);
+            dn = fma(gk, f.den[q], dn);
+        }
+        // dn > 0: the pixel itself is good and lies inside its own support
+        f.u[p] = n0 / dn;
+        f.u[P + p] = n1 / dn;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *mask, double *u, double *num,
+                              double *den, cudaStream_t s) {
+    if (!(sigma > 0.0)) return cudaSuccess;
+    FilterArgs f;
+    f.ny = d.ny; f.nx = d.nx;
+    f.r = (int)floor(4.0 * sigma + 0.5);
+    f.inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    f.mask = mask; f.u = u; f.num = num; f.den = den;
+    const size_t P = (size_t)d.ny * d.nx;
+    size_t blocks = (P + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    const size_t smem = sizeof(double) * (f.r + 1);      // r <= 4096 (sigma <= 1024)
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {
+        if ((e = cudaFuncSetAttribute(k_filter_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_filter_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+            return e;
+    }
+    k_filter_rows<<<(unsigned)blocks, 256, smem, s>>>(f);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_filter_cols<<<(unsigned)blocks, 256, smem, s>>>(f);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pixvar(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
                           const float *I_ref, const float *w, const double *u, const double *delta,

@@ -36,7 +36,7 @@ constexpr int kTransMax = 17 * 17;     // translation update: shifts within +-8 
 
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
-    size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp;
+    size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp, filt_den;
     // precision forms only (zero size otherwise)
     size_t At, G, Tt, nvalid, Rm, cand, edge, keys;
     int Npad;
@@ -65,6 +65,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.tacc_sum = off;   off += align256(sizeof(double) * kTransMax * (size_t)d.n_frames);
     L.tacc_cnt = off;   off += align256(sizeof(unsigned long long) * kTransMax * (size_t)d.n_frames);
     L.delta_tmp = off;  off += align256(sizeof(double) * 2 * (size_t)d.n_frames);
+    L.filt_den = off;   off += align256(sizeof(double) * P);        // the map filter's row pass
     L.Npad = 0;
     L.At = L.G = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.keys = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
@@ -150,6 +151,8 @@ cudaError_t launch_update_translations(const pxst_dims &d, int Ty, int Tx, int q
                                        const float *var, WsHeader *hdr, double *acc_sum,
                                        unsigned long long *acc_cnt, double *delta_out, double *err_out,
                                        cudaStream_t s);
+cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *mask, double *u, double *num,
+                              double *den, cudaStream_t s);
 // learn (and cache) the integer shift span of a translation array outside any capture
 void prime_shift_span(const pxst_dims &d, const double *delta, cudaStream_t s);
 cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float *w,

@@ -115,3 +115,22 @@ def test_update_translations_exact_integer():
                                         start, (3, 3), quadratic=False)
     np.testing.assert_array_equal(d_g, delta)
     assert np.all(e_g == 0.0)
+
+
+@pytest.mark.parametrize("sigma", [0.0, 1.0, 2.5])
+def test_filter_map_parity(scan, sigma):
+    """The sigma regularisation of the map against the oracle's direct 2-D sum."""
+    import torch
+    import paper_2003_12726_gb300 as px
+    from gpu_util import dev, dims_of
+    s = scan
+    rng = np.random.default_rng(gen.BASE_SEED + 91)
+    u = s.u_init + rng.normal(0, 0.4, s.u_init.shape)
+    want = oracle.filter_map(s.M, u, sigma)
+    d = dims_of(s.frames, s.ref_shape)
+    ut = dev(u, torch.float64)
+    ws = px.workspace(d)
+    px.filter_map(d, sigma, dev(s.M, torch.uint8), ut, ws)
+    got = ut.cpu().numpy()
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-9)
+    assert np.array_equal(got[:, s.M == 0], u[:, s.M == 0])
