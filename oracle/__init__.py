@@ -58,6 +58,7 @@ def _bind(L):
     L.pxst_oracle_frame_window.argtypes = [i32] * 7 + [P] * 7 + [i32, P]
     L.pxst_oracle_update_translations.argtypes = [i32] * 8 + [P] * 9
     L.pxst_oracle_filter_map.argtypes = [i32, i32, dbl, P, P, P]
+    L.pxst_oracle_update_pixel_map_frac.argtypes = [i32] * 8 + [P] * 9 + [i32]
     return L
 
 
@@ -255,3 +256,17 @@ def filter_map(M, u, sigma, L=None):
     out = np.empty_like(u)
     (L or lib()).pxst_oracle_filter_map(ny, nx, float(sigma), _p(M), _p(u), _p(out))
     return out
+
+
+def update_pixel_map_frac(frames, W, M, Iref, w, delta, u, window, sub, threads=None, L=None):
+    """The non-integer candidate option: the integer search, then the candidates on a 1/sub
+    grid within one pixel of its minimum: (u_new [2][ny][nx], err [ny][nx])."""
+    frames, W, M, Iref, w, delta, u = (_f32(frames), _f32(W), _u8(M), _f64(Iref), _f64(w), _f64(delta), _f64(u))
+    N, ny, nx = frames.shape
+    Sy, Sx = window
+    u_out = u.copy()
+    err = np.full((ny, nx), np.nan)
+    (L or lib()).pxst_oracle_update_pixel_map_frac(N, ny, nx, Iref.shape[0], Iref.shape[1], Sy, Sx, int(sub),
+                                                   _p(frames), _p(W), _p(M), _p(Iref), _p(w), _p(delta), _p(u),
+                                                   _p(u_out), _p(err), int(threads or default_threads()))
+    return u_out, err

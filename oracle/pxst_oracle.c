@@ -23,7 +23,10 @@
  *     pixels for integer shifts of one frame's translation, argmin and the same 3x3
  *     paraboloid;
  *   - filter_map, the "sigma" regularisation of the pixel map (end of section "Update pixel
- *     mapping"): a Gaussian filter of the map.
+ *     mapping"): a Gaussian filter of the map;
+ *   - update_pixel_map_frac, the first sub-pixel option of section "Update pixel mapping":
+ *     the error evaluated at non-integer candidates (bilinear reads, section "Sub-pixel
+ *     interpolation") instead of the paraboloid.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   R1  the bilinear weight multiplies both the M*W*I term and the M*W^2 term;
@@ -405,6 +408,68 @@ void pxst_oracle_iterate(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx, 
                                      w, delta, u_inout, u_inout, err_out, 0, ny, nthreads);
     }
     /* I_ref and w are those built in the last iteration's step (i) */
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* fractional candidates (the non-integer option of section "Update pixel mapping")   */
+/* ---------------------------------------------------------------------------------- */
+
+/* R15 after the integer search (R5-R8, no fit) of pixel p gives c*, the candidates
+ *     c* + (a, b) / s, a, b in [-s, s], are evaluated by the same rule (R6, R7) with
+ *     fractional reads; u = the first minimum in row-major order (a outer), its error is
+ *     reported; a pixel whose integer search found no finite error keeps its u. */
+void pxst_oracle_update_pixel_map_frac(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx, int sub,
+                                       const float *frames, const float *W, const uint8_t *M,
+                                       const double *Iref, const double *w, const double *delta,
+                                       const double *u_in, double *u_out, double *err_out, int nthreads)
+{
+    upm_ctx c = {N, ny, nx, Ry, Rx, Sy, Sx, frames, W, M, Iref, w, delta, u_in};
+    const int64_t P = (int64_t)ny * nx;
+    const int nwin = (2 * Sy + 1) * (2 * Sx + 1);
+    if (nthreads <= 0) nthreads = 1;
+    #pragma omp parallel num_threads(nthreads)
+    {
+        double *e = (double *)malloc(sizeof(double) * nwin);
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t p = 0; p < P; ++p) {
+            double u0, u1, er;
+            update_one(&c, 0, p, e, &u0, &u1, &er);
+            if (M[p] && er < INFINITY) {
+                const double Wv = (double)W[p];
+                double best_e = INFINITY, b0 = u0, b1 = u1;
+                for (int a = -sub; a <= sub; ++a) {
+                    for (int b = -sub; b <= sub; ++b) {
+                        const double c0 = u0 + (double)a / sub, c1 = u1 + (double)b / sub;
+                        double error = 0.0, var = 0.0;
+                        int nvalid = 0;
+                        for (int n = 0; n < N; ++n) {
+                            double R;
+                            if (!pxst_oracle_gather(Iref, w, Ry, Rx, c0 - delta[2 * n], c1 - delta[2 * n + 1], &R))
+                                continue;
+                            const double In = (double)frames[(int64_t)n * P + p];
+                            const double res = In - Wv * R, dev = In - Wv;
+                            error += res * res;
+                            var += dev * dev;
+                            nvalid += 1;
+                        }
+                        const double ev = nvalid == 0 ? INFINITY : (var > 0.0 ? error / var : error);
+                        if (ev < best_e) {                                  /* strict <: first minimum */
+                            best_e = ev;
+                            b0 = c0;
+                            b1 = c1;
+                        }
+                    }
+                }
+                u0 = b0;
+                u1 = b1;
+                er = best_e;
+            }
+            u_out[p] = u0;
+            u_out[P + p] = u1;
+            if (err_out) err_out[p] = er;
+        }
+        free(e);
+    }
 }
 
 /* ---------------------------------------------------------------------------------- */

@@ -514,4 +514,48 @@ def pin_filter_preserves_linear_and_constant(L):
     np.testing.assert_array_equal(oracle.filter_map(M, u, 0.0, L=L), u)
 
 
+# ---------------------------------------------------------------------------------------
+# fractional candidates (the non-integer option of section "Update pixel mapping")
+# ---------------------------------------------------------------------------------------
+
+def _bilinear_np(Iref, q0, q1):
+    """Plain bilinear interpolation of a fully covered grid (independent of the oracle)."""
+    i0, j0 = np.floor(q0).astype(int), np.floor(q1).astype(int)
+    fy, fx = q0 - i0, q1 - j0
+    return ((1 - fy) * (1 - fx) * Iref[i0, j0] + (1 - fy) * fx * Iref[i0, j0 + 1] +
+            fy * (1 - fx) * Iref[i0 + 1, j0] + fy * fx * Iref[i0 + 1, j0 + 1])
+
+
+def pin_frac_exact_on_bilinear_data(L):
+    """Frames rendered by bilinear reads of the grid reference at maps on a quarter-pixel
+    grid: the error vanishes at the true map, so the quarter-pixel search recovers it
+    exactly (and a unit step, sub = 1, leaves the integer search's answer)."""
+    import scipy.ndimage as ndi
+    rng = np.random.default_rng(51)
+    N, ny, nx, R = 16, 7, 8, (40, 44)
+    # a speckle-like reference (correlated over ~2 pixels), so that the integer search's
+    # minimum lies next to the true map
+    Iref = ndi.gaussian_filter(rng.random(R), 1.5, mode="wrap")
+    Iref = 0.5 + (Iref - Iref.min()) / (Iref.max() - Iref.min())
+    u = np.empty((2, ny, nx))
+    u[0] = 12 + np.arange(ny)[:, None] * 1.5 + rng.integers(0, 4, (ny, nx)) / 4.0
+    u[1] = 10 + np.arange(nx)[None, :] * 1.25 + rng.integers(0, 4, (ny, nx)) / 4.0
+    delta = np.stack([rng.integers(0, 6, N), rng.integers(-3, 4, N)], axis=1).astype(np.float64)
+    W = rng.uniform(200, 400, (ny, nx))
+    frames = np.stack([W * _bilinear_np(Iref, u[0] - delta[n, 0], u[1] - delta[n, 1]) for n in range(N)])
+    M = np.ones((ny, nx), np.uint8)
+    start = np.round(u)
+    got, err = oracle.update_pixel_map_frac(frames.astype(np.float32), W.astype(np.float32), M, Iref, np.ones(R),
+                                            delta, start, (2, 2), 4, L=L)
+    np.testing.assert_array_equal(got, u)
+    ui, ei = oracle.update_pixel_map(frames.astype(np.float32), W.astype(np.float32), M, Iref, np.ones(R), delta,
+                                     start, (2, 2), quadratic=False, L=L)
+    g1, e1 = oracle.update_pixel_map_frac(frames.astype(np.float32), W.astype(np.float32), M, Iref, np.ones(R),
+                                          delta, start, (2, 2), 1, L=L)
+    # sub = 1: the integer minimum's 3x3, whose first minimum is that minimum unless a
+    # neighbour ties it exactly
+    assert np.mean(np.all(g1 == ui, axis=0)) > 0.95
+    assert np.all(e1 <= ei)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -45,6 +45,10 @@ MUTANTS = {
     "invalid_frame_counted": ("if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) continue;",
                               "if (!pxst_oracle_gather(c->Iref, c->w, c->Ry, c->Rx, q0, q1, &R)) R = 0.0;"),
     "pixel_var_dropped": ("s2 += v * v;", "s2 += 1.0;"),
+    "frac_step_halved": ("const double c0 = u0 + (double)a / sub, c1 = u1 + (double)b / sub;",
+                         "const double c0 = u0 + (double)a / (2 * sub), c1 = u1 + (double)b / sub;"),
+    "frac_adds_delta": ("if (!pxst_oracle_gather(Iref, w, Ry, Rx, c0 - delta[2 * n], c1 - delta[2 * n + 1], &R))",
+                        "if (!pxst_oracle_gather(Iref, w, Ry, Rx, c0 + delta[2 * n], c1 - delta[2 * n + 1], &R))"),
     "filter_unnormalised": ("u_out[p] = num0 / den;", "u_out[p] = num0;"),
     "filter_ignores_mask": ("if (!M[q]) continue;", "(void)q;"),
     "filter_width_halved": ("const double g = exp(-(double)(a * a + b * b) / (2.0 * sigma * sigma));",
