@@ -237,8 +237,16 @@ def pxst_arm(args, rank, world, local_rank):
         tot_t = torch.empty(1, dtype=torch.float64, device="cuda")
         re_t = torch.empty(tuple(s.ref_shape), dtype=torch.float32, device="cuda")
 
+    frac = args.frac
+
     def step():
-        rec.run(1)
+        if frac:
+            # the non-integer candidate option instead of the paraboloid
+            px.make_object_map(rec.dims, rec.frames, rec.W, rec.M, rec.u, rec.delta, rec.I_ref, rec.w, rec.ws)
+            px.update_pixel_map_fractional(rec.dims, rec.opts, frac, rec.frames, rec.W, rec.M, rec.I_ref, rec.w,
+                                           rec.delta, rec.u, rec.ws, rec.err)
+        else:
+            rec.run(1)
         if full:
             px.filter_map(rec.dims, 1.0, rec.M, rec.u, rec.ws)
             px.update_translations(rec.dims, tw, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta,
@@ -367,6 +375,7 @@ def pxst_arm(args, rank, world, local_rank):
                        "detector": list(s.frames.shape[1:]), "window": list(s.window),
                        "reference": list(s.ref_shape), "form": args.form, "quadratic": True,
                        "evals_per_step": ev_step, "parallelism": f"replicas{world}", "autotuned": tuned,
+                       "subpixel": f"fractional candidates, 1/{frac} grid" if frac else "3x3 paraboloid",
                        "loop": "full: reference image, pixel map, map filter (sigma 1), translations (window "
                                f"{list(tw)}), figures of merit" if full else "reference image, pixel map",
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
@@ -511,6 +520,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic tile shape")
+    ap.add_argument("--frac", type=int, default=0, help="fractional candidates on a 1/FRAC grid instead of the fit")
     ap.add_argument("--loop", default="main", choices=["main", "full"],
                     help="main: steps (i)+(ii) of the main loop; full: + translations and figures of merit")
     ap.add_argument("--requests", type=int, default=500, help="serve: number of scans")

@@ -190,7 +190,8 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 #define PXST_K_ERROR      10  /* calc_error (with the per-pixel variance) */
 #define PXST_K_TRANS      11  /* update_translations (with the per-pixel variance) */
 #define PXST_K_FILTER     12  /* filter_map */
-#define PXST_K_COUNT      13
+#define PXST_K_FRAC       13  /* update_pixel_map_fractional: the fractional candidates */
+#define PXST_K_COUNT      14
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);
@@ -231,6 +232,19 @@ pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32
                                      const float *frames, const float *W, const uint8_t *mask,
                                      const float *I_ref, const float *w, const double *u, double *delta_inout,
                                      double *frame_err, void *workspace, size_t ws_bytes, void *stream);
+
+/* pxst_update_pixel_map_fractional: the non-integer option of section "Update pixel mapping"
+ * instead of the paraboloid. update_pixel_map without the fit (any form) gives each pixel's
+ * integer minimum c*; then the candidates c* + (a, b) / sub, a, b in [-sub, sub], are
+ * evaluated by the same masked rule with bilinear reads at the fractional positions, and u
+ * becomes the first minimum in row-major order (err_out, if given, its error). A pixel whose
+ * c* has no valid frame keeps its map. sub in [1, 8], else PXST_ERR_ARG; opts->quadratic is
+ * ignored. Work: (2 sub + 1)^2 x N evaluations per pixel on top of the integer search. */
+pxst_status pxst_update_pixel_map_fractional(const pxst_dims *dims, const pxst_options *opts, int32_t sub,
+                                             const float *frames, const float *W, const uint8_t *mask,
+                                             const float *I_ref, const float *w, const double *delta,
+                                             double *u_inout, float *err_out, void *workspace, size_t ws_bytes,
+                                             void *stream);
 
 /* pxst_filter_map: the "sigma" regularisation of the pixel map named at the end of section
  * "Update pixel mapping": u(x) <- sum_y g(x - y) M(y) u(y) / sum_y g(x - y) M(y) for pixels

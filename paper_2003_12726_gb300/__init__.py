@@ -26,7 +26,7 @@ FORM_BF16 = 1
 FORM_TF32 = 2
 KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms",
            "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore", "calc_error",
-           "update_translations", "filter_map"]
+           "update_translations", "filter_map", "upm_fractional"]
 
 
 class PxstError(RuntimeError):
@@ -114,6 +114,8 @@ def lib():
         L.pxst_update_translations.restype = i32
         L.pxst_filter_map.argtypes = [D, C.c_double, P, P, P, sz, P]
         L.pxst_filter_map.restype = i32
+        L.pxst_update_pixel_map_fractional.argtypes = [D, O, i32] + [P] * 9 + [sz, P]
+        L.pxst_update_pixel_map_fractional.restype = i32
         _lib = L
     return _lib
 
@@ -124,7 +126,7 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
             "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations",
-            "pxst_filter_map"]
+            "pxst_filter_map", "pxst_update_pixel_map_fractional"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -499,3 +501,18 @@ def filter_map(dims: Dims, sigma, M, u, ws, stream=None):
     _raise(lib().pxst_filter_map(C.byref(dims.c()), float(sigma), _check(M, torch.uint8, (dims.ny, dims.nx), "M"),
                                  _check(u, torch.float64, (2, dims.ny, dims.nx), "u"), C.c_void_p(ws.data_ptr()),
                                  ws.numel(), _stream(stream)), "filter_map")
+
+
+def update_pixel_map_fractional(dims: Dims, opts: Options, sub, frames, W, M, I_ref, w, delta, u, ws, err=None,
+                                stream=None):
+    """pxst_update_pixel_map_fractional: the integer search, then candidates on a 1/sub grid
+    within one pixel of its minimum (u updated in place)."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    _raise(lib().pxst_update_pixel_map_fractional(
+        C.byref(dims.c()), C.byref(opts.c()), int(sub), _check(frames, torch.float32, (N, ny, nx), "frames"),
+        _check(W, torch.float32, (ny, nx), "W"), _check(M, torch.uint8, (ny, nx), "M"),
+        _check(I_ref, torch.float32, (Ry, Rx), "I_ref"), _check(w, torch.float32, (Ry, Rx), "w"),
+        _check(delta, torch.float64, (N, 2), "delta"), _check(u, torch.float64, (2, ny, nx), "u"),
+        _check(err, torch.float32, (ny, nx), "err") if err is not None else None,
+        C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)), "update_pixel_map_fractional")

@@ -367,6 +367,29 @@ pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32
     return PXST_OK;
 }
 
+pxst_status pxst_update_pixel_map_fractional(const pxst_dims *dims, const pxst_options *opts, int32_t sub,
+                                             const float *frames, const float *W, const uint8_t *mask,
+                                             const float *I_ref, const float *w, const double *delta,
+                                             double *u_inout, float *err_out, void *workspace, size_t ws_bytes,
+                                             void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!opts_ok(opts) || sub < 1 || sub > 8) return PXST_ERR_ARG;
+    if (!frames || !W || !mask || !I_ref || !w || !delta || !u_inout) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, opts->form, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    pxst_options o = *opts;
+    o.quadratic = 0;                          // the integer minimum, then the fractional grid about it
+    st = run_update(*dims, o, frames, W, mask, I_ref, w, delta, u_inout, err_out, ws, s);
+    if (st != PXST_OK) return st;
+    Timed t(PXST_K_FRAC, s);
+    PXST_TRY(launch_frac_refine(*dims, sub, frames, W, mask, I_ref, w, ws.shifts, u_inout, err_out, s));
+    return PXST_OK;
+}
+
 pxst_status pxst_filter_map(const pxst_dims *dims, double sigma, const uint8_t *mask, double *u_inout,
                             void *workspace, size_t ws_bytes, void *stream) {
     if (!dims_ok(dims)) return PXST_ERR_SHAPE;
@@ -468,6 +491,7 @@ const char *pxst_kernel_name(int32_t k) {
         case PXST_K_ERROR: return "calc_error";
         case PXST_K_TRANS: return "update_translations";
         case PXST_K_FILTER: return "filter_map";
+        case PXST_K_FRAC: return "upm_fractional";
         default: return "?";
     }
 }

@@ -373,7 +373,95 @@ __global__ void __launch_bounds__(256) k_filter_cols(FilterArgs f) {
     }
 }
 
+// ---- fractional candidates (the non-integer option of section "Update pixel mapping") -------
+// After the integer search (no fit) every pixel's map is its minimum c*; the candidates
+// c* + (a, b) / s, |a|, |b| <= s, are evaluated by the masked rule with fractional reads (one
+// thread per pixel, one row of 2s + 1 candidates per pass over the frames); u = the first
+// minimum in row-major order. A pixel whose c* has no valid frame keeps its map.
+constexpr int kFracMax = 8;
+
+struct FracArgs {
+    int N, ny, nx, Ry, Rx, sub;
+    const float *frames, *W;
+    const uint8_t *mask;
+    const float *Iref, *w;
+    const FrameShift *shifts;
+    double *u;
+    float *err_out;
+};
+
+__global__ void __launch_bounds__(128) k_frac_refine(FracArgs a) {
+    const size_t P = (size_t)a.ny * a.nx;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P || !a.mask[p]) return;
+    const double u0 = a.u[p], u1 = a.u[P + p];
+    if (!isfinite(u0) || !isfinite(u1) || fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) return;
+    const int c0 = (int)floor(u0 + 0.5), c1 = (int)floor(u1 + 0.5);
+    const float Wv = a.W[p];
+    const int wn = 2 * a.sub + 1;
+    const float inv = 1.0f / (float)a.sub;
+    unsigned long long key = ~0ull;
+    float e_centre = INFINITY;
+    for (int ia = 0; ia < wn; ++ia) {
+        const float fa = (float)(ia - a.sub) * inv;
+        float err[2 * kFracMax + 1], var[2 * kFracMax + 1];
+        int nv[2 * kFracMax + 1];
+#pragma unroll
+        for (int k = 0; k < 2 * kFracMax + 1; ++k) {
+            err[k] = var[k] = 0.0f;
+            nv[k] = 0;
+        }
+        for (int n = 0; n < a.N; ++n) {
+            const FrameShift s = a.shifts[n];
+            const float I = __ldg(a.frames + (size_t)n * P + p);
+            const float t = I - Wv;
+            float fy = fa + s.fy;
+            const float gy = floorf(fy);
+            fy -= gy;
+            const int i0 = c0 + s.ky + (int)gy;
+#pragma unroll
+            for (int k = 0; k < 2 * kFracMax + 1; ++k) {
+                if (k >= wn) continue;
+                float fx = (float)(k - a.sub) * inv + s.fx;
+                const float gx = floorf(fx);
+                fx -= gx;
+                float R;
+                if (gather_masked(a.Iref, a.w, a.Ry, a.Rx, i0, c1 + s.kx + (int)gx, fy, fx, R)) {
+                    const float d = fmaf(-Wv, R, I);
+                    err[k] = fmaf(d, d, err[k]);
+                    var[k] = fmaf(t, t, var[k]);
+                    ++nv[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * kFracMax + 1; ++k) {
+            if (k >= wn) continue;
+            const float e = nv[k] == 0 ? INFINITY : (var[k] > 0.0f ? err[k] / var[k] : err[k]);
+            if (ia == a.sub && k == a.sub) e_centre = e;
+            key = min(key, ((unsigned long long)__float_as_uint(e) << 32) | (unsigned)(ia * wn + k));
+        }
+    }
+    if (!(e_centre < INFINITY)) return;               // no valid frame at c*: the map is kept
+    const int best = (int)(key & 0xffffffffu);
+    a.u[p] = (double)c0 + (double)(best / wn - a.sub) / a.sub;
+    a.u[P + p] = (double)c1 + (double)(best % wn - a.sub) / a.sub;
+    if (a.err_out) a.err_out[p] = __uint_as_float((unsigned)(key >> 32));
+}
+
 }  // namespace
+
+cudaError_t launch_frac_refine(const pxst_dims &d, int sub, const float *frames, const float *W, const uint8_t *mask,
+                               const float *I_ref, const float *w, const FrameShift *shifts, double *u,
+                               float *err_out, cudaStream_t s) {
+    FracArgs a;
+    a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx; a.sub = sub;
+    a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts; a.u = u;
+    a.err_out = err_out;
+    const size_t P = (size_t)d.ny * d.nx;
+    k_frac_refine<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *mask, double *u, double *num,
                               double *den, cudaStream_t s) {
