@@ -59,6 +59,9 @@ def _bind(L):
     L.pxst_oracle_update_translations.argtypes = [i32] * 8 + [P] * 9
     L.pxst_oracle_filter_map.argtypes = [i32, i32, dbl, P, P, P]
     L.pxst_oracle_update_pixel_map_frac.argtypes = [i32] * 8 + [P] * 9 + [i32]
+    L.pxst_oracle_contrast.argtypes = [i64, P, P]
+    L.pxst_oracle_contrast.restype = dbl
+    L.pxst_oracle_defocus_sweep.argtypes = [i32] * 5 + [P] * 5 + [i32, P, i32, P, P]
     return L
 
 
@@ -270,3 +273,21 @@ def update_pixel_map_frac(frames, W, M, Iref, w, delta, u, window, sub, threads=
                                                    _p(frames), _p(W), _p(M), _p(Iref), _p(w), _p(delta), _p(u),
                                                    _p(u_out), _p(err), int(threads or default_threads()))
     return u_out, err
+
+
+def contrast(Iref, w, L=None):
+    """Standard deviation over mean of I_ref over the pixels with w > 0."""
+    Iref, w = _f64(Iref), _f64(w)
+    return float((L or lib()).pxst_oracle_contrast(Iref.size, _p(Iref), _p(w)))
+
+
+def defocus_sweep(frames, W, M, u, delta, ref_shape, sy, sx, L=None):
+    """fit_defocus_registration: the contrast of the reference image for each pair of map
+    scales (sy[ky], sx[kx]) about the detector's central pixel: [len(sy)][len(sx)]."""
+    frames, W, M, u, delta = _f32(frames), _f32(W), _u8(M), _f64(u), _f64(delta)
+    sy, sx = _f64(sy), _f64(sx)
+    N, ny, nx = frames.shape
+    out = np.empty((sy.size, sx.size))
+    (L or lib()).pxst_oracle_defocus_sweep(N, ny, nx, ref_shape[0], ref_shape[1], _p(frames), _p(W), _p(M), _p(u),
+                                           _p(delta), sy.size, _p(sy), sx.size, _p(sx), _p(out))
+    return out

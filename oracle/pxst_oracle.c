@@ -26,7 +26,9 @@
  *     mapping"): a Gaussian filter of the map;
  *   - update_pixel_map_frac, the first sub-pixel option of section "Update pixel mapping":
  *     the error evaluated at non-integer candidates (bilinear reads, section "Sub-pixel
- *     interpolation") instead of the paraboloid.
+ *     interpolation") instead of the paraboloid;
+ *   - defocus_sweep, fit_defocus_registration of section "Initialisation": a reference
+ *     image built for a range of magnifications, scored by its contrast.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   R1  the bilinear weight multiplies both the M*W*I term and the M*W^2 term;
@@ -408,6 +410,60 @@ void pxst_oracle_iterate(int N, int ny, int nx, int Ry, int Rx, int Sy, int Sx, 
                                      w, delta, u_inout, u_inout, err_out, 0, ny, nthreads);
     }
     /* I_ref and w are those built in the last iteration's step (i) */
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* defocus registration (fit_defocus_registration, section "Initialisation")          */
+/* ---------------------------------------------------------------------------------- */
+
+/* R16 a magnification guess M scales the map about the detector's central pixel
+ *     (i_c, j_c) = (ny/2, nx/2) (integer division): u'_a(x) = u_a(x_c) + s_a (u_a(x) - u_a(x_c))
+ *     per axis a, s_a the ratio of the guessed to the current magnification, the translations
+ *     unchanged; the reference image is make_object_map with u'; its contrast is the standard
+ *     deviation over its mean, both over the reference pixels with w > 0 (0 if none or the
+ *     mean is 0). contrast[ky * nsx + kx] for the pair (sy[ky], sx[kx]). */
+double pxst_oracle_contrast(int64_t R, const double *Iref, const double *w)
+{
+    double s1 = 0.0, s2 = 0.0;
+    int64_t n = 0;
+    for (int64_t c = 0; c < R; ++c) {
+        if (!(w[c] > 0.0)) continue;
+        s1 += Iref[c];
+        n += 1;
+    }
+    if (n == 0) return 0.0;
+    const double mean = s1 / (double)n;
+    for (int64_t c = 0; c < R; ++c) {
+        if (!(w[c] > 0.0)) continue;
+        const double d = Iref[c] - mean;
+        s2 += d * d;
+    }
+    if (mean == 0.0) return 0.0;
+    return sqrt(s2 / (double)n) / mean;
+}
+
+void pxst_oracle_defocus_sweep(int N, int ny, int nx, int Ry, int Rx, const float *frames, const float *W,
+                               const uint8_t *M, const double *u, const double *delta, int nsy, const double *sy,
+                               int nsx, const double *sx, double *contrast)
+{
+    const int64_t P = (int64_t)ny * nx, R = (int64_t)Ry * Rx;
+    const int64_t pc = (int64_t)(ny / 2) * nx + nx / 2;
+    double *us = (double *)malloc(sizeof(double) * 2 * (size_t)P);
+    double *Iref = (double *)malloc(sizeof(double) * (size_t)R);
+    double *w = (double *)malloc(sizeof(double) * (size_t)R);
+    for (int ky = 0; ky < nsy; ++ky) {
+        for (int kx = 0; kx < nsx; ++kx) {
+            for (int64_t p = 0; p < P; ++p) {
+                us[p] = u[pc] + sy[ky] * (u[p] - u[pc]);
+                us[P + p] = u[P + pc] + sx[kx] * (u[P + p] - u[P + pc]);
+            }
+            pxst_oracle_make_object_map(N, ny, nx, Ry, Rx, frames, W, M, us, delta, Iref, w);
+            contrast[ky * nsx + kx] = pxst_oracle_contrast(R, Iref, w);
+        }
+    }
+    free(us);
+    free(Iref);
+    free(w);
 }
 
 /* ---------------------------------------------------------------------------------- */

@@ -558,4 +558,44 @@ def pin_frac_exact_on_bilinear_data(L):
     assert np.all(e1 <= ei)
 
 
+# ---------------------------------------------------------------------------------------
+# defocus registration (fit_defocus_registration, section "Initialisation")
+# ---------------------------------------------------------------------------------------
+
+def pin_defocus_contrast_definition(L):
+    """Unit scales give make_object_map's reference image (pinned separately), whose contrast
+    is numpy's std / mean over the covered pixels; constant frames have contrast 0 at every
+    scale."""
+    rng = np.random.default_rng(61)
+    frames, W, M, u, delta, R = _fractional_scan(rng)
+    got = oracle.defocus_sweep(frames, W, M, u, delta, R, [1.0], [1.0], L=L)
+    Iref, w = oracle.make_object_map(frames, W, M, u, delta, R, L=L)
+    cov = w > 0
+    np.testing.assert_allclose(got[0, 0], Iref[cov].std() / Iref[cov].mean(), rtol=1e-12)
+    fr_c, W_c, M_c, u_c, d_c, R_c = _fractional_scan(rng, const=0.75)
+    sweep = oracle.defocus_sweep(fr_c, W_c, M_c, u_c, d_c, R_c, [0.97, 1.0, 1.03], [0.98, 1.02], L=L)
+    assert np.all(np.abs(sweep) < 1e-12), sweep
+
+
+def pin_defocus_recovers_magnification(L):
+    """Noiseless frames rendered from the continuous field at the true magnification, a base
+    map with the wrong one: the sweep's contrast is highest at the scale that restores the
+    true magnification on each axis."""
+    # translations spanning 36 pixels, so that a 2 % scale error misregisters the frames by
+    # a good fraction of the speckle size
+    s = gen.tiny2d(n_side=4, det=48, step=12, ref=170, sigma=1.5, mag=1.4, offset=50.0, aberr=0.0, window=3,
+                   seed=gen.BASE_SEED + 63, noise=False)
+    # the base map: slopes 4 % too small on rows and 4 % too large on columns
+    ny, nx = s.M.shape
+    pc = (ny // 2, nx // 2)
+    u = s.u_true.copy()
+    u[0] = u[0][pc] + (1 / 1.04) * (u[0] - u[0][pc])
+    u[1] = u[1][pc] + (1 / 0.96) * (u[1] - u[1][pc])
+    sy = np.array([0.98, 1.00, 1.02, 1.04, 1.06, 1.08])
+    sx = np.array([0.92, 0.94, 0.96, 0.98, 1.00, 1.02])
+    c = oracle.defocus_sweep(s.frames, s.W, s.M, u, s.delta, s.ref_shape, sy, sx, L=L)
+    ky, kx = np.unravel_index(np.argmax(c), c.shape)
+    assert (sy[ky], sx[kx]) == (1.04, 0.96), (sy[ky], sx[kx], c)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

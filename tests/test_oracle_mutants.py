@@ -49,6 +49,8 @@ MUTANTS = {
                          "const double c0 = u0 + (double)a / (2 * sub), c1 = u1 + (double)b / sub;"),
     "frac_adds_delta": ("if (!pxst_oracle_gather(Iref, w, Ry, Rx, c0 - delta[2 * n], c1 - delta[2 * n + 1], &R))",
                         "if (!pxst_oracle_gather(Iref, w, Ry, Rx, c0 + delta[2 * n], c1 - delta[2 * n + 1], &R))"),
+    "contrast_not_normalised": ("return sqrt(s2 / (double)n) / mean;", "return sqrt(s2 / (double)n);"),
+    "sweep_scale_inverted": ("us[p] = u[pc] + sy[ky] * (u[p] - u[pc]);", "us[p] = u[pc] + (u[p] - u[pc]) / sy[ky];"),
     "filter_unnormalised": ("u_out[p] = num0 / den;", "u_out[p] = num0;"),
     "filter_ignores_mask": ("if (!M[q]) continue;", "(void)q;"),
     "filter_width_halved": ("const double g = exp(-(double)(a * a + b * b) / (2.0 * sigma * sigma));",
