@@ -191,7 +191,8 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 #define PXST_K_TRANS      11  /* update_translations (with the per-pixel variance) */
 #define PXST_K_FILTER     12  /* filter_map */
 #define PXST_K_FRAC       13  /* update_pixel_map_fractional: the fractional candidates */
-#define PXST_K_COUNT      14
+#define PXST_K_DEFOCUS    14  /* defocus_sweep (includes its make_object_map launches) */
+#define PXST_K_COUNT      15
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);
@@ -245,6 +246,18 @@ pxst_status pxst_update_pixel_map_fractional(const pxst_dims *dims, const pxst_o
                                              const float *I_ref, const float *w, const double *delta,
                                              double *u_inout, float *err_out, void *workspace, size_t ws_bytes,
                                              void *stream);
+
+/* pxst_defocus_sweep (fit_defocus_registration, section "Initialisation"): for every pair of
+ * map scales (sy[ky], sx[kx]) (host arrays, each in (0, 100), at most 64 pairs), the map is
+ * scaled about the detector's central pixel (ny/2, nx/2), u'_a = u_a(centre) + s_a (u_a -
+ * u_a(centre)), with the translations unchanged, make_object_map builds the reference image
+ * (left in I_ref, w: the last pair's), and contrast[ky * n_sx + kx] (device double) receives
+ * its standard deviation over its mean over the reference pixels with w > 0 (0 if none). The
+ * pair with the highest contrast is the magnification estimate. */
+pxst_status pxst_defocus_sweep(const pxst_dims *dims, const float *frames, const float *W, const uint8_t *mask,
+                               const double *u, const double *delta, int32_t n_sy, const double *sy, int32_t n_sx,
+                               const double *sx, double *contrast, float *I_ref, float *w, void *workspace,
+                               size_t ws_bytes, void *stream);
 
 /* pxst_filter_map: the "sigma" regularisation of the pixel map named at the end of section
  * "Update pixel mapping": u(x) <- sum_y g(x - y) M(y) u(y) / sum_y g(x - y) M(y) for pixels

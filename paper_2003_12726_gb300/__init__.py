@@ -26,7 +26,7 @@ FORM_BF16 = 1
 FORM_TF32 = 2
 KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms",
            "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore", "calc_error",
-           "update_translations", "filter_map", "upm_fractional"]
+           "update_translations", "filter_map", "upm_fractional", "defocus_sweep"]
 
 
 class PxstError(RuntimeError):
@@ -116,6 +116,8 @@ def lib():
         L.pxst_filter_map.restype = i32
         L.pxst_update_pixel_map_fractional.argtypes = [D, O, i32] + [P] * 9 + [sz, P]
         L.pxst_update_pixel_map_fractional.restype = i32
+        L.pxst_defocus_sweep.argtypes = [D] + [P] * 5 + [i32, P, i32, P] + [P] * 4 + [sz, P]
+        L.pxst_defocus_sweep.restype = i32
         _lib = L
     return _lib
 
@@ -126,7 +128,7 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
             "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations",
-            "pxst_filter_map", "pxst_update_pixel_map_fractional"]
+            "pxst_filter_map", "pxst_update_pixel_map_fractional", "pxst_defocus_sweep"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -516,3 +518,23 @@ def update_pixel_map_fractional(dims: Dims, opts: Options, sub, frames, W, M, I_
         _check(delta, torch.float64, (N, 2), "delta"), _check(u, torch.float64, (2, ny, nx), "u"),
         _check(err, torch.float32, (ny, nx), "err") if err is not None else None,
         C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)), "update_pixel_map_fractional")
+
+
+def defocus_sweep(dims: Dims, frames, W, M, u, delta, sy, sx, I_ref, w, ws, stream=None):
+    """pxst_defocus_sweep: contrast of the reference image for every pair of map scales
+    (sy[ky], sx[kx]) about the detector centre; returns a float64 CUDA tensor [len(sy)][len(sx)]."""
+    torch = _torch()
+    N, ny, nx, Ry, Rx = dims.n_frames, dims.ny, dims.nx, dims.ref_ny, dims.ref_nx
+    sy = np.ascontiguousarray(sy, dtype=np.float64)
+    sx = np.ascontiguousarray(sx, dtype=np.float64)
+    out = torch.empty((sy.size, sx.size), dtype=torch.float64, device=frames.device)
+    _raise(lib().pxst_defocus_sweep(C.byref(dims.c()), _check(frames, torch.float32, (N, ny, nx), "frames"),
+                                    _check(W, torch.float32, (ny, nx), "W"), _check(M, torch.uint8, (ny, nx), "M"),
+                                    _check(u, torch.float64, (2, ny, nx), "u"),
+                                    _check(delta, torch.float64, (N, 2), "delta"),
+                                    int(sy.size), sy.ctypes.data_as(C.c_void_p), int(sx.size),
+                                    sx.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
+                                    _check(I_ref, torch.float32, (Ry, Rx), "I_ref"),
+                                    _check(w, torch.float32, (Ry, Rx), "w"), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                    _stream(stream)), "defocus_sweep")
+    return out

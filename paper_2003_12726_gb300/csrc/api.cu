@@ -390,6 +390,38 @@ pxst_status pxst_update_pixel_map_fractional(const pxst_dims *dims, const pxst_o
     return PXST_OK;
 }
 
+pxst_status pxst_defocus_sweep(const pxst_dims *dims, const float *frames, const float *W, const uint8_t *mask,
+                               const double *u, const double *delta, int32_t n_sy, const double *sy, int32_t n_sx,
+                               const double *sx, double *contrast, float *I_ref, float *w, void *workspace,
+                               size_t ws_bytes, void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!frames || !W || !mask || !u || !delta || !sy || !sx || !contrast || !I_ref || !w) return PXST_ERR_ARG;
+    if (n_sy < 1 || n_sx < 1 || n_sy * n_sx > 64) return PXST_ERR_ARG;
+    for (int k = 0; k < n_sy; ++k)
+        if (!(sy[k] > 0.0 && sy[k] < 100.0)) return PXST_ERR_ARG;
+    for (int k = 0; k < n_sx; ++k)
+        if (!(sx[k] > 0.0 && sx[k] < 100.0)) return PXST_ERR_ARG;
+    Ws ws;
+    pxst_status st = carve(*dims, PXST_FORM_FP32, workspace, ws_bytes, ws);
+    if (st != PXST_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_prepare(*dims, delta, ws, s);
+    if (st != PXST_OK) return st;
+    const int npairs = n_sy * n_sx;
+    double *acc = ws.tacc_sum;                        // 3 sums per pair (>= kTransMax doubles)
+    PXST_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * npairs, s));
+    Timed t(PXST_K_DEFOCUS, s);
+    for (int ky = 0; ky < n_sy; ++ky)
+        for (int kx = 0; kx < n_sx; ++kx) {
+            PXST_TRY(launch_scale_map(*dims, sy[ky], sx[kx], u, ws.u_save, s));
+            st = run_omap(*dims, frames, W, mask, ws.u_save, I_ref, w, ws, s);
+            if (st != PXST_OK) return st;
+            PXST_TRY(launch_contrast_sums(*dims, I_ref, w, acc + 3 * (ky * n_sx + kx), s));
+        }
+    PXST_TRY(launch_contrast_final(npairs, acc, contrast, s));
+    return PXST_OK;
+}
+
 pxst_status pxst_filter_map(const pxst_dims *dims, double sigma, const uint8_t *mask, double *u_inout,
                             void *workspace, size_t ws_bytes, void *stream) {
     if (!dims_ok(dims)) return PXST_ERR_SHAPE;
@@ -492,6 +524,7 @@ const char *pxst_kernel_name(int32_t k) {
         case PXST_K_TRANS: return "update_translations";
         case PXST_K_FILTER: return "filter_map";
         case PXST_K_FRAC: return "upm_fractional";
+        case PXST_K_DEFOCUS: return "defocus_sweep";
         default: return "?";
     }
 }

@@ -449,7 +449,84 @@ __global__ void __launch_bounds__(128) k_frac_refine(FracArgs a) {
     if (a.err_out) a.err_out[p] = __uint_as_float((unsigned)(key >> 32));
 }
 
+// ---- defocus registration (fit_defocus_registration, section "Initialisation") -----------------
+// One pair of map scales: u' = u(x_c) + s (u - u(x_c)) per axis about the central pixel.
+__global__ void __launch_bounds__(256) k_scale_map(int ny, int nx, double sy, double sx, const double *__restrict__ u,
+                                                   double *__restrict__ us) {
+    const size_t P = (size_t)ny * nx, pc = (size_t)(ny / 2) * nx + nx / 2;
+    const double c0 = u[pc], c1 = u[P + pc];
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        us[p] = c0 + sy * (u[p] - c0);
+        us[P + p] = c1 + sx * (u[P + p] - c1);
+    }
+}
+
+// sums of I_ref, I_ref^2 and the count over w > 0, then the contrast std / mean
+__global__ void __launch_bounds__(256) k_contrast_sums(size_t R, const float *__restrict__ Iref,
+                                                       const float *__restrict__ w, double *acc) {
+    __shared__ double s1[8], s2[8], sn[8];
+    double a1 = 0.0, a2 = 0.0, an = 0.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < R; c += (size_t)gridDim.x * blockDim.x)
+        if (w[c] > 0.0f) {
+            const double v = Iref[c];
+            a1 += v;
+            a2 = fma(v, v, a2);
+            an += 1.0;
+        }
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    an = warp_sum(an);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s1[warp] = a1;
+        s2[warp] = a2;
+        sn[warp] = an;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0, tn = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            t1 += s1[k];
+            t2 += s2[k];
+            tn += sn[k];
+        }
+        atomicAdd(acc, t1);
+        atomicAdd(acc + 1, t2);
+        atomicAdd(acc + 2, tn);
+    }
+}
+
+__global__ void k_contrast_final(int npairs, const double *__restrict__ acc, double *__restrict__ contrast) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    const double n = acc[3 * k + 2];
+    const double mean = n > 0.0 ? acc[3 * k] / n : 0.0;
+    const double var = n > 0.0 ? fmax(acc[3 * k + 1] / n - mean * mean, 0.0) : 0.0;
+    contrast[k] = (n > 0.0 && mean != 0.0) ? sqrt(var) / mean : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_scale_map(const pxst_dims &d, double sy, double sx, const double *u, double *us, cudaStream_t s) {
+    const size_t P = (size_t)d.ny * d.nx;
+    size_t blocks = (P + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_scale_map<<<(unsigned)blocks, 256, 0, s>>>(d.ny, d.nx, sy, sx, u, us);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contrast_sums(const pxst_dims &d, const float *I_ref, const float *w, double *acc, cudaStream_t s) {
+    const size_t R = (size_t)d.ref_ny * d.ref_nx;
+    size_t blocks = (R + 255) / 256;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    k_contrast_sums<<<(unsigned)blocks, 256, 0, s>>>(R, I_ref, w, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contrast_final(int npairs, const double *acc, double *contrast, cudaStream_t s) {
+    k_contrast_final<<<(npairs + 127) / 128, 128, 0, s>>>(npairs, acc, contrast);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_frac_refine(const pxst_dims &d, int sub, const float *frames, const float *W, const uint8_t *mask,
                                const float *I_ref, const float *w, const FrameShift *shifts, double *u,

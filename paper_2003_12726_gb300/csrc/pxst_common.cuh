@@ -153,6 +153,9 @@ cudaError_t launch_update_translations(const pxst_dims &d, int Ty, int Tx, int q
                                        cudaStream_t s);
 cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *mask, double *u, double *num,
                               double *den, cudaStream_t s);
+cudaError_t launch_scale_map(const pxst_dims &d, double sy, double sx, const double *u, double *us, cudaStream_t s);
+cudaError_t launch_contrast_sums(const pxst_dims &d, const float *I_ref, const float *w, double *acc, cudaStream_t s);
+cudaError_t launch_contrast_final(int npairs, const double *acc, double *contrast, cudaStream_t s);
 cudaError_t launch_frac_refine(const pxst_dims &d, int sub, const float *frames, const float *W, const uint8_t *mask,
                                const float *I_ref, const float *w, const FrameShift *shifts, double *u,
                                float *err_out, cudaStream_t s);

@@ -190,3 +190,44 @@ def test_fractional_candidates_parity(scan, sub):
     assert agree >= parity.ARGMIN_AGREE, agree
     ok = same
     np.testing.assert_allclose(eg.ravel()[good][ok], eo.ravel()[good][ok], rtol=1e-4, atol=1e-7)
+
+
+def _gpu_sweep(s, u, sy, sx):
+    import torch
+    import paper_2003_12726_gb300 as px
+    from gpu_util import dev, dims_of
+    d = dims_of(s.frames, s.ref_shape)
+    I = torch.empty(s.ref_shape, dtype=torch.float32, device="cuda")
+    w = torch.empty(s.ref_shape, dtype=torch.float32, device="cuda")
+    ws = px.workspace(d)
+    c = px.defocus_sweep(d, dev(s.frames, torch.float32), dev(s.W, torch.float32), dev(s.M, torch.uint8),
+                         dev(u, torch.float64), dev(s.delta, torch.float64), sy, sx, I, w, ws)
+    return c.cpu().numpy()
+
+
+def test_defocus_sweep_parity(scan):
+    """fit_defocus_registration's contrast per pair of map scales against the oracle's."""
+    s = scan
+    sy = np.array([0.98, 1.0, 1.02])
+    sx = np.array([0.97, 1.0, 1.01, 1.03])
+    want = oracle.defocus_sweep(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape, sy, sx)
+    got = _gpu_sweep(s, s.u_init, sy, sx)
+    np.testing.assert_allclose(got, want, rtol=2e-5)
+    print(s.name, "contrast", got.round(5).tolist())
+
+
+def test_defocus_sweep_recovers_magnification():
+    """Noiseless frames at the true magnification, a base map 4 % off on each axis: the
+    highest contrast restores it (the oracle pin's case, on the GPU)."""
+    s = gen.tiny2d(n_side=4, det=48, step=12, ref=170, sigma=1.5, mag=1.4, offset=50.0, aberr=0.0, window=3,
+                   seed=gen.BASE_SEED + 63, noise=False)
+    ny, nx = s.M.shape
+    pc = (ny // 2, nx // 2)
+    u = s.u_true.copy()
+    u[0] = u[0][pc] + (1 / 1.04) * (u[0] - u[0][pc])
+    u[1] = u[1][pc] + (1 / 0.96) * (u[1] - u[1][pc])
+    sy = np.array([0.98, 1.00, 1.02, 1.04, 1.06, 1.08])
+    sx = np.array([0.92, 0.94, 0.96, 0.98, 1.00, 1.02])
+    c = _gpu_sweep(s, u, sy, sx)
+    ky, kx = np.unravel_index(np.argmax(c), c.shape)
+    assert (sy[ky], sx[kx]) == (1.04, 0.96), c
