@@ -391,6 +391,55 @@ class Reconstruction:
         return h2d, d2h
 
 
+class HostStream:
+    """Many steps of one scan fed from pinned host memory, end to end: every step copies its
+    inputs (frames, whitefield, mask, translations, initial map) host to device, iterates, and
+    copies the map and the error back. Two device input buffers alternate, so that step k+1's
+    host-to-device copy (on a copy stream) runs while step k computes (on the compute stream);
+    the reference image, error and workspace of `rec` serve every step, in order."""
+
+    def __init__(self, rec, pinned):
+        torch = _torch()
+        self.rec = rec
+        self.h = pinned
+        self.copy = torch.cuda.Stream()
+        self.compute = torch.cuda.Stream()
+        mk = lambda t: torch.empty_like(t)
+        self.bufs = [dict(frames=rec.frames, W=rec.W, M=rec.M, delta=rec.delta, u=rec.u),
+                     dict(frames=mk(rec.frames), W=mk(rec.W), M=mk(rec.M), delta=mk(rec.delta), u=mk(rec.u))]
+        self.copied = [torch.cuda.Event(), torch.cuda.Event()]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
+        for e in self.done:
+            e.record(self.compute)
+        self.h2d = sum(pinned[k].numel() * pinned[k].element_size() for k in ("frames", "W", "M", "delta", "u"))
+        self.d2h = pinned["u_out"].numel() * 8 + pinned["err_out"].numel() * 4
+
+    def run(self, steps, n_iter=1):
+        """`steps` end-to-end steps; returns on the host at once (work is queued). Per step:
+        (h2d bytes, d2h bytes) = (self.h2d, self.d2h)."""
+        torch = _torch()
+        r = self.rec
+        for k in range(steps):
+            b = self.bufs[k & 1]
+            self.copy.wait_event(self.done[k & 1])                # the buffer's previous step is done
+            with torch.cuda.stream(self.copy):
+                for key in ("frames", "W", "M", "delta", "u"):
+                    b[key].copy_(self.h[key], non_blocking=True)
+                self.copied[k & 1].record(self.copy)
+            self.compute.wait_event(self.copied[k & 1])
+            with torch.cuda.stream(self.compute):
+                iterate(r.dims, r.opts, n_iter, b["frames"], b["W"], b["M"], b["delta"], b["u"], r.I_ref, r.w,
+                        r.err, r.ws, self.compute)
+                self.h["u_out"].copy_(b["u"], non_blocking=True)
+                self.h["err_out"].copy_(r.err, non_blocking=True)
+                self.done[k & 1].record(self.compute)
+        return self.h2d, self.d2h
+
+    def synchronize(self):
+        self.compute.synchronize()
+        self.copy.synchronize()
+
+
 def tensor_check(form, A, B, stream=None):
     """pxst_tensor_check: D = A . B^T on the tensor cores (A [128][K], B [256][K], CUDA
     tensors of bfloat16 for FORM_BF16 or float32 for FORM_TF32). Returns (D, status bits)."""

@@ -106,3 +106,25 @@ def test_autotune(form):
     same = np.all(np.abs(r.u.cpu().numpy() - uo) <= parity.U_TOL, axis=0)[s.M > 0]
     assert same.mean() >= parity.ARGMIN_AGREE - 0.004, same.mean()
     print("form", form, "tuned tile", tile, "ms", ms)
+
+
+def test_host_stream_matches_plain_steps():
+    """HostStream (inputs from pinned host memory every step, copies overlapped with the
+    previous step's compute on two device buffers) gives every step the result of one plain
+    iteration from the host map."""
+    import torch
+    import paper_2003_12726_gb300 as px
+    s = gen.tiny2d(n_side=5, det=64, step=4, ref=150, window=6, sigma=1.5, mag=1.2, seed=gen.BASE_SEED + 77)
+    ref = _rec(s, 0)
+    ref.run(1)
+    want_u, want_e = ref.u.cpu().numpy(), ref.err.cpu().numpy()
+    rec = _rec(s, 0)
+    pinned = rec.pin_host_buffers(s.frames, s.W, s.M, s.delta, s.u_init)
+    hs = px.HostStream(rec, pinned)
+    h2d, d2h = hs.run(5)
+    hs.synchronize()
+    assert h2d == s.frames.nbytes + s.W.nbytes + s.M.nbytes + s.delta.nbytes + s.u_init.nbytes
+    got_u, got_e = pinned["u_out"].numpy(), pinned["err_out"].numpy()
+    agree = np.all(np.abs(got_u - want_u) <= parity.U_TOL, axis=0)[s.M > 0].mean()
+    assert agree >= 0.999, agree
+    np.testing.assert_allclose(got_e[s.M > 0], want_e[s.M > 0], rtol=1e-5)
