@@ -43,11 +43,10 @@ struct Ws {
     FrameShift *shifts;
     int *exact_list;
     double *num, *den;
-    void *At, *G;
+    void *At, *G, *A2, *V;
     float *Tt, *Rm;
     int *nvalid, *cand;
     uint8_t *edge;
-    unsigned long long *keys;
     int Npad;
 };
 
@@ -70,12 +69,13 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     w.den = reinterpret_cast<double *>(b + L.den);
     w.At = b + L.At;
     w.G = b + L.G;
+    w.A2 = b + L.A2;
+    w.V = b + L.V;
     w.Tt = reinterpret_cast<float *>(b + L.Tt);
     w.nvalid = reinterpret_cast<int *>(b + L.nvalid);
     w.Rm = reinterpret_cast<float *>(b + L.Rm);
     w.cand = reinterpret_cast<int *>(b + L.cand);
     w.edge = reinterpret_cast<uint8_t *>(b + L.edge);
-    w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);
     w.Npad = L.Npad;
     return PXST_OK;
 }
@@ -216,22 +216,22 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
         // 3x3 about the minimum
         if (!operands_ready) {
             Timed t(PXST_K_TPREP, s);
-            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, s));
+            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, w.A2, s));
         }
         {
             Timed t(PXST_K_GTABLE, s);
-            PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.G, w.Tt, w.nvalid, w.Rm, s));
+            PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.G, w.V, w.Tt, w.nvalid, w.Rm, s));
         }
         {
             Timed t(PXST_K_TSEARCH, s);
-            PXST_TRY(launch_tsearch(d, o, w.Npad, w.At, w.G, mask, u, w.Tt, w.nvalid, w.hdr, w.cand,
-                                    w.edge, w.exact_list, s));
+            PXST_TRY(cudaMemsetAsync(&w.hdr->n_edge_tiles, 0, sizeof(int), s));
+            PXST_TRY(launch_tsearch(d, o, w.Npad, w.At, w.A2, w.G, w.V, mask, W, u, w.Tt, w.nvalid, w.hdr,
+                                    w.cand, w.edge, w.exact_list, s));
         }
         // few frames make the reduced-precision ranking noisier: rescore more of it
         const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
         Timed t(PXST_K_RESCORE, s);
-        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.nvalid, w.shifts, w.cand, w.edge,
-                                w.exact_list, w.keys, w.hdr, u, err_out, s));
+        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.shifts, w.cand, w.edge, w.hdr, u, err_out, s));
     } else if (d.n_frames <= search_max_frames()) {
         int sy, sx;
         shift_span(d, delta, s, sy, sx);
@@ -313,7 +313,7 @@ pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_
     if (st != PXST_OK) return st;
     if (opts->form != PXST_FORM_FP32 && n_iter > 0) {
         Timed t(PXST_K_TPREP, s);
-        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, s));
+        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, ws.A2, s));
     }
     for (int it = 0; it < n_iter; ++it) {
         st = run_omap(*dims, frames, W, mask, u_inout, I_ref, w, ws, s);

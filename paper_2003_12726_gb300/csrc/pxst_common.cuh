@@ -25,7 +25,8 @@ struct WsHeader {
     int n_exact;       // pixels appended to the global-path list by the last update
     int n_exact_cta;   // pixels of the last update with a strip evaluated by the per-frame rule
     int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
-    int pad[57];
+    int n_edge_tiles;  // tensor forms: tiles listed for the masked ranking
+    int pad[56];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 
@@ -38,7 +39,7 @@ constexpr int kTransMax = 17 * 17;     // translation update: shifts within +-8 
 struct WsLayout {
     size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp, filt_den;
     // precision forms only (zero size otherwise)
-    size_t At, G, Tt, nvalid, Rm, cand, edge, keys;
+    size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge;
     int Npad;
     size_t total;
 };
@@ -67,18 +68,19 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.delta_tmp = off;  off += align256(sizeof(double) * 2 * (size_t)d.n_frames);
     L.filt_den = off;   off += align256(sizeof(double) * P);        // the map filter's row pass
     L.Npad = 0;
-    L.At = L.G = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.keys = off;
+    L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
         const size_t es = form == PXST_FORM_TF32 ? 4 : 2;
         L.Npad = tensor_npad(d.n_frames, form);
         L.At = off;     off += align256(es * P * L.Npad);
         L.G = off;      off += align256(es * R * L.Npad);
+        L.A2 = off;     off += align256(es * P * L.Npad);     // A~^2 and V: the masked ranking
+        L.V = off;      off += align256(es * R * L.Npad);
         L.Tt = off;     off += align256(sizeof(float) * R);
         L.nvalid = off; off += align256(sizeof(int) * R);
         L.Rm = off;     off += align256(sizeof(float) * R);
         L.cand = off;   off += align256(sizeof(int) * kTopK * P);
         L.edge = off;   off += align256(P);
-        L.keys = off;   off += align256(sizeof(unsigned long long) * P);
     }
     L.total = off;
     return L;
@@ -118,19 +120,19 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
                           cudaStream_t stream);
 cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
-                           const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
-                           const FrameShift *shifts, const int *cand, const uint8_t *edge,
-                           const int *edge_list, unsigned long long *keys, WsHeader *hdr, double *u,
-                           float *err_out, cudaStream_t stream);
+                           const float *W, const uint8_t *mask, const float *Rm, const FrameShift *shifts,
+                           const int *cand, const uint8_t *edge, WsHeader *hdr, double *u, float *err_out,
+                           cudaStream_t stream);
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
-                         const uint8_t *mask, void *At, cudaStream_t stream);
+                         const uint8_t *mask, void *At, void *A2, cudaStream_t stream);
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
-                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, float *Rm,
+                          const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
                           cudaStream_t stream);
-cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *G,
-                           const uint8_t *mask, const double *u, const float *Tt, const int *nvalid,
-                           WsHeader *hdr, int *cand, uint8_t *edge, int *edge_list, cudaStream_t stream);
+cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *A2,
+                           const void *G, const void *V, const uint8_t *mask, const float *W, const double *u,
+                           const float *Tt, const int *nvalid, WsHeader *hdr, int *cand, uint8_t *edge,
+                           int *tile_list, cudaStream_t stream);
 cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float *frames,
                          const float *W, const uint8_t *mask, const float *I_ref,
                          const float *w, const FrameShift *shifts, WsHeader *hdr,

@@ -135,13 +135,15 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
 // ==========================================================================================
 
 // A~ [Npad/KB][ny][nx][KB] (frame blocks of one 128-byte operand row, zero for masked
-// pixels and padding frames): a 32-frame x 32-pixel transpose through shared memory.
+// pixels and padding frames) and A~^2 in the same layout: a 32-frame x 32-pixel transpose
+// through shared memory.
 // The frame-block-major layout makes each TMA box a few contiguous runs of pixels.
 template <typename T>
 __global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
                                                const float *__restrict__ frames,
                                                const float *__restrict__ W,
-                                               const uint8_t *__restrict__ mask, T *__restrict__ At) {
+                                               const uint8_t *__restrict__ mask, T *__restrict__ At,
+                                               T *__restrict__ A2) {
     __shared__ float tile[32][33];
     const size_t P = (size_t)ny * nx;
     const size_t p0 = (size_t)blockIdx.x * 32;
@@ -159,18 +161,23 @@ __global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
     for (int r = ty; r < 32; r += 8) {
         const size_t p = p0 + r;
         const int n = n0 + tx;
-        if (p < P && n < Npad) At[((size_t)(n / KB) * P + p) * KB + (n % KB)] = T(tile[tx][r]);
+        if (p < P && n < Npad) {
+            const float v = tile[tx][r];
+            const size_t o = ((size_t)(n / KB) * P + p) * KB + (n % KB);
+            At[o] = T(v);
+            A2[o] = T(v * v);              // A~^2: the variance contraction of the masked ranking
+        }
     }
 }
 
-// G~ [Npad/KB][Ry][Rx][KB], T~, n_valid and the NaN-masked reference per reference pixel;
-// one warp per reference pixel.
+// G~ [Npad/KB][Ry][Rx][KB], the validity V in the same layout, T~, n_valid and the
+// NaN-masked reference per reference pixel; one warp per reference pixel.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                                                 const float *__restrict__ Iref, const float *__restrict__ w,
                                                 const FrameShift *__restrict__ shifts, T *__restrict__ G,
-                                                float *__restrict__ Tt, int *__restrict__ nvalid,
-                                                float *__restrict__ Rm) {
+                                                T *__restrict__ V, float *__restrict__ Tt,
+                                                int *__restrict__ nvalid, float *__restrict__ Rm) {
     constexpr int KB = 128 / sizeof(T);
     const int lane = threadIdx.x & 31;
     const size_t R = (size_t)Ry * Rx;
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
         float t = 0.0f;
         int nv = 0;
         for (int n = lane; n < Npad; n += 32) {
-            float g = 0.0f;
+            float g = 0.0f, vf = 0.0f;
             if (n < N) {
                 const FrameShift s = shifts[n];
                 float Rv;
@@ -188,10 +195,13 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                     const T gt = T(Rv - 1.0f);
                     g = float(gt);
                     t = fmaf(g, g, t);
+                    vf = 1.0f;
                     ++nv;
                 }
             }
-            G[((size_t)(n / KB) * R + c) * KB + (n % KB)] = T(g);
+            const size_t o = ((size_t)(n / KB) * R + c) * KB + (n % KB);
+            G[o] = T(g);
+            V[o] = T(vf);                  // validity: the masked ranking's variance operand
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -215,6 +225,9 @@ constexpr int TS_EPI_WARPS = 8;               // two per TMEM lane quarter, spli
 constexpr int TS_THREADS = 64 + 32 * TS_EPI_WARPS;   // producer, MMA, epilogue warps
 constexpr int TS_A_BYTES = 128 * 128, TS_B_BYTES = 256 * 128;
 constexpr int TS_SMEM = TS_STAGES * (TS_A_BYTES + TS_B_BYTES) + 1024;
+// masked ranking: each stage holds A~, A~^2, G~ and V; two stages
+constexpr int TSM_STAGES = 2;
+constexpr int TSM_SMEM = TSM_STAGES * 2 * (TS_A_BYTES + TS_B_BYTES) + 1024;
 constexpr int TS_MAX_ORDER = 64;              // chunk rows / columns visited centre-first
 
 struct TSearchArgs {
@@ -226,7 +239,9 @@ struct TSearchArgs {
     WsHeader *hdr;
     int *cand;          // [P][kTopK] window indices of the best candidates, best first (-1: none)
     uint8_t *edge;      // [P] 1: a candidate of the pixel reads an invalid reference pixel
-    int *edge_list;     // those pixels, hdr->n_exact of them (in no particular order)
+    int *tile_list;     // tiles holding such pixels, hdr->n_edge_tiles of them (any order)
+    int tiles_x;        // tiles per detector row (to decode a listed tile)
+    const float *W;     // masked ranking: the whitefield (the key of a zero-variance candidate)
 };
 
 // Insert (qv, idx) into the ascending list bq/bi when it beats an entry (strict <, so of
@@ -267,6 +282,23 @@ __device__ __forceinline__ void scan_row(const float (&v)[32], const float *__re
     }
 }
 
+// The masked ranking's segment: with S = sum_n V A~^2 (second accumulator), a candidate's
+// error over its valid frames is 1 + (T~ - 2 C~) / S, so the key is (T~ - 2 C~) / S; where
+// S = 0 the error is W^2 T~ (not normalised), key W^2 T~ - 1; sT holds T~ (+inf for a
+// candidate with no valid frame).
+template <int TK>
+__device__ __forceinline__ void scan_row_masked(const float (&v)[32], const float (&v2)[32],
+                                                const float *__restrict__ sT, uint32_t use, int rowbase, float W2,
+                                                float (&bq)[TK], int (&bi)[TK]) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const float t = sT[i];
+        float qv = v2[i] > 0.0f ? __fdividef(fmaf(-2.0f, v[i], t), v2[i]) : fmaf(W2, t, -1.0f);
+        qv = (((use >> i) & 1u) && t < INFINITY) ? qv : INFINITY;
+        if (__any_sync(0xffffffffu, qv < bq[TK - 1])) topk_insert<TK>(bq, bi, qv, rowbase + i);
+    }
+}
+
 // Visit order of n chunk rows (or columns): the one holding the tile's centre first, then
 // alternately outwards, so that the best candidates are met early and later chunks rarely
 // change a pixel's list.
@@ -280,9 +312,14 @@ __device__ inline void centre_first(int *ord, int n, int c) {
     }
 }
 
-template <bool TF32, int TK, int PTY, int CCW>
+// MASKED: the second pass over the listed tiles, which ranks every candidate of their pixels
+// that have candidates not valid in every frame, with both contractions in TMEM (one
+// 512-column buffer: D1 = A~ G~^T at column 0, D2 = A~^2 V^T at column 256).
+template <bool TF32, int TK, int PTY, int CCW, bool MASKED>
 __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant__ CUtensorMap tA,
                                                            const __grid_constant__ CUtensorMap tB,
+                                                           const __grid_constant__ CUtensorMap tA2,
+                                                           const __grid_constant__ CUtensorMap tV,
                                                            TSearchArgs a) {
     constexpr int TS_TY = PTY, TS_TX = 128 / PTY;  // pixel tile
     constexpr int TS_CR = 256 / CCW, TS_CC = CCW;  // candidate chunk
@@ -291,9 +328,13 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     constexpr int KB = TF32 ? 32 : 64;       // frames per 128-byte operand row
     constexpr int KSTEP = TF32 ? 8 : 16;     // frames per MMA
     constexpr uint32_t IDESC = tc::instr_desc(TF32 ? 2u : 1u, 128, 256);
+    constexpr int NS = MASKED ? TSM_STAGES : TS_STAGES;                 // pipeline stages
+    constexpr int NBUF = MASKED ? 1 : 2;                                // TMEM accumulator buffers
+    constexpr int SB = (MASKED ? 2 : 1) * (TS_A_BYTES + TS_B_BYTES);    // bytes per stage
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t bar_full[TS_STAGES], bar_empty[TS_STAGES], bar_tfull[2], bar_tempty[2];
+    __shared__ int s_tile_edge;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ int s_box[4];
@@ -307,11 +348,22 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t P = (size_t)a.ny * a.nx;
-    const int x0 = blockIdx.x * TS_TX, y0 = blockIdx.y * TS_TY;
+    int tile_x = blockIdx.x, tile_y = blockIdx.y;
+    if (MASKED) {
+        // the listed tiles only
+        if ((int)blockIdx.x >= a.hdr->n_edge_tiles) return;
+        const int t = a.tile_list[blockIdx.x];
+        tile_x = t % a.tiles_x;
+        tile_y = t / a.tiles_x;
+    }
+    const int x0 = tile_x * TS_TX, y0 = tile_y * TS_TY;
     volatile int *abortp = &abort_flag;
 
     if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
-    if (tid == 0) *abortp = 0;
+    if (tid == 0) {
+        *abortp = 0;
+        s_tile_edge = 0;
+    }
     __syncthreads();
     if (tid < 128) {
         const int x = x0 + (tid % TS_TX), y = y0 + (tid / TS_TX);
@@ -342,17 +394,21 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     const bool ordered = nrc <= TS_MAX_ORDER && ncc <= TS_MAX_ORDER;
 
     if (tid == 0) {
-        for (int i = 0; i < TS_STAGES; ++i) {
+        for (int i = 0; i < NS; ++i) {
             tc::mbar_init(&bar_full[i], 1);
             tc::mbar_init(&bar_empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             tc::mbar_init(&bar_tfull[i], 1);
             tc::mbar_init(&bar_tempty[i], TS_EPI_WARPS);
         }
         tc::fence_mbar_init();
         tc::prefetch_tmap(&tA);
         tc::prefetch_tmap(&tB);
+        if (MASKED) {
+            tc::prefetch_tmap(&tA2);
+            tc::prefetch_tmap(&tV);
+        }
         if (ordered) {
             centre_first(s_rord, nrc, ((s_box[0] + s_box[1]) / 2 - ur0) / TS_CR);
             centre_first(s_cord, ncc, ((s_box[2] + s_box[3]) / 2 - uc0) / TS_CC);
@@ -381,23 +437,28 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                 int row0, col0;
                 chunk_origin(j, row0, col0);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % TS_STAGES;
-                    if (!tc::mbar_wait(&bar_empty[s], ((it / TS_STAGES) & 1) ^ 1, abortp)) {
+                    const int s = it % NS;
+                    if (!tc::mbar_wait(&bar_empty[s], ((it / NS) & 1) ^ 1, abortp)) {
                         *abortp = 1;
                         break;
                     }
-                    uint8_t *As = smem + s * (TS_A_BYTES + TS_B_BYTES);
+                    // stage layout: A~ | G~ (| A~^2 | V)
+                    uint8_t *As = smem + s * SB;
                     uint8_t *Bs = As + TS_A_BYTES;
-                    tc::mbar_expect_tx(&bar_full[s], TS_A_BYTES + TS_B_BYTES);
+                    tc::mbar_expect_tx(&bar_full[s], SB);
                     tc::tma_load_4d(As, &tA, &bar_full[s], 0, x0, y0, kb);
                     tc::tma_load_4d(Bs, &tB, &bar_full[s], 0, col0, row0, kb);
+                    if (MASKED) {
+                        tc::tma_load_4d(Bs + TS_B_BYTES, &tA2, &bar_full[s], 0, x0, y0, kb);
+                        tc::tma_load_4d(Bs + TS_B_BYTES + TS_A_BYTES, &tV, &bar_full[s], 0, col0, row0, kb);
+                    }
                 }
             }
             // let every copy this CTA issued land before the CTA can exit
-            for (int k = 0; k < TS_STAGES && k < it; ++k) {
-                const int i2 = it - 1 - k, s = i2 % TS_STAGES;
+            for (int k = 0; k < NS && k < it; ++k) {
+                const int i2 = it - 1 - k, s = i2 % NS;
                 volatile int never = 0;
-                tc::mbar_wait(&bar_full[s], (i2 / TS_STAGES) & 1, &never);
+                tc::mbar_wait(&bar_full[s], (i2 / NS) & 1, &never);
             }
         }
     } else if (warp == 1) {
@@ -405,26 +466,31 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
         if (lane == 0) {
             int it = 0;
             for (int j = 0; j < nchunks && !*abortp; ++j) {
-                const int buf = j & 1;
-                if (!tc::mbar_wait(&bar_tempty[buf], ((j >> 1) & 1) ^ 1, abortp)) {
+                const int buf = j % NBUF;
+                if (!tc::mbar_wait(&bar_tempty[buf], ((j / NBUF) & 1) ^ 1, abortp)) {
                     *abortp = 1;
                     break;
                 }
                 tc::tc_fence_after();
                 const uint32_t d = tmem + buf * 256;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = it % TS_STAGES;
-                    if (!tc::mbar_wait(&bar_full[s], (it / TS_STAGES) & 1, abortp)) {
+                    const int s = it % NS;
+                    if (!tc::mbar_wait(&bar_full[s], (it / NS) & 1, abortp)) {
                         *abortp = 1;
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(smem + s * (TS_A_BYTES + TS_B_BYTES));
+                    const uint32_t a0 = tc::smem_u32(smem + s * SB);
                     const uint32_t b0 = a0 + TS_A_BYTES;
+                    const uint32_t a20 = b0 + TS_B_BYTES, v0 = a20 + TS_A_BYTES;
 #pragma unroll
-                    for (int k = 0; k < KB / KSTEP; ++k)
+                    for (int k = 0; k < KB / KSTEP; ++k) {
                         tc::mma<TF32>(d, tc::smem_desc_sw128(a0 + k * 32), tc::smem_desc_sw128(b0 + k * 32),
                                       IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                        if (MASKED)
+                            tc::mma<TF32>(tmem + 256, tc::smem_desc_sw128(a20 + k * 32),
+                                          tc::smem_desc_sw128(v0 + k * 32), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+                    }
                     tc::mma_commit(&bar_empty[s]);
                 }
                 if (*abortp) break;
@@ -448,7 +514,17 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             bi[m] = -1;
         }
         bool edge = false;
-        // T~ and validity of segment `ew` of chunk j (+inf / clear bit: not valid in every frame)
+        // masked pass: the pixels it ranks (those with candidates not valid in every frame)
+        bool mine = act;
+        float W2 = 0.0f;
+        if (MASKED && act) {
+            const size_t pix = (size_t)(y0 + p / TS_TX) * a.nx + (x0 + p % TS_TX);
+            mine = a.edge[pix] != 0;
+            const float Wv = a.W[pix];
+            W2 = Wv * Wv;
+        }
+        // T~ and validity of segment `ew` of chunk j (+inf / clear bit: not valid in every
+        // frame; in the masked pass: with no valid frame)
         auto fetch = [&](int j, float &t, bool &ok) {
             int row0, col0;
             chunk_origin(j, row0, col0);
@@ -457,7 +533,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             ok = false;
             if (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) {
                 const size_t c = (size_t)gy * a.Rx + gx;
-                ok = __ldg(a.nvalid + c) == a.N;
+                const int nv = __ldg(a.nvalid + c);
+                ok = MASKED ? nv > 0 : nv == a.N;
                 if (ok) t = __ldg(a.Tt + c);
             }
         };
@@ -471,14 +548,14 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
         for (int j = 0; j < nchunks; ++j) {
-            const int buf = j & 1;
+            const int buf = j % NBUF, sbuf = j & 1;       // accumulator buffer, staged-terms buffer
             int row0, col0;
             chunk_origin(j, row0, col0);
             float tn = INFINITY;
             bool okn = false;
             if (j + 1 < nchunks) fetch(j + 1, tn, okn);
             // a wait that ran out stops every epilogue warp after the same barrier below
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], (j >> 1) & 1, abortp));
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], (j / NBUF) & 1, abortp));
             if (!ok) *abortp = 1;
             tc::tc_fence_after();
             if (ok) {
@@ -490,25 +567,31 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                     const int ilo = max(0, cj - a.Sx - c0), ihi = min(31, cj + a.Sx - c0);
                     const uint32_t colmask =
                         ilo > ihi ? 0u : ((ihi == 31 ? 0xffffffffu : ((1u << (ihi + 1)) - 1u)) & ~((1u << ilo) - 1u));
-                    const uint32_t inmask = (act && aa >= -a.Sy && aa <= a.Sy) ? colmask : 0u;
+                    const uint32_t inmask = (mine && aa >= -a.Sy && aa <= a.Sy) ? colmask : 0u;
                     if (__all_sync(0xffffffffu, inmask == 0u)) continue;
                     float v[32];
                     tc::tmem_ld32(tmem + buf * 256 + g * 32 + ((uint32_t)(q * 32) << 16), v);
-                    const uint32_t vm = s_vm[buf][g];
-                    edge = edge || (inmask & ~vm) != 0u;
+                    const uint32_t vm = s_vm[sbuf][g];
                     const uint32_t use = inmask & vm;
                     const int rowbase = (aa + a.Sy) * wxn + (c0 - cj + a.Sx);
-                    if (__all_sync(0xffffffffu, use == 0xffffffffu))
-                        scan_row<TK, true>(v, &s_T[buf][g * 32], use, rowbase, bq, bi);
-                    else
-                        scan_row<TK, false>(v, &s_T[buf][g * 32], use, rowbase, bq, bi);
+                    if (MASKED) {
+                        float v2[32];
+                        tc::tmem_ld32(tmem + 256 + g * 32 + ((uint32_t)(q * 32) << 16), v2);
+                        scan_row_masked<TK>(v, v2, &s_T[sbuf][g * 32], use, rowbase, W2, bq, bi);
+                    } else {
+                        edge = edge || (inmask & ~vm) != 0u;
+                        if (__all_sync(0xffffffffu, use == 0xffffffffu))
+                            scan_row<TK, true>(v, &s_T[sbuf][g * 32], use, rowbase, bq, bi);
+                        else
+                            scan_row<TK, false>(v, &s_T[sbuf][g * 32], use, rowbase, bq, bi);
+                    }
                 }
             }
             tc::tc_fence_before();
             if (j + 1 < nchunks) {
-                s_T[buf ^ 1][ew * 32 + lane] = tn;
+                s_T[sbuf ^ 1][ew * 32 + lane] = tn;
                 const uint32_t vm = __ballot_sync(0xffffffffu, okn);
-                if (lane == 0) s_vm[buf ^ 1][ew] = vm;
+                if (lane == 0) s_vm[sbuf ^ 1][ew] = vm;
             }
             asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
             if (lane == 0) tc::mbar_arrive(&bar_tempty[buf]);
@@ -524,7 +607,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             s_medge[p] = edge ? 1 : 0;
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
-        if (h == 0 && act && !*abortp) {
+        if (h == 0 && mine && !*abortp) {
 #pragma unroll
             for (int m = 0; m < TK; ++m)
                 if (s_mq[p][m] < bq[TK - 1]) topk_insert<TK>(bq, bi, s_mq[p][m], s_mi[p][m]);
@@ -532,14 +615,22 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             const size_t pix = (size_t)y * a.nx + x;
 #pragma unroll
             for (int m = 0; m < kTopK; ++m) a.cand[pix * kTopK + m] = m < TK ? bi[m] : -1;
-            const bool e = edge || s_medge[p];
-            a.edge[pix] = e ? 1 : 0;
-            if (e) a.edge_list[atomicAdd(&a.hdr->n_exact, 1)] = (int)pix;
+            if (!MASKED) {
+                const bool e = edge || s_medge[p];
+                a.edge[pix] = e ? 1 : 0;
+                if (e) {
+                    atomicAdd(&a.hdr->n_exact, 1);
+                    s_tile_edge = 1;
+                }
+            }
         }
     }
     if (tid == 0 && *abortp) atomicOr(&a.hdr->status, PXST_DEV_TIMEOUT);
     tc::tc_fence_before();
     __syncthreads();
+    // the tile holds pixels for the masked pass
+    if (!MASKED && tid == 0 && s_tile_edge && !*abortp)
+        a.tile_list[atomicAdd(&a.hdr->n_edge_tiles, 1)] = tile_y * a.tiles_x + tile_x;
     if (warp == 1) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, 512);
@@ -551,42 +642,46 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
 // ---- host launchers for the precision form --------------------------------------------------
 
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
-                         const uint8_t *mask, void *At, cudaStream_t stream) {
+                         const uint8_t *mask, void *At, void *A2, cudaStream_t stream) {
     const size_t P = (size_t)d.ny * d.nx;
     dim3 grid((unsigned)((P + 31) / 32), (unsigned)((Npad + 31) / 32));
     if (form == PXST_FORM_TF32)
         k_tprep<float><<<grid, 256, 0, stream>>>(d.n_frames, Npad, d.ny, d.nx, frames, W, mask,
-                                                 static_cast<float *>(At));
+                                                 static_cast<float *>(At), static_cast<float *>(A2));
     else
         k_tprep<__nv_bfloat16><<<grid, 256, 0, stream>>>(d.n_frames, Npad, d.ny, d.nx, frames, W, mask,
-                                                         static_cast<__nv_bfloat16 *>(At));
+                                                         static_cast<__nv_bfloat16 *>(At),
+                                                         static_cast<__nv_bfloat16 *>(A2));
     return cudaGetLastError();
 }
 
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
-                          const FrameShift *shifts, void *G, float *Tt, int *nvalid, float *Rm,
+                          const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
                           cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
     size_t blocks = (R + 7) / 8;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (form == PXST_FORM_TF32)
         k_gtable<float><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref, w,
-                                                               shifts, static_cast<float *>(G), Tt, nvalid, Rm);
+                                                               shifts, static_cast<float *>(G),
+                                                               static_cast<float *>(V), Tt, nvalid, Rm);
     else
         k_gtable<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref,
                                                                        w, shifts, static_cast<__nv_bfloat16 *>(G),
-                                                                       Tt, nvalid, Rm);
+                                                                       static_cast<__nv_bfloat16 *>(V), Tt, nvalid,
+                                                                       Rm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *G,
-                           const uint8_t *mask, const double *u, const float *Tt, const int *nvalid,
-                           WsHeader *hdr, int *cand, uint8_t *edge, int *edge_list, cudaStream_t stream) {
+cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *A2,
+                           const void *G, const void *V, const uint8_t *mask, const float *W, const double *u,
+                           const float *Tt, const int *nvalid, WsHeader *hdr, int *cand, uint8_t *edge,
+                           int *tile_list, cudaStream_t stream) {
     const bool tf32 = o.form == PXST_FORM_TF32;
     const uint64_t es = tf32 ? 4 : 2;
     const uint32_t kb = tf32 ? 32 : 64;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    CUtensorMap tA, tB;
+    CUtensorMap tA, tB, tA2, tV;
     const uint64_t nkb = (uint64_t)Npad / kb, row = (uint64_t)kb * es;     // 128-byte rows
     const uint64_t dA[4] = {kb, (uint64_t)d.nx, (uint64_t)d.ny, nkb};
     const uint64_t sA[3] = {row, row * d.nx, row * d.nx * d.ny};
@@ -597,29 +692,38 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     const uint64_t dB[4] = {kb, (uint64_t)d.ref_nx, (uint64_t)d.ref_ny, nkb};
     const uint64_t sB[3] = {row, row * d.ref_nx, row * d.ref_nx * d.ref_ny};
     const uint32_t bB[4] = {kb, ccw, 256 / ccw, 1};
-    cudaError_t e = tmap_encode(&tA, dt, 4, const_cast<void *>(At), dA, sA, bA);
-    if (e != cudaSuccess) return e;
-    e = tmap_encode(&tB, dt, 4, const_cast<void *>(G), dB, sB, bB);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if ((e = tmap_encode(&tA, dt, 4, const_cast<void *>(At), dA, sA, bA)) != cudaSuccess) return e;
+    if ((e = tmap_encode(&tB, dt, 4, const_cast<void *>(G), dB, sB, bB)) != cudaSuccess) return e;
+    if ((e = tmap_encode(&tA2, dt, 4, const_cast<void *>(A2), dA, sA, bA)) != cudaSuccess) return e;
+    if ((e = tmap_encode(&tV, dt, 4, const_cast<void *>(V), dB, sB, bB)) != cudaSuccess) return e;
     TSearchArgs a;
     a.N = d.n_frames; a.Npad = Npad; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.mask = mask; a.u = u; a.Tt = Tt; a.nvalid = nvalid; a.hdr = hdr;
-    a.cand = cand; a.edge = edge; a.edge_list = edge_list;
-    dim3 grid((d.nx + 128 / pty - 1) / (128 / pty), (d.ny + pty - 1) / pty);
+    a.cand = cand; a.edge = edge; a.tile_list = tile_list; a.W = W;
+    const unsigned gx = (d.nx + 128 / pty - 1) / (128 / pty), gy = (d.ny + pty - 1) / pty;
+    a.tiles_x = (int)gx;
     // list length: the candidates the rescore reads (4 unless more are asked for)
     const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
-    auto go = [&](auto kern) {
-        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
-        if (r == cudaSuccess) kern<<<grid, TS_THREADS, TS_SMEM, stream>>>(tA, tB, a);
-        return r;
+    // the ranking of every tile, then the masked ranking of the tiles it listed (a grid of
+    // one CTA per tile, of which those beyond the list's length return at once)
+    auto go = [&](auto plain, auto masked) {
+        cudaError_t r = cudaFuncSetAttribute(plain, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+        if (r != cudaSuccess) return r;
+        plain<<<dim3(gx, gy), TS_THREADS, TS_SMEM, stream>>>(tA, tB, tA2, tV, a);
+        if ((r = cudaGetLastError()) != cudaSuccess) return r;
+        r = cudaFuncSetAttribute(masked, cudaFuncAttributeMaxDynamicSharedMemorySize, TSM_SMEM);
+        if (r != cudaSuccess) return r;
+        masked<<<gx * gy, TS_THREADS, TSM_SMEM, stream>>>(tA, tB, tA2, tV, a);
+        return cudaGetLastError();
     };
     auto by_shape = [&](auto tf32_tag, auto tk_tag) {
         constexpr bool T = decltype(tf32_tag)::value;
         constexpr int K = decltype(tk_tag)::value;
         switch (shape) {
-            case 1: return go(k_tsearch<T, K, 4, 64>);
-            case 2: return go(k_tsearch<T, K, 2, 128>);
-            default: return go(k_tsearch<T, K, 8, 32>);
+            case 1: return go(k_tsearch<T, K, 4, 64, false>, k_tsearch<T, K, 4, 64, true>);
+            case 2: return go(k_tsearch<T, K, 2, 128, false>, k_tsearch<T, K, 2, 128, true>);
+            default: return go(k_tsearch<T, K, 8, 32, false>, k_tsearch<T, K, 8, 32, true>);
         }
     };
     using t_ = std::true_type;
@@ -628,7 +732,7 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
         e = rk <= 4 ? by_shape(t_{}, std::integral_constant<int, 4>{}) : by_shape(t_{}, std::integral_constant<int, 8>{});
     else
         e = rk <= 4 ? by_shape(f_{}, std::integral_constant<int, 4>{}) : by_shape(f_{}, std::integral_constant<int, 8>{});
-    return e == cudaSuccess ? cudaGetLastError() : e;
+    return e;
 }
 
 }  // namespace pxst

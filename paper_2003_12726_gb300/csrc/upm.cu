@@ -814,27 +814,19 @@ cudaError_t launch_L(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
 
 // ------------------------------------------------------------------------------------
 // Rescore of the tensor-core forms: exact FP32 errors of the candidates the reduced-
-// precision ranking kept, of every candidate of the pixel that is not valid in every frame
-// (the ranking leaves those out: their error is normalised by a variance over fewer
-// frames), and of the 3x3 about the best, then the FP64 fit.
-//   k_rescore_edge: one warp per listed pixel with such candidates; the lanes split the
-//     window (the listed candidates included) and reduce to the lexicographic minimum;
-//     the pixel's frames are staged in shared memory by all 32 lanes at once.
-//   k_rescore: one block per 128 consecutive pixels, one thread per pixel; the frames
-//     stream through a 4-stage cp.async pipeline in shared memory while each thread
-//     evaluates the 3x3 about its first candidate (or the warp's minimum) and the other
-//     listed candidates; the reference is read through the cache.
+// precision ranking kept (for pixels with candidates not valid in every frame, the masked
+// ranking's), and of the 3x3 about the best, then the FP64 fit. k_rescore: one block per
+// 128 consecutive pixels, one thread per pixel; the frames stream through a 4-stage
+// cp.async pipeline in shared memory while each thread evaluates the 3x3 about its first
+// candidate and the other kept candidates; the reference is read through the cache.
 struct RescoreArgs {
     int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ncand;
     const float *frames, *W;
     const uint8_t *mask;
     const float *Rm;          // I_ref where w > 0, NaN elsewhere
-    const int *nvalid;        // frames in which each reference pixel is a valid candidate
     const FrameShift *shifts;
     const int *cand;          // [P][kTopK] window indices, -1 = none
     const uint8_t *edge;      // [P] 1: some candidate of the pixel is not valid in every frame
-    const int *edge_list;     // the pixels with edge = 1; hdr->n_exact of them
-    unsigned long long *keys; // [P] packed (e, window index) minimum of those pixels
     WsHeader *hdr;
     double *u;
     float *err_out;
@@ -942,163 +934,6 @@ __device__ void eval_batch(const RescoreArgs &a, size_t pix, float Wv, const int
     for (int k = 0; k < B; ++k) e[k] = cs[k].e();
 }
 
-constexpr int RE_F = 512;     // frames staged per warp, and shifts per block
-constexpr int RE_B = 4;       // candidates per lane per pass over the frames
-constexpr int RE_L = 512;     // listed candidates held per warp (static smem <= 48 KB)
-
-// One pass over the frames for up to 32 x RE_B listed candidates of one pixel (lane l takes
-// entries l, l + 32, ...; neighbouring lanes hold neighbouring window positions).
-__device__ __forceinline__ void edge_batch(const RescoreArgs &a, const int *list, int b0, int cnt, int lane,
-                                           float *sIw, const int4 *sS, size_t pix, int ci, int cj, float Wv,
-                                           int wxn, unsigned long long &key) {
-    const size_t P = (size_t)a.ny * a.nx;
-    int cy[RE_B], cx[RE_B], id[RE_B], base[RE_B];
-    bool on[RE_B], safe[RE_B];
-    CandSums cs[RE_B];
-    bool all_safe = true;
-#pragma unroll
-    for (int k = 0; k < RE_B; ++k) {
-        const int e = b0 + 32 * k + lane;
-        on[k] = e < cnt;
-        id[k] = on[k] ? list[e] : 0;
-        cy[k] = on[k] ? ci + id[k] / wxn - a.Sy : 0;
-        cx[k] = on[k] ? cj + id[k] % wxn - a.Sx : 0;
-        base[k] = cy[k] * a.Rx + cx[k];
-        safe[k] = on[k] && span_safe(a, cy[k], cy[k], cx[k], cx[k]);
-        all_safe = all_safe && (!on[k] || safe[k]);
-        cs[k].zero();
-    }
-    all_safe = __all_sync(0xffffffffu, all_safe);
-    for (int f0 = 0; f0 < a.N; f0 += RE_F) {
-        const int nf = min(RE_F, a.N - f0);
-        if (a.N > RE_F) {
-            // more frames than one staged slice: stage this one (one slice is staged per pixel)
-            __syncwarp();
-            for (int l = lane; l < nf; l += 32) sIw[l] = __ldcs(a.frames + (size_t)(f0 + l) * P + pix);
-            __syncwarp();
-        }
-        for (int f = 0; f < nf; ++f) {
-            const float I = sIw[f];
-            const float t = I - Wv;
-            int4 q4;
-            if (f0 == 0) {
-                q4 = sS[f];
-            } else {
-                const FrameShift s = a.shifts[f0 + f];
-                q4 = make_int4(s.ky, s.kx, s.ky * a.Rx + s.kx, (s.fy == 0.0f && s.fx == 0.0f) ? 1 : 0);
-            }
-            if (q4.w && all_safe) {                    // the same for every lane
-#pragma unroll
-                for (int k = 0; k < RE_B; ++k) {
-                    if (!on[k]) continue;
-                    const float R = __ldg(a.Rm + (base[k] + q4.z));
-                    cs[k].add(R == R, R, I, t, Wv);
-                }
-            } else if (q4.w) {
-#pragma unroll
-                for (int k = 0; k < RE_B; ++k) {
-                    if (!on[k]) continue;
-                    const float R = read_int(a, cy[k], cx[k], base[k], safe[k], q4.x, q4.y, q4.z);
-                    cs[k].add(R == R, R, I, t, Wv);
-                }
-            } else {
-                const FrameShift s = a.shifts[f0 + f];
-#pragma unroll
-                for (int k = 0; k < RE_B; ++k) {
-                    if (!on[k]) continue;
-                    float R;
-                    const bool ok = gather_rm(a.Rm, a.Ry, a.Rx, cy[k] + s.ky, cx[k] + s.kx, s.fy, s.fx, R);
-                    cs[k].add(ok, R, I, t, Wv);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < RE_B; ++k)
-        if (on[k]) key = min(key, pack_key(cs[k].e(), id[k]));
-}
-
-__global__ void __launch_bounds__(256, 3) k_rescore_edge(RescoreArgs a) {
-    __shared__ float sI[8][RE_F];
-    __shared__ int sL[8][RE_L];
-    __shared__ int4 sS[RE_F];                         // (ky, kx, ky Rx + kx, whole shift)
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    // the shifts of the first RE_F frames, once per block (later frames: global memory)
-    for (int n = threadIdx.x; n < min(a.N, RE_F); n += blockDim.x) {
-        const FrameShift s = a.shifts[n];
-        sS[n] = make_int4(s.ky, s.kx, s.ky * a.Rx + s.kx, (s.fy == 0.0f && s.fx == 0.0f) ? 1 : 0);
-    }
-    __syncthreads();
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const size_t P = (size_t)a.ny * a.nx;
-    const int count = min(a.hdr->n_exact, (int)min(P, (size_t)INT_MAX));
-    const int wxn = 2 * a.Sx + 1, nwin = (2 * a.Sy + 1) * wxn;
-    int *list = sL[wib];
-    float *sIw = sI[wib];
-    for (int it = warp; it < count; it += nwarps) {
-        const size_t pix = (size_t)a.edge_list[it];
-        // listed by the ranking kernel, so M = 1 and u is finite and in range
-        const int ci = (int)floor(a.u[pix] + 0.5), cj = (int)floor(a.u[P + pix] + 0.5);
-        const float Wv = a.W[pix];
-        unsigned long long key = ~0ull;
-        __syncwarp();
-        if (a.N <= RE_F)
-            for (int l = lane; l < a.N; l += 32) sIw[l] = __ldcs(a.frames + (size_t)l * P + pix);
-        // the list: the ranking's candidates, then every window position that is not valid in
-        // every frame, in row-major order; whole batches are evaluated as the list fills and
-        // the remainder is carried to the front
-        int cnt;
-        {
-            const int idx = lane < a.ncand ? a.cand[pix * kTopK + lane] : -1;
-            const unsigned m = __ballot_sync(0xffffffffu, idx >= 0);
-            if (idx >= 0) list[__popc(m & ((1u << lane) - 1u))] = idx;
-            cnt = __popc(m);
-        }
-        int pos0 = 0;
-        while (true) {
-            for (; pos0 < nwin && cnt + 32 <= RE_L; pos0 += 32) {
-                const int pos = pos0 + lane;
-                bool inv = false;
-                if (pos < nwin) {
-                    const int y = ci + pos / wxn - a.Sy, x = cj + pos % wxn - a.Sx;
-                    inv = !(y >= 0 && y < a.Ry && x >= 0 && x < a.Rx) ||
-                          __ldg(a.nvalid + (size_t)y * a.Rx + x) != a.N;
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, inv);
-                if (inv) list[cnt + __popc(m & ((1u << lane) - 1u))] = pos;
-                cnt += __popc(m);
-            }
-            const bool last = pos0 >= nwin;
-            const int nproc = last ? cnt : (cnt / (32 * RE_B)) * (32 * RE_B);
-            __syncwarp();
-            for (int b0 = 0; b0 < nproc; b0 += 32 * RE_B)
-                edge_batch(a, list, b0, cnt, lane, sIw, sS, pix, ci, cj, Wv, wxn, key);
-            if (last) break;
-            // carry the remainder (fewer than one batch, after at least one whole batch)
-            __syncwarp();
-            const int rem = cnt - nproc;
-            int v = lane < rem ? list[nproc + lane] : 0;
-            int v2 = lane + 32 < rem ? list[nproc + lane + 32] : 0;
-            int v3 = lane + 64 < rem ? list[nproc + lane + 64] : 0;
-            int v4 = lane + 96 < rem ? list[nproc + lane + 96] : 0;
-            __syncwarp();
-            if (lane < rem) list[lane] = v;
-            if (lane + 32 < rem) list[lane + 32] = v2;
-            if (lane + 64 < rem) list[lane + 64] = v3;
-            if (lane + 96 < rem) list[lane + 96] = v4;
-            cnt = rem;
-            __syncwarp();
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
-            key = min(key, o);
-        }
-        if (lane == 0) a.keys[pix] = key;
-    }
-}
-
 constexpr int RS_T = 128;     // pixels per block
 constexpr int RS_F = 16;      // frames per pipeline stage
 constexpr int RS_S = 4;       // pipeline stages
@@ -1152,20 +987,15 @@ __global__ void __launch_bounds__(RS_T) k_rescore(RescoreArgs a) {
     int xid[XK > 0 ? XK : 1];                         // listed candidates outside that 3x3
     int nxk = 0;
     if (act) {
-        if (a.edge[pix]) {
-            key = a.keys[pix];                        // minimum over the whole window
-            if (__uint_as_float((unsigned int)(key >> 32)) < INFINITY) c0 = (int)(key & 0xffffffffu);
-        } else {
-            c0 = a.cand[pix * kTopK];
+        c0 = a.cand[pix * kTopK];
 #pragma unroll
-            for (int m = 1; m <= XK; ++m) {
-                const int idx = m < a.ncand ? a.cand[pix * kTopK + m] : -1;
-                const bool far = idx >= 0 && c0 >= 0 && (abs(idx / wxn - c0 / wxn) > 1 || abs(idx % wxn - c0 % wxn) > 1);
+        for (int m = 1; m <= XK; ++m) {
+            const int idx = m < a.ncand ? a.cand[pix * kTopK + m] : -1;
+            const bool far = idx >= 0 && c0 >= 0 && (abs(idx / wxn - c0 / wxn) > 1 || abs(idx % wxn - c0 % wxn) > 1);
 #pragma unroll
-                for (int q = 0; q < XK; ++q)
-                    if (q == nxk && far) xid[q] = idx;
-                nxk += far ? 1 : 0;
-            }
+            for (int q = 0; q < XK; ++q)
+                if (q == nxk && far) xid[q] = idx;
+            nxk += far ? 1 : 0;
         }
     }
     const bool run = act && c0 >= 0;
@@ -1435,17 +1265,14 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
 }
 
 cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
-                           const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
-                           const FrameShift *shifts, const int *cand, const uint8_t *edge,
-                           const int *edge_list, unsigned long long *keys, WsHeader *hdr, double *u,
-                           float *err_out, cudaStream_t stream) {
+                           const float *W, const uint8_t *mask, const float *Rm, const FrameShift *shifts,
+                           const int *cand, const uint8_t *edge, WsHeader *hdr, double *u, float *err_out,
+                           cudaStream_t stream) {
     RescoreArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0; a.ncand = ncand;
-    a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.nvalid = nvalid; a.shifts = shifts;
-    a.cand = cand; a.edge = edge; a.edge_list = edge_list; a.keys = keys;
-    a.hdr = hdr; a.u = u; a.err_out = err_out;
-    k_rescore_edge<<<152 * 8, 256, 0, stream>>>(a);
+    a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.shifts = shifts;
+    a.cand = cand; a.edge = edge; a.hdr = hdr; a.u = u; a.err_out = err_out;
     const size_t P = (size_t)d.ny * d.nx;
     const unsigned blocks = (unsigned)((P + RS_T - 1) / RS_T);
     if (ncand <= 4)

@@ -60,8 +60,8 @@ def _inputs(s, hole):
     Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
     I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
     if hole:
-        # an uncovered patch inside the reference: candidates reading it lose frames and are
-        # evaluated by the masked rule instead of being ranked on the tensor cores
+        # an uncovered patch inside the reference: candidates reading it lose frames, and
+        # their pixels are ranked again with the variance over their valid frames
         Ry, Rx = s.ref_shape
         w32[Ry // 2 - 3:Ry // 2 + 3, Rx // 2 - 4:Rx // 2 + 4] = 0.0
         I32[w32 == 0] = 0.0
@@ -73,9 +73,9 @@ def _inputs(s, hole):
 @pytest.mark.parametrize("hole", [False, True], ids=["covered", "hole"])
 @pytest.mark.parametrize("form", [1, 2], ids=["bf16", "tf32"])
 def test_tensor_form_parity(tscan, form, hole):
-    """BF16 / TF32 ranking on the tensor cores + exact FP32 evaluation of the best few (and of
-    every candidate that is not valid in every frame) against the FP64 oracle, with the same
-    tolerances as the FP32 form."""
+    """BF16 / TF32 ranking on the tensor cores (the masked ranking for pixels with candidates
+    not valid in every frame) + exact FP32 evaluation of the best few against the FP64 oracle,
+    with the same tolerances as the FP32 form."""
     import parity
     from gpu_util import gpu_update
     s = tscan
