@@ -45,7 +45,7 @@ struct Ws {
     double *num, *den;
     void *At, *G, *A2, *V;
     float *Tt, *Rm;
-    int *nvalid, *cand;
+    int *nvalid, *cand, *wlist;
     uint8_t *edge;
     int Npad;
 };
@@ -76,6 +76,7 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     w.Rm = reinterpret_cast<float *>(b + L.Rm);
     w.cand = reinterpret_cast<int *>(b + L.cand);
     w.edge = reinterpret_cast<uint8_t *>(b + L.edge);
+    w.wlist = reinterpret_cast<int *>(b + L.wlist);
     w.Npad = L.Npad;
     return PXST_OK;
 }
@@ -211,12 +212,12 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
                        bool operands_ready = false) {
     PXST_TRY(cudaMemsetAsync(&w.hdr->n_exact, 0, 2 * sizeof(int), s));   // n_exact, n_exact_cta
     if (o.form != PXST_FORM_FP32) {
-        // tensor-core ranking of every candidate that is valid in every frame, then exact
-        // FP32 errors of the best few per pixel, of every candidate that is not, and of the
-        // 3x3 about the minimum
+        // tensor-core ranking of every candidate that is valid in every frame, the masked
+        // ranking of the pixels with candidates that are not, then exact FP32 errors of the
+        // best few per pixel and of the 3x3 about the minimum
         if (!operands_ready) {
             Timed t(PXST_K_TPREP, s);
-            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, w.A2, s));
+            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, s));
         }
         {
             Timed t(PXST_K_GTABLE, s);
@@ -231,7 +232,7 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
         // few frames make the reduced-precision ranking noisier: rescore more of it
         const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
         Timed t(PXST_K_RESCORE, s);
-        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.shifts, w.cand, w.edge, w.hdr, u, err_out, s));
+        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.nvalid, w.shifts, w.cand, w.hdr, w.wlist, u, err_out, s));
     } else if (d.n_frames <= search_max_frames()) {
         int sy, sx;
         shift_span(d, delta, s, sy, sx);
@@ -313,7 +314,7 @@ pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_
     if (st != PXST_OK) return st;
     if (opts->form != PXST_FORM_FP32 && n_iter > 0) {
         Timed t(PXST_K_TPREP, s);
-        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, ws.A2, s));
+        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, s));
     }
     for (int it = 0; it < n_iter; ++it) {
         st = run_omap(*dims, frames, W, mask, u_inout, I_ref, w, ws, s);

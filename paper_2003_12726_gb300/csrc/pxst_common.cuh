@@ -26,7 +26,8 @@ struct WsHeader {
     int n_exact_cta;   // pixels of the last update with a strip evaluated by the per-frame rule
     int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
     int n_edge_tiles;  // tensor forms: tiles listed for the masked ranking
-    int pad[56];
+    int n_rescore_warps;   // tensor forms: warps listed for the general rescore
+    int pad[55];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 
@@ -39,7 +40,7 @@ constexpr int kTransMax = 17 * 17;     // translation update: shifts within +-8 
 struct WsLayout {
     size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp, filt_den;
     // precision forms only (zero size otherwise)
-    size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge;
+    size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge, wlist;
     int Npad;
     size_t total;
 };
@@ -68,7 +69,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.delta_tmp = off;  off += align256(sizeof(double) * 2 * (size_t)d.n_frames);
     L.filt_den = off;   off += align256(sizeof(double) * P);        // the map filter's row pass
     L.Npad = 0;
-    L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = off;
+    L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.wlist = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
         const size_t es = form == PXST_FORM_TF32 ? 4 : 2;
         L.Npad = tensor_npad(d.n_frames, form);
@@ -81,6 +82,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
         L.Rm = off;     off += align256(sizeof(float) * R);
         L.cand = off;   off += align256(sizeof(int) * kTopK * P);
         L.edge = off;   off += align256(P);
+        L.wlist = off;  off += align256(sizeof(int) * (P / 32 + 1));   // warps for the general rescore
     }
     L.total = off;
     return L;
@@ -120,16 +122,16 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           int *exact_list, double *u, float *err_out, int span_y, int span_x,
                           cudaStream_t stream);
 cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
-                           const float *W, const uint8_t *mask, const float *Rm, const FrameShift *shifts,
-                           const int *cand, const uint8_t *edge, WsHeader *hdr, double *u, float *err_out,
-                           cudaStream_t stream);
+                           const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
+                           const FrameShift *shifts, const int *cand, WsHeader *hdr, int *wlist, double *u,
+                           float *err_out, cudaStream_t stream);
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
-                         const uint8_t *mask, void *At, void *A2, cudaStream_t stream);
+                         const uint8_t *mask, void *At, cudaStream_t stream);
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
                           const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
                           cudaStream_t stream);
-cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *A2,
+cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, void *A2,
                            const void *G, const void *V, const uint8_t *mask, const float *W, const double *u,
                            const float *Tt, const int *nvalid, WsHeader *hdr, int *cand, uint8_t *edge,
                            int *tile_list, cudaStream_t stream);
@@ -187,6 +189,31 @@ __device__ __forceinline__ bool gather_masked(const float *__restrict__ Iref,
         const size_t c = (size_t)ii * Rx + jj;
         if (!(__ldg(w + c) > 0.0f)) continue;
         num = fmaf(wt[k], __ldg(Iref + c), num);
+        den += wt[k];
+    }
+    if (!(den > 0.0f)) return false;
+    R = num / den;
+    return true;
+}
+
+// R_n at (i0 + fy, j0 + fx) by the masked renormalised bilinear gather, read from the
+// NaN-masked reference (the same arithmetic as gather_masked); false: frame not valid.
+__device__ __forceinline__ bool gather_rm(const float *__restrict__ Rm, int Ry, int Rx, int i0, int j0,
+                                          float fy, float fx, float &R) {
+    if (fy == 0.0f && fx == 0.0f) {
+        if (i0 < 0 || i0 >= Ry || j0 < 0 || j0 >= Rx) return false;
+        R = __ldg(Rm + (size_t)i0 * Rx + j0);
+        return R == R;
+    }
+    const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx), fy * fx};
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
+        if (wt[k] == 0.0f || ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;
+        const float r = __ldg(Rm + (size_t)ii * Rx + jj);
+        if (r != r) continue;
+        num = fmaf(wt[k], r, num);
         den += wt[k];
     }
     if (!(den > 0.0f)) return false;

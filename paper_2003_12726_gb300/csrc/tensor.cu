@@ -1,7 +1,7 @@
 // tensor.cu -- tensor-core (tcgen05) precision forms of update_pixel_map on sm_103a.
 //
-// Kernels: the operand preparation (k_tprep, k_gtable), the tensor-core ranking of every
-// candidate (k_tsearch) and a diagnostic contraction (k_tc_check) that checks the tcgen05
+// Kernels: the operand preparation (k_tprep, k_gtable, k_tsquare), the tensor-core ranking
+// of every candidate (k_tsearch, and its masked pass) and a diagnostic contraction (k_tc_check) that checks the tcgen05
 // machinery: TMA loads with 128-byte swizzle into shared memory, tcgen05.mma accumulating
 // in TMEM, and tcgen05.ld read-back.
 #include <cuda.h>
@@ -135,63 +135,118 @@ __global__ void __launch_bounds__(128) k_tc_check(const __grid_constant__ CUtens
 // ==========================================================================================
 
 // A~ [Npad/KB][ny][nx][KB] (frame blocks of one 128-byte operand row, zero for masked
-// pixels and padding frames) and A~^2 in the same layout: a 32-frame x 32-pixel transpose
-// through shared memory.
+// pixels and padding frames): one block per frame block x 64 pixels. The frames are read in
+// coalesced rows of 64 pixels, transposed through shared memory and written as 16-byte
+// pieces of each pixel's operand row (a warp writes 512 contiguous bytes).
 // The frame-block-major layout makes each TMA box a few contiguous runs of pixels.
+constexpr int TP_PIX = 64;
 template <typename T>
-__global__ void __launch_bounds__(256) k_tprep(int N, int Npad, int ny, int nx,
-                                               const float *__restrict__ frames,
+__global__ void __launch_bounds__(256) k_tprep(int N, int ny, int nx, const float *__restrict__ frames,
                                                const float *__restrict__ W,
-                                               const uint8_t *__restrict__ mask, T *__restrict__ At,
-                                               T *__restrict__ A2) {
-    __shared__ float tile[32][33];
+                                               const uint8_t *__restrict__ mask, T *__restrict__ At) {
+    constexpr int KB = 128 / sizeof(T);       // frames per operand row
+    constexpr int EPP = 16 / sizeof(T);       // elements per 16-byte piece
+    __shared__ float tile[KB][TP_PIX + 1];
     const size_t P = (size_t)ny * nx;
-    const size_t p0 = (size_t)blockIdx.x * 32;
-    const int n0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 8 rows of 32
-    for (int r = ty; r < 32; r += 8) {
-        const int n = n0 + r;
-        const size_t p = p0 + tx;
-        float v = 0.0f;
-        if (n < N && p < P && mask[p]) v = __ldg(frames + (size_t)n * P + p) / __ldg(W + p) - 1.0f;
-        tile[r][tx] = v;
+    const size_t p0 = (size_t)blockIdx.x * TP_PIX;
+    const int kb = blockIdx.y, n0 = kb * KB;
+    const int col = threadIdx.x & (TP_PIX - 1), r0 = threadIdx.x / TP_PIX;   // 4 rows of 64
+    const size_t p = p0 + col;
+    const bool on = p < P && mask[p];
+    // the operand only ranks candidates, so I * (1/W) stands in for I / W
+    const float rw = on ? __frcp_rn(__ldg(W + p)) : 0.0f;
+    float f[KB / 4];
+#pragma unroll
+    for (int i = 0; i < KB / 4; ++i) {            // every load in flight before the first use
+        const int n = n0 + r0 + 4 * i;
+        f[i] = (on && n < N) ? __ldcs(frames + (size_t)n * P + p) : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < KB / 4; ++i) {
+        const int n = n0 + r0 + 4 * i;
+        tile[r0 + 4 * i][col] = (on && n < N) ? fmaf(f[i], rw, -1.0f) : 0.0f;
     }
     __syncthreads();
-    constexpr int KB = 128 / sizeof(T);
-    for (int r = ty; r < 32; r += 8) {
-        const size_t p = p0 + r;
-        const int n = n0 + tx;
-        if (p < P && n < Npad) {
-            const float v = tile[tx][r];
-            const size_t o = ((size_t)(n / KB) * P + p) * KB + (n % KB);
-            At[o] = T(v);
-            A2[o] = T(v * v);              // A~^2: the variance contraction of the masked ranking
-        }
+    for (int q = threadIdx.x; q < TP_PIX * 8; q += 256) {
+        const int pp = q >> 3, piece = q & 7;    // pixel of the block, 16-byte piece of its row
+        if (p0 + pp >= P) continue;
+        uint4 out;
+        T *o = reinterpret_cast<T *>(&out);
+#pragma unroll
+        for (int e = 0; e < EPP; ++e) o[e] = T(tile[piece * EPP + e][pp]);
+        *reinterpret_cast<uint4 *>(At + ((size_t)kb * P + p0 + pp) * KB + piece * EPP) = out;
     }
 }
 
-// G~ [Npad/KB][Ry][Rx][KB], the validity V in the same layout, T~, n_valid and the
-// NaN-masked reference per reference pixel; one warp per reference pixel.
+// A~^2 (the masked ranking's variance operand, in A~'s layout) for the tiles the masked
+// ranking visits: one block per listed tile, of which those beyond the list's length return
+// at once; 16-byte pieces of the tile's operand rows, squared elementwise.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
-                                                const float *__restrict__ Iref, const float *__restrict__ w,
+__global__ void __launch_bounds__(256) k_tsquare(int nkb, int ny, int nx, int pty, int tiles_x,
+                                                 const WsHeader *__restrict__ hdr, const int *__restrict__ tile_list,
+                                                 const T *__restrict__ At, T *__restrict__ A2) {
+    constexpr int KB = 128 / sizeof(T), EPP = 16 / sizeof(T);
+    if ((int)blockIdx.x >= hdr->n_edge_tiles) return;
+    const int tl = tile_list[blockIdx.x];
+    const int tx = 128 / pty;
+    const int x0 = (tl % tiles_x) * tx, y0 = (tl / tiles_x) * pty;
+    const size_t P = (size_t)ny * nx;
+    for (int q = threadIdx.x; q < nkb * 128 * 8; q += 256) {
+        const int piece = q & 7, pix = (q >> 3) & 127, kb = q >> 10;
+        const int x = x0 + pix % tx, y = y0 + pix / tx;
+        if (x >= nx || y >= ny) continue;
+        const size_t o = ((size_t)kb * P + (size_t)y * nx + x) * KB + piece * EPP;
+        uint4 v = *reinterpret_cast<const uint4 *>(At + o);
+        T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+        for (int k = 0; k < EPP; ++k) {
+            const float f = float(e[k]);
+            e[k] = T(f * f);
+        }
+        *reinterpret_cast<uint4 *>(A2 + o) = v;
+    }
+}
+
+// The reference with uncovered pixels as NaN (the gathers below and the exact rescore read it).
+__global__ void __launch_bounds__(256) k_rmask(size_t R, const float *__restrict__ Iref,
+                                               const float *__restrict__ w, float *__restrict__ Rm) {
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < R; c += (size_t)gridDim.x * blockDim.x)
+        Rm[c] = __ldg(w + c) > 0.0f ? __ldg(Iref + c) : __int_as_float(0x7fc00000);
+}
+
+// G~ [Npad/KB][Ry][Rx][KB], the validity V (0 or 1) in the same layout, T~ and n_valid,
+// gathered from the NaN-masked reference: one block per 32 consecutive reference pixels. For each frame block
+// the 8 warps gather with lanes over the 32 pixels (one frame's reads coalesce), the values
+// are transposed through shared memory and written as 32 operand rows of 128 bytes
+// (4 KB contiguous per array).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx, const float *__restrict__ Rm,
                                                 const FrameShift *__restrict__ shifts, T *__restrict__ G,
                                                 T *__restrict__ V, float *__restrict__ Tt,
-                                                int *__restrict__ nvalid, float *__restrict__ Rm) {
+                                                int *__restrict__ nvalid) {
     constexpr int KB = 128 / sizeof(T);
-    const int lane = threadIdx.x & 31;
+    constexpr int RW = 33;                         // words per padded shared row (32 + 1)
+    __shared__ uint32_t sg[32 * RW], sv[32 * RW];
+    __shared__ float s_t[8][32];
+    __shared__ int s_n[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t R = (size_t)Ry * Rx;
-    for (size_t c = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; c < R;
-         c += ((size_t)gridDim.x * blockDim.x) >> 5) {
-        const int cy = (int)(c / Rx), cx = (int)(c % Rx);
-        float t = 0.0f;
-        int nv = 0;
-        for (int n = lane; n < Npad; n += 32) {
+    const size_t c0 = (size_t)blockIdx.x * 32, c = c0 + lane;
+    const bool inr = c < R;
+    const int cy = inr ? (int)(c / Rx) : 0, cx = inr ? (int)(c % Rx) : 0;
+    T *rowg = reinterpret_cast<T *>(sg + lane * RW), *rowv = reinterpret_cast<T *>(sv + lane * RW);
+    float t = 0.0f;
+    int nv = 0;
+    const int nkb = Npad / KB;
+    for (int kb = 0; kb < nkb; ++kb) {
+#pragma unroll
+        for (int jj = 0; jj < KB / 8; ++jj) {
+            const int j = warp + 8 * jj, n = kb * KB + j;
             float g = 0.0f, vf = 0.0f;
-            if (n < N) {
+            if (inr && n < N) {
                 const FrameShift s = shifts[n];
                 float Rv;
-                if (gather_masked(Iref, w, Ry, Rx, cy + s.ky, cx + s.kx, s.fy, s.fx, Rv)) {
+                if (gather_rm(Rm, Ry, Rx, cy + s.ky, cx + s.kx, s.fy, s.fx, Rv)) {
                     const T gt = T(Rv - 1.0f);
                     g = float(gt);
                     t = fmaf(g, g, t);
@@ -199,21 +254,35 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                     ++nv;
                 }
             }
-            const size_t o = ((size_t)(n / KB) * R + c) * KB + (n % KB);
-            G[o] = T(g);
-            V[o] = T(vf);                  // validity: the masked ranking's variance operand
+            rowg[j] = T(g);
+            rowv[j] = T(vf);
         }
+        __syncthreads();
+        uint32_t *G32 = reinterpret_cast<uint32_t *>(G) + (size_t)kb * R * 32;
+        uint32_t *V32 = reinterpret_cast<uint32_t *>(V) + (size_t)kb * R * 32;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            t += __shfl_xor_sync(0xffffffffu, t, off);
-            nv += __shfl_xor_sync(0xffffffffu, nv, off);
+        for (int i = 0; i < 4; ++i) {
+            const int q = threadIdx.x + 256 * i, r = q >> 5, k = q & 31;
+            if (c0 + r < R) {
+                G32[(c0 + r) * 32 + k] = sg[r * RW + k];
+                V32[(c0 + r) * 32 + k] = sv[r * RW + k];
+            }
         }
-        if (lane == 0) {
-            Tt[c] = t;
-            nvalid[c] = nv;
-            // the reference with uncovered pixels as NaN, for the exact rescore
-            Rm[c] = __ldg(w + c) > 0.0f ? __ldg(Iref + c) : __int_as_float(0x7fc00000);
+        __syncthreads();
+    }
+    s_t[warp][lane] = t;
+    s_n[warp][lane] = nv;
+    __syncthreads();
+    if (warp == 0 && inr) {
+        float tt = 0.0f;
+        int nn = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            tt += s_t[k][lane];
+            nn += s_n[k][lane];
         }
+        Tt[c] = tt;
+        nvalid[c] = nn;
     }
 }
 
@@ -642,16 +711,15 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
 // ---- host launchers for the precision form --------------------------------------------------
 
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
-                         const uint8_t *mask, void *At, void *A2, cudaStream_t stream) {
+                         const uint8_t *mask, void *At, cudaStream_t stream) {
     const size_t P = (size_t)d.ny * d.nx;
-    dim3 grid((unsigned)((P + 31) / 32), (unsigned)((Npad + 31) / 32));
+    const int KB = form == PXST_FORM_TF32 ? 32 : 64;
+    dim3 grid((unsigned)((P + TP_PIX - 1) / TP_PIX), (unsigned)(Npad / KB));
     if (form == PXST_FORM_TF32)
-        k_tprep<float><<<grid, 256, 0, stream>>>(d.n_frames, Npad, d.ny, d.nx, frames, W, mask,
-                                                 static_cast<float *>(At), static_cast<float *>(A2));
+        k_tprep<float><<<grid, 256, 0, stream>>>(d.n_frames, d.ny, d.nx, frames, W, mask, static_cast<float *>(At));
     else
-        k_tprep<__nv_bfloat16><<<grid, 256, 0, stream>>>(d.n_frames, Npad, d.ny, d.nx, frames, W, mask,
-                                                         static_cast<__nv_bfloat16 *>(At),
-                                                         static_cast<__nv_bfloat16 *>(A2));
+        k_tprep<__nv_bfloat16><<<grid, 256, 0, stream>>>(d.n_frames, d.ny, d.nx, frames, W, mask,
+                                                         static_cast<__nv_bfloat16 *>(At));
     return cudaGetLastError();
 }
 
@@ -659,21 +727,19 @@ cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I
                           const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
                           cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
-    size_t blocks = (R + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_rmask<<<(unsigned)std::min<size_t>((R + 255) / 256, 152 * 16), 256, 0, stream>>>(R, I_ref, w, Rm);
+    const unsigned blocks = (unsigned)((R + 31) / 32);
     if (form == PXST_FORM_TF32)
-        k_gtable<float><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref, w,
-                                                               shifts, static_cast<float *>(G),
-                                                               static_cast<float *>(V), Tt, nvalid, Rm);
+        k_gtable<float><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts,
+                                                     static_cast<float *>(G), static_cast<float *>(V), Tt, nvalid);
     else
-        k_gtable<__nv_bfloat16><<<(unsigned)blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, I_ref,
-                                                                       w, shifts, static_cast<__nv_bfloat16 *>(G),
-                                                                       static_cast<__nv_bfloat16 *>(V), Tt, nvalid,
-                                                                       Rm);
+        k_gtable<__nv_bfloat16><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts,
+                                                             static_cast<__nv_bfloat16 *>(G),
+                                                             static_cast<__nv_bfloat16 *>(V), Tt, nvalid);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, const void *A2,
+cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, void *A2,
                            const void *G, const void *V, const uint8_t *mask, const float *W, const double *u,
                            const float *Tt, const int *nvalid, WsHeader *hdr, int *cand, uint8_t *edge,
                            int *tile_list, cudaStream_t stream) {
@@ -711,6 +777,14 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
         cudaError_t r = cudaFuncSetAttribute(plain, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
         if (r != cudaSuccess) return r;
         plain<<<dim3(gx, gy), TS_THREADS, TS_SMEM, stream>>>(tA, tB, tA2, tV, a);
+        if ((r = cudaGetLastError()) != cudaSuccess) return r;
+        if (tf32)
+            k_tsquare<float><<<gx * gy, 256, 0, stream>>>((int)nkb, d.ny, d.nx, (int)pty, (int)gx, hdr, tile_list,
+                                                          static_cast<const float *>(At), static_cast<float *>(A2));
+        else
+            k_tsquare<__nv_bfloat16><<<gx * gy, 256, 0, stream>>>(
+                (int)nkb, d.ny, d.nx, (int)pty, (int)gx, hdr, tile_list, static_cast<const __nv_bfloat16 *>(At),
+                static_cast<__nv_bfloat16 *>(A2));
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
         r = cudaFuncSetAttribute(masked, cudaFuncAttributeMaxDynamicSharedMemorySize, TSM_SMEM);
         if (r != cudaSuccess) return r;

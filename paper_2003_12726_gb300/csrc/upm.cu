@@ -20,7 +20,8 @@
 // masked renormalised reads from global memory, lexicographic warp argmin, FP64 fit.
 // It serves tiles whose reference window does not fit in shared memory and scans with
 // too many frames to stage.
-// Rescore (k_rescore): the exact stage of the tensor-core forms, one thread per pixel.
+// Rescore (k_rescore_lean, k_rescore_general): the exact stage of the tensor-core forms,
+// one thread per pixel.
 #include <climits>
 #include <cmath>
 
@@ -816,18 +817,20 @@ cudaError_t launch_L(const SearchArgs &a, const Plan &pl, cudaStream_t stream) {
 // Rescore of the tensor-core forms: exact FP32 errors of the candidates the reduced-
 // precision ranking kept (for pixels with candidates not valid in every frame, the masked
 // ranking's), and of the 3x3 about the best, then the FP64 fit. k_rescore: one block per
-// 128 consecutive pixels, one thread per pixel; the frames stream through a 4-stage
-// cp.async pipeline in shared memory while each thread evaluates the 3x3 about its first
-// candidate and the other kept candidates; the reference is read through the cache.
+// 128 consecutive pixels, one thread per pixel; each thread streams its own pixel's frames
+// through a 3-stage cp.async pipeline in shared memory (no block barrier in the loop, so
+// warps run at their own pace) while it evaluates the 3x3 about its first candidate and the
+// other kept candidates; the reference is read through the cache.
 struct RescoreArgs {
     int N, ny, nx, Ry, Rx, Sy, Sx, quadratic, ncand;
     const float *frames, *W;
     const uint8_t *mask;
     const float *Rm;          // I_ref where w > 0, NaN elsewhere
+    const int *nvalid;        // frames in which each reference pixel is a valid candidate
     const FrameShift *shifts;
     const int *cand;          // [P][kTopK] window indices, -1 = none
-    const uint8_t *edge;      // [P] 1: some candidate of the pixel is not valid in every frame
     WsHeader *hdr;
+    int *wlist;               // warps (pixel index / 32) left to the general kernel
     double *u;
     float *err_out;
 };
@@ -835,31 +838,6 @@ struct RescoreArgs {
 // The frames stream through once: their loads are marked streaming (evict first), so that
 // they do not displace the masked reference and the validity counts, which every pixel
 // re-reads.
-
-// R_n at (i0 + fy, j0 + fx) by the masked renormalised bilinear gather, read from the
-// NaN-masked reference (the same arithmetic as gather_masked); false: frame not valid.
-__device__ __forceinline__ bool gather_rm(const float *__restrict__ Rm, int Ry, int Rx, int i0, int j0,
-                                          float fy, float fx, float &R) {
-    if (fy == 0.0f && fx == 0.0f) {
-        if (i0 < 0 || i0 >= Ry || j0 < 0 || j0 >= Rx) return false;
-        R = __ldg(Rm + (size_t)i0 * Rx + j0);
-        return R == R;
-    }
-    const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx), fy * fx};
-    float num = 0.0f, den = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
-        if (wt[k] == 0.0f || ii < 0 || ii >= Ry || jj < 0 || jj >= Rx) continue;
-        const float r = __ldg(Rm + (size_t)ii * Rx + jj);
-        if (r != r) continue;
-        num = fmaf(wt[k], r, num);
-        den += wt[k];
-    }
-    if (!(den > 0.0f)) return false;
-    R = num / den;
-    return true;
-}
 
 // Running sums of one candidate over the frames where it is valid.
 struct CandSums {
@@ -934,37 +912,42 @@ __device__ void eval_batch(const RescoreArgs &a, size_t pix, float Wv, const int
     for (int k = 0; k < B; ++k) e[k] = cs[k].e();
 }
 
-constexpr int RS_T = 128;     // pixels per block
 constexpr int RS_F = 16;      // frames per pipeline stage
-constexpr int RS_S = 4;       // pipeline stages
+constexpr int RS_S = 3;       // pipeline stages
+constexpr int RL_T = 64;      // lean kernel: pixels per block
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
-// XK: listed candidates beyond the first that may lie outside its 3x3 (rescore length - 1)
+// The candidates one thread rescores: the 3x3 about the first kept candidate c0 (a window
+// index) and up to XK other kept candidates that lie outside that 3x3.
 template <int XK>
-__global__ void __launch_bounds__(RS_T) k_rescore(RescoreArgs a) {
-    __shared__ __align__(16) float sfr[RS_S][RS_F][RS_T];
-    __shared__ __align__(16) FrameShift ssh[RS_S][RS_F];
-    const size_t P = (size_t)a.ny * a.nx;
-    const size_t p0 = (size_t)blockIdx.x * RS_T;
-    const int t = threadIdx.x;
-    const size_t pix = p0 + t;
-    const int wxn = 2 * a.Sx + 1;
+struct PixCands {
+    static constexpr int NX = XK > 0 ? XK : 1;
+    bool act;                 // a good pixel with a usable map value
+    bool run;                 // ... and the ranking kept a candidate
+    int ci, cj;               // the rounded map: the window centre
+    float Wv;
+    int c0, y0, x0, base0;    // c0, its reference pixel and flat index
+    bool safe9;               // every shift's reads of the 3x3 stay on the grid
+    bool in9[9];              // 3x3 point inside the window
+    int nxk;
+    int xid[NX], xy[NX], xx[NX], xbase[NX];
+    bool xsafe[NX];
+};
 
-    // ---- this thread's pixel and its candidates --------------------------------------------
-    bool act = false;
-    int ci = 0, cj = 0;
-    float Wv = 0.0f;
+template <int XK>
+__device__ __forceinline__ void pix_setup(const RescoreArgs &a, size_t pix, PixCands<XK> &pc) {
+    const size_t P = (size_t)a.ny * a.nx;
+    const int wxn = 2 * a.Sx + 1;
+    pc.act = false;
+    pc.ci = pc.cj = 0;
+    pc.Wv = 0.0f;
     if (pix < P) {
         if (!a.mask[pix]) {
             if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
@@ -975,167 +958,85 @@ __global__ void __launch_bounds__(RS_T) k_rescore(RescoreArgs a) {
             } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
                 atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
             } else {
-                ci = (int)floor(u0 + 0.5);
-                cj = (int)floor(u1 + 0.5);
-                Wv = a.W[pix];
-                act = true;
+                pc.ci = (int)floor(u0 + 0.5);
+                pc.cj = (int)floor(u1 + 0.5);
+                pc.Wv = a.W[pix];
+                pc.act = true;
             }
         }
     }
-    unsigned long long key = ~0ull;
-    int c0 = -1;                                      // window index the 3x3 is centred on
-    int xid[XK > 0 ? XK : 1];                         // listed candidates outside that 3x3
-    int nxk = 0;
-    if (act) {
-        c0 = a.cand[pix * kTopK];
+    pc.c0 = -1;
+    pc.nxk = 0;
+    if (pc.act) {
+        pc.c0 = a.cand[pix * kTopK];
 #pragma unroll
         for (int m = 1; m <= XK; ++m) {
             const int idx = m < a.ncand ? a.cand[pix * kTopK + m] : -1;
-            const bool far = idx >= 0 && c0 >= 0 && (abs(idx / wxn - c0 / wxn) > 1 || abs(idx % wxn - c0 % wxn) > 1);
+            const bool far =
+                idx >= 0 && pc.c0 >= 0 && (abs(idx / wxn - pc.c0 / wxn) > 1 || abs(idx % wxn - pc.c0 % wxn) > 1);
 #pragma unroll
             for (int q = 0; q < XK; ++q)
-                if (q == nxk && far) xid[q] = idx;
-            nxk += far ? 1 : 0;
+                if (q == pc.nxk && far) pc.xid[q] = idx;
+            pc.nxk += far ? 1 : 0;
         }
     }
-    const bool run = act && c0 >= 0;
-    const int a0 = run ? c0 / wxn : 0, b0 = run ? c0 % wxn : 0;
-    const int y0 = ci + a0 - a.Sy, x0 = cj + b0 - a.Sx;             // reference pixel of c0
-    const int base0 = y0 * a.Rx + x0;
-    const bool safe9 = run && span_safe(a, y0 - 1, y0 + 1, x0 - 1, x0 + 1);
-    bool in9[9];
+    pc.run = pc.act && pc.c0 >= 0;
+    const int a0 = pc.run ? pc.c0 / wxn : 0, b0 = pc.run ? pc.c0 % wxn : 0;
+    pc.y0 = pc.ci + a0 - a.Sy;
+    pc.x0 = pc.cj + b0 - a.Sx;
+    pc.base0 = pc.y0 * a.Rx + pc.x0;
+    pc.safe9 = pc.run && span_safe(a, pc.y0 - 1, pc.y0 + 1, pc.x0 - 1, pc.x0 + 1);
 #pragma unroll
     for (int jn = 0; jn < 9; ++jn) {
         const int na = a0 + jn / 3 - 1, nb = b0 + jn % 3 - 1;
-        in9[jn] = run && na >= 0 && na <= 2 * a.Sy && nb >= 0 && nb < wxn;
+        pc.in9[jn] = pc.run && na >= 0 && na <= 2 * a.Sy && nb >= 0 && nb < wxn;
     }
-    int xy[XK > 0 ? XK : 1], xx[XK > 0 ? XK : 1], xbase[XK > 0 ? XK : 1];
-    bool xsafe[XK > 0 ? XK : 1];
 #pragma unroll
     for (int q = 0; q < XK; ++q) {
-        const bool on = run && q < nxk;
-        xy[q] = on ? ci + xid[q] / wxn - a.Sy : 0;
-        xx[q] = on ? cj + xid[q] % wxn - a.Sx : 0;
-        xbase[q] = xy[q] * a.Rx + xx[q];
-        xsafe[q] = on && span_safe(a, xy[q], xy[q], xx[q], xx[q]);
+        const bool on = pc.run && q < pc.nxk;
+        pc.xy[q] = on ? pc.ci + pc.xid[q] / wxn - a.Sy : pc.y0;      // unused: c0 (a harmless read)
+        pc.xx[q] = on ? pc.cj + pc.xid[q] % wxn - a.Sx : pc.x0;
+        pc.xbase[q] = pc.xy[q] * a.Rx + pc.xx[q];
+        pc.xsafe[q] = on ? span_safe(a, pc.xy[q], pc.xy[q], pc.xx[q], pc.xx[q]) : pc.safe9;
     }
-    // lean: no pixel of the warp has a candidate that is not valid in every frame, and every
-    // read stays on the grid; only the errors are summed (the variance is the pixel's own)
-    bool ok_lean = !run || (!a.edge[pix] && safe9);
-#pragma unroll
-    for (int q = 0; q < XK; ++q) ok_lean = ok_lean && (q >= nxk || xsafe[q]);
-    const bool lean = __all_sync(0xffffffffu, ok_lean);
-    float var_all = 0.0f;
-    CandSums s9[9], sx[XK > 0 ? XK : 1];
-#pragma unroll
-    for (int jn = 0; jn < 9; ++jn) s9[jn].zero();
-#pragma unroll
-    for (int q = 0; q < XK; ++q) sx[q].zero();
+}
 
-    // ---- frames through the cp.async pipeline -----------------------------------------------
-    const int nst = (a.N + RS_F - 1) / RS_F;
-    const bool vec = (P % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.frames) & 15) == 0) && p0 + RS_T <= P;
-    auto issue = [&](int st) {
-        if (st < nst) {
-            const int buf = st % RS_S;
-            if (vec) {
-                // 16 frames x 32 chunks of 4 pixels: 4 per thread
+// Every candidate the pixel evaluates (the whole 3x3 and the other kept ones) lies on the
+// reference grid, is valid in every frame (its validity count is N) and reads on the grid
+// for every shift: the lean kernel may skip the per-frame rule.
+template <int XK>
+__device__ __forceinline__ bool pix_lean(const RescoreArgs &a, const PixCands<XK> &pc) {
+    if (!pc.run) return true;
+    bool ok = pc.safe9 && pc.y0 >= 1 && pc.y0 + 1 < a.Ry && pc.x0 >= 1 && pc.x0 + 1 < a.Rx;
+    if (!ok) return false;
 #pragma unroll
-                for (int r = 0; r < (RS_F * RS_T / 4) / RS_T; ++r) {
-                    const int q = r * RS_T + t, f = q / (RS_T / 4), x4 = (q % (RS_T / 4)) * 4;
-                    const int n = st * RS_F + f;
-                    if (n < a.N) cp_async16(&sfr[buf][f][x4], a.frames + (size_t)n * P + p0 + x4);
-                }
-            } else {
-#pragma unroll 4
-                for (int f = 0; f < RS_F; ++f) {
-                    const int n = st * RS_F + f;
-                    if (n < a.N && pix < P) cp_async4(&sfr[buf][f][t], a.frames + (size_t)n * P + pix);
-                }
-            }
-            if (t < RS_F && st * RS_F + t < a.N) cp_async16(&ssh[buf][t], a.shifts + st * RS_F + t);
-        }
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int st = 0; st < RS_S - 1; ++st) issue(st);
-    for (int st = 0; st < nst; ++st) {
-        issue(st + RS_S - 1);
-        cp_async_wait<RS_S - 1>();
-        __syncthreads();
-        const int buf = st % RS_S;
-        if (run) {
-            const int nf = min(RS_F, a.N - st * RS_F);
-            for (int f = 0; f < nf; ++f) {
-                const FrameShift s = ssh[buf][f];
-                const float I = sfr[buf][f][t];
-                const float tt = I - Wv;
-                if (lean && s.fy == 0.0f && s.fx == 0.0f) {      // the same for every lane
-                    const int off = s.ky * a.Rx + s.kx;
-                    var_all = fmaf(tt, tt, var_all);
-#pragma unroll
-                    for (int jn = 0; jn < 9; ++jn) {
-                        if (!in9[jn]) continue;
-                        const float R = __ldg(a.Rm + (base0 + (jn / 3 - 1) * a.Rx + (jn % 3 - 1) + off));
-                        const float d = fmaf(-Wv, R, I);
-                        s9[jn].err = fmaf(d, d, s9[jn].err);
-                    }
-#pragma unroll
-                    for (int q = 0; q < XK; ++q) {
-                        if (q >= nxk) continue;
-                        const float R = __ldg(a.Rm + (xbase[q] + off));
-                        const float d = fmaf(-Wv, R, I);
-                        sx[q].err = fmaf(d, d, sx[q].err);
-                    }
-                } else {
-                    var_all = fmaf(tt, tt, var_all);
-#pragma unroll
-                    for (int jn = 0; jn < 9; ++jn) {
-                        if (!in9[jn]) continue;
-                        const int dy = jn / 3 - 1, dx = jn % 3 - 1;
-                        float R;
-                        const bool ok = read_any(a, y0 + dy, x0 + dx, base0 + dy * a.Rx + dx, safe9, s, R);
-                        s9[jn].add(ok, R, I, tt, Wv);
-                    }
-#pragma unroll
-                    for (int q = 0; q < XK; ++q) {
-                        if (q >= nxk) continue;
-                        float R;
-                        const bool ok = read_any(a, xy[q], xx[q], xbase[q], xsafe[q], s, R);
-                        sx[q].add(ok, R, I, tt, Wv);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    cp_async_wait<0>();
-    if (!act) return;
-
-    // ---- minimum, 3x3, fit ----------------------------------------------------------------------
-    if (lean) {
-        // every frame was valid for every candidate (the general branch above, taken for
-        // frames with a fractional shift, summed var and the count the same way)
-#pragma unroll
-        for (int jn = 0; jn < 9; ++jn) {
-            s9[jn].var = var_all;
-            s9[jn].nv = a.N;
-        }
-#pragma unroll
-        for (int q = 0; q < XK; ++q) {
-            sx[q].var = var_all;
-            sx[q].nv = a.N;
-        }
-    }
-    float f9[9];
-#pragma unroll
-    for (int jn = 0; jn < 9; ++jn) {
-        f9[jn] = in9[jn] ? s9[jn].e() : INFINITY;
-        if (in9[jn]) key = min(key, pack_key(f9[jn], c0 + (jn / 3 - 1) * wxn + (jn % 3 - 1)));
-    }
+    for (int jn = 0; jn < 9; ++jn)
+        ok = ok && __ldg(a.nvalid + pc.base0 + (jn / 3 - 1) * a.Rx + (jn % 3 - 1)) == a.N;
 #pragma unroll
     for (int q = 0; q < XK; ++q)
-        if (q < nxk) key = min(key, pack_key(sx[q].e(), xid[q]));
+        if (q < pc.nxk)
+            ok = ok && pc.xsafe[q] && (unsigned)pc.xy[q] < (unsigned)a.Ry && (unsigned)pc.xx[q] < (unsigned)a.Rx &&
+                 __ldg(a.nvalid + pc.xbase[q]) == a.N;
+    return ok;
+}
+
+// The lexicographic minimum over the evaluated candidates (f9: the 3x3 about c0, +inf
+// outside the window; fx: the other kept ones), the 3x3 about it when it is not c0
+// (evaluated here, frames from global memory), the FP64 fit and the outputs.
+template <int XK>
+__device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, const PixCands<XK> &pc, float (&f9)[9],
+                                           const float (&fx)[PixCands<XK>::NX]) {
+    const size_t P = (size_t)a.ny * a.nx;
+    const int wxn = 2 * a.Sx + 1;
+    unsigned long long key = ~0ull;
+    if (pc.run) {
+#pragma unroll
+        for (int jn = 0; jn < 9; ++jn)
+            if (pc.in9[jn]) key = min(key, pack_key(f9[jn], pc.c0 + (jn / 3 - 1) * wxn + (jn % 3 - 1)));
+#pragma unroll
+        for (int q = 0; q < XK; ++q)
+            if (q < pc.nxk) key = min(key, pack_key(fx[q], pc.xid[q]));
+    }
     const float be = __uint_as_float((unsigned int)(key >> 32));
     if (!(be < INFINITY)) {
         if (a.err_out) a.err_out[pix] = INFINITY;
@@ -1145,30 +1046,246 @@ __global__ void __launch_bounds__(RS_T) k_rescore(RescoreArgs a) {
     const int ia = bi / wxn, ib = bi % wxn;
     double da = 0.0, db = 0.0;
     if (a.quadratic) {
-        if (bi != c0) {
-            // the minimum moved off the evaluated 3x3: evaluate the one about it
-            int cy[8], cx[8];
-            float e8[8];
+        if (bi != pc.c0) {
+            // the minimum moved off the evaluated 3x3: evaluate the one about it, 4 at a time
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int jn = m < 4 ? m : m + 1;
-                cy[m] = ci + ia + jn / 3 - 1 - a.Sy;
-                cx[m] = cj + ib + jn % 3 - 1 - a.Sx;
-            }
-            eval_batch<8>(a, pix, Wv, cy, cx, 8, e8);
+            for (int h = 0; h < 2; ++h) {
+                int cy[4], cx[4];
+                float e4[4];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int jn = m < 4 ? m : m + 1;
-                const int na = ia + jn / 3 - 1, nb = ib + jn % 3 - 1;
-                f9[jn] = (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) ? INFINITY : e8[m];
+                for (int m = 0; m < 4; ++m) {
+                    const int k = 4 * h + m, jn = k < 4 ? k : k + 1;
+                    cy[m] = pc.ci + ia + jn / 3 - 1 - a.Sy;
+                    cx[m] = pc.cj + ib + jn % 3 - 1 - a.Sx;
+                }
+                eval_batch<4>(a, pix, pc.Wv, cy, cx, 4, e4);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int k = 4 * h + m, jn = k < 4 ? k : k + 1;
+                    const int na = ia + jn / 3 - 1, nb = ib + jn % 3 - 1;
+                    f9[jn] = (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) ? INFINITY : e4[m];
+                }
             }
             f9[4] = be;
         }
         refine3x3(f9, da, db);
     }
-    a.u[pix] = (double)(ci + ia - a.Sy) + da;
-    a.u[P + pix] = (double)(cj + ib - a.Sx) + db;
+    a.u[pix] = (double)(pc.ci + ia - a.Sy) + da;
+    a.u[P + pix] = (double)(pc.cj + ib - a.Sx) + db;
     if (a.err_out) a.err_out[pix] = be;
+}
+
+// Lean rescore: one block per 64 consecutive pixels, one thread per pixel, for warps whose
+// every pixel passes pix_lean; a warp that does not is appended to the list of
+// k_rescore_general and leaves. Each thread streams its own pixel's frames through a
+// 3-stage cp.async pipeline in shared memory (the copies a thread waits for are its own:
+// no block barrier). For a whole-pixel shift the 3x3 is read as three rows of three from
+// one row pointer each; every 3x3 point is summed (those outside the window are dropped at
+// the end) and the variance is the pixel's own over all frames.
+template <int XK>
+__global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
+    __shared__ __align__(16) float sfr[RS_S][RS_F][RL_T];    // column t: thread t's pixel only
+    const size_t P = (size_t)a.ny * a.nx;
+    const int t = threadIdx.x;
+    const size_t pix = (size_t)blockIdx.x * RL_T + t;
+    PixCands<XK> pc;
+    pix_setup<XK>(a, pix, pc);
+    if (!__all_sync(0xffffffffu, pix_lean<XK>(a, pc))) {
+        if ((t & 31) == 0) a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)(pix >> 5);
+        return;
+    }
+    // other kept candidates: as many as the warp's longest list (the rest read c0)
+    const int nxw = __reduce_max_sync(0xffffffffu, pc.nxk);
+    float e9[9], ex[PixCands<XK>::NX], var = 0.0f;
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) e9[jn] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < XK; ++q) ex[q] = 0.0f;
+    const float Wv = pc.Wv;
+    const int nst = (a.N + RS_F - 1) / RS_F;
+    auto issue = [&](int st) {
+        if (st < nst && pc.run) {
+            const int buf = st % RS_S;
+#pragma unroll
+            for (int f = 0; f < RS_F; ++f) {
+                const int n = st * RS_F + f;
+                if (n < a.N) cp_async4(&sfr[buf][f][t], a.frames + (size_t)n * P + pix);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < RS_S - 1; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + RS_S - 1);
+        cp_async_wait<RS_S - 1>();
+        const int buf = st % RS_S;
+        if (pc.run) {
+            const int nf = min(RS_F, a.N - st * RS_F);
+#pragma unroll 2
+            for (int f = 0; f < nf; ++f) {
+                const FrameShift s = a.shifts[st * RS_F + f];
+                const float I = sfr[buf][f][t];
+                const float tt = I - Wv;
+                var = fmaf(tt, tt, var);
+                if (s.fy == 0.0f && s.fx == 0.0f) {          // the same for every lane
+                    const int off = s.ky * a.Rx + s.kx;
+                    const float *r0 = a.Rm + (pc.base0 + off);
+                    const float *rm = r0 - a.Rx, *rp = r0 + a.Rx;
+                    const float R[9] = {__ldg(rm - 1), __ldg(rm), __ldg(rm + 1), __ldg(r0 - 1), __ldg(r0),
+                                        __ldg(r0 + 1), __ldg(rp - 1), __ldg(rp), __ldg(rp + 1)};
+#pragma unroll
+                    for (int jn = 0; jn < 9; ++jn) {
+                        const float d = fmaf(-Wv, R[jn], I);
+                        e9[jn] = fmaf(d, d, e9[jn]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < XK; ++q) {
+                        if (q >= nxw) break;
+                        const float d = fmaf(-Wv, __ldg(a.Rm + (pc.xbase[q] + off)), I);
+                        ex[q] = fmaf(d, d, ex[q]);
+                    }
+                } else {
+                    // a fractional shift: the masked bilinear read (valid: the counts are N)
+#pragma unroll
+                    for (int jn = 0; jn < 9; ++jn) {
+                        float R;
+                        if (gather_rm(a.Rm, a.Ry, a.Rx, pc.y0 + jn / 3 - 1 + s.ky, pc.x0 + jn % 3 - 1 + s.kx, s.fy,
+                                      s.fx, R)) {
+                            const float d = fmaf(-Wv, R, I);
+                            e9[jn] = fmaf(d, d, e9[jn]);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < XK; ++q) {
+                        if (q >= nxw) break;
+                        float R;
+                        if (gather_rm(a.Rm, a.Ry, a.Rx, pc.xy[q] + s.ky, pc.xx[q] + s.kx, s.fy, s.fx, R)) {
+                            const float d = fmaf(-Wv, R, I);
+                            ex[q] = fmaf(d, d, ex[q]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if (!pc.act) return;
+    // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
+    float f9[9], fxe[PixCands<XK>::NX];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) f9[jn] = pc.in9[jn] ? (var > 0.0f ? e9[jn] / var : e9[jn]) : INFINITY;
+#pragma unroll
+    for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? (var > 0.0f ? ex[q] / var : ex[q]) : INFINITY;
+    pix_finish<XK>(a, pix, pc, f9, fxe);
+}
+
+// General rescore: one block per warp listed by k_rescore_lean (blocks beyond the list's
+// length return at once), with the per-frame rule of the masked renormalised reads: each
+// candidate sums its error and variance over the frames where it is valid. The block's 4
+// warps take the same 32 pixels and a quarter of the frames each (so that the few listed
+// warps still fill the GPU); their sums are added in warp order and warp 0 finishes.
+constexpr int RG_W = 4;
+template <int XK>
+__global__ void __launch_bounds__(32 * RG_W) k_rescore_general(RescoreArgs a) {
+    constexpr int NC = 9 + PixCands<XK>::NX;                      // candidates per pixel
+    constexpr int STAGE_BYTES = RG_W * RS_S * RS_F * 32 * 4;       // frames, per warp
+    constexpr int SUM_BYTES = (RG_W - 1) * NC * 32 * 12;           // partial sums, warps 1..
+    __shared__ __align__(16) uint8_t sraw[STAGE_BYTES > SUM_BYTES ? STAGE_BYTES : SUM_BYTES];
+    if ((int)blockIdx.x >= a.hdr->n_rescore_warps) return;
+    const size_t P = (size_t)a.ny * a.nx;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t pix = (size_t)a.wlist[blockIdx.x] * 32 + lane;
+    PixCands<XK> pc;
+    pix_setup<XK>(a, pix, pc);
+    CandSums s9[9], sx[PixCands<XK>::NX];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) s9[jn].zero();
+#pragma unroll
+    for (int q = 0; q < XK; ++q) sx[q].zero();
+    const float Wv = pc.Wv;
+    // this warp's frames [fb, fe), staged in its own part of the buffer, column = lane
+    float(*sfr)[RS_F][32] = reinterpret_cast<float(*)[RS_F][32]>(sraw) + wid * RS_S;
+    const int qn = (a.N + RG_W - 1) / RG_W;
+    const int fb = min(a.N, wid * qn), fe = min(a.N, fb + qn);
+    const int nst = (fe - fb + RS_F - 1) / RS_F;
+    auto issue = [&](int st) {
+        if (st < nst && pc.run) {
+            const int buf = st % RS_S;
+#pragma unroll
+            for (int f = 0; f < RS_F; ++f) {
+                const int n = fb + st * RS_F + f;
+                if (n < fe) cp_async4(&sfr[buf][f][lane], a.frames + (size_t)n * P + pix);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < RS_S - 1; ++st) issue(st);
+    for (int st = 0; st < nst; ++st) {
+        issue(st + RS_S - 1);
+        cp_async_wait<RS_S - 1>();
+        const int buf = st % RS_S;
+        if (pc.run) {
+            const int nf = min(RS_F, fe - fb - st * RS_F);
+            for (int f = 0; f < nf; ++f) {
+                const FrameShift s = a.shifts[fb + st * RS_F + f];
+                const float I = sfr[buf][f][lane];
+                const float tt = I - Wv;
+#pragma unroll
+                for (int jn = 0; jn < 9; ++jn) {
+                    if (!pc.in9[jn]) continue;
+                    const int dy = jn / 3 - 1, dx = jn % 3 - 1;
+                    float R;
+                    const bool ok = read_any(a, pc.y0 + dy, pc.x0 + dx, pc.base0 + dy * a.Rx + dx, pc.safe9, s, R);
+                    s9[jn].add(ok, R, I, tt, Wv);
+                }
+#pragma unroll
+                for (int q = 0; q < XK; ++q) {
+                    if (q >= pc.nxk) continue;
+                    float R;
+                    const bool ok = read_any(a, pc.xy[q], pc.xx[q], pc.xbase[q], pc.xsafe[q], s, R);
+                    sx[q].add(ok, R, I, tt, Wv);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();                                   // every warp is done with its frames
+    // partial sums of warps 1.. : [warp - 1][candidate][lane] (err, var, nv)
+    float *se = reinterpret_cast<float *>(sraw);
+    float *sv = se + (RG_W - 1) * NC * 32;
+    int *sn = reinterpret_cast<int *>(sv + (RG_W - 1) * NC * 32);
+    if (wid > 0) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const CandSums &c = k < 9 ? s9[k] : sx[k < 9 + XK ? k - 9 : 0];
+            const int o = ((wid - 1) * NC + k) * 32 + lane;
+            se[o] = c.err;
+            sv[o] = c.var;
+            sn[o] = c.nv;
+        }
+    }
+    __syncthreads();
+    if (wid > 0 || !pc.act) return;
+#pragma unroll
+    for (int w = 1; w < RG_W; ++w) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (k >= 9 + XK) break;
+            CandSums &c = k < 9 ? s9[k] : sx[k - 9];
+            const int o = ((w - 1) * NC + k) * 32 + lane;
+            c.err += se[o];
+            c.var += sv[o];
+            c.nv += sn[o];
+        }
+    }
+    float f9[9], fxe[PixCands<XK>::NX];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) f9[jn] = pc.in9[jn] ? s9[jn].e() : INFINITY;
+#pragma unroll
+    for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? sx[q].e() : INFINITY;
+    pix_finish<XK>(a, pix, pc, f9, fxe);
 }
 
 }  // namespace
@@ -1265,20 +1382,25 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
 }
 
 cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
-                           const float *W, const uint8_t *mask, const float *Rm, const FrameShift *shifts,
-                           const int *cand, const uint8_t *edge, WsHeader *hdr, double *u, float *err_out,
-                           cudaStream_t stream) {
+                           const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
+                           const FrameShift *shifts, const int *cand, WsHeader *hdr, int *wlist, double *u,
+                           float *err_out, cudaStream_t stream) {
     RescoreArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0; a.ncand = ncand;
-    a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.shifts = shifts;
-    a.cand = cand; a.edge = edge; a.hdr = hdr; a.u = u; a.err_out = err_out;
+    a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.nvalid = nvalid; a.shifts = shifts;
+    a.cand = cand; a.hdr = hdr; a.wlist = wlist; a.u = u; a.err_out = err_out;
     const size_t P = (size_t)d.ny * d.nx;
-    const unsigned blocks = (unsigned)((P + RS_T - 1) / RS_T);
-    if (ncand <= 4)
-        k_rescore<3><<<blocks, RS_T, 0, stream>>>(a);
-    else
-        k_rescore<7><<<blocks, RS_T, 0, stream>>>(a);
+    const unsigned lblocks = (unsigned)((P + RL_T - 1) / RL_T), gblocks = (unsigned)((P + 31) / 32);
+    cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_warps, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    if (ncand <= 4) {
+        k_rescore_lean<3><<<lblocks, RL_T, 0, stream>>>(a);
+        k_rescore_general<3><<<gblocks, 32 * RG_W, 0, stream>>>(a);
+    } else {
+        k_rescore_lean<7><<<lblocks, RL_T, 0, stream>>>(a);
+        k_rescore_general<7><<<gblocks, 32 * RG_W, 0, stream>>>(a);
+    }
     return cudaGetLastError();
 }
 
