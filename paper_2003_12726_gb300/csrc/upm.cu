@@ -107,7 +107,8 @@ __device__ __forceinline__ void accum_strip_exact(const float *__restrict__ fr, 
                                                   const FrameShift *__restrict__ sh, int n0,
                                                   int step, int N, const float *__restrict__ win,
                                                   int WS, float Wv, float (&err)[L],
-                                                  float (&var)[L], float (&nv)[L]) {
+                                                  float (&var)[L], float (&nv)[L],
+                                                  unsigned cm = 0xffffffffu) {
     for (int n = n0; n < N; n += step) {
         const FrameShift s = sh[n];
         const float I = fr[n * pitch + p];
@@ -117,6 +118,7 @@ __device__ __forceinline__ void accum_strip_exact(const float *__restrict__ fr, 
         const float w10 = s.fy * (1.0f - s.fx), w11 = s.fy * s.fx;
 #pragma unroll
         for (int k = 0; k < L; ++k) {
+            if (!((cm >> k) & 1u)) continue;          // a column the fast path evaluated
             const float v00 = wp[k];
             const float v01 = s.fx != 0.0f ? wp[k + 1] : 0.0f;
             const float v10 = s.fy != 0.0f ? wp[WS + k] : 0.0f;
@@ -195,7 +197,8 @@ __device__ __forceinline__ bool lex_less(float e, int i, float e2, int i2) {
 constexpr int kGroup = 4;            // pixels per group: consecutive columns of one row
 constexpr int kSplit = 4;            // lanes that share one strip, each taking every 4th frame
 constexpr int kSearchThreads = 256;
-constexpr int kExactWords = 512;     // bitmask of strips for the exact phase (16384 bits)
+constexpr int kExactList = 4096;     // (strip, pixel, NaN columns) entries for the exact phase
+constexpr int kWinRowsMax = 512;     // window rows with a coverage flag (taller windows: no flag)
 static_assert(kSplit == kGroup, "the reduce-scatter hands lane j the sums of pixel j");
 
 // One strip of L consecutive absolute reference columns on one reference row, for the
@@ -326,16 +329,27 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
     __shared__ unsigned long long s_key[TP];
     __shared__ float s_nb[9][TP];
     __shared__ int s_gr0[NG], s_gc0[NG], s_gns[NG], s_goff[NG + 1];
-    __shared__ unsigned int s_xbits[kExactWords];    // bit 4*item + j: strip needs the exact phase
+    // exact phase: entries (item << 13) | (j << 11) | mask of the columns that read an
+    // invalid reference pixel in some frame; s_rowany: the window row holds a valid cell
+    __shared__ unsigned int s_xlist[kExactList];
+    __shared__ int s_xn;
+    __shared__ unsigned char s_rowany[kWinRowsMax];
     __shared__ int s_glob[TP];                       // 1: the pixel is left to the global path
 
     const int tid = threadIdx.x;
     const size_t P = (size_t)a.ny * a.nx;
 
     if (tid < 4) s_box[tid] = (tid & 1) ? INT_MIN : INT_MAX;
-    for (int q = tid; q < kExactWords; q += NT) s_xbits[q] = 0u;
-    for (int n = tid; n < a.N; n += NT) sh[n] = a.shifts[n];
-    __syncthreads();
+    if (tid == 0) s_xn = 0;
+    for (int q = tid; q < kWinRowsMax; q += NT) s_rowany[q] = 0;
+    int fy_local = 0;
+    for (int n = tid; n < a.N; n += NT) {
+        const FrameShift f = a.shifts[n];
+        sh[n] = f;
+        fy_local |= f.fy != 0.0f;
+    }
+    // some frame reads the row below its integer shift (a fractional ss translation)
+    const int any_fy = __syncthreads_or(fy_local);
     for (int p = tid; p < TP; p += NT) {
         const int x = blockIdx.x * 32 + (p & 31), y = blockIdx.y * TY + (p >> 5);
         int act = 0, ci = 0, cj = 0;
@@ -440,8 +454,11 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
             if (__ldg(a.w + g) > 0.0f) v = __ldg(a.Iref + g);
         }
         win[idx] = v;
+        if (v == v && idx / WS < kWinRowsMax) s_rowany[idx / WS] = 1;
     }
     __syncthreads();
+    const int WH = (int)WHl;
+    const int kmin_y = a.hdr->kmin_y, kmax_y = a.hdr->kmax_y;
 
     // ---- search: strips of the groups' window unions, 4 lanes per strip ----------------
     const int j = tid & (kSplit - 1);
@@ -480,28 +497,40 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
         if (aa < -a.Sy || aa > a.Sy) continue;
         const int bofs = c - s_cj[p];
         const float var = s_var[p];
-        bool nan_seen = false;
+        unsigned cm = 0u;                            // window columns whose error is NaN
 #pragma unroll
         for (int k = 0; k < L; ++k) {
             e[k] = var > 0.0f ? e[k] / var : e[k];
             const int b = bofs + k;
-            nan_seen = nan_seen || (isnan(e[k]) && b >= -a.Sx && b <= a.Sx);
+            if (isnan(e[k]) && b >= -a.Sx && b <= a.Sx) cm |= 1u << k;
         }
-        if (nan_seen) {
-            s_slow[p] = 1;
-            const int bit = item * kSplit + j;
-            if (bit < kExactWords * 32)              // evaluated by the whole CTA below
-                atomicOr(&s_xbits[bit >> 5], 1u << (bit & 31));
-            else
-                s_glob[p] = 1;                       // beyond the bitmask: the global path
-            continue;
+        if (cm) {
+            // every frame reads window rows r + ky (+1 for a fractional ss shift); if none of
+            // them holds a valid cell, no frame is valid for any column: the error is +inf
+            const int q0 = r - wy0 + kmin_y, q1 = r - wy0 + kmax_y + any_fy;
+            bool none = WH <= kWinRowsMax;
+            for (int q = q0; none && q <= q1; ++q) none = s_rowany[q] == 0;
+            if (none) {
+#pragma unroll
+                for (int k = 0; k < L; ++k)
+                    if ((cm >> k) & 1u) e[k] = INFINITY;
+                cm = 0u;
+            } else {
+                s_slow[p] = 1;
+                const int slot = item < (1 << 19) ? atomicAdd(&s_xn, 1) : kExactList;
+                if (slot < kExactList)               // evaluated by the whole CTA below
+                    s_xlist[slot] = ((unsigned)item << 13) | ((unsigned)j << 11) | cm;
+                else
+                    s_glob[p] = 1;                   // beyond the list: the global path
+            }
         }
+        // the columns every frame of which was valid: the fast path's value is the exact one
         float be = INFINITY;
         int bi = -1;
 #pragma unroll
         for (int k = 0; k < L; ++k) {
             const int b = bofs + k;
-            if (b < -a.Sx || b > a.Sx) continue;
+            if (b < -a.Sx || b > a.Sx || ((cm >> k) & 1u)) continue;
             const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
             if (a.ebuf) ebuf[p * nwin + idx] = e[k];
             if (bi < 0 || e[k] < be) {
@@ -513,70 +542,63 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
     }
     __syncthreads();
 
-    // ---- strips that read invalid reference pixels: per-frame rule, 4 lanes per strip ----
-    // Each warp drains bitmask words in a fixed order, 8 strips at a time; every exact
-    // error is formed by the same frame split and reduction, so results do not depend on
-    // scheduling.
+    // ---- columns that read invalid reference pixels: per-frame rule, 4 lanes per entry ----
+    // Each warp takes 8 list entries at a time; every exact error is formed by the same
+    // frame split and reduction whichever warp takes its entry, so results do not depend
+    // on scheduling.
     {
         const int lane = tid & 31, warp = tid >> 5, slot = lane >> 2;
-        const int nwords = min((units + 31) >> 5, kExactWords);
-        for (int wd = warp; wd < nwords; wd += NT / 32) {
-            unsigned int m = s_xbits[wd];
-            while (m) {                              // m is the same in every lane of the warp
-                int mybit = -1;
+        const int nent = min(s_xn, kExactList);
+        for (int e0 = warp * 8; e0 < nent; e0 += NT / 4) {
+            const int ent = e0 + slot;
+            const bool valid = ent < nent;
+            float err[L], var[L], nv[L];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (!m) break;
-                    const int b = __ffs(m) - 1;
-                    if (q == slot) mybit = b;
-                    m &= m - 1;
+            for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
+            int p = 0, r = 0, c = 0;
+            unsigned cm = 0u;
+            if (valid) {
+                const unsigned x = s_xlist[ent];
+                const int item = (int)(x >> 13);
+                cm = x & 0x7ffu;
+                int lo = 0, hi = NG - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_goff[mid] <= item) lo = mid; else hi = mid - 1;
                 }
-                const bool valid = mybit >= 0;
-                float err[L], var[L], nv[L];
-#pragma unroll
-                for (int k = 0; k < L; ++k) err[k] = var[k] = nv[k] = 0.0f;
-                int p = 0, r = 0, c = 0;
-                if (valid) {
-                    const int bit = wd * 32 + mybit, item = bit / kSplit;
-                    int lo = 0, hi = NG - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_goff[mid] <= item) lo = mid; else hi = mid - 1;
-                    }
-                    const int loc = item - s_goff[lo], ns = s_gns[lo];
-                    r = s_gr0[lo] + loc / ns;
-                    c = s_gc0[lo] + (loc % ns) * L;
-                    p = lo * kGroup + (bit % kSplit);
-                    accum_strip_exact<L>(fr, FP, p, sh, j, kSplit, a.N, win + (r - wy0) * WS + (c - wx0),
-                                         WS, s_W[p], err, var, nv);
-                }
-#pragma unroll
-                for (int k = 0; k < L; ++k)
-#pragma unroll
-                    for (int off = 1; off < kSplit; off <<= 1) {
-                        err[k] += __shfl_xor_sync(0xffffffffu, err[k], off);
-                        var[k] += __shfl_xor_sync(0xffffffffu, var[k], off);
-                        nv[k] += __shfl_xor_sync(0xffffffffu, nv[k], off);
-                    }
-                if (!valid || j != 0) continue;
-                const int aa = r - s_ci[p], bofs = c - s_cj[p];
-                float e[L];
-                finish_exact<L>(err, var, nv, a.N, s_var[p], e);
-                float be = INFINITY;
-                int bi = -1;
-#pragma unroll
-                for (int k = 0; k < L; ++k) {
-                    const int b = bofs + k;
-                    if (b < -a.Sx || b > a.Sx) continue;
-                    const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
-                    if (a.ebuf) ebuf[p * nwin + idx] = e[k];
-                    if (bi < 0 || e[k] < be) {
-                        be = e[k];
-                        bi = idx;
-                    }
-                }
-                if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
+                const int loc = item - s_goff[lo], ns = s_gns[lo];
+                r = s_gr0[lo] + loc / ns;
+                c = s_gc0[lo] + (loc % ns) * L;
+                p = lo * kGroup + (int)((x >> 11) & 3u);
+                accum_strip_exact<L>(fr, FP, p, sh, j, kSplit, a.N, win + (r - wy0) * WS + (c - wx0), WS, s_W[p],
+                                     err, var, nv, cm);
             }
+#pragma unroll
+            for (int k = 0; k < L; ++k)
+#pragma unroll
+                for (int off = 1; off < kSplit; off <<= 1) {
+                    err[k] += __shfl_xor_sync(0xffffffffu, err[k], off);
+                    var[k] += __shfl_xor_sync(0xffffffffu, var[k], off);
+                    nv[k] += __shfl_xor_sync(0xffffffffu, nv[k], off);
+                }
+            if (!valid || j != 0) continue;
+            const int aa = r - s_ci[p], bofs = c - s_cj[p];
+            float e[L];
+            finish_exact<L>(err, var, nv, a.N, s_var[p], e);
+            float be = INFINITY;
+            int bi = -1;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const int b = bofs + k;
+                if (!((cm >> k) & 1u)) continue;
+                const int idx = (aa + a.Sy) * wxn + (b + a.Sx);
+                if (a.ebuf) ebuf[p * nwin + idx] = e[k];
+                if (bi < 0 || e[k] < be) {
+                    be = e[k];
+                    bi = idx;
+                }
+            }
+            if (bi >= 0) atomicMin(&s_key[p], pack_key(be, bi));
         }
     }
     __syncthreads();
