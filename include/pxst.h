@@ -72,9 +72,11 @@ typedef struct {
     int32_t form;          /* PXST_FORM_* */
     int32_t rescore_k;     /* tensor forms: candidates per pixel re-evaluated in FP32:
                               4 or 8 (0 = 8 below 128 frames, else 4) */
-    int32_t tile;          /* tile shape (0 = automatic). FP32 form: tile height in rows of 32
-                              pixels, 1, 2, 4 or 8 (a height whose staging does not fit falls
-                              back to the automatic choice). Tensor forms: 0 = 8 x 16 pixels
+    int32_t tile;          /* tile shape (0 = automatic). FP32 form: bits 0-3 the tile height in
+                              rows of 32 pixels, 0 (automatic), 1, 2, 4 or 8 (a height whose
+                              staging does not fit falls back to the automatic choice); bits
+                              4-5 the strip length, 0 (automatic), 1, 2, 3 = 7, 9, 11 window
+                              columns per strip. Tensor forms: 0 = 8 x 16 pixels
                               against 8 x 32 candidates, 1 = 4 x 32 / 4 x 64, 2 = 2 x 64 /
                               2 x 128. Any other value is PXST_ERR_ARG. */
     int64_t timeout_ns;    /* reserved for device-side waits (0 = default) */

@@ -28,7 +28,8 @@ bool opts_ok(const pxst_options *o) {
     if (o->quadratic != 0 && o->quadratic != 1) return false;
     if (o->form != PXST_FORM_FP32 && o->form != PXST_FORM_BF16 && o->form != PXST_FORM_TF32) return false;
     if (o->rescore_k != 0 && o->rescore_k != 4 && o->rescore_k != 8) return false;
-    if (o->form == PXST_FORM_FP32 ? (o->tile != 0 && o->tile != 1 && o->tile != 2 && o->tile != 4 && o->tile != 8)
+    const int ty = o->tile & 15, ls = o->tile >> 4;
+    if (o->form == PXST_FORM_FP32 ? (o->tile < 0 || ls > 3 || (ty != 0 && ty != 1 && ty != 2 && ty != 4 && ty != 8))
                                   : (o->tile < 0 || o->tile > 2))
         return false;
     return true;

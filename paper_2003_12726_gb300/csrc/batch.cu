@@ -29,7 +29,13 @@ namespace {
 
 // tile shapes a form can take (0: automatic / the default shape)
 std::vector<int> tile_candidates(int form) {
-    if (form == PXST_FORM_FP32) return {0, 1, 2, 4, 8};
+    if (form == PXST_FORM_FP32) {
+        // tile heights (automatic, 1, 2, 4, 8 rows of 32 pixels) x strip lengths (automatic, 7, 9, 11)
+        std::vector<int> v;
+        for (int l : {0, 1, 2, 3})
+            for (int ty : {0, 1, 2, 4, 8}) v.push_back(ty | (l << 4));
+        return v;
+    }
     return {0, 1, 2};
 }
 

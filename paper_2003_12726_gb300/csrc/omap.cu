@@ -2,7 +2,7 @@
 // per-candidate reference terms, for sm_103a.
 //
 //   prepare    : -Delta[n] -> (integer shift, fraction) per frame, and their range.
-//   scatter    : each CTA (1024 threads, one pixel each) owns a 32 x 32 pixel tile and a
+//   scatter    : each CTA (512 threads, one pixel each) owns a 16 x 32 pixel tile and a
 //                chunk of frames, cut into groups of consecutive frames whose reference
 //                footprint (the tile's u range widened by the group's translation range,
 //                +1 for the bilinear corner) fits in shared memory. Each group adds
@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restric
 }
 
 // ------------------------------------------------------------------------------------
-constexpr int SC_TX = 32, SC_TY = 32;                  // 32 x 32 pixels, one per thread
+constexpr int SC_TX = 32, SC_TY = 16;                  // 32 x 16 pixels, one per thread
 constexpr int SC_THREADS = SC_TX * SC_TY;
-constexpr int SC_CAP = 16384;                          // cells (num + den: 128 KB)
+constexpr int SC_CAP = 12288;                          // cells (num + den: 96 KB): 2 CTAs per SM
 constexpr int SC_PREFETCH = 4;                         // frames loaded ahead of their scatter
 
 struct ScatterArgs {
@@ -63,11 +63,12 @@ struct ScatterArgs {
     double *num, *den;
 };
 
-// One CTA per 32 x 32 pixel tile and chunk of frames. The chunk is cut into consecutive
+// One CTA per 16 x 32 pixel tile and chunk of frames (two CTAs per SM, so that one's
+// barriers overlap the other's accumulation). The chunk is cut into consecutive
 // groups of frames whose footprint (the tile's floor(u) range widened by the group's
 // integer shifts, +1 for a carry and +1 for the second corner) fits in shared memory;
 // each group is accumulated there with FP32 atomics and flushed to the FP64 accumulators.
-__global__ void __launch_bounds__(SC_THREADS) k_scatter(ScatterArgs a) {
+__global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     extern __shared__ float sm[];
     float *s_num = sm;
     float *s_den = sm + SC_CAP;

@@ -1323,7 +1323,9 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     Plan pl;
     const int wxn = 2 * o.win_x + 1;
     const size_t nwin = (size_t)(2 * o.win_y + 1) * wxn;
-    pl.L = pick_strip(wxn);
+    // strip length: requested (tile bits 4-5: 1, 2, 3 = 7, 9, 11 columns) or the least waste
+    const int ty_req = o.tile & 15, l_req = o.tile >> 4;
+    pl.L = l_req == 1 ? 7 : l_req == 2 ? 9 : l_req == 3 ? 11 : pick_strip(wxn);
     const size_t N = (size_t)d.n_frames, shifts_b = N * sizeof(FrameShift);
     const size_t sm_per_sm = 228 * 1024;
     // window estimate for a local magnification up to 2 (unknown span: the largest window)
@@ -1342,7 +1344,7 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
     int best_ebuf = 0;
     for (int ebuf = 1; ebuf >= 0; --ebuf)
         for (int ty = 8; ty >= 1; ty >>= 1) {
-            if (o.tile > 0 && ty != o.tile) continue;          // a requested tile height
+            if (ty_req > 0 && ty != ty_req) continue;          // a requested tile height
             size_t st = 0;
             int cr = 1;
             cudaError_t e = variant_info_any(pl.L, ty, st, cr);
@@ -1365,10 +1367,10 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                 break;
             }
         }
-    if (best_score < 0 && o.tile > 0) {
-        // the requested height does not fit: the automatic choice
+    if (best_score < 0 && ty_req > 0) {
+        // the requested height does not fit: the automatic height (the strip length kept)
         pxst_options o2 = o;
-        o2.tile = 0;
+        o2.tile = o.tile & ~15;
         return launch_search(d, o2, frames, W, mask, I_ref, w, shifts, hdr, exact_list, u, err_out, span_y, span_x,
                              stream);
     }

@@ -97,7 +97,10 @@ def test_autotune(form):
     r.run(1)                                  # a reference image to search against
     u0 = r.u.clone()
     tile, ms = px.autotune(r, trials=2)
-    assert tile in ((0, 1, 2, 4, 8) if form == 0 else (0, 1, 2)) and ms > 0
+    if form == 0:     # tile height (bits 0-3) and strip length (bits 4-5)
+        assert (tile & 15) in (0, 1, 2, 4, 8) and 0 <= tile >> 4 <= 3 and ms > 0
+    else:
+        assert tile in (0, 1, 2) and ms > 0
     assert torch.equal(r.u, u0)               # the map is restored
     # the tuned shape keeps parity: one iteration from the restored state vs the oracle's
     u_start = u0.cpu().numpy()

@@ -83,6 +83,22 @@ def test_update_pixel_map_parity(scan, hole):
     print(s.name, "hole" if hole else "", rep, "exact-path pixels:", n_exact)
 
 
+@pytest.mark.parametrize("tile", [0x11, 0x22, 0x34, 0x18], ids=["L7-TY1", "L9-TY2", "L11-TY4", "L7-TY8"])
+def test_update_strip_lengths(scan, tile):
+    """Every strip length (7, 9, 11 window columns) and tile height the FP32 search can be
+    asked for, on the reference with an uncovered patch, against the oracle."""
+    s = scan
+    inp, I32, w32 = _update_inputs(s, True)
+    ug_i, eg_i = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=False,
+                            tile=tile)
+    ug_q, eg_q = gpu_update(s.frames, s.W, s.M, I32, w32, s.delta, s.u_init, s.window, quadratic=True,
+                            tile=tile)
+    pix = np.flatnonzero(s.M.ravel())
+    rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
+                              ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
+    print(s.name, hex(tile), rep)
+
+
 def test_iterate_parity(scan):
     """One full iteration (both steps) through pxst_iterate against the oracle's."""
     s = scan
