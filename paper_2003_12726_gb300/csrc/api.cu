@@ -44,6 +44,8 @@ struct Ws {
     FrameShift *shifts;
     int *exact_list;
     double *num, *den;
+    int *fclass;
+    float *dcls;
     void *At, *G, *A2, *V;
     float *Tt, *Rm;
     int *nvalid, *cand, *wlist;
@@ -68,6 +70,8 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     w.exact_list = reinterpret_cast<int *>(b + L.exact_list);
     w.num = reinterpret_cast<double *>(b + L.num);
     w.den = reinterpret_cast<double *>(b + L.den);
+    w.fclass = reinterpret_cast<int *>(b + L.fclass);
+    w.dcls = reinterpret_cast<float *>(b + L.dcls);
     w.At = b + L.At;
     w.G = b + L.G;
     w.A2 = b + L.A2;
@@ -189,7 +193,7 @@ pxst_status cuda_status(cudaError_t e) {
 
 pxst_status run_prepare(const pxst_dims &d, const double *delta, Ws &w, cudaStream_t s) {
     Timed t(PXST_K_PREPARE, s);
-    PXST_TRY(launch_prepare(d, delta, w.hdr, w.shifts, 1, s));
+    PXST_TRY(launch_prepare(d, delta, w.hdr, w.shifts, w.fclass, 1, s));
     return PXST_OK;
 }
 
@@ -198,7 +202,7 @@ pxst_status run_omap(const pxst_dims &d, const float *frames, const float *W,
                      cudaStream_t s) {
     {
         Timed t(PXST_K_SCATTER, s);
-        PXST_TRY(launch_scatter(d, frames, W, mask, u, w.shifts, w.hdr, w.num, w.den, s));
+        PXST_TRY(launch_scatter(d, frames, W, mask, u, w.shifts, w.hdr, w.num, w.den, w.dcls, w.fclass, s));
     }
     {
         Timed t(PXST_K_NORMALISE, s);

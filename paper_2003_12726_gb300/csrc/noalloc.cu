@@ -89,8 +89,8 @@ extern "C" pxst_status pxst_make_object_map_noalloc(const pxst_dims *dims, const
     // the array keeps the previous call's contents: the header starts at zero here and the
     // scatter launch clears the accumulators it uses before adding to them
     e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
-    if (e == cudaSuccess) e = launch_prepare(*dims, delta, hdr, shifts, 1, s);
-    if (e == cudaSuccess) e = launch_scatter(*dims, frames, W, mask, u, shifts, hdr, num, den, s);
+    if (e == cudaSuccess) e = launch_prepare(*dims, delta, hdr, shifts, nullptr, 1, s);
+    if (e == cudaSuccess) e = launch_scatter(*dims, frames, W, mask, u, shifts, hdr, num, den, nullptr, nullptr, s);
     if (e == cudaSuccess) e = launch_normalise(*dims, num, den, I_ref, w, s);
     if (e != cudaSuccess) {
         std::fprintf(stderr, "pxst_make_object_map_noalloc: %s\n", cudaGetErrorString(e));

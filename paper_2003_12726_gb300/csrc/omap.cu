@@ -12,6 +12,7 @@
 //                global memory.
 //   normalise  : I_ref = num / den (FP64 divide) where den > 0, else 0; w = den.
 //   refterms   : T[c] = sum_n V R^2 and n_valid[c] = sum_n V over the reference grid.
+#include <algorithm>
 #include <climits>
 
 #include "pxst_common.cuh"
@@ -20,12 +21,19 @@ namespace pxst {
 namespace {
 
 // ------------------------------------------------------------------------------------
+// Also groups the frames by their fractional shift (fy, fx), compared bit for bit: class
+// r is the r-th distinct pair in frame order; fclass[n] is frame n's class.
 __global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restrict__ delta,
-                                                  WsHeader *hdr, FrameShift *shifts,
+                                                  WsHeader *hdr, FrameShift *shifts, int *fclass,
                                                   int reset_exact) {
     __shared__ int s[4];
+    __shared__ int s_nlead;
+    __shared__ unsigned int s_fy[kClassFramesMax], s_fx[kClassFramesMax];
+    __shared__ int s_lead[kClassFramesMax];
+    const bool classes = fclass != nullptr && N <= kClassFramesMax;
     if (threadIdx.x == 0) {
         s[0] = INT_MAX; s[1] = INT_MIN; s[2] = INT_MAX; s[3] = INT_MIN;
+        s_nlead = 0;
     }
     __syncthreads();
     int mn_y = INT_MAX, mx_y = INT_MIN, mn_x = INT_MAX, mx_x = INT_MIN;
@@ -36,6 +44,10 @@ __global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restric
         shifts[n] = fs;
         mn_y = min(mn_y, fs.ky); mx_y = max(mx_y, fs.ky);
         mn_x = min(mn_x, fs.kx); mx_x = max(mx_x, fs.kx);
+        if (classes) {
+            s_fy[n] = __float_as_uint(fs.fy);
+            s_fx[n] = __float_as_uint(fs.fx);
+        }
     }
     atomicMin(&s[0], mn_y); atomicMax(&s[1], mx_y);
     atomicMin(&s[2], mn_x); atomicMax(&s[3], mx_x);
@@ -44,7 +56,38 @@ __global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restric
         hdr->kmin_y = s[0]; hdr->kmax_y = s[1];
         hdr->kmin_x = s[2]; hdr->kmax_x = s[3];
         if (reset_exact) hdr->n_exact = 0;
+        if (!classes) hdr->n_classes = kMaxClasses + 1;
     }
+    if (!classes) return;
+    // the first frame with the same pair (the loop ends at m = n at the latest)
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        int m = 0;
+        while (s_fy[m] != s_fy[n] || s_fx[m] != s_fx[n]) ++m;
+        s_lead[n] = m;
+    }
+    __syncthreads();
+    // each first frame's rank among the first frames (its class); kept in s_fx's place
+    // after the pairs are read
+    int rank_of[(kClassFramesMax + 1023) / 1024];
+    for (int n = threadIdx.x, i = 0; n < N; n += blockDim.x, ++i) {
+        int r = -1;
+        if (s_lead[n] == n) {
+            r = 0;
+            for (int m = 0; m < n; ++m) r += s_lead[m] == m;
+            atomicMax(&s_nlead, r + 1);
+            if (r < kMaxClasses) {
+                hdr->cls_fy[r] = __uint_as_float(s_fy[n]);
+                hdr->cls_fx[r] = __uint_as_float(s_fx[n]);
+            }
+        }
+        rank_of[i] = r;
+    }
+    __syncthreads();
+    for (int n = threadIdx.x, i = 0; n < N; n += blockDim.x, ++i)
+        if (rank_of[i] >= 0) s_fx[n] = (unsigned int)rank_of[i];
+    __syncthreads();
+    for (int n = threadIdx.x; n < N; n += blockDim.x) fclass[n] = (int)min(s_fx[s_lead[n]], (unsigned)kMaxClasses);
+    if (threadIdx.x == 0) hdr->n_classes = s_nlead;
 }
 
 // ------------------------------------------------------------------------------------
@@ -61,6 +104,7 @@ struct ScatterArgs {
     const FrameShift *shifts;
     WsHeader *hdr;
     double *num, *den;
+    float *dcls;           // per-class weight images (NULL: the scatter forms the weights)
 };
 
 // One CTA per 16 x 32 pixel tile and chunk of frames (two CTAs per SM, so that one's
@@ -112,7 +156,11 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     }
     __syncthreads();
     if (s_rng[0] == INT_MAX || n0 >= n1) return;      // no active pixel in the tile
-    const float WW = Wv * Wv;
+    // the weights of pixels whose zero-shift corners stay on the grid for every fraction
+    // class are formed per class (k_dscatter, k_dgather); only the others add them here
+    const bool split = a.dcls != nullptr && a.hdr->n_classes <= kMaxClasses;
+    const bool dom = act && iy >= 0 && iy <= a.Ry - 3 && ix >= 0 && ix <= a.Rx - 3;
+    const float WW = (split && dom) ? 0.0f : Wv * Wv;
 
     for (int gs = n0; gs < n1;) {
         if (threadIdx.x == 0) {
@@ -195,18 +243,18 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 if (fits) {
                     const int c00 = (by - r0) * Wd + (bx - c0);
                     atomicAdd(&s_num[c00], ln0);
-                    atomicAdd(&s_den[c00], ld0);
+                    if (ld0 != 0.0f) atomicAdd(&s_den[c00], ld0);
                     if (right) {
                         atomicAdd(&s_num[c00 + 1], rn0);
-                        atomicAdd(&s_den[c00 + 1], rd0);
+                        if (rd0 != 0.0f) atomicAdd(&s_den[c00 + 1], rd0);
                     }
                     if (row1 || (take && (prn1 != 0.0f || prd1 != 0.0f))) {
                         atomicAdd(&s_num[c00 + Wd], ln1);
-                        atomicAdd(&s_den[c00 + Wd], ld1);
+                        if (ld1 != 0.0f) atomicAdd(&s_den[c00 + Wd], ld1);
                     }
                     if (row1 && right) {
                         atomicAdd(&s_num[c00 + Wd + 1], rn1);
-                        atomicAdd(&s_den[c00 + Wd + 1], rd1);
+                        if (rd1 != 0.0f) atomicAdd(&s_den[c00 + Wd + 1], rd1);
                     }
                 } else {
                     const float vn[4] = {ln0, right ? rn0 : 0.0f, ln1, right ? rn1 : 0.0f};
@@ -218,7 +266,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                         if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;
                         const size_t gi = (size_t)gy * a.Rx + gx;
                         atomicAdd(&a.num[gi], (double)vn[k]);
-                        atomicAdd(&a.den[gi], (double)vd[k]);
+                        if (vd[k] != 0.0f) atomicAdd(&a.den[gi], (double)vd[k]);
                     }
                 }
             }
@@ -231,8 +279,8 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 const int gy = r0 + c / Wd, gx = c0 + c % Wd;
                 if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;   // corners off the grid
                 const size_t gi = (size_t)gy * a.Rx + gx;
-                atomicAdd(&a.num[gi], (double)nm);
-                atomicAdd(&a.den[gi], (double)dn);
+                if (nm != 0.0f) atomicAdd(&a.num[gi], (double)nm);
+                if (dn != 0.0f) atomicAdd(&a.den[gi], (double)dn);
             }
         __syncthreads();
         gs = g1;
@@ -240,6 +288,76 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
 }
 
 // ------------------------------------------------------------------------------------
+// ---- the reference weights per fractional-shift class ----------------------------------
+// For a pixel whose corners stay on the grid, frame n adds b(u + f_n - corner) W^2 at
+// corner + k_n, where (k_n, f_n) split -Delta_n into an integer and a fraction: the image
+// D_f of those terms for a zero integer shift depends on the frame only through its class
+// f, and the frame's terms are D_f moved by k_n. So den(c) gains sum_n D_class(n)(c - k_n):
+// one scatter of W^2 per class (P x 4 terms) and one gather per cell and frame, instead of
+// a shared-memory atomic per pixel, frame and corner.
+__global__ void __launch_bounds__(256) k_dzero(size_t R, const WsHeader *__restrict__ hdr, float *__restrict__ dcls) {
+    const int nc = hdr->n_classes;
+    if (nc > kMaxClasses) return;
+    const size_t total = (size_t)nc * R;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        dcls[i] = 0.0f;
+}
+
+// One thread per pixel, blockIdx.y = class: the zero-shift corner terms b W^2, with the
+// fraction split and the corner arithmetic of k_scatter.
+__global__ void __launch_bounds__(256) k_dscatter(int ny, int nx, int Ry, int Rx, const float *__restrict__ W,
+                                                  const uint8_t *__restrict__ mask, const double *__restrict__ u,
+                                                  const WsHeader *__restrict__ hdr, float *__restrict__ dcls) {
+    const int f = blockIdx.y;
+    if (hdr->n_classes > kMaxClasses || f >= hdr->n_classes) return;
+    const size_t P = (size_t)ny * nx, R = (size_t)Ry * Rx;
+    const size_t pix = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (pix >= P || !mask[pix]) return;
+    const double u0 = u[pix], u1 = u[P + pix];
+    if (!isfinite(u0) || !isfinite(u1) || fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) return;
+    const double f0 = floor(u0), f1 = floor(u1);
+    int iy = (int)f0, ix = (int)f1;
+    float fy = (float)(u0 - f0), fx = (float)(u1 - f1);
+    if (fy >= 1.0f) { fy = 0.0f; iy += 1; }
+    if (fx >= 1.0f) { fx = 0.0f; ix += 1; }
+    if (iy < 0 || iy > Ry - 3 || ix < 0 || ix > Rx - 3) return;      // k_scatter adds these
+    const float Wv = W[pix], WW = Wv * Wv;
+    int by = iy, bx = ix;
+    float sy = fy + hdr->cls_fy[f], sx = fx + hdr->cls_fx[f];
+    if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
+    if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
+    const float b[4] = {(1.0f - sy) * (1.0f - sx) * WW, (1.0f - sy) * sx * WW, sy * (1.0f - sx) * WW, sy * sx * WW};
+    float *D = dcls + (size_t)f * R;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (b[k] != 0.0f) atomicAdd(D + (size_t)(by + (k >> 1)) * Rx + (bx + (k & 1)), b[k]);
+}
+
+// One thread per reference cell: den(c) += sum_n D_class(n)(c - k_n), FP32 over runs of 32
+// frames, FP64 across them.
+__global__ void __launch_bounds__(256) k_dgather(int N, int Ry, int Rx, const FrameShift *__restrict__ shifts,
+                                                 const int *__restrict__ fclass, const WsHeader *__restrict__ hdr,
+                                                 const float *__restrict__ dcls, double *__restrict__ den) {
+    if (hdr->n_classes > kMaxClasses) return;
+    const size_t R = (size_t)Ry * Rx;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < R; c += (size_t)gridDim.x * blockDim.x) {
+        const int cy = (int)(c / Rx), cx = (int)(c % Rx);
+        double acc = 0.0;
+        float part = 0.0f;
+        for (int n = 0; n < N; ++n) {
+            const int ty = cy - __ldg(&shifts[n].ky), tx = cx - __ldg(&shifts[n].kx);
+            if ((unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
+                part += __ldg(dcls + (size_t)__ldg(fclass + n) * R + (size_t)ty * Rx + tx);
+            if ((n & 31) == 31) {
+                acc += part;
+                part = 0.0f;
+            }
+        }
+        acc += part;
+        if (acc != 0.0) den[c] += acc;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_normalise(size_t R, const double *__restrict__ num,
                                                    const double *__restrict__ den,
                                                    float *__restrict__ I_ref,
@@ -286,14 +404,15 @@ int grid_for(size_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_prepare(const pxst_dims &d, const double *delta, WsHeader *hdr,
-                           FrameShift *shifts, int reset_exact, cudaStream_t stream) {
-    k_prepare<<<1, 1024, 0, stream>>>(d.n_frames, delta, hdr, shifts, reset_exact);
+                           FrameShift *shifts, int *fclass, int reset_exact, cudaStream_t stream) {
+    k_prepare<<<1, 1024, 0, stream>>>(d.n_frames, delta, hdr, shifts, fclass, reset_exact);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float *W,
                            const uint8_t *mask, const double *u, const FrameShift *shifts,
-                           WsHeader *hdr, double *num, double *den, cudaStream_t stream) {
+                           WsHeader *hdr, double *num, double *den, float *dcls, const int *fclass,
+                           cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
     cudaError_t e = cudaMemsetAsync(num, 0, sizeof(double) * R, stream);
     if (e != cudaSuccess) return e;
@@ -305,7 +424,7 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
     ScatterArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.frames = frames; a.W = W; a.mask = mask; a.u = u; a.shifts = shifts; a.hdr = hdr;
-    a.num = num; a.den = den;
+    a.num = num; a.den = den; a.dcls = (dcls && fclass) ? dcls : nullptr;
     const int gx = (d.nx + SC_TX - 1) / SC_TX;
     const int gy = (d.ny + SC_TY - 1) / SC_TY;
     const long long tiles = (long long)gx * gy;
@@ -319,7 +438,17 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
     nch = (d.n_frames + a.chunk - 1) / a.chunk;
     dim3 grid(gx, gy, (unsigned)nch);
     k_scatter<<<grid, SC_THREADS, smem, stream>>>(a);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.dcls) {
+        const size_t P = (size_t)d.ny * d.nx;
+        k_dzero<<<152 * 8, 256, 0, stream>>>(R, hdr, dcls);
+        k_dscatter<<<dim3((unsigned)((P + 255) / 256), kMaxClasses), 256, 0, stream>>>(d.ny, d.nx, d.ref_ny, d.ref_nx,
+                                                                                     W, mask, u, hdr, dcls);
+        k_dgather<<<(unsigned)std::min<size_t>((R + 255) / 256, 152 * 64), 256, 0, stream>>>(
+            d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr, dcls, den);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_normalise(const pxst_dims &d, const double *num, const double *den,

@@ -27,9 +27,16 @@ struct WsHeader {
     int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
     int n_edge_tiles;  // tensor forms: tiles listed for the masked ranking
     int n_rescore_warps;   // tensor forms: warps listed for the general rescore
-    int pad[55];
+    // frames grouped by their fractional shift (fy, fx): the reference weights of make_object_map
+    // are formed per class (n_classes > kMaxClasses: too many classes, the scatter forms them)
+    int n_classes;
+    float cls_fy[8], cls_fx[8];
+    int pad[38];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
+
+constexpr int kMaxClasses = 8;          // fractional-shift classes of the weight image
+constexpr int kClassFramesMax = 2048;   // frames the class assignment handles (more: no classes)
 
 // Candidates per pixel kept by the tensor-core ranking (the rescore evaluates the first
 // 4 or all 8 of them exactly).
@@ -39,6 +46,7 @@ constexpr int kTransMax = 17 * 17;     // translation update: shifts within +-8 
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
     size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp, filt_den;
+    size_t fclass, dcls;     // class of each frame; one zero-shift weight image per class
     // precision forms only (zero size otherwise)
     size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge, wlist;
     int Npad;
@@ -68,6 +76,8 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.tacc_cnt = off;   off += align256(sizeof(unsigned long long) * kTransMax * (size_t)d.n_frames);
     L.delta_tmp = off;  off += align256(sizeof(double) * 2 * (size_t)d.n_frames);
     L.filt_den = off;   off += align256(sizeof(double) * P);        // the map filter's row pass
+    L.fclass = off;     off += align256(sizeof(int) * (size_t)d.n_frames);
+    L.dcls = off;       off += align256(sizeof(float) * kMaxClasses * R);
     L.Npad = 0;
     L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.wlist = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
@@ -107,11 +117,15 @@ constexpr double kMaxCoord = 1.0e8;
 constexpr int kSearchSmemBudget = 200 * 1024;   // dynamic shared memory per CTA (bytes)
 
 // Launch helpers implemented in the .cu files (all asynchronous on `stream`).
+// fclass: the class of each frame (NULL: no classes; the scatter then forms the weights)
 cudaError_t launch_prepare(const pxst_dims &d, const double *delta, WsHeader *hdr,
-                           FrameShift *shifts, int reset_exact, cudaStream_t stream);
+                           FrameShift *shifts, int *fclass, int reset_exact, cudaStream_t stream);
+// dcls, fclass: the per-class weight images and the frames' classes (NULL: the scatter
+// forms the reference weights itself, as the no-allocation entry point does)
 cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float *W,
                            const uint8_t *mask, const double *u, const FrameShift *shifts,
-                           WsHeader *hdr, double *num, double *den, cudaStream_t stream);
+                           WsHeader *hdr, double *num, double *den, float *dcls, const int *fclass,
+                           cudaStream_t stream);
 cudaError_t launch_normalise(const pxst_dims &d, const double *num, const double *den,
                              float *I_ref, float *w, cudaStream_t stream);
 // span_y / span_x: range of the integer frame shifts (for sizing the shared-memory
