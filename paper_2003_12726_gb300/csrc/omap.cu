@@ -13,6 +13,7 @@
 //   normalise  : I_ref = num / den (FP64 divide) where den > 0, else 0; w = den.
 //   refterms   : T[c] = sum_n V R^2 and n_valid[c] = sum_n V over the reference grid.
 #include <algorithm>
+#include <type_traits>
 #include <climits>
 
 #include "pxst_common.cuh"
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(1024) k_prepare(int N, const double *__restric
 constexpr int SC_TX = 32, SC_TY = 16;                  // 32 x 16 pixels, one per thread
 constexpr int SC_THREADS = SC_TX * SC_TY;
 constexpr int SC_CAP = 12288;                          // cells (num + den: 96 KB): 2 CTAs per SM
-constexpr int SC_PREFETCH = 4;                         // frames loaded ahead of their scatter
+constexpr int SC_PREFETCH = 8;                         // frames in flight while the previous 8 scatter
+constexpr int SC_GROUP_MAX = 512;                      // frames per group (their shifts in shared memory)
 
 struct ScatterArgs {
     int N, ny, nx, Ry, Rx, chunk;
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     float *s_den = sm + SC_CAP;
     __shared__ int s_rng[4];
     __shared__ int s_grp[6];       // group [start, end), footprint origin r0, c0, height, width
+    __shared__ __align__(16) FrameShift s_sh[SC_GROUP_MAX];   // the group's shifts
 
     const int x = blockIdx.x * SC_TX + (threadIdx.x % SC_TX);
     const int y = blockIdx.y * SC_TY + (threadIdx.x / SC_TX);
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
             int kmn_y = INT_MAX, kmx_y = INT_MIN, kmn_x = INT_MAX, kmx_x = INT_MIN;
             int ge = gs;
             long long H = 0, Wd = 0;
-            while (ge < n1) {
+            while (ge < n1 && ge - gs < SC_GROUP_MAX) {
                 const FrameShift f = a.shifts[ge];
                 const int a0 = min(kmn_y, f.ky), a1 = max(kmx_y, f.ky);
                 const int b0 = min(kmn_x, f.kx), b1 = max(kmx_x, f.kx);
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 s_num[c] = 0.0f;
                 s_den[c] = 0.0f;
             }
+        for (int q = threadIdx.x; q < g1 - g0; q += SC_THREADS) s_sh[q] = a.shifts[g0 + q];
         __syncthreads();
         // Every lane of a warp (one pixel row, consecutive columns) runs the frame loop so
         // that neighbouring lanes can merge contributions: when lane l+1's left corner is
@@ -202,75 +206,102 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
         // corners to lane l+1, which adds both with one atomic per row. Corners whose
         // bilinear weight is exactly zero are skipped.
         const int lane = threadIdx.x & 31;
-        for (int n = g0; n < g1; n += SC_PREFETCH) {
-            float I[SC_PREFETCH];
-            FrameShift S[SC_PREFETCH];
+        // warps none of whose pixels adds weights here run a loop without them
+        const bool warp_den = __any_sync(0xffffffffu, act && WW != 0.0f);
+        auto frames_loop = [&](auto den_tag) {
+            constexpr bool DEN = decltype(den_tag)::value;
+            // frames stream through a register double buffer: the next 8 frames' loads are
+            // in flight while the current 8 are scattered (the frames are read once: streaming)
+            float In[SC_PREFETCH];
 #pragma unroll
             for (int jf = 0; jf < SC_PREFETCH; ++jf)
-                if (n + jf < g1) {
-                    S[jf] = a.shifts[n + jf];
-                    I[jf] = act ? __ldg(a.frames + (size_t)(n + jf) * P + pix) : 0.0f;
+                In[jf] = (act && g0 + jf < g1) ? __ldcs(a.frames + (size_t)(g0 + jf) * P + pix) : 0.0f;
+            for (int n = g0; n < g1; n += SC_PREFETCH) {
+                float I[SC_PREFETCH];
+#pragma unroll
+                for (int jf = 0; jf < SC_PREFETCH; ++jf) {
+                    I[jf] = In[jf];
+                    const int m = n + SC_PREFETCH + jf;
+                    In[jf] = (act && m < g1) ? __ldcs(a.frames + (size_t)m * P + pix) : 0.0f;
                 }
 #pragma unroll
-            for (int jf = 0; jf < SC_PREFETCH; ++jf) {
-                if (n + jf >= g1) break;                    // uniform over the CTA
-                int by = iy + S[jf].ky, bx = ix + S[jf].kx;
-                float sy = fy + S[jf].fy, sx = fx + S[jf].fx;
-                if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
-                if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
-                if (!act) { by = INT_MIN; bx = INT_MIN; }
-                const float WI = Wv * I[jf];
-                // right corners (top, bottom) and left corners, numerator and weight
-                float rn0 = (1.0f - sy) * sx * WI, rd0 = (1.0f - sy) * sx * WW;
-                float rn1 = sy * sx * WI, rd1 = sy * sx * WW;
-                float ln0 = (1.0f - sy) * (1.0f - sx) * WI, ld0 = (1.0f - sy) * (1.0f - sx) * WW;
-                float ln1 = sy * (1.0f - sx) * WI, ld1 = sy * (1.0f - sx) * WW;
-                const int pbx = __shfl_up_sync(0xffffffffu, bx, 1);
-                const int pby = __shfl_up_sync(0xffffffffu, by, 1);
-                const float prn0 = __shfl_up_sync(0xffffffffu, rn0, 1);
-                const float prd0 = __shfl_up_sync(0xffffffffu, rd0, 1);
-                const float prn1 = __shfl_up_sync(0xffffffffu, rn1, 1);
-                const float prd1 = __shfl_up_sync(0xffffffffu, rd1, 1);
-                const bool take = act && lane > 0 && pby == by && pbx != INT_MIN && pbx + 1 == bx;
-                const bool given = __shfl_down_sync(0xffffffffu, take ? 1 : 0, 1) && lane < 31;
-                if (take) {
-                    ln0 += prn0; ld0 += prd0;
-                    ln1 += prn1; ld1 += prd1;
-                }
-                if (!act) continue;
-                const bool row1 = sy != 0.0f;                // bottom corners carry weight
-                const bool right = sx != 0.0f && !given;     // right corners not handed over
-                if (fits) {
-                    const int c00 = (by - r0) * Wd + (bx - c0);
-                    atomicAdd(&s_num[c00], ln0);
-                    if (ld0 != 0.0f) atomicAdd(&s_den[c00], ld0);
-                    if (right) {
-                        atomicAdd(&s_num[c00 + 1], rn0);
-                        if (rd0 != 0.0f) atomicAdd(&s_den[c00 + 1], rd0);
+                for (int jf = 0; jf < SC_PREFETCH; ++jf) {
+                    if (n + jf >= g1) break;                    // uniform over the CTA
+                    const FrameShift S = s_sh[n + jf - g0];
+                    int by = iy + S.ky, bx = ix + S.kx;
+                    float sy = fy + S.fy, sx = fx + S.fx;
+                    if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
+                    if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
+                    if (!act) { by = INT_MIN; bx = INT_MIN; }
+                    const float WI = Wv * I[jf];
+                    // right corners (top, bottom) and left corners, numerator and weight
+                    float rn0 = (1.0f - sy) * sx * WI, rn1 = sy * sx * WI;
+                    float ln0 = (1.0f - sy) * (1.0f - sx) * WI, ln1 = sy * (1.0f - sx) * WI;
+                    float rd0 = 0.0f, rd1 = 0.0f, ld0 = 0.0f, ld1 = 0.0f;
+                    if constexpr (DEN) {
+                        rd0 = (1.0f - sy) * sx * WW;
+                        rd1 = sy * sx * WW;
+                        ld0 = (1.0f - sy) * (1.0f - sx) * WW;
+                        ld1 = sy * (1.0f - sx) * WW;
                     }
-                    if (row1 || (take && (prn1 != 0.0f || prd1 != 0.0f))) {
-                        atomicAdd(&s_num[c00 + Wd], ln1);
-                        if (ld1 != 0.0f) atomicAdd(&s_den[c00 + Wd], ld1);
+                    const int pbx = __shfl_up_sync(0xffffffffu, bx, 1);
+                    const int pby = __shfl_up_sync(0xffffffffu, by, 1);
+                    const float prn0 = __shfl_up_sync(0xffffffffu, rn0, 1);
+                    const float prn1 = __shfl_up_sync(0xffffffffu, rn1, 1);
+                    float prd0 = 0.0f, prd1 = 0.0f;
+                    if constexpr (DEN) {
+                        prd0 = __shfl_up_sync(0xffffffffu, rd0, 1);
+                        prd1 = __shfl_up_sync(0xffffffffu, rd1, 1);
                     }
-                    if (row1 && right) {
-                        atomicAdd(&s_num[c00 + Wd + 1], rn1);
-                        if (rd1 != 0.0f) atomicAdd(&s_den[c00 + Wd + 1], rd1);
+                    const bool take = act && lane > 0 && pby == by && pbx != INT_MIN && pbx + 1 == bx;
+                    const bool given = __shfl_down_sync(0xffffffffu, take ? 1 : 0, 1) && lane < 31;
+                    if (take) {
+                        ln0 += prn0;
+                        ln1 += prn1;
+                        if constexpr (DEN) {
+                            ld0 += prd0;
+                            ld1 += prd1;
+                        }
                     }
-                } else {
-                    const float vn[4] = {ln0, right ? rn0 : 0.0f, ln1, right ? rn1 : 0.0f};
-                    const float vd[4] = {ld0, right ? rd0 : 0.0f, ld1, right ? rd1 : 0.0f};
+                    if (!act) continue;
+                    const bool row1 = sy != 0.0f;                // bottom corners carry weight
+                    const bool right = sx != 0.0f && !given;     // right corners not handed over
+                    if (fits) {
+                        const int c00 = (by - r0) * Wd + (bx - c0);
+                        atomicAdd(&s_num[c00], ln0);
+                        if (DEN && ld0 != 0.0f) atomicAdd(&s_den[c00], ld0);
+                        if (right) {
+                            atomicAdd(&s_num[c00 + 1], rn0);
+                            if (DEN && rd0 != 0.0f) atomicAdd(&s_den[c00 + 1], rd0);
+                        }
+                        if (row1 || (take && (prn1 != 0.0f || prd1 != 0.0f))) {
+                            atomicAdd(&s_num[c00 + Wd], ln1);
+                            if (DEN && ld1 != 0.0f) atomicAdd(&s_den[c00 + Wd], ld1);
+                        }
+                        if (row1 && right) {
+                            atomicAdd(&s_num[c00 + Wd + 1], rn1);
+                            if (DEN && rd1 != 0.0f) atomicAdd(&s_den[c00 + Wd + 1], rd1);
+                        }
+                    } else {
+                        const float vn[4] = {ln0, right ? rn0 : 0.0f, ln1, right ? rn1 : 0.0f};
+                        const float vd[4] = {ld0, right ? rd0 : 0.0f, ld1, right ? rd1 : 0.0f};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int gy = by + (k >> 1), gx = bx + (k & 1);
-                        if (vd[k] == 0.0f && vn[k] == 0.0f) continue;
-                        if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;
-                        const size_t gi = (size_t)gy * a.Rx + gx;
-                        atomicAdd(&a.num[gi], (double)vn[k]);
-                        if (vd[k] != 0.0f) atomicAdd(&a.den[gi], (double)vd[k]);
+                        for (int k = 0; k < 4; ++k) {
+                            const int gy = by + (k >> 1), gx = bx + (k & 1);
+                            if (vd[k] == 0.0f && vn[k] == 0.0f) continue;
+                            if (gy < 0 || gy >= a.Ry || gx < 0 || gx >= a.Rx) continue;
+                            const size_t gi = (size_t)gy * a.Rx + gx;
+                            atomicAdd(&a.num[gi], (double)vn[k]);
+                            if (DEN && vd[k] != 0.0f) atomicAdd(&a.den[gi], (double)vd[k]);
+                        }
                     }
                 }
             }
-        }
+        };
+        if (warp_den)
+            frames_loop(std::true_type{});
+        else
+            frames_loop(std::false_type{});
         __syncthreads();
         if (fits)
             for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {
