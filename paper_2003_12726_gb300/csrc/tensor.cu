@@ -311,6 +311,7 @@ struct TSearchArgs {
     int *tile_list;     // tiles holding such pixels, hdr->n_edge_tiles of them (any order)
     int tiles_x;        // tiles per detector row (to decode a listed tile)
     const float *W;     // masked ranking: the whitefield (the key of a zero-variance candidate)
+    int ares;           // first pass: 0 = A~ streams with G~; k > 0 = A~ resident, k G~ stages
 };
 
 // Insert (qv, idx) into the ascending list bq/bi when it beats an entry (strict <, so of
@@ -332,11 +333,15 @@ __device__ __forceinline__ void topk_insert(float (&bq)[TK], int (&bi)[TK], floa
 
 // One chunk row of 32 candidates for the warp's 32 pixels: q = T~ - 2 C~, where sT holds
 // T~ (+inf for a candidate that is not valid in every frame). Lanes whose window does not
-// hold column i (bit i of inmask clear) skip it; the insertion runs only when some lane of
-// the warp improves its list.
+// hold column i (bit i of inmask clear) skip it. The segment's keys are formed first; if
+// none of them beats any lane's K-th key (the lists only improve, so none could later in
+// the segment either), the segment is done with one vote; otherwise the insertion runs,
+// candidate by candidate, only when some lane of the warp improves its list.
 template <int TK, bool FULL>
 __device__ __forceinline__ void scan_row(const float (&v)[32], const float *__restrict__ sT, uint32_t inmask,
                                          int rowbase, float (&bq)[TK], int (&bi)[TK]) {
+    float q[32];
+    float mn = INFINITY;
 #pragma unroll
     for (int i4 = 0; i4 < 32; i4 += 4) {
         const float4 t4 = *reinterpret_cast<const float4 *>(sT + i4);
@@ -344,11 +349,15 @@ __device__ __forceinline__ void scan_row(const float (&v)[32], const float *__re
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int i = i4 + e;
-            float qv = fmaf(-2.0f, v[i], tt[e]);
-            if (!FULL) qv = ((inmask >> i) & 1u) ? qv : INFINITY;
-            if (__any_sync(0xffffffffu, qv < bq[TK - 1])) topk_insert<TK>(bq, bi, qv, rowbase + i);
+            q[i] = fmaf(-2.0f, v[i], tt[e]);
+            if (!FULL) q[i] = ((inmask >> i) & 1u) ? q[i] : INFINITY;
+            mn = fminf(mn, q[i]);
         }
     }
+    if (!__any_sync(0xffffffffu, mn < bq[TK - 1])) return;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (__any_sync(0xffffffffu, q[i] < bq[TK - 1])) topk_insert<TK>(bq, bi, q[i], rowbase + i);
 }
 
 // The masked ranking's segment: with S = sum_n V A~^2 (second accumulator), a candidate's
@@ -359,13 +368,19 @@ template <int TK>
 __device__ __forceinline__ void scan_row_masked(const float (&v)[32], const float (&v2)[32],
                                                 const float *__restrict__ sT, uint32_t use, int rowbase, float W2,
                                                 float (&bq)[TK], int (&bi)[TK]) {
+    float q[32];
+    float mn = INFINITY;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         const float t = sT[i];
-        float qv = v2[i] > 0.0f ? __fdividef(fmaf(-2.0f, v[i], t), v2[i]) : fmaf(W2, t, -1.0f);
-        qv = (((use >> i) & 1u) && t < INFINITY) ? qv : INFINITY;
-        if (__any_sync(0xffffffffu, qv < bq[TK - 1])) topk_insert<TK>(bq, bi, qv, rowbase + i);
+        const float qv = v2[i] > 0.0f ? __fdividef(fmaf(-2.0f, v[i], t), v2[i]) : fmaf(W2, t, -1.0f);
+        q[i] = (((use >> i) & 1u) && t < INFINITY) ? qv : INFINITY;
+        mn = fminf(mn, q[i]);
     }
+    if (!__any_sync(0xffffffffu, mn < bq[TK - 1])) return;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (__any_sync(0xffffffffu, q[i] < bq[TK - 1])) topk_insert<TK>(bq, bi, q[i], rowbase + i);
 }
 
 // Visit order of n chunk rows (or columns): the one holding the tile's centre first, then
@@ -397,12 +412,16 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     constexpr int KB = TF32 ? 32 : 64;       // frames per 128-byte operand row
     constexpr int KSTEP = TF32 ? 8 : 16;     // frames per MMA
     constexpr uint32_t IDESC = tc::instr_desc(TF32 ? 2u : 1u, 128, 256);
-    constexpr int NS = MASKED ? TSM_STAGES : TS_STAGES;                 // pipeline stages
     constexpr int NBUF = MASKED ? 1 : 2;                                // TMEM accumulator buffers
-    constexpr int SB = (MASKED ? 2 : 1) * (TS_A_BYTES + TS_B_BYTES);    // bytes per stage
+    // A-resident mode: the tile's A~ (the same for every chunk) is loaded once, before the
+    // chunks, and only G~ streams through the stage ring
+    const int ares = MASKED ? 0 : a.ares;
+    const int NS = ares ? ares : (MASKED ? TSM_STAGES : TS_STAGES);    // pipeline stages
+    const int SB = ares ? TS_B_BYTES : (MASKED ? 2 : 1) * (TS_A_BYTES + TS_B_BYTES);   // bytes per stage
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t bar_full[TS_STAGES], bar_empty[TS_STAGES], bar_tfull[2], bar_tempty[2];
+    __shared__ __align__(8) uint64_t bar_afull;       // A-resident mode: every A~ block landed
     __shared__ int s_tile_edge;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -461,12 +480,14 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     const int nchunks = nrc * ncc;
     const int nkb = a.Npad / KB;
     const bool ordered = nrc <= TS_MAX_ORDER && ncc <= TS_MAX_ORDER;
+    uint8_t *stage0 = smem + (ares ? nkb * TS_A_BYTES : 0);     // the stage ring
 
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) {
             tc::mbar_init(&bar_full[i], 1);
             tc::mbar_init(&bar_empty[i], 1);
         }
+        tc::mbar_init(&bar_afull, 1);
         for (int i = 0; i < NBUF; ++i) {
             tc::mbar_init(&bar_tfull[i], 1);
             tc::mbar_init(&bar_tempty[i], TS_EPI_WARPS);
@@ -501,6 +522,11 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     if (warp == 0) {
         // ---- TMA producer ---------------------------------------------------------------
         if (lane == 0) {
+            if (ares) {
+                // the tile's A~, all frame blocks, once
+                tc::mbar_expect_tx(&bar_afull, (uint32_t)(nkb * TS_A_BYTES));
+                for (int kb = 0; kb < nkb; ++kb) tc::tma_load_4d(smem + kb * TS_A_BYTES, &tA, &bar_afull, 0, x0, y0, kb);
+            }
             int it = 0;
             for (int j = 0; j < nchunks && !*abortp; ++j) {
                 int row0, col0;
@@ -510,6 +536,11 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                     if (!tc::mbar_wait(&bar_empty[s], ((it / NS) & 1) ^ 1, abortp)) {
                         *abortp = 1;
                         break;
+                    }
+                    if (ares) {
+                        tc::mbar_expect_tx(&bar_full[s], SB);
+                        tc::tma_load_4d(stage0 + s * SB, &tB, &bar_full[s], 0, col0, row0, kb);
+                        continue;
                     }
                     // stage layout: A~ | G~ (| A~^2 | V)
                     uint8_t *As = smem + s * SB;
@@ -529,11 +560,16 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                 volatile int never = 0;
                 tc::mbar_wait(&bar_full[s], (i2 / NS) & 1, &never);
             }
+            if (ares) {
+                volatile int never = 0;
+                tc::mbar_wait(&bar_afull, 0, &never);
+            }
         }
     } else if (warp == 1) {
         // ---- MMA issuer -------------------------------------------------------------------
         if (lane == 0) {
             int it = 0;
+            if (ares && !tc::mbar_wait(&bar_afull, 0, abortp)) *abortp = 1;
             for (int j = 0; j < nchunks && !*abortp; ++j) {
                 const int buf = j % NBUF;
                 if (!tc::mbar_wait(&bar_tempty[buf], ((j / NBUF) & 1) ^ 1, abortp)) {
@@ -549,8 +585,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(smem + s * SB);
-                    const uint32_t b0 = a0 + TS_A_BYTES;
+                    const uint32_t a0 = ares ? tc::smem_u32(smem + kb * TS_A_BYTES) : tc::smem_u32(smem + s * SB);
+                    const uint32_t b0 = ares ? tc::smem_u32(stage0 + s * SB) : a0 + TS_A_BYTES;
                     const uint32_t a20 = b0 + TS_B_BYTES, v0 = a20 + TS_A_BYTES;
 #pragma unroll
                     for (int k = 0; k < KB / KSTEP; ++k) {
@@ -774,9 +810,25 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     // the ranking of every tile, then the masked ranking of the tiles it listed (a grid of
     // one CTA per tile, of which those beyond the list's length return at once)
     auto go = [&](auto plain, auto masked) {
-        cudaError_t r = cudaFuncSetAttribute(plain, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+        // A~ resident when it and three (else two) G~ stages fit the CTA's shared memory
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, plain);
         if (r != cudaSuccess) return r;
-        plain<<<dim3(gx, gy), TS_THREADS, TS_SMEM, stream>>>(tA, tB, tA2, tV, a);
+        int dev = 0, optin = 0;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+        if ((r = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return r;
+        int smem = TS_SMEM;
+        a.ares = 0;
+        for (int st = 3; st >= 2 && !a.ares; --st) {
+            const long long need = 1024 + (long long)nkb * TS_A_BYTES + (long long)st * TS_B_BYTES;
+            if (need + (long long)fa.sharedSizeBytes <= optin) {
+                a.ares = st;
+                smem = (int)need;
+            }
+        }
+        r = cudaFuncSetAttribute(plain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (r != cudaSuccess) return r;
+        plain<<<dim3(gx, gy), TS_THREADS, smem, stream>>>(tA, tB, tA2, tV, a);
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
         if (tf32)
             k_tsquare<float><<<gx * gy, 256, 0, stream>>>((int)nkb, d.ny, d.nx, (int)pty, (int)gx, hdr, tile_list,
@@ -786,6 +838,7 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
                 (int)nkb, d.ny, d.nx, (int)pty, (int)gx, hdr, tile_list, static_cast<const __nv_bfloat16 *>(At),
                 static_cast<__nv_bfloat16 *>(A2));
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
+        a.ares = 0;
         r = cudaFuncSetAttribute(masked, cudaFuncAttributeMaxDynamicSharedMemorySize, TSM_SMEM);
         if (r != cudaSuccess) return r;
         masked<<<gx * gy, TS_THREADS, TSM_SMEM, stream>>>(tA, tB, tA2, tV, a);

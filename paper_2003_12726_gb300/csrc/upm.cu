@@ -1118,9 +1118,12 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
     }
     // other kept candidates: as many as the warp's longest list (the rest read c0)
     const int nxw = __reduce_max_sync(0xffffffffu, pc.nxk);
-    float e9[9], ex[PixCands<XK>::NX], var = 0.0f;
+    // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
+    // packed FMA advances two sums
+    float2 acc[5];
 #pragma unroll
-    for (int jn = 0; jn < 9; ++jn) e9[jn] = 0.0f;
+    for (int k = 0; k < 5; ++k) acc[k] = make_float2(0.0f, 0.0f);
+    float ex[PixCands<XK>::NX];
 #pragma unroll
     for (int q = 0; q < XK; ++q) ex[q] = 0.0f;
     const float Wv = pc.Wv;
@@ -1148,8 +1151,7 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
             for (int f = 0; f < nf; ++f) {
                 const FrameShift s = a.shifts[st * RS_F + f];
                 const float I = sfr[buf][f][t];
-                const float tt = I - Wv;
-                var = fmaf(tt, tt, var);
+                const float2 I2 = make_float2(I, I), nW2 = make_float2(-Wv, -Wv);
                 if (s.fy == 0.0f && s.fx == 0.0f) {          // the same for every lane
                     const int off = s.ky * a.Rx + s.kx;
                     const float *r0 = a.Rm + (pc.base0 + off);
@@ -1157,10 +1159,13 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
                     const float R[9] = {__ldg(rm - 1), __ldg(rm), __ldg(rm + 1), __ldg(r0 - 1), __ldg(r0),
                                         __ldg(r0 + 1), __ldg(rp - 1), __ldg(rp), __ldg(rp + 1)};
 #pragma unroll
-                    for (int jn = 0; jn < 9; ++jn) {
-                        const float d = fmaf(-Wv, R[jn], I);
-                        e9[jn] = fmaf(d, d, e9[jn]);
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 d = __ffma2_rn(nW2, make_float2(R[2 * k], R[2 * k + 1]), I2);
+                        acc[k] = __ffma2_rn(d, d, acc[k]);
                     }
+                    // (I - W R8, I - W): the last point and the variance term
+                    const float2 d8 = __ffma2_rn(nW2, make_float2(R[8], 1.0f), I2);
+                    acc[4] = __ffma2_rn(d8, d8, acc[4]);
 #pragma unroll
                     for (int q = 0; q < XK; ++q) {
                         if (q >= nxw) break;
@@ -1168,6 +1173,8 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
                         ex[q] = fmaf(d, d, ex[q]);
                     }
                 } else {
+                    const float tt = I - Wv;
+                    acc[4].y = fmaf(tt, tt, acc[4].y);
                     // a fractional shift: the masked bilinear read (valid: the counts are N)
 #pragma unroll
                     for (int jn = 0; jn < 9; ++jn) {
@@ -1175,7 +1182,8 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
                         if (gather_rm(a.Rm, a.Ry, a.Rx, pc.y0 + jn / 3 - 1 + s.ky, pc.x0 + jn % 3 - 1 + s.kx, s.fy,
                                       s.fx, R)) {
                             const float d = fmaf(-Wv, R, I);
-                            e9[jn] = fmaf(d, d, e9[jn]);
+                            float &e = (jn & 1) ? acc[jn >> 1].y : acc[jn >> 1].x;
+                            e = fmaf(d, d, e);
                         }
                     }
 #pragma unroll
@@ -1194,9 +1202,13 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
     cp_async_wait<0>();
     if (!pc.act) return;
     // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
+    const float var = acc[4].y;
     float f9[9], fxe[PixCands<XK>::NX];
 #pragma unroll
-    for (int jn = 0; jn < 9; ++jn) f9[jn] = pc.in9[jn] ? (var > 0.0f ? e9[jn] / var : e9[jn]) : INFINITY;
+    for (int jn = 0; jn < 9; ++jn) {
+        const float e = (jn & 1) ? acc[jn >> 1].y : acc[jn >> 1].x;
+        f9[jn] = pc.in9[jn] ? (var > 0.0f ? e / var : e) : INFINITY;
+    }
 #pragma unroll
     for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? (var > 0.0f ? ex[q] / var : ex[q]) : INFINITY;
     pix_finish<XK>(a, pix, pc, f9, fxe);
