@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
 // (M = 128) against candidate chunks of (256 / CCW) x CCW reference pixels (N = 256).
 // Shape 0: 8 x 16 pixels, 8 x 32 candidates; 1: 4 x 32, 4 x 64; 2: 2 x 64, 2 x 128.
 constexpr int TS_STAGES = 4;
-constexpr int TS_EPI_WARPS = 8;               // two per TMEM lane quarter, splitting the chunk rows
+constexpr int TS_EPG = 3;                     // epilogue warps per TMEM lane quarter
+constexpr int TS_EPI_WARPS = 4 * TS_EPG;      // they split a chunk's 8 segments: g = h, h + 3, ...
 constexpr int TS_THREADS = 64 + 32 * TS_EPI_WARPS;   // producer, MMA, epilogue warps
 constexpr int TS_A_BYTES = 128 * 128, TS_B_BYTES = 256 * 128;
 constexpr int TS_SMEM = TS_STAGES * (TS_A_BYTES + TS_B_BYTES) + 1024;
@@ -430,9 +431,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
     __shared__ int s_rord[TS_MAX_ORDER], s_cord[TS_MAX_ORDER];
     __shared__ __align__(16) float s_T[2][256];
     __shared__ uint32_t s_vm[2][8];
-    __shared__ float s_mq[128][TK];
-    __shared__ int s_mi[128][TK];
-    __shared__ uint8_t s_medge[128];
+    __shared__ float s_mq[TS_EPG - 1][128][TK];      // the lists of the warps h > 0, merged by h = 0
+    __shared__ int s_mi[TS_EPG - 1][128][TK];
+    __shared__ uint8_t s_medge[TS_EPG - 1][128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t P = (size_t)a.ny * a.nx;
@@ -603,9 +604,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             }
         }
     } else {
-        // ---- epilogue: 8 warps; TMEM lane quarter q = warp % 4; the chunk's 8 segments of 32
-        //      candidates (TMEM columns 32 g ..) are split h, h + 2, ... --------------------------
-        const int ew = warp - 2;                      // 0..7: also the segment this warp stages
+        // ---- epilogue: 4 x TS_EPG warps; TMEM lane quarter q = warp % 4; the chunk's 8 segments
+        //      of 32 candidates (TMEM columns 32 g ..) are split h, h + TS_EPG, ... -------------
+        const int ew = warp - 2;                      // the segment this warp stages (if < 8)
         const int q = warp & 3, h = ew >> 2;
         const int p = q * 32 + lane;                  // pixel of the tile = TMEM lane
         const bool act = s_act[p] != 0;
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                 if (ok) t = __ldg(a.Tt + c);
             }
         };
-        {
+        if (ew < 8) {
             float t;
             bool ok;
             fetch(0, t, ok);
@@ -658,14 +659,14 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             chunk_origin(j, row0, col0);
             float tn = INFINITY;
             bool okn = false;
-            if (j + 1 < nchunks) fetch(j + 1, tn, okn);
+            if (j + 1 < nchunks && ew < 8) fetch(j + 1, tn, okn);
             // a wait that ran out stops every epilogue warp after the same barrier below
             const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], (j / NBUF) & 1, abortp));
             if (!ok) *abortp = 1;
             tc::tc_fence_after();
             if (ok) {
 #pragma unroll 1
-                for (int g = h; g < 8; g += 2) {
+                for (int g = h; g < 8; g += TS_EPG) {
                     const int r = g / SPR, c0 = col0 + (g % SPR) * 32;
                     const int aa = row0 + r - ci;
                     // this pixel's window columns within the segment: [ilo, ihi]
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                 }
             }
             tc::tc_fence_before();
-            if (j + 1 < nchunks) {
+            if (j + 1 < nchunks && ew < 8) {
                 s_T[sbuf ^ 1][ew * 32 + lane] = tn;
                 const uint32_t vm = __ballot_sync(0xffffffffu, okn);
                 if (lane == 0) s_vm[sbuf ^ 1][ew] = vm;
@@ -702,26 +703,30 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             if (lane == 0) tc::mbar_arrive(&bar_tempty[buf]);
             if (*abortp) break;
         }
-        // merge the two lists of each pixel (rows of the two halves), write the result
-        if (h == 1) {
+        // merge the lists of each pixel (in warp order h = 1, 2, ...), write the result
+        if (h > 0) {
 #pragma unroll
             for (int m = 0; m < TK; ++m) {
-                s_mq[p][m] = bq[m];
-                s_mi[p][m] = bi[m];
+                s_mq[h - 1][p][m] = bq[m];
+                s_mi[h - 1][p][m] = bi[m];
             }
-            s_medge[p] = edge ? 1 : 0;
+            s_medge[h - 1][p] = edge ? 1 : 0;
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_EPI_WARPS) : "memory");
         if (h == 0 && mine && !*abortp) {
 #pragma unroll
-            for (int m = 0; m < TK; ++m)
-                if (s_mq[p][m] < bq[TK - 1]) topk_insert<TK>(bq, bi, s_mq[p][m], s_mi[p][m]);
+            for (int w = 0; w < TS_EPG - 1; ++w)
+#pragma unroll
+                for (int m = 0; m < TK; ++m)
+                    if (s_mq[w][p][m] < bq[TK - 1]) topk_insert<TK>(bq, bi, s_mq[w][p][m], s_mi[w][p][m]);
             const int x = x0 + (p % TS_TX), y = y0 + (p / TS_TX);
             const size_t pix = (size_t)y * a.nx + x;
 #pragma unroll
             for (int m = 0; m < kTopK; ++m) a.cand[pix * kTopK + m] = m < TK ? bi[m] : -1;
             if (!MASKED) {
-                const bool e = edge || s_medge[p];
+                bool e = edge;
+#pragma unroll
+                for (int w = 0; w < TS_EPG - 1; ++w) e = e || s_medge[w][p];
                 a.edge[pix] = e ? 1 : 0;
                 if (e) {
                     atomicAdd(&a.hdr->n_exact, 1);
