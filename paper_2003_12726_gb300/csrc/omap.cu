@@ -365,28 +365,53 @@ __global__ void __launch_bounds__(256) k_dscatter(int ny, int nx, int Ry, int Rx
 }
 
 // One thread per reference cell: den(c) += sum_n D_class(n)(c - k_n), FP32 over runs of 32
-// frames, FP64 across them.
+// frames, FP64 across them. The block stages 256 frames' shifts and classes at a time in
+// shared memory, and each thread keeps 8 frames' reads in flight.
+constexpr int DG_FRAMES = 256;
 __global__ void __launch_bounds__(256) k_dgather(int N, int Ry, int Rx, const FrameShift *__restrict__ shifts,
                                                  const int *__restrict__ fclass, const WsHeader *__restrict__ hdr,
                                                  const float *__restrict__ dcls, double *__restrict__ den) {
+    __shared__ int s_cls[DG_FRAMES], s_ky[DG_FRAMES], s_kx[DG_FRAMES];   // the frames' class and shift
     if (hdr->n_classes > kMaxClasses) return;
     const size_t R = (size_t)Ry * Rx;
-    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < R; c += (size_t)gridDim.x * blockDim.x) {
-        const int cy = (int)(c / Rx), cx = (int)(c % Rx);
-        double acc = 0.0;
-        float part = 0.0f;
-        for (int n = 0; n < N; ++n) {
-            const int ty = cy - __ldg(&shifts[n].ky), tx = cx - __ldg(&shifts[n].kx);
-            if ((unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
-                part += __ldg(dcls + (size_t)__ldg(fclass + n) * R + (size_t)ty * Rx + tx);
-            if ((n & 31) == 31) {
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const bool inside = c < R;
+    const int cy = inside ? (int)(c / Rx) : 0, cx = inside ? (int)(c % Rx) : 0;
+    double acc = 0.0;
+    float part = 0.0f;
+    for (int n0 = 0; n0 < N; n0 += DG_FRAMES) {
+        const int nf = min(DG_FRAMES, N - n0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+            const FrameShift f = shifts[n0 + q];
+            s_ky[q] = f.ky;
+            s_kx[q] = f.kx;
+            s_cls[q] = fclass[n0 + q];
+        }
+        __syncthreads();
+        if (!inside) continue;
+        for (int q0 = 0; q0 < nf; q0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int q = q0 + e;
+                v[e] = 0.0f;
+                if (q < nf) {
+                    const int ty = cy - s_ky[q], tx = cx - s_kx[q];
+                    if ((unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
+                        v[e] = __ldg(dcls + (size_t)s_cls[q] * R + (size_t)ty * Rx + tx);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) part += v[e];
+            if (((n0 + q0) & 31) == 24) {       // every 32 frames
                 acc += part;
                 part = 0.0f;
             }
         }
-        acc += part;
-        if (acc != 0.0) den[c] += acc;
     }
+    acc += part;
+    if (inside && acc != 0.0) den[c] += acc;
 }
 
 __global__ void __launch_bounds__(256) k_normalise(size_t R, const double *__restrict__ num,
@@ -475,7 +500,7 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
         k_dzero<<<152 * 8, 256, 0, stream>>>(R, hdr, dcls);
         k_dscatter<<<dim3((unsigned)((P + 255) / 256), kMaxClasses), 256, 0, stream>>>(d.ny, d.nx, d.ref_ny, d.ref_nx,
                                                                                      W, mask, u, hdr, dcls);
-        k_dgather<<<(unsigned)std::min<size_t>((R + 255) / 256, 152 * 64), 256, 0, stream>>>(
+        k_dgather<<<(unsigned)((R + 255) / 256), 256, 0, stream>>>(
             d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr, dcls, den);
         e = cudaGetLastError();
     }
