@@ -30,8 +30,15 @@ import gen  # noqa: E402
 
 METRIC = "PXST iteration time & pixel·shift·frame evals/s; served scans/s, p50/p99"
 UNIT = "pixel·shift·frame evals/s"
-KERNEL_SOURCES = ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/csrc/omap.cu",
-                  "paper_2003_12726_gb300/csrc/pxst_common.cuh"]
+# the sources each timed kernel group is built from (a recorded DRAM traffic is used only
+# while their hash is unchanged)
+KERNEL_SOURCES = {
+    "upm_search": ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/csrc/pxst_common.cuh"],
+    "upm_rescore": ["paper_2003_12726_gb300/csrc/upm.cu", "paper_2003_12726_gb300/csrc/pxst_common.cuh"],
+    "omap_scatter": ["paper_2003_12726_gb300/csrc/omap.cu", "paper_2003_12726_gb300/csrc/pxst_common.cuh"],
+    "tensor_search": ["paper_2003_12726_gb300/csrc/tensor.cu", "paper_2003_12726_gb300/csrc/tc_ptx.cuh",
+                      "paper_2003_12726_gb300/csrc/pxst_common.cuh"],
+}
 
 
 FORMS = {"fp32": 0, "bf16": 1, "tf32": 2}
@@ -60,9 +67,9 @@ def evals_per_step(s):
     return int(s.M.sum()) * (2 * Sy + 1) * (2 * Sx + 1) * s.frames.shape[0]
 
 
-def kernel_hash():
+def kernel_hash(name):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES.get(name, []):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -175,13 +182,15 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------
-def load_traffic(name, khash):
+def load_traffic(workload, name):
+    """DRAM bytes per launch of kernel group `name` on `workload` from profiles/traffic.json,
+    or None when none is recorded for the current sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        e = d.get(name)
-        if e and e.get("kernel_hash") == khash:
+        e = d.get(workload, {}).get(name)
+        if e and e.get("kernel_hash") == kernel_hash(name):
             return e.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -356,6 +365,15 @@ def pxst_arm(args, rank, world, local_rank):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
+    elif name == "upm_rescore":
+        # the exact stage of the tensor forms: at least the 3x3 about each pixel's first
+        # candidate, 2 FP32 FMA per pixel, frame and point
+        flop = 4.0 * 9 * int(s.M.sum()) * s.frames.shape[0]
+        achieved = flop / (avg_ms * 1e-3) / 1e12
+        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
     elif name == "update_translations":
         # per pixel, frame and shift: the masked bilinear read (8 flop), d = I - W R (2),
         # d^2 / var (2): 12 flop; plus the per-pixel variance pass (one read per frame)
@@ -376,7 +394,7 @@ def pxst_arm(args, rank, world, local_rank):
         peak = float(pk["hbm_gbs"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "kernel": name, "avg_launch_ms": avg_ms, "peak_basis": f"{basis} HBM copy bandwidth"}
-    roof["traffic"] = load_traffic(name, kernel_hash())
+    roof["traffic"] = load_traffic(args.workload + ("" if form == 0 else "-" + args.form), name)
 
     clocks = sampler.summary(t_wall0 - 0.2, t_wall1 + 0.2) if sampler else None
     if clocks and clocks.get("samples", 0) == 0:

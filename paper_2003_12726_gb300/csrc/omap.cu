@@ -364,21 +364,37 @@ __global__ void __launch_bounds__(256) k_dscatter(int ny, int nx, int Ry, int Rx
         if (b[k] != 0.0f) atomicAdd(D + (size_t)(by + (k >> 1)) * Rx + (bx + (k & 1)), b[k]);
 }
 
-// One thread per reference cell: den(c) += sum_n D_class(n)(c - k_n), FP32 over runs of 32
-// frames, FP64 across them. The block stages 256 frames' shifts and classes at a time in
-// shared memory, and each thread keeps 8 frames' reads in flight.
+// den(c) += sum_n D_class(n)(c - k_n), FP32 over runs of 32 frames, FP64 across them. Each
+// warp covers 128 consecutive cells, a thread the cells lane, lane + 32, lane + 64, lane + 96
+// (every read of the warp one coalesced line); the block stages 256 frames' shifts and
+// classes at a time in shared memory, and each thread keeps 4 frames x 4 cells of reads in
+// flight.
 constexpr int DG_FRAMES = 256;
+constexpr int DG_CELLS = 4;
 __global__ void __launch_bounds__(256) k_dgather(int N, int Ry, int Rx, const FrameShift *__restrict__ shifts,
                                                  const int *__restrict__ fclass, const WsHeader *__restrict__ hdr,
                                                  const float *__restrict__ dcls, double *__restrict__ den) {
     __shared__ int s_cls[DG_FRAMES], s_ky[DG_FRAMES], s_kx[DG_FRAMES];   // the frames' class and shift
     if (hdr->n_classes > kMaxClasses) return;
     const size_t R = (size_t)Ry * Rx;
-    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const bool inside = c < R;
-    const int cy = inside ? (int)(c / Rx) : 0, cx = inside ? (int)(c % Rx) : 0;
-    double acc = 0.0;
-    float part = 0.0f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t cbase = ((size_t)blockIdx.x * 8 + warp) * (32 * DG_CELLS) + lane;
+    int cy[DG_CELLS], cx[DG_CELLS];
+    bool in[DG_CELLS];
+#pragma unroll
+    for (int k = 0; k < DG_CELLS; ++k) {
+        const size_t c = cbase + 32 * k;
+        in[k] = c < R;
+        cy[k] = in[k] ? (int)(c / Rx) : -1;
+        cx[k] = in[k] ? (int)(c % Rx) : 0;
+    }
+    double acc[DG_CELLS];
+    float part[DG_CELLS];
+#pragma unroll
+    for (int k = 0; k < DG_CELLS; ++k) {
+        acc[k] = 0.0;
+        part[k] = 0.0f;
+    }
     for (int n0 = 0; n0 < N; n0 += DG_FRAMES) {
         const int nf = min(DG_FRAMES, N - n0);
         __syncthreads();
@@ -389,29 +405,40 @@ __global__ void __launch_bounds__(256) k_dgather(int N, int Ry, int Rx, const Fr
             s_cls[q] = fclass[n0 + q];
         }
         __syncthreads();
-        if (!inside) continue;
-        for (int q0 = 0; q0 < nf; q0 += 8) {
-            float v[8];
+        for (int q0 = 0; q0 < nf; q0 += 4) {
+            float v[4][DG_CELLS];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < 4; ++e) {
                 const int q = q0 + e;
-                v[e] = 0.0f;
-                if (q < nf) {
-                    const int ty = cy - s_ky[q], tx = cx - s_kx[q];
-                    if ((unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
-                        v[e] = __ldg(dcls + (size_t)s_cls[q] * R + (size_t)ty * Rx + tx);
+                const bool fr = q < nf;
+                const int ky = fr ? s_ky[q] : 0, kx = fr ? s_kx[q] : 0;
+                const float *D = dcls + (size_t)(fr ? s_cls[q] : 0) * R;
+#pragma unroll
+                for (int k = 0; k < DG_CELLS; ++k) {
+                    const int ty = cy[k] - ky, tx = cx[k] - kx;
+                    v[e][k] = (fr && in[k] && (unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
+                                  ? __ldg(D + (size_t)ty * Rx + tx)
+                                  : 0.0f;
                 }
             }
 #pragma unroll
-            for (int e = 0; e < 8; ++e) part += v[e];
-            if (((n0 + q0) & 31) == 24) {       // every 32 frames
-                acc += part;
-                part = 0.0f;
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int k = 0; k < DG_CELLS; ++k) part[k] += v[e][k];
+            if (((n0 + q0) & 31) == 28) {       // every 32 frames
+#pragma unroll
+                for (int k = 0; k < DG_CELLS; ++k) {
+                    acc[k] += part[k];
+                    part[k] = 0.0f;
+                }
             }
         }
     }
-    acc += part;
-    if (inside && acc != 0.0) den[c] += acc;
+#pragma unroll
+    for (int k = 0; k < DG_CELLS; ++k) {
+        acc[k] += part[k];
+        if (in[k] && acc[k] != 0.0) den[cbase + 32 * k] += acc[k];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_normalise(size_t R, const double *__restrict__ num,
@@ -500,7 +527,7 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
         k_dzero<<<152 * 8, 256, 0, stream>>>(R, hdr, dcls);
         k_dscatter<<<dim3((unsigned)((P + 255) / 256), kMaxClasses), 256, 0, stream>>>(d.ny, d.nx, d.ref_ny, d.ref_nx,
                                                                                      W, mask, u, hdr, dcls);
-        k_dgather<<<(unsigned)((R + 255) / 256), 256, 0, stream>>>(
+        k_dgather<<<(unsigned)((R + 256 * DG_CELLS - 1) / (256 * DG_CELLS)), 256, 0, stream>>>(
             d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr, dcls, den);
         e = cudaGetLastError();
     }
