@@ -62,6 +62,21 @@ def make_workload(name, rank):
     return fn(seed=seed)
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over the ranks (x itself on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, world, ms_total, steps):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank_step * world * steps / (ms_total / 1e3)
+
+
 def evals_per_step(s):
     Sy, Sx = s.window
     return int(s.M.sum()) * (2 * Sy + 1) * (2 * Sx + 1) * s.frames.shape[0]
@@ -304,12 +319,9 @@ def pxst_arm(args, rank, world, local_rank):
     ktimes = px.timing_read()
     px.timing_enable(False)
     n_exact = px.last_exact_count(rec.ws)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / args.steps
-    value = ev_step * world / (ms / 1e3) * args.steps
+    value = job_rate(ev_step, world, ms, args.steps)
 
     # ---- end to end through the public API with pinned host buffers ------------------------
     # every step copies its inputs in and its map and error out (HostStream: the next step's
@@ -330,12 +342,10 @@ def pxst_arm(args, rank, world, local_rank):
     hs.synchronize()
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
+    ms_e2e = max_over_ranks(ms_e2e, dist, "cuda")
     if dist:
-        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
         dist.barrier()
-    e2e_value = ev_step * world / (ms_e2e / 1e3) * args.steps
+    e2e_value = job_rate(ev_step, world, ms_e2e, args.steps)
     if sampler:
         sampler.stop()
     if rank != 0:
