@@ -60,9 +60,12 @@ typedef struct {
 
 /* Arithmetic form of the candidate search. */
 #define PXST_FORM_FP32  0   /* direct sum of (I - W R)^2 in FP32 on CUDA cores */
-#define PXST_FORM_BF16  1   /* cross term on tensor cores, BF16 operands, FP32 accumulation;
-                               the best rescore_k candidates per pixel, the 3x3 about the
-                               minimum and the fit are then evaluated exactly as in FP32 */
+#define PXST_FORM_BF16  1   /* cross term on tensor cores, BF16 operands, FP32 accumulation
+                               (pixels with candidates not valid in every frame ranked again
+                               with each candidate's variance over its valid frames, a second
+                               contraction); the best rescore_k candidates per pixel, the 3x3
+                               about the minimum and the fit are then evaluated exactly as in
+                               FP32 */
 #define PXST_FORM_TF32  2   /* as PXST_FORM_BF16 with TF32 operands */
 
 typedef struct {
@@ -180,14 +183,15 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
  * pxst_timing_read() synchronises the recorded events and returns, for kernel k,
  * the number of launches and their summed duration in ms. Kernel ids: */
 #define PXST_K_PREPARE    0   /* per-frame shift table */
-#define PXST_K_SCATTER    1   /* make_object_map scatter (includes the accumulator clear) */
+#define PXST_K_SCATTER    1   /* make_object_map scatter (includes the accumulator clear and the
+                                 reference weights per fractional-shift class) */
 #define PXST_K_NORMALISE  2   /* make_object_map normalisation */
 #define PXST_K_SEARCH     3   /* update_pixel_map candidate search + refinement */
 #define PXST_K_EXACT      4   /* update_pixel_map exact path */
 #define PXST_K_REFTERMS   5   /* reference_terms */
 #define PXST_K_TPREP      6   /* tensor forms: centred frames, once per call */
 #define PXST_K_GTABLE     7   /* tensor forms: shifted reference per frame, T~ and n_valid */
-#define PXST_K_TSEARCH    8   /* tensor forms: tensor-core ranking of every candidate */
+#define PXST_K_TSEARCH    8   /* tensor forms: tensor-core ranking of every candidate (both passes) */
 #define PXST_K_RESCORE    9   /* tensor forms: exact FP32 evaluation of the best candidates */
 #define PXST_K_ERROR      10  /* calc_error (with the per-pixel variance) */
 #define PXST_K_TRANS      11  /* update_translations (with the per-pixel variance) */
