@@ -204,6 +204,62 @@ def pin_upm_window_by_indexing(L):
         np.testing.assert_allclose(e, want, rtol=1e-12)
 
 
+def _bruteforce_window(frames, W, Iref, w, delta, u, window, i, j):
+    """e over the window by a literal loop over "Update pixel mapping" with fractional
+    translations: R_n(c) is the masked, renormalised bilinear read at c - Delta_n ("Sub-pixel
+    interpolation": corners inside the grid with w > 0 and a nonzero weight count, their
+    weights renormalised), a frame with no such corner is left out of both sums."""
+    Sy, Sx = window
+    Ry, Rx = Iref.shape
+    ci = int(np.floor(u[0, i, j] + 0.5))
+    cj = int(np.floor(u[1, i, j] + 0.5))
+    Wv = float(W[i, j])
+    e = np.empty((2 * Sy + 1, 2 * Sx + 1))
+    for a in range(-Sy, Sy + 1):
+        for b in range(-Sx, Sx + 1):
+            err = var = 0.0
+            nv = 0
+            for n in range(frames.shape[0]):
+                p0, p1 = ci + a - float(delta[n, 0]), cj + b - float(delta[n, 1])
+                f0, f1 = int(np.floor(p0)), int(np.floor(p1))
+                t0, t1 = p0 - f0, p1 - f1
+                num = den = 0.0
+                for (di, dj, wt) in ((0, 0, (1 - t0) * (1 - t1)), (0, 1, (1 - t0) * t1),
+                                     (1, 0, t0 * (1 - t1)), (1, 1, t0 * t1)):
+                    qi, qj = f0 + di, f1 + dj
+                    if wt == 0.0 or not (0 <= qi < Ry and 0 <= qj < Rx) or w[qi, qj] <= 0:
+                        continue
+                    num += wt * float(Iref[qi, qj])
+                    den += wt
+                if den <= 0.0:
+                    continue
+                I = float(frames[n, i, j])
+                err += (I - Wv * num / den) ** 2
+                var += (I - Wv) ** 2
+                nv += 1
+            e[a + Sy, b + Sx] = np.inf if nv == 0 else (err / var if var > 0 else err)
+    return e, (ci, cj)
+
+
+def pin_upm_window_bruteforce_fractional(L):
+    """The window errors of a few pixels, fractional translations on both axes and an
+    uncovered patch (frames partly and wholly invalid), by a literal loop on tiny inputs."""
+    rng = np.random.default_rng(11)
+    frames, W, M, u, delta, R = _fractional_scan(rng)
+    Iref = rng.uniform(0.5, 1.5, size=R)
+    w = rng.uniform(0.5, 2.0, size=R)
+    w[20:23, 25:40] = 0.0
+    w[30, :] = 0.0
+    window = (2, 3)
+    for (i, j) in [(0, 0), (4, 5), (8, 10), (6, 2), (2, 9), (5, 7)]:
+        e, c = oracle.pixel_window(frames, W, M, Iref, w, delta, u, window, i * frames.shape[2] + j, L=L)
+        want, cw = _bruteforce_window(frames, W, Iref, w, delta, u, window, i, j)
+        assert c == cw, (c, cw)
+        assert np.array_equal(np.isinf(e), np.isinf(want))
+        fin = np.isfinite(want)
+        np.testing.assert_allclose(e[fin], want[fin], rtol=1e-12)
+
+
 def pin_upm_exact_search(L):
     """Noiseless frames rendered from the grid at integer positions: the error at the
     truth is 0 and the argmin lands on the truth, starting anywhere in the window."""
