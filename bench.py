@@ -1,12 +1,17 @@
-"""Benchmark of the PXST main loop on GB300: one step = one iteration (make_object_map +
-update_pixel_map) of the 1-D lens scan (121 frames of 512 x 1536, window +-1 x +-24),
-synthetic data from the seeded generator.
+"""Benchmark of the PXST main loop on GB300. The default workload is the 2-D precision scan
+(400 frames of 1024 x 1024 on a 20 x 20 grid of 4 px steps, reference 1200 x 1200, window
++-16 x +-16), synthetic data from the seeded generator. A step is one main-loop iteration
+(make_object_map, then update_pixel_map with the 3x3 fit) from the scan's initial map.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pxst|reference]
+                    [--workload NAME] [--form all|fp32|bf16|tf32]
 
-Prints one JSON line (rank 0). `value` is pixel-shift-frame evaluations per second over
-the whole job; `ms_per_step` the iteration time. Under torchrun each rank runs its own
-scan (seed + rank): weak scaling, no collective on the data path.
+Prints one JSON line (rank 0). With --form all (the default) the plain FP32 form and the
+tensor-core BF16 and TF32 forms are timed on the same device-resident scan; `value` and
+`ms_per_step` are the BF16 form's (pixel-shift-frame evaluations per second over the whole
+job; iteration time), and `forms` carries every form's time, rooflines, launches, end-to-end
+rate and its error against the FP64 oracle on stated row stripes. Under torchrun each rank
+runs its own scan (seed + rank): weak scaling, no collective on the data path.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -220,52 +225,159 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def pxst_arm(args, rank, world, local_rank):
+def stripe_rows(s, rows_per_stripe=4):
+    """The detector rows the accuracy comparison and the oracle's timed sample use: the first
+    rows holding good pixels (where candidates read uncovered reference pixels) and the
+    central rows."""
+    ny = s.frames.shape[1]
+    active = np.flatnonzero(s.M.any(axis=1))
+    top = int(active[0]) if active.size else 0
+    mid = max(top + rows_per_stripe, ny // 2 - rows_per_stripe // 2)
+    rows = sorted(set(range(top, min(ny, top + rows_per_stripe))) |
+                  set(range(mid, min(ny, mid + rows_per_stripe))))
+    return rows
+
+
+def oracle_leg(s, threads=None):
+    """The oracle on a bounded sample of one main-loop iteration: make_object_map of the whole
+    scan, then update_pixel_map (integer and with the 3x3 fit) of the pixels of a few row
+    stripes. Returns the oracle's results (for the per-form accuracy below) and its timing,
+    from which the whole iteration's CPU time is extrapolated by the good-pixel count."""
+    import oracle
+    threads = threads or oracle.default_threads()
+    rows = stripe_rows(s)
+    nx = s.frames.shape[2]
+    pix = np.array([r * nx + c for r in rows for c in range(nx) if s.M[r, c]], dtype=np.int64)
+    t0 = time.perf_counter()
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    t_omap = time.perf_counter() - t0
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    I64, w64 = I32.astype(np.float64), w32.astype(np.float64)
+    t0 = time.perf_counter()
+    uo_q, eo_q = oracle.update_pixels(s.frames, s.W, s.M, I64, w64, s.delta, s.u_init, s.window, pix,
+                                      quadratic=True, threads=threads)
+    t_upm = time.perf_counter() - t0
+    uo_i, eo_i = oracle.update_pixels(s.frames, s.W, s.M, I64, w64, s.delta, s.u_init, s.window, pix,
+                                      quadratic=False, threads=threads)
+    Sy, Sx = s.window
+    nwin = (2 * Sy + 1) * (2 * Sx + 1)
+    n_good = int(s.M.sum())
+    t_iter = t_omap + t_upm * n_good / max(pix.size, 1)
+    rate = n_good * nwin * s.frames.shape[0] / t_iter
+    return dict(Io=Io, wo=wo, I32=I32, w32=w32, pix=pix, rows=rows, uo_q=uo_q.T, eo_q=eo_q, uo_i=uo_i.T,
+                eo_i=eo_i, rate=rate, t_omap=t_omap, t_upm=t_upm, threads=threads,
+                sample=f"make_object_map of the whole scan ({t_omap:.1f} s) + update_pixel_map with the 3x3 fit of "
+                       f"{pix.size} good pixels in detector rows {rows[0]}-{rows[len(rows) // 2 - 1]} and "
+                       f"{rows[len(rows) // 2]}-{rows[-1]} ({t_upm:.1f} s), extrapolated to all {n_good} good pixels")
+
+
+def accuracy(s, orc, u_int, e_int, u_q):
+    """The GPU's update against the oracle's on the stripe pixels, both searching the oracle's
+    reference image (rounded to float32): integer argmin agreement, the pixels where they differ
+    and whether each is a near-tie (the oracle's own error at the GPU's pick within
+    1e-5 e_min + 1e-7 sum I^2 / var of its minimum), and the sub-pixel map difference where the
+    integer picks agree."""
+    import oracle
+    pix = orc["pix"]
+    nx = s.frames.shape[2]
+    ug_i = u_int.reshape(2, -1)[:, pix]
+    ug_q = u_q.reshape(2, -1)[:, pix]
+    eg_i = e_int.ravel()[pix]
+    same = np.all(ug_i == orc["uo_i"], axis=0)
+    bad = np.flatnonzero(~same)
+    Sy, Sx = s.window
+    I64, w64 = orc["I32"].astype(np.float64), orc["w32"].astype(np.float64)
+    ties = 0
+    for k in bad[:200]:
+        p = int(pix[k])
+        e, (ci, cj) = oracle.pixel_window(s.frames, s.W, s.M, I64, w64, s.delta, s.u_init, s.window, p)
+        a_ = int(round(ug_i[0, k])) - ci + Sy
+        b_ = int(round(ug_i[1, k])) - cj + Sx
+        if not (0 <= a_ <= 2 * Sy and 0 <= b_ <= 2 * Sx):
+            continue
+        I = s.frames[:, p // nx, p % nx].astype(np.float64)
+        Wv = float(s.W.ravel()[p])
+        scale = float(np.sum(I * I) / max(np.sum((I - Wv) ** 2), 1e-300))
+        emin = float(np.min(e))
+        ties += int(e[a_, b_] - emin <= 1e-5 * emin + 1e-7 * scale)
+    du = np.abs(ug_q - orc["uo_q"])[:, same]
+    fin = same & np.isfinite(orc["eo_i"])
+    rel = np.abs(eg_i[fin] - orc["eo_i"][fin]) / np.maximum(np.abs(orc["eo_i"][fin]), 1e-30)
+    return {"pixels": int(pix.size), "argmin_agree": float(same.mean()) if pix.size else 1.0,
+            "differing": int(bad.size), "differing_near_ties": ties,
+            "u_max_abs_err_px": float(du.max()) if du.size else 0.0,
+            "u_rms_err_px": float(np.sqrt(np.mean(du ** 2))) if du.size else 0.0,
+            "err_max_rel": float(rel.max()) if rel.size else 0.0}
+
+
+def kernel_roofline(name, avg_ms, s, ev_step, form, pk, basis, sms, sm_mhz):
+    """Algorithmic work of one launch of kernel group `name` over its average launch time,
+    against the peak that bounds it."""
+    N = s.frames.shape[0]
+    P = s.frames.shape[1] * s.frames.shape[2]
+    R = s.ref_shape[0] * s.ref_shape[1]
+    n_good = int(s.M.sum())
+    alu = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_basis = f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"
+    if name == "tensor_search":
+        work, unit, bound = 2.0 * ev_step / 1e12, "TFLOP/s", "tensor"        # cross term: one multiply-add per eval
+        peak = float(pk["bf16_tflops"]) * (0.5 if form == 2 else 1.0)
+        pb = f"{basis} dense bf16 cuBLAS burst" + (" x 0.5 (nominal tf32/bf16 ratio)" if form == 2 else "")
+    elif name in ("upm_search", "upm_exact"):
+        work, unit, bound, peak, pb = 4.0 * ev_step / 1e12, "TFLOP/s", "alu", alu, alu_basis   # 2 FMA per eval
+    elif name == "upm_rescore":
+        # at least the 3x3 about each pixel's first candidate: 2 FMA per pixel, frame and point
+        work, unit, bound, peak, pb = 4.0 * 9 * n_good * N / 1e12, "TFLOP/s", "alu", alu, alu_basis
+    elif name == "tensor_gtable":
+        # G~ and V written once per reference pixel and frame (2 x element size), the reference read
+        es = 4 if form == 2 else 2
+        work, unit, bound = (2.0 * es * R * N + 8.0 * R) / 1e9, "GB/s", "hbm"
+        peak, pb = float(pk["hbm_gbs"]), f"{basis} HBM copy bandwidth"
+    elif name == "tensor_prep":
+        es = 4 if form == 2 else 2
+        work, unit, bound = (4.0 * N * P + es * N * P + 5.0 * P) / 1e9, "GB/s", "hbm"
+        peak, pb = float(pk["hbm_gbs"]), f"{basis} HBM copy bandwidth"
+    else:
+        # make_object_map: frames once, the map, W and M per pixel, FP64 flush and the outputs
+        work, unit, bound = (4.0 * N * P + 21.0 * P + 32.0 * R) / 1e9, "GB/s", "hbm"
+        peak, pb = float(pk["hbm_gbs"]), f"{basis} HBM copy bandwidth"
+    achieved = work / (avg_ms * 1e-3)
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "kernel": name, "avg_launch_ms": avg_ms, "peak_basis": pb}
+
+
+def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
+    """Autotune, warm up and time one arithmetic form on the device-resident scan; then the
+    same steps end to end from pinned host buffers. A step is one main-loop iteration
+    (make_object_map, update_pixel_map) from the initial map u0."""
     import torch
     import paper_2003_12726_gb300 as px
-
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    s = make_workload(args.workload, rank)
-    ev_step = evals_per_step(s)
-    form = FORMS[args.form]
-    rec = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, form=form)
-    u0 = rec.u.clone()
+    form = FORMS[form_name]
+    rec = px.Reconstruction.from_device(base.frames, base.W, base.M, base.delta, u0, s.ref_shape, s.window,
+                                        form=form)
     stream = torch.cuda.current_stream()
     tuned = None
     if not args.no_autotune:
-        # the tile shape the autotuner picks on this scan (one iteration first, so that the
-        # search runs against a reference image); the map is restored afterwards
-        rec.run(1)
+        rec.run(1)                       # a reference image to search against; the map is restored
         tile, tms = px.autotune(rec, trials=3)
-        rec.u.copy_(u0)
         tuned = {"tile": tile, "update_ms": tms}
-    sampler = ClockSampler(local_rank) if rank == 0 else None
-    for _ in range(args.warmup):
-        rec.run(1)
-    torch.cuda.synchronize()
-    code, bits = px.get_status(rec.ws)
-    if code != 0:
-        raise RuntimeError(f"device status {code} bits {bits}")
 
-    # the paper's full iteration: + update translations (iii) and figures of merit (iv)
-    full = args.loop == "full"
+    # the paper's full iteration adds the map filter, the translation update (iii) and the
+    # figures of merit (iv); --frac replaces the 3x3 fit by fractional candidates
+    full, frac = args.loop == "full", args.frac
+    delta0 = rec.delta.clone()
     if full:
         tw = (0, 2) if s.window[0] <= 1 else (1, 1)
-        delta0 = rec.delta.clone()
         pe_t = torch.empty((rec.dims.ny, rec.dims.nx), dtype=torch.float32, device="cuda")
         fe_t = torch.empty(rec.dims.n_frames, dtype=torch.float64, device="cuda")
         tot_t = torch.empty(1, dtype=torch.float64, device="cuda")
         re_t = torch.empty(tuple(s.ref_shape), dtype=torch.float32, device="cuda")
 
-    frac = args.frac
-
     def step():
+        rec.u.copy_(u0)
+        if full:
+            rec.delta.copy_(delta0)
         if frac:
-            # the non-integer candidate option instead of the paraboloid
             px.make_object_map(rec.dims, rec.frames, rec.W, rec.M, rec.u, rec.delta, rec.I_ref, rec.w, rec.ws)
             px.update_pixel_map_fractional(rec.dims, rec.opts, frac, rec.frames, rec.W, rec.M, rec.I_ref, rec.w,
                                            rec.delta, rec.u, rec.ws, rec.err)
@@ -277,18 +389,19 @@ def pxst_arm(args, rank, world, local_rank):
                                    rec.ws, fe_t)
             px.calc_error(rec.dims, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta, rec.ws, pe_t,
                           fe_t, tot_t, re_t)
-    if full:
-        for _ in range(2):
-            step()
-        torch.cuda.synchronize()
-        rec.delta.copy_(delta0)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    code, bits = px.get_status(rec.ws)
+    if code != 0:
+        raise RuntimeError(f"{form_name}: device status {code} bits {bits}")
 
-    # ---- device-resident timed region -------------------------------------------------
-    rec.u.copy_(u0)
+    # ---- device-resident timed region -----------------------------------------------------
     px.timing_enable(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    n0 = px.launch_count()
     t_wall0 = time.time()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -299,33 +412,41 @@ def pxst_arm(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     t_wall1 = time.time()
-    if full:
-        rec.delta.copy_(delta0)
+    launches = px.launch_count() - n0
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    ktimes = px.timing_read()
+    px.timing_enable(False)
+    n_exact = px.last_exact_count(rec.ws)
+    code, bits = px.get_status(rec.ws)
+    if code != 0:
+        raise RuntimeError(f"{form_name}: device status {code} bits {bits} after the timed steps")
+
+    rec.delta.copy_(delta0)
     sweep = None
     if full:
         # initialisation: fit_defocus_registration over 5 x 5 map scales (timed once, warm)
         sc = [0.96, 0.98, 1.0, 1.02, 1.04]
-        Ib = torch.empty_like(rec.I_ref)
-        wb = torch.empty_like(rec.w)
+        Ib, wb = torch.empty_like(rec.I_ref), torch.empty_like(rec.w)
         px.defocus_sweep(rec.dims, rec.frames, rec.W, rec.M, u0, rec.delta, sc, sc, Ib, wb, rec.ws)
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
         cmap = px.defocus_sweep(rec.dims, rec.frames, rec.W, rec.M, u0, rec.delta, sc, sc, Ib, wb, rec.ws)
-        g1.record(stream)
+        d1.record(stream)
         torch.cuda.synchronize()
         best = divmod(int(torch.argmax(cmap).item()), len(sc))
-        sweep = {"pairs": len(sc) ** 2, "ms": g0.elapsed_time(g1), "best_scales": [sc[best[0]], sc[best[1]]]}
-    ms = e0.elapsed_time(e1)
-    ktimes = px.timing_read()
-    px.timing_enable(False)
-    n_exact = px.last_exact_count(rec.ws)
-    ms = max_over_ranks(ms, dist, "cuda")
-    ms_step = ms / args.steps
-    value = job_rate(ev_step, world, ms, args.steps)
+        sweep = {"pairs": len(sc) ** 2, "ms": d0.elapsed_time(d1), "best_scales": [sc[best[0]], sc[best[1]]]}
+
+    # ---- the configuration's 10 iterations in one pxst_iterate call ------------------------
+    rec.u.copy_(u0)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    rec.run(s.n_iter)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_iter10 = g0.elapsed_time(g1) / s.n_iter
 
     # ---- end to end through the public API with pinned host buffers ------------------------
-    # every step copies its inputs in and its map and error out (HostStream: the next step's
-    # copy overlaps this step's compute, on two device input buffers)
     pinned = rec.pin_host_buffers(s.frames, s.W, s.M, s.delta, s.u_init)
     hs = px.HostStream(rec, pinned)
     h2d, d2h = hs.run(2)
@@ -333,7 +454,6 @@ def pxst_arm(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(hs.copy)
     hs.compute.wait_stream(hs.copy)
@@ -341,11 +461,66 @@ def pxst_arm(args, rank, world, local_rank):
     f1.record(hs.compute)
     hs.synchronize()
     torch.cuda.synchronize()
-    ms_e2e = f0.elapsed_time(f1)
-    ms_e2e = max_over_ranks(ms_e2e, dist, "cuda")
-    if dist:
-        dist.barrier()
-    e2e_value = job_rate(ev_step, world, ms_e2e, args.steps)
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, "cuda")
+    hs = None
+
+    # ---- accuracy on the oracle's stripes: both sides search the oracle's reference --------
+    acc = None
+    if orc is not None:
+        Id = torch.as_tensor(orc["I32"]).cuda()
+        wd = torch.as_tensor(orc["w32"]).cuda()
+        out = {}
+        for q in (False, True):
+            o = px.Options(s.window[0], s.window[1], q, form, tile=rec.opts.tile)
+            ud = u0.clone()
+            err = torch.empty((rec.dims.ny, rec.dims.nx), dtype=torch.float32, device="cuda")
+            px.update_pixel_map(rec.dims, o, rec.frames, rec.W, rec.M, Id, wd, rec.delta, ud, err, rec.ws)
+            code, bits = px.get_status(rec.ws)
+            if code != 0:
+                raise RuntimeError(f"{form_name}: device status {code} bits {bits} in the accuracy run")
+            out[q] = (ud.cpu().numpy(), err.cpu().numpy().astype(np.float64))
+        acc = accuracy(s, orc, out[False][0], out[False][1], out[True][0])
+    res = {"ms_per_step": ms / args.steps, "ms_per_iteration_10": ms_iter10, "tuned": tuned,
+           "ktimes": ktimes, "launches": launches, "exact_pixels": n_exact, "e2e_ms": ms_e2e / args.steps,
+           "h2d": h2d, "d2h": d2h, "t_wall": (t_wall0, t_wall1), "accuracy": acc, "sweep": sweep}
+    del rec
+    torch.cuda.empty_cache()
+    return res
+
+
+def pxst_arm(args, rank, world, local_rank):
+    import torch
+    import paper_2003_12726_gb300 as px
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    s = make_workload(args.workload, rank)
+    ev_step = evals_per_step(s)
+    forms = ["fp32", "bf16", "tf32"] if args.form == "all" else [args.form]
+    headline = "bf16" if "bf16" in forms else forms[0]
+    # the scan's inputs stay resident; every form runs on the same device arrays
+    base = px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window)
+    u0 = base.u.clone()
+    orc = None
+    if world == 1 and not args.no_cpu_baseline:
+        orc = oracle_leg(s)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    iref_err = None
+    if orc is not None:
+        # the reference image of the first iteration (the same kernels serve every form)
+        Ig = torch.empty(tuple(s.ref_shape), dtype=torch.float32, device="cuda")
+        wg = torch.empty_like(Ig)
+        px.make_object_map(base.dims, base.frames, base.W, base.M, u0, base.delta, Ig, wg, base.ws)
+        Ig, wg = Ig.cpu().numpy().astype(np.float64), wg.cpu().numpy().astype(np.float64)
+        sel = orc["wo"] > 1e-4 * orc["wo"].max()
+        rl2 = lambda a, b: float(np.sqrt(np.sum((a - b) ** 2) / max(np.sum(b ** 2), 1e-300)))
+        iref_err = {"iref_rel_l2": rl2(Ig[sel], orc["Io"][sel]), "w_rel_l2": rl2(wg, orc["wo"]),
+                    "coverage_mismatch": int(np.count_nonzero((wg > 0) != (orc["wo"] > 0))),
+                    "over": "reference pixels with oracle weight > 1e-4 max (I_ref); all (w)"}
+    results = {f: time_form(args, s, base, u0, f, dist, world, orc, sampler) for f in forms}
     if sampler:
         sampler.stop()
     if rank != 0:
@@ -353,91 +528,55 @@ def pxst_arm(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel ------------------------------------------------
     pk, basis = peaks()
-    name = max(ktimes, key=lambda k: ktimes[k][1])
-    launches, tot = ktimes[name]
-    avg_ms = tot / max(launches, 1)
-    props = torch.cuda.get_device_properties(local_rank)
-    sms = props.multi_processor_count
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    if name == "tensor_search":
-        flop = 2.0 * ev_step                                  # cross term: one multiply-add per evaluation
-        achieved = flop / (avg_ms * 1e-3) / 1e12
-        peak = float(pk["bf16_tflops"]) * (0.5 if form == 2 else 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
-                "peak_basis": f"{basis} dense bf16 cuBLAS burst" + (" x 0.5 (nominal tf32/bf16 ratio)" if form == 2 else "")}
-    elif name in ("upm_search", "upm_exact"):
-        flop = 4.0 * ev_step                                  # 2 FP32 FMA per evaluation
-        achieved = flop / (avg_ms * 1e-3) / 1e12
-        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12            # FP32 lanes x FMA x clock
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
-    elif name == "upm_rescore":
-        # the exact stage of the tensor forms: at least the 3x3 about each pixel's first
-        # candidate, 2 FP32 FMA per pixel, frame and point
-        flop = 4.0 * 9 * int(s.M.sum()) * s.frames.shape[0]
-        achieved = flop / (avg_ms * 1e-3) / 1e12
-        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
-    elif name == "update_translations":
-        # per pixel, frame and shift: the masked bilinear read (8 flop), d = I - W R (2),
-        # d^2 / var (2): 12 flop; plus the per-pixel variance pass (one read per frame)
-        ntr = (2 * tw[0] + 1) * (2 * tw[1] + 1)
-        flop = 12.0 * int(s.M.sum()) * s.frames.shape[0] * ntr
-        achieved = flop / (avg_ms * 1e-3) / 1e12
-        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": name, "avg_launch_ms": avg_ms,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"}
-    else:
-        P = s.frames.shape[1] * s.frames.shape[2]
-        R = s.ref_shape[0] * s.ref_shape[1]
-        nbytes = 4.0 * s.frames.shape[0] * P + 21.0 * P + 32.0 * R
-        if name == "calc_error":              # frames read twice (variance, then the error terms)
-            nbytes = 8.0 * s.frames.shape[0] * P + 21.0 * P + 4.0 * P + 8.0 * s.frames.shape[0] + 20.0 * R
-        achieved = nbytes / (avg_ms * 1e-3) / 1e9
-        peak = float(pk["hbm_gbs"])
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "kernel": name, "avg_launch_ms": avg_ms, "peak_basis": f"{basis} HBM copy bandwidth"}
-    roof["traffic"] = load_traffic(args.workload + ("" if form == 0 else "-" + args.form), name)
-
-    clocks = sampler.summary(t_wall0 - 0.2, t_wall1 + 0.2) if sampler else None
-    if clocks and clocks.get("samples", 0) == 0:
-        clocks = sampler.summary()
+    per_form = {}
+    for f, r in results.items():
+        kt = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in r["ktimes"].items() if v[0]}
+        roofs = {k: kernel_roofline(k, kt[k], s, ev_step, FORMS[f], pk, basis, sms, sm_mhz)
+                 for k in kt if k not in ("prepare", "omap_normalise")}
+        dom = max(kt, key=lambda k: kt[k] * r["ktimes"][k][0])
+        roofs[dom]["traffic"] = load_traffic(args.workload + ("" if f == "fp32" else "-" + f), dom)
+        clocks = sampler.summary(r["t_wall"][0] - 0.2, r["t_wall"][1] + 0.2) if sampler else None
+        per_form[f] = {"ms_per_step": r["ms_per_step"], "value": job_rate(ev_step, world, r["ms_per_step"], 1),
+                       "ms_per_iteration_of_10": r["ms_per_iteration_10"],
+                       "e2e": {"value": job_rate(ev_step, world, r["e2e_ms"], 1), "ms_per_step": r["e2e_ms"]},
+                       "dominant_kernel": dom, "roofline": roofs[dom], "kernel_rooflines": roofs,
+                       "kernel_ms": kt, "gpu_launches": r["launches"], "autotuned": r["tuned"],
+                       "exact_path_pixels": r["exact_pixels"], "accuracy_vs_oracle": r["accuracy"],
+                       "clocks": clocks}
+        if r["sweep"]:
+            per_form[f]["defocus_sweep"] = r["sweep"]
+    h = per_form[headline]
+    rh = results[headline]
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        rate, rows, sec, threads = cpu_sample(s, target_s=args.cpu_s)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{rows} detector rows of {s.frames.shape[1]}: make_object_map of the stripe + "
-                         f"update_pixel_map of the stripe, {sec:.1f} s"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form], "data": "synthetic",
-            "config": {"workload": s.name, "frames": int(s.frames.shape[0]),
-                       "detector": list(s.frames.shape[1:]), "window": list(s.window),
-                       "reference": list(s.ref_shape), "form": args.form, "quadratic": True,
-                       "evals_per_step": ev_step, "parallelism": f"replicas{world}", "autotuned": tuned,
-                       "subpixel": f"fractional candidates, 1/{frac} grid" if frac else "3x3 paraboloid",
-                       "loop": "full: reference image, pixel map, map filter (sigma 1), translations (window "
-                               f"{list(tw)}), figures of merit" if full else "reference image, pixel map",
+    if orc is not None:
+        cpu = {"value": orc["rate"], "unit": UNIT, "cores": orc["threads"], "kind": "oracle", "sample": orc["sample"]}
+    clocks = sampler.summary(min(r["t_wall"][0] for r in results.values()) - 0.2,
+                             max(r["t_wall"][1] for r in results.values()) + 0.2) if sampler else None
+    dt = {"fp32": "f32", "bf16": "bf16/f32", "tf32": "tf32/f32"}
+    line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dt[headline], "data": "synthetic",
+            "config": {"workload": s.name, "frames": int(s.frames.shape[0]), "detector": list(s.frames.shape[1:]),
+                       "window": list(s.window), "reference": list(s.ref_shape), "form": headline,
+                       "forms_timed": forms, "quadratic": True, "evals_per_step": ev_step,
+                       "parallelism": f"replicas{world}",
+                       "step": "one main-loop iteration (make_object_map, update_pixel_map with the 3x3 fit) from "
+                               "the scan's initial map, restored on the device before each step",
+                       "subpixel": f"fractional candidates, 1/{args.frac} grid" if args.frac else "3x3 paraboloid",
+                       "loop": "full: reference image, pixel map, map filter (sigma 1), translations, figures of "
+                               "merit" if args.loop == "full" else "reference image, pixel map",
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
-            "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": ms_e2e / args.steps,
-                    "api": "HostStream: pinned host inputs in, map and error out, every step; the next "
-                           "step's copy overlaps this step's compute. Each step is one iteration from the "
-                           "host's initial map, while the device loop iterates from the previous step's "
-                           "map (whose sub-pixel fractions make the scatter slower)"},
-            "gpu_launches": int(sum(v[0] for v in ktimes.values())),
-            "kernel_ms": {k: (v[1] / v[0] if v[0] else 0.0) for k, v in ktimes.items()},
-            "exact_path_pixels": n_exact, "clocks": clocks}
-    if sweep:
-        line["defocus_sweep"] = sweep
+            "roofline": h["roofline"], "cpu_baseline": cpu,
+            "e2e": {"value": h["e2e"]["value"], "unit": UNIT, "h2d_bytes_per_step": rh["h2d"],
+                    "d2h_bytes_per_step": rh["d2h"], "ms_per_step": h["e2e"]["ms_per_step"],
+                    "api": "HostStream: every step copies the frames, whitefield, mask, translations and initial "
+                           "map from pinned host memory, runs pxst_iterate for one iteration and copies the map and "
+                           "error back; the next step's copy overlaps this step's compute"},
+            "gpu_launches": h["gpu_launches"], "kernel_ms": h["kernel_ms"], "exact_path_pixels": h["exact_path_pixels"],
+            "forms": per_form, "iref_error_vs_oracle": iref_err, "clocks": clocks}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -561,15 +700,16 @@ def serve_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="pxst", choices=["pxst", "reference"])
-    ap.add_argument("--workload", default="lens1d", choices=sorted(WORKLOADS),
-                    help="lens1d (the benchmark workload) or a smaller/larger scan for profiling")
-    ap.add_argument("--form", default="fp32", choices=sorted(FORMS),
-                    help="arithmetic of the candidate search: fp32 (CUDA cores) or the tensor-core bf16/tf32")
+    ap.add_argument("--workload", default="precision2d", choices=sorted(WORKLOADS),
+                    help="precision2d (the benchmark workload: the largest single-GPU scan) or another scan")
+    ap.add_argument("--form", default="all", choices=["all"] + sorted(FORMS),
+                    help="arithmetic of the candidate search: all three, fp32 (CUDA cores) or the tensor-core "
+                         "bf16/tf32")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--ref-step-s", type=float, default=6.0, help="oracle seconds per reference step")
+    ap.add_argument("--ref-step-s", type=float, default=4.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic tile shape")
@@ -581,6 +721,8 @@ def main():
     ap.add_argument("--mem-gb", type=float, default=96.0, help="serve: device memory budget")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.form == "all" and args.workload in ("batch64", "serve"):
+        args.form = "bf16"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -113,8 +113,11 @@ pxst_status pxst_make_object_map(const pxst_dims *dims, const float *frames, con
  * library holds until the process exits. The paper has no counterpart to this entry point.
  *   Limits: n_frames <= 8192 and ref_ny * ref_nx <= 1048576; larger sizes return
  *   PXST_ERR_NOMEM (with a message on stderr) before anything is launched.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
+ *   The first call on a device (and the first after the device's context was reset or
+ *   re-created) looks up the array's device address (cudaGetSymbolAddress) with that device
+ *   current; with lazy module loading (the CUDA default) that first call is also the one
+ *   that loads the library's device code and reserves the array, so make it as a warm-up
+ *   before the rest of the GPU's memory is taken and before any stream capture.
  *   All calls share the one array and it keeps the last call's contents (each call clears
  *   what it accumulates into): calls that may overlap on the GPU, on any stream, race.
  *   Device-side status bits of this call are not reported (there is no workspace to read).
@@ -320,6 +323,11 @@ void pxst_batch_destroy(pxst_batch batch);
  * process. Synchronises `stream`; PXST_ERR_ARG on a capturing stream. */
 pxst_status pxst_autotune(const pxst_scan *scan, int32_t trials, void *stream, int32_t *best_tile,
                           float *best_ms);
+
+/* Running total of the kernel launches this library has issued in this process (every
+ * entry point; launches captured into a graph are counted once, at capture). A caller
+ * reads it before and after a region to count the kernels that region launched. */
+pxst_status pxst_launch_count(int64_t *count_out);
 
 /* Human-readable text for a status code. */
 const char *pxst_status_string(pxst_status s);

@@ -95,6 +95,8 @@ def lib():
         L.pxst_status_string.argtypes = [i32]
         L.pxst_status_string.restype = C.c_char_p
         L.pxst_version.restype = C.c_char_p
+        L.pxst_launch_count.argtypes = [C.POINTER(i64)]
+        L.pxst_launch_count.restype = i32
         L.pxst_tensor_check.argtypes = [i32, i32, P, P, P, P, P]
         L.pxst_tensor_check.restype = i32
         S = C.POINTER(_Scan)
@@ -128,7 +130,7 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
             "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations",
-            "pxst_filter_map", "pxst_update_pixel_map_fractional", "pxst_defocus_sweep"]
+            "pxst_filter_map", "pxst_update_pixel_map_fractional", "pxst_defocus_sweep", "pxst_launch_count"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -301,6 +303,13 @@ def timing_read():
 
 def version():
     return lib().pxst_version().decode()
+
+
+def launch_count():
+    """Kernel launches this library has issued in the process so far (pxst_launch_count)."""
+    n = C.c_int64()
+    _raise(lib().pxst_launch_count(C.byref(n)), "launch_count")
+    return int(n.value)
 
 
 # ---------------------------------------------------------------------------------------

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" boundary of libpxst.so: argument checks, workspace carving,
 // launch sequencing, device status, and per-kernel event timing.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -258,7 +259,24 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
     return PXST_OK;
 }
 
+// ---- device properties and the launch counter -------------------------------------------
+constexpr int kMaxDev = 64;
+std::atomic<int> g_sms[kMaxDev];
+std::atomic<long long> g_launches{0};
+
 }  // namespace
+
+int pxst::device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 148;
+    int n = g_sms[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 148;
+    g_sms[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
+void pxst::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void pxst::prime_shift_span(const pxst_dims &d, const double *delta, cudaStream_t s) {
     int sy, sx;
@@ -546,6 +564,12 @@ const char *pxst_status_string(pxst_status s) {
         case PXST_ERR_TIMEOUT: return "device-side wait timed out";
         default: return "unknown status";
     }
+}
+
+pxst_status pxst_launch_count(int64_t *count_out) {
+    if (!count_out) return PXST_ERR_ARG;
+    *count_out = g_launches.load(std::memory_order_relaxed);
+    return PXST_OK;
 }
 
 const char *pxst_version(void) { return "pxst 0.1 (sm_103a)"; }

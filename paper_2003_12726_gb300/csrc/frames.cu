@@ -510,21 +510,21 @@ __global__ void k_contrast_final(int npairs, const double *__restrict__ acc, dou
 cudaError_t launch_scale_map(const pxst_dims &d, double sy, double sx, const double *u, double *us, cudaStream_t s) {
     const size_t P = (size_t)d.ny * d.nx;
     size_t blocks = (P + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_scale_map<<<(unsigned)blocks, 256, 0, s>>>(d.ny, d.nx, sy, sx, u, us);
+    if (blocks > (size_t)device_sms() * 8) blocks = (size_t)device_sms() * 8;
+    k_scale_map<<<(unsigned)blocks, 256, 0, s>>>(d.ny, d.nx, sy, sx, u, us); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_contrast_sums(const pxst_dims &d, const float *I_ref, const float *w, double *acc, cudaStream_t s) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
     size_t blocks = (R + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
-    k_contrast_sums<<<(unsigned)blocks, 256, 0, s>>>(R, I_ref, w, acc);
+    if (blocks > (size_t)device_sms() * 4) blocks = (size_t)device_sms() * 4;
+    k_contrast_sums<<<(unsigned)blocks, 256, 0, s>>>(R, I_ref, w, acc); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_contrast_final(int npairs, const double *acc, double *contrast, cudaStream_t s) {
-    k_contrast_final<<<(npairs + 127) / 128, 128, 0, s>>>(npairs, acc, contrast);
+    k_contrast_final<<<(npairs + 127) / 128, 128, 0, s>>>(npairs, acc, contrast); note_launch();
     return cudaGetLastError();
 }
 
@@ -536,7 +536,7 @@ cudaError_t launch_frac_refine(const pxst_dims &d, int sub, const float *frames,
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts; a.u = u;
     a.err_out = err_out;
     const size_t P = (size_t)d.ny * d.nx;
-    k_frac_refine<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(a);
+    k_frac_refine<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(a); note_launch();
     return cudaGetLastError();
 }
 
@@ -550,7 +550,7 @@ cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *m
     f.mask = mask; f.u = u; f.num = num; f.den = den;
     const size_t P = (size_t)d.ny * d.nx;
     size_t blocks = (P + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > (size_t)device_sms() * 8) blocks = (size_t)device_sms() * 8;
     const size_t smem = sizeof(double) * (f.r + 1);      // r <= 4096 (sigma <= 1024)
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) {
@@ -560,9 +560,9 @@ cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *m
                 cudaSuccess)
             return e;
     }
-    k_filter_rows<<<(unsigned)blocks, 256, smem, s>>>(f);
+    k_filter_rows<<<(unsigned)blocks, 256, smem, s>>>(f); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_filter_cols<<<(unsigned)blocks, 256, smem, s>>>(f);
+    k_filter_cols<<<(unsigned)blocks, 256, smem, s>>>(f); note_launch();
     return cudaGetLastError();
 }
 
@@ -570,7 +570,7 @@ cudaError_t launch_pixvar(const pxst_dims &d, const float *frames, const float *
                           const float *I_ref, const float *w, const double *u, const double *delta,
                           const FrameShift *shifts, float *var, WsHeader *hdr, cudaStream_t s) {
     const size_t P = (size_t)d.ny * d.nx;
-    k_pixvar<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, var, hdr));
+    k_pixvar<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, var, hdr)); note_launch();
     return cudaGetLastError();
 }
 
@@ -590,18 +590,18 @@ cudaError_t launch_calc_error(const pxst_dims &d, const float *frames, const flo
     float *numf = reinterpret_cast<float *>(num), *denf = reinterpret_cast<float *>(den);   // R floats each
     ErrorOut o{pixel_err, frame_err, total, ref_err ? numf : nullptr, ref_err ? denf : nullptr};
     size_t blocks = (P + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > (size_t)device_sms() * 4) blocks = (size_t)device_sms() * 4;
     const size_t smem = (frame_err && d.n_frames <= kErrFramesSmem) ? sizeof(double) * d.n_frames : 0;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_calc_error, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     k_calc_error<<<(unsigned)blocks, 256, smem, s>>>(
-        merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, const_cast<float *>(var), hdr), o);
+        merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, const_cast<float *>(var), hdr), o); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ref_err) {
         blocks = (R + 255) / 256;
-        if (blocks > 152 * 16) blocks = 152 * 16;
-        k_err_normalise<<<(unsigned)blocks, 256, 0, s>>>((int)R, numf, denf, ref_err);
+        if (blocks > (size_t)device_sms() * 16) blocks = (size_t)device_sms() * 16;
+        k_err_normalise<<<(unsigned)blocks, 256, 0, s>>>((int)R, numf, denf, ref_err); note_launch();
         e = cudaGetLastError();
     }
     return e;
@@ -625,9 +625,9 @@ cudaError_t launch_update_translations(const pxst_dims &d, int Ty, int Tx, int q
     size_t g = (P + 255) / 256;
     if (g > 32) g = 32;                 // blocks per frame
     dim3 grid((unsigned)g, (unsigned)d.n_frames);
-    k_trans_acc<<<grid, 256, 0, s>>>(t);
+    k_trans_acc<<<grid, 256, 0, s>>>(t); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_trans_fit<<<(d.n_frames + 127) / 128, 128, 0, s>>>(t);
+    k_trans_fit<<<(d.n_frames + 127) / 128, 128, 0, s>>>(t); note_launch();
     return cudaGetLastError();
 }
 

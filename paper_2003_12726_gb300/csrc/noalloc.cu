@@ -10,7 +10,12 @@
 // The array is a file-scope __device__ variable: every GPU on which the library's module
 // is loaded holds it (about 16.1 MiB) until the process exits. Host code must not pass
 // the variable's name to a kernel (on the host it only stands in for the symbol); the
-// device address is looked up once per device with cudaGetSymbolAddress and cached.
+// device address is looked up with cudaGetSymbolAddress once per device and context and
+// cached. With lazy module loading (the CUDA default) the first call on a device is also
+// the one that loads this module and so reserves the array: make it before the GPU's
+// memory is otherwise taken, and before any stream capture.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -32,20 +37,53 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the context the address was looked up in, and the address. A device reset or
+// a new primary context reloads the module, and the array may then sit elsewhere, so an
+// address is reused only while the current context is the one it was looked up in.
+unsigned long long g_ctx_id[kMaxDevices] = {};
 void *g_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up on first use).
+typedef CUresult (*PFN_ctxGetCurrent)(CUcontext *);
+typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long *);
+PFN_ctxGetCurrent g_get_current = nullptr;
+PFN_ctxGetId g_get_id = nullptr;
+
+// Identifier of the current context (unique for the life of the process), or 0 if the driver
+// cannot report one: then the address is looked up again on every call.
+unsigned long long current_context_id() {
+    if (!g_get_current || !g_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f1, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !f1 ||
+            cudaGetDriverEntryPoint("cuCtxGetId", &f2, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f2)
+            return 0;
+        g_get_current = reinterpret_cast<PFN_ctxGetCurrent>(f1);
+        g_get_id = reinterpret_cast<PFN_ctxGetId>(f2);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up (with the device
+// current) the first time it is needed in each context.
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = p;
+        // the lookup has made the device's context current if none was: record that one
+        g_ctx_id[dev] = current_context_id();
     }
     *out = g_addr[dev];
     return cudaSuccess;

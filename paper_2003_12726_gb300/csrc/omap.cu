@@ -481,14 +481,15 @@ __global__ void __launch_bounds__(256) k_refterms(int N, int Ry, int Rx,
 
 int grid_for(size_t n, int threads) {
     size_t b = (n + threads - 1) / threads;
-    return (int)(b > 152 * 16 ? 152 * 16 : (b == 0 ? 1 : b));
+    const size_t cap = (size_t)device_sms() * 16;
+    return (int)(b > cap ? cap : (b == 0 ? 1 : b));
 }
 
 }  // namespace
 
 cudaError_t launch_prepare(const pxst_dims &d, const double *delta, WsHeader *hdr,
                            FrameShift *shifts, int *fclass, int reset_exact, cudaStream_t stream) {
-    k_prepare<<<1, 1024, 0, stream>>>(d.n_frames, delta, hdr, shifts, fclass, reset_exact);
+    k_prepare<<<1, 1024, 0, stream>>>(d.n_frames, delta, hdr, shifts, fclass, reset_exact); note_launch();
     return cudaGetLastError();
 }
 
@@ -511,8 +512,9 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
     const int gx = (d.nx + SC_TX - 1) / SC_TX;
     const int gy = (d.ny + SC_TY - 1) / SC_TY;
     const long long tiles = (long long)gx * gy;
-    // split the frames only when there are too few tiles to fill 152 SMs twice
-    long long nch = (304 + tiles - 1) / tiles;
+    // split the frames only when there are too few tiles to fill every SM twice
+    const long long fill = 2LL * device_sms();
+    long long nch = (fill + tiles - 1) / tiles;
     nch = nch < 1 ? 1 : nch;
     const long long maxch = (d.n_frames + 7) / 8;
     if (nch > maxch) nch = maxch;
@@ -520,15 +522,15 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
     a.chunk = (int)((d.n_frames + nch - 1) / nch);
     nch = (d.n_frames + a.chunk - 1) / a.chunk;
     dim3 grid(gx, gy, (unsigned)nch);
-    k_scatter<<<grid, SC_THREADS, smem, stream>>>(a);
+    k_scatter<<<grid, SC_THREADS, smem, stream>>>(a); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.dcls) {
         const size_t P = (size_t)d.ny * d.nx;
-        k_dzero<<<152 * 8, 256, 0, stream>>>(R, hdr, dcls);
+        k_dzero<<<device_sms() * 8, 256, 0, stream>>>(R, hdr, dcls); note_launch();
         k_dscatter<<<dim3((unsigned)((P + 255) / 256), kMaxClasses), 256, 0, stream>>>(d.ny, d.nx, d.ref_ny, d.ref_nx,
-                                                                                     W, mask, u, hdr, dcls);
+                                                                                     W, mask, u, hdr, dcls); note_launch();
         k_dgather<<<(unsigned)((R + 256 * DG_CELLS - 1) / (256 * DG_CELLS)), 256, 0, stream>>>(
-            d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr, dcls, den);
+            d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr, dcls, den); note_launch();
         e = cudaGetLastError();
     }
     return e;
@@ -537,7 +539,7 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
 cudaError_t launch_normalise(const pxst_dims &d, const double *num, const double *den,
                              float *I_ref, float *w, cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
-    k_normalise<<<grid_for(R, 256), 256, 0, stream>>>(R, num, den, I_ref, w);
+    k_normalise<<<grid_for(R, 256), 256, 0, stream>>>(R, num, den, I_ref, w); note_launch();
     return cudaGetLastError();
 }
 
@@ -546,7 +548,7 @@ cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float 
                             cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
     k_refterms<<<grid_for(R, 256), 256, 0, stream>>>(d.n_frames, d.ref_ny, d.ref_nx, I_ref, w,
-                                                     shifts, T, n_valid);
+                                                     shifts, T, n_valid); note_launch();
     return cudaGetLastError();
 }
 

@@ -116,6 +116,12 @@ constexpr double kMaxCoord = 1.0e8;
 // Launch-time configuration of the search kernel.
 constexpr int kSearchSmemBudget = 200 * 1024;   // dynamic shared memory per CTA (bytes)
 
+// Streaming multiprocessors of the current device (queried once per device and cached):
+// grids that stride over their work are sized in multiples of it.
+int device_sms();
+// Count kernel launches made by this library (pxst_launch_count reports the running total).
+void note_launch(int n = 1);
+
 // Launch helpers implemented in the .cu files (all asynchronous on `stream`).
 // fclass: the class of each frame (NULL: no classes; the scatter then forms the weights)
 cudaError_t launch_prepare(const pxst_dims &d, const double *delta, WsHeader *hdr,

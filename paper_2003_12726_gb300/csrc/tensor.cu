@@ -761,6 +761,7 @@ cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *fr
     else
         k_tprep<__nv_bfloat16><<<grid, 256, 0, stream>>>(d.n_frames, d.ny, d.nx, frames, W, mask,
                                                          static_cast<__nv_bfloat16 *>(At));
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -768,7 +769,7 @@ cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I
                           const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
                           cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
-    k_rmask<<<(unsigned)std::min<size_t>((R + 255) / 256, 152 * 16), 256, 0, stream>>>(R, I_ref, w, Rm);
+    k_rmask<<<(unsigned)std::min<size_t>((R + 255) / 256, (size_t)device_sms() * 16), 256, 0, stream>>>(R, I_ref, w, Rm); note_launch();
     const unsigned blocks = (unsigned)((R + 31) / 32);
     if (form == PXST_FORM_TF32)
         k_gtable<float><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts,
@@ -777,6 +778,7 @@ cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I
         k_gtable<__nv_bfloat16><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts,
                                                              static_cast<__nv_bfloat16 *>(G),
                                                              static_cast<__nv_bfloat16 *>(V), Tt, nvalid);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -833,7 +835,7 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
         }
         r = cudaFuncSetAttribute(plain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (r != cudaSuccess) return r;
-        plain<<<dim3(gx, gy), TS_THREADS, smem, stream>>>(tA, tB, tA2, tV, a);
+        plain<<<dim3(gx, gy), TS_THREADS, smem, stream>>>(tA, tB, tA2, tV, a); note_launch();
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
         if (tf32)
             k_tsquare<float><<<gx * gy, 256, 0, stream>>>((int)nkb, d.ny, d.nx, (int)pty, (int)gx, hdr, tile_list,
@@ -842,11 +844,12 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
             k_tsquare<__nv_bfloat16><<<gx * gy, 256, 0, stream>>>(
                 (int)nkb, d.ny, d.nx, (int)pty, (int)gx, hdr, tile_list, static_cast<const __nv_bfloat16 *>(At),
                 static_cast<__nv_bfloat16 *>(A2));
+        note_launch();
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
         a.ares = 0;
         r = cudaFuncSetAttribute(masked, cudaFuncAttributeMaxDynamicSharedMemorySize, TSM_SMEM);
         if (r != cudaSuccess) return r;
-        masked<<<gx * gy, TS_THREADS, TSM_SMEM, stream>>>(tA, tB, tA2, tV, a);
+        masked<<<gx * gy, TS_THREADS, TSM_SMEM, stream>>>(tA, tB, tA2, tV, a); note_launch();
         return cudaGetLastError();
     };
     auto by_shape = [&](auto tf32_tag, auto tk_tag) {
@@ -893,10 +896,16 @@ extern "C" pxst_status pxst_tensor_check(int32_t form, int32_t K, const void *A,
     cudaError_t e;
     if (tf32) {
         e = cudaFuncSetAttribute(k_tc_check<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) k_tc_check<true><<<1, 128, smem, s>>>(ta, tb, K, D, status);
+        if (e == cudaSuccess) {
+            k_tc_check<true><<<1, 128, smem, s>>>(ta, tb, K, D, status);
+            note_launch();
+        }
     } else {
         e = cudaFuncSetAttribute(k_tc_check<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess) k_tc_check<false><<<1, 128, smem, s>>>(ta, tb, K, D, status);
+        if (e == cudaSuccess) {
+            k_tc_check<false><<<1, 128, smem, s>>>(ta, tb, K, D, status);
+            note_launch();
+        }
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? PXST_OK : PXST_ERR_CUDA;

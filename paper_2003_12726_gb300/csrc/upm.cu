@@ -790,7 +790,7 @@ cudaError_t launch_one(const SearchArgs &a, const Plan &pl, cudaStream_t stream)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + 31) / 32, (a.ny + TY - 1) / TY);
-    kern<<<grid, kSearchThreads, pl.smem, stream>>>(a);
+    kern<<<grid, kSearchThreads, pl.smem, stream>>>(a); note_launch();
     return cudaGetLastError();
 }
 
@@ -1413,7 +1413,7 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.shifts = shifts;
     a.hdr = hdr; a.list = exact_list; a.u = u; a.err_out = err_out;
-    k_exact<<<152 * 4, 256, 0, stream>>>(a);
+    k_exact<<<device_sms() * 4, 256, 0, stream>>>(a); note_launch();
     return cudaGetLastError();
 }
 
@@ -1431,11 +1431,11 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
     cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_warps, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
     if (ncand <= 4) {
-        k_rescore_lean<3><<<lblocks, RL_T, 0, stream>>>(a);
-        k_rescore_general<3><<<gblocks, 32 * RG_W, 0, stream>>>(a);
+        k_rescore_lean<3><<<lblocks, RL_T, 0, stream>>>(a); note_launch();
+        k_rescore_general<3><<<gblocks, 32 * RG_W, 0, stream>>>(a); note_launch();
     } else {
-        k_rescore_lean<7><<<lblocks, RL_T, 0, stream>>>(a);
-        k_rescore_general<7><<<gblocks, 32 * RG_W, 0, stream>>>(a);
+        k_rescore_lean<7><<<lblocks, RL_T, 0, stream>>>(a); note_launch();
+        k_rescore_general<7><<<gblocks, 32 * RG_W, 0, stream>>>(a); note_launch();
     }
     return cudaGetLastError();
 }

@@ -50,3 +50,26 @@ def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
         px.make_object_map_noalloc(d, t(2, 4, 4), t(4, 4), t(4, 4, dt=torch.uint8), t(2, 4, 4, dt=torch.float64),
                                    t(2, 2, dt=torch.float64), t(1100, 1000), t(1100, 1000))
     assert e.value.code == -5
+
+
+def test_noalloc_calls_take_no_device_memory():
+    """After one warm-up call (which loads the library's device code and with it the fixed
+    scratch), further calls leave the device's free memory exactly as it was: nothing is
+    allocated per call. The inputs and outputs are set up before the measured window."""
+    import torch
+    import paper_2003_12726_gb300 as px
+    from gpu_util import dev, dims_of
+    s = gen.tiny2d(n_side=3, det=40, ref=120, offset=25.0, window=3, seed=gen.BASE_SEED + 78)
+    d = dims_of(s.frames, s.ref_shape)
+    args = (dev(s.frames, torch.float32), dev(s.W, torch.float32), dev(s.M, torch.uint8),
+            dev(s.u_init, torch.float64), dev(s.delta, torch.float64))
+    I = torch.empty(s.ref_shape, dtype=torch.float32, device="cuda")
+    w = torch.empty_like(I)
+    px.make_object_map_noalloc(d, *args, I, w)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        px.make_object_map_noalloc(d, *args, I, w)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
