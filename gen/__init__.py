@@ -9,8 +9,10 @@ points with uniform random amplitudes a_m, evaluated exactly wherever a frame sa
 A bilinear interpolant of the grid would bias the truth-recovery pins toward the method's
 own interpolation, so it is deliberately not used.
 
-Every pixel map generated here is separable, u[0] = fy(i) and u[1] = fx(j), which makes
-the rendering a pair of 1-D band sums per frame.
+Most pixel maps generated here are separable, u[0] = fy(i) and u[1] = fx(j), which makes
+the rendering a pair of 1-D band sums per frame; `make_scan_general` renders any map (a
+rotation or a curl term couples the axes) by evaluating the field at every sample point,
+and can mark isolated bad pixels inside the good region of the mask.
 
 Conventions (shared with the C ABI):
   frames  float32 [N][ny][nx]      Poisson counts (or the noiseless expectation)
@@ -111,6 +113,30 @@ class Field:
         """Field on the outer product of row positions py and column positions px."""
         return 0.5 + (self._raw(np.asarray(py, np.float64), np.asarray(px, np.float64)) - self.lo) / (self.hi - self.lo)
 
+    def points(self, py, px, chunk=1 << 14):
+        """Field at arbitrary points (py[k], px[k]): every point sums its (2K+1)^2 taps,
+        in chunks of points evaluated on a thread pool."""
+        py = np.ascontiguousarray(py, np.float64).ravel()
+        px = np.ascontiguousarray(px, np.float64).ravel()
+        out = np.empty(py.size)
+
+        def one(k0):
+            k1 = min(py.size, k0 + chunk)
+            iy, wy = self._taps(py[k0:k1])
+            ix, wx = self._taps(px[k0:k1])
+            if iy.max() >= self.a.shape[0] or ix.max() >= self.a.shape[1]:
+                raise ValueError("field evaluated too far outside its coefficient grid")
+            # sum over the row taps of (row tap weight x the row's column-tap sum)
+            flat = self.a.ravel()
+            acc = np.zeros(k1 - k0)
+            for r in range(iy.shape[1]):
+                taps = flat[iy[:, r, None] * self.a.shape[1] + ix]       # [points][2K+1]
+                acc += wy[:, r] * np.einsum("kj,kj->k", taps, wx)
+            out[k0:k1] = acc
+        with ThreadPoolExecutor(_threads()) as ex:
+            list(ex.map(one, range(0, py.size, chunk)))
+        return 0.5 + (out - self.lo) / (self.hi - self.lo)
+
     def grid(self, ref_shape):
         Ry, Rx = ref_shape
         return self.separable(np.arange(Ry, dtype=np.float64), np.arange(Rx, dtype=np.float64))
@@ -166,6 +192,85 @@ def make_scan(name, *, ny, nx, ref_shape, sigma, delta, uy, ux, uy0, ux0, W, win
                 delta=delta, ref_shape=tuple(int(v) for v in ref_shape),
                 Iref_true=fld.grid(ref_shape), window=tuple(window), n_iter=n_iter,
                 sigma=sigma, meta=dict(seed=seed, noise=noise, **(extra or {})))
+
+
+def make_scan_general(name, *, ref_shape, sigma, delta, u_true, u_init, W, window, n_iter, seed, noise=True,
+                      bad_frac=0.0, extra=None):
+    """Render a scan with any pixel map u_true [2][ny][nx] (u_init: the initial estimate):
+    frame n samples the continuous field at u_true - Delta[n] point by point. With
+    bad_frac > 0 that fraction of the good pixels (W >= 5 % of its peak), drawn at random
+    among those whose 8 neighbours are all good, is marked bad (M = 0): isolated defects
+    inside the good region, as a mask made from outliers against their neighbours has."""
+    rng = np.random.default_rng(seed)
+    fld = Field(ref_shape, sigma, rng)
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    u_true = np.ascontiguousarray(u_true, dtype=np.float64)
+    n = delta.shape[0]
+    _, ny, nx = u_true.shape
+    Wd = np.asarray(W, dtype=np.float64)
+    frames = np.empty((n, ny, nx), dtype=np.float32)
+    for k in range(n):
+        f = fld.points(u_true[0] - delta[k, 0], u_true[1] - delta[k, 1]).reshape(ny, nx)
+        img = Wd * f
+        frames[k] = (rng.poisson(img) if noise else img).astype(np.float32)
+    M = (Wd >= 0.05 * Wd.max()).astype(np.uint8)
+    if bad_frac > 0:
+        inner = np.zeros_like(M)
+        good = M > 0
+        inner[1:-1, 1:-1] = good[1:-1, 1:-1] & good[:-2, 1:-1] & good[2:, 1:-1] & good[1:-1, :-2] & \
+            good[1:-1, 2:] & good[:-2, :-2] & good[:-2, 2:] & good[2:, :-2] & good[2:, 2:]
+        cand = np.flatnonzero(inner.ravel())
+        k = int(round(bad_frac * good.sum()))
+        # isolated: a drawn pixel none of whose 8 neighbours was drawn before it
+        chosen = np.zeros(M.size, dtype=bool)
+        for p in rng.permutation(cand):
+            if k == 0:
+                break
+            i, j = divmod(int(p), nx)
+            if not chosen.reshape(ny, nx)[i - 1:i + 2, j - 1:j + 2].any():
+                chosen[p] = True
+                k -= 1
+        M.ravel()[chosen] = 0
+    return Scan(name=name, frames=frames, W=np.ascontiguousarray(Wd.astype(np.float32)), M=M, u_true=u_true,
+                u_init=np.ascontiguousarray(u_init, dtype=np.float64), delta=delta,
+                ref_shape=tuple(int(v) for v in ref_shape), Iref_true=fld.grid(ref_shape), window=tuple(window),
+                n_iter=n_iter, sigma=sigma, meta=dict(seed=seed, noise=noise, bad_frac=bad_frac, **(extra or {})))
+
+
+def nonsep2d(n_side=4, det=64, step=6, ref=170, sigma=2.0, mag=1.3, offset=40.0, theta=0.03, curl=0.8,
+             aberr=2.0, window=5, n_iter=3, seed=BASE_SEED + 30, noise=True, bad_frac=0.01, ny=None, nx=None,
+             peak=1000.0, w_sigma=None, jitter=0.0, name=None):
+    """A 2-D scan whose pixel map couples the axes: a small rotation theta (curl 2 theta)
+    and a sinusoidal shear of amplitude `curl` on top of the magnification and a cubic
+    aberration per axis,
+        u_y = offset + mag y - theta (x - cx) + aberr t_y^3 + curl sin(2 pi x / nx),
+        u_x = offset + mag x + theta (y - cy) + aberr t_x^3 + curl sin(2 pi y / ny),
+    so a tile's candidate windows do not stack into rows and columns; the initial map is the
+    linear part (no aberration, no shear). Translations on an n_side^2 grid of `step`
+    (plus a uniform jitter of up to `jitter` px per axis, from its own seeded stream: a
+    fractional part on both axes), Gaussian whitefield, and bad_frac of the good pixels
+    marked bad at random."""
+    ny = det if ny is None else ny
+    nx = det if nx is None else nx
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    cy, cx = (ny - 1) / 2.0, (nx - 1) / 2.0
+    ty, tx = (y - cy) / max(cy, 1.0), (x - cx) / max(cx, 1.0)
+    lin_y = offset + mag * y - theta * (x - cx)
+    lin_x = offset + mag * x + theta * (y - cy)
+    u_true = np.stack(np.broadcast_arrays(lin_y + aberr * ty ** 3 + curl * np.sin(2 * np.pi * x / nx),
+                                          lin_x + aberr * tx ** 3 + curl * np.sin(2 * np.pi * y / ny)))
+    u_init = np.stack(np.broadcast_arrays(lin_y + 0.0 * x, lin_x + 0.0 * y))
+    ws = w_sigma if w_sigma is not None else 0.34 * max(ny, nx)
+    W = peak * np.exp(-((y - cy) ** 2 + (x - cx) ** 2) / (2.0 * ws * ws))
+    rs = (ref, ref) if np.isscalar(ref) else tuple(ref)
+    delta = grid_delta(n_side, step)
+    if jitter > 0:
+        delta = delta + np.random.default_rng(seed + 1).uniform(0.0, jitter, size=delta.shape)
+    return make_scan_general(name or f"nonsep2d-{n_side * n_side}x{ny}x{nx}-w{window}", ref_shape=rs, sigma=sigma,
+                             delta=delta, u_true=u_true, u_init=u_init, W=W,
+                             window=(window, window), n_iter=n_iter, seed=seed, noise=noise, bad_frac=bad_frac,
+                             extra=dict(theta=theta, curl=curl))
 
 
 # --------------------------------------------------------------------------------------

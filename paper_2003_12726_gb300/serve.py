@@ -30,6 +30,7 @@ class Request:
     n_iter: int = 10
     form: int = FORM_FP32
     tile: int = 0
+    quadratic: bool = True              # the 3x3 fit (False: integer argmin)
     keep_result: bool = False
     # filled by the server
     admitted: float | None = None
@@ -93,7 +94,7 @@ class Server:
                 with torch.cuda.stream(self.admit_stream):
                     sc = r.make()
                     rec = Reconstruction.from_device(sc.frames, sc.W, sc.M, sc.delta, sc.u_init, sc.ref_shape,
-                                                     sc.window, form=r.form, tile=r.tile)
+                                                     sc.window, quadratic=r.quadratic, form=r.form, tile=r.tile)
                 ready = torch.cuda.Event()
                 ready.record(self.admit_stream)
                 st = self.streams[nxt % len(self.streams)]
@@ -116,7 +117,8 @@ class Server:
                     r = slot.req
                     r.done = t_start.elapsed_time(slot.event) / 1e3
                     if r.keep_result:
-                        r.result = dict(u=slot.rec.u.clone(), I_ref=slot.rec.I_ref.clone(), err=slot.rec.err.clone())
+                        r.result = dict(u=slot.rec.u.clone(), I_ref=slot.rec.I_ref.clone(), w=slot.rec.w.clone(),
+                                        err=slot.rec.err.clone())
                     active.remove(slot)
                     used -= slot.nbytes
                     del slot

@@ -65,3 +65,24 @@ def gpu_iterate(frames, W, M, delta, u, ref_shape, window, n_iter, quadratic=Tru
     code, bits = px.get_status(ws)
     assert code == 0, (code, bits)
     return ud.cpu().numpy(), Iref.cpu().numpy(), w.cpu().numpy(), err.cpu().numpy().astype(np.float64)
+
+
+def gpu_iteration_pair(s, u_start, form=0, tile=0):
+    """One main-loop iteration (pxst_iterate, n_iter = 1) from u_start without and with the
+    3x3 fit: two tuples (u, err, I_ref, w) for parity.check_iteration."""
+    out = []
+    for q in (False, True):
+        t = torch()
+        d = dims_of(s.frames, s.ref_shape)
+        o = px.Options(int(s.window[0]), int(s.window[1]), q, form, tile=tile)
+        ud = dev(u_start, t.float64)
+        Iref = t.empty(s.ref_shape, dtype=t.float32, device="cuda")
+        w = t.empty(s.ref_shape, dtype=t.float32, device="cuda")
+        err = t.empty(s.M.shape, dtype=t.float32, device="cuda")
+        ws = px.workspace(d, o)
+        px.iterate(d, o, 1, dev(s.frames, t.float32), dev(s.W, t.float32), dev(s.M, t.uint8),
+                   dev(s.delta, t.float64), ud, Iref, w, err, ws)
+        code, bits = px.get_status(ws)
+        assert code == 0, (code, bits)
+        out.append((ud.cpu().numpy(), err.cpu().numpy().astype(np.float64), Iref.cpu().numpy(), w.cpu().numpy()))
+    return out[0], out[1]

@@ -37,15 +37,19 @@ def check_omap(Iref_gpu, w_gpu, Iref_or, w_or):
     return dict(iref_rel_l2=r_i, w_rel_l2=r_w, coverage_mismatch=cov_mismatch)
 
 
-def check_update(inp, pix, u_gpu_int, err_gpu_int, u_gpu_q, err_gpu_q):
+def check_update(inp, pix, u_gpu_int, err_gpu_int, u_gpu_q, err_gpu_q, check_fit=True):
     """inp: dict(frames, W, M, Iref, w, delta, u, window) -- the oracle's inputs (Iref/w as
     used by both sides); pix: flat pixel indices to compare (all M = 1 pixels, or a sample);
-    u_gpu_*: [2][K] for those pixels; err_gpu_*: [K]."""
+    u_gpu_*: [2][K] for those pixels; err_gpu_*: [K]. check_fit=False checks the integer
+    picks and their errors only."""
     frames, W, M, Iref, w, delta, u, window = (inp[k] for k in
                                                ("frames", "W", "M", "Iref", "w", "delta", "u", "window"))
     pix = np.asarray(pix, dtype=np.int64)
     uo_int, eo_int = oracle.update_pixels(frames, W, M, Iref, w, delta, u, window, pix, quadratic=False)
-    uo_q, eo_q = oracle.update_pixels(frames, W, M, Iref, w, delta, u, window, pix, quadratic=True)
+    if check_fit:
+        uo_q, eo_q = oracle.update_pixels(frames, W, M, Iref, w, delta, u, window, pix, quadratic=True)
+    else:
+        uo_q, u_gpu_q = uo_int, u_gpu_int
     uo_int, uo_q = uo_int.T, uo_q.T
     same = np.all(u_gpu_int == uo_int, axis=0)
     agree = float(np.mean(same)) if pix.size else 1.0
@@ -81,3 +85,49 @@ def check_update(inp, pix, u_gpu_int, err_gpu_int, u_gpu_q, err_gpu_q):
     return dict(pixels=int(pix.size), argmin_agree=agree, near_ties=int(bad.size),
                 max_du=max_du, rms_du=float(np.sqrt(np.mean(du ** 2))) if du.size else 0.0,
                 max_err_rel=max_rel, worst_tie_ratio=worst_gap)
+
+
+def check_iteration(s, u_start, gpu_int, gpu_q):
+    """One main-loop iteration on the GPU against the oracle, with the full criterion.
+
+    gpu_int, gpu_q: (u, err, I_ref, w) of the GPU's iteration from u_start without and with
+    the 3x3 fit. The GPU's reference image must match the oracle's make_object_map from
+    u_start (check_omap); the GPU's update must then pass check_update against the oracle's
+    update run on the GPU's own reference image and weights read back as FP64, so that both
+    sides search the same reference and every differing pick must be an oracle near-tie."""
+    u_i, e_i, I_i, w_i = gpu_int
+    u_q, e_q, I_q, w_q = gpu_q
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, u_start, s.delta, s.ref_shape)
+    rep_o = check_omap(I_q, w_q, Io, wo)
+    # both calls build their reference from the same map: identical up to the FP64 atomics' order
+    assert rel_l2(I_i.astype(np.float64), I_q.astype(np.float64)) < 1e-6
+    inp = dict(frames=s.frames, W=s.W, M=s.M, Iref=I_q.astype(np.float64), w=w_q.astype(np.float64),
+               delta=s.delta, u=u_start, window=s.window)
+    if not np.array_equal(I_i, I_q):
+        # the integer call searched its own (rounding-level different) reference: rerun
+        # the comparison of its picks against that one
+        inp_i = dict(inp, Iref=I_i.astype(np.float64), w=w_i.astype(np.float64))
+    else:
+        inp_i = inp
+    pix = np.flatnonzero(s.M.ravel())
+    rep_u = check_update(inp, pix, u_i.reshape(2, -1)[:, pix], e_i.ravel()[pix], u_q.reshape(2, -1)[:, pix],
+                         e_q.ravel()[pix]) if inp_i is inp else _check_split(inp_i, inp, pix, u_i, e_i, u_q, e_q)
+    return dict(omap=rep_o, update=rep_u)
+
+
+def _check_split(inp_i, inp_q, pix, u_i, e_i, u_q, e_q):
+    """check_update when the integer and fitted GPU calls searched references that differ by
+    rounding: the integer picks against the oracle on the first, the fit on the second
+    (where the integer picks of both calls agree)."""
+    rep = check_update(inp_i, pix, u_i.reshape(2, -1)[:, pix], e_i.ravel()[pix], u_i.reshape(2, -1)[:, pix],
+                       e_i.ravel()[pix], check_fit=False)
+    uo_i, _ = oracle.update_pixels(inp_q["frames"], inp_q["W"], inp_q["M"], inp_q["Iref"], inp_q["w"],
+                                   inp_q["delta"], inp_q["u"], inp_q["window"], pix, quadratic=False)
+    uo_q, _ = oracle.update_pixels(inp_q["frames"], inp_q["W"], inp_q["M"], inp_q["Iref"], inp_q["w"],
+                                   inp_q["delta"], inp_q["u"], inp_q["window"], pix, quadratic=True)
+    same = np.all(u_i.reshape(2, -1)[:, pix] == uo_i.T, axis=0)
+    du = np.abs(u_q.reshape(2, -1)[:, pix] - uo_q.T)[:, same]
+    max_du = float(du.max()) if du.size else 0.0
+    assert max_du <= U_TOL, f"sub-pixel u differs by {max_du:.3e} px"
+    rep["max_du"] = max_du
+    return rep

@@ -24,9 +24,15 @@ def _scans():
     ]
 
 
-def _rec(s, form):
+def _rec(s, form, quadratic=True):
     import paper_2003_12726_gb300 as px
-    return px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, form=form)
+    return px.Reconstruction(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, quadratic=quadratic,
+                             form=form)
+
+
+def _host(r):
+    """(u, err, I_ref, w) of a Reconstruction on the host, for parity.check_iteration."""
+    return (r.u.cpu().numpy(), r.err.cpu().numpy().astype(np.float64), r.I_ref.cpu().numpy(), r.w.cpu().numpy())
 
 
 def _same(ra, rb, M):
@@ -69,23 +75,21 @@ def test_batch_matches_each_scan_alone():
 
 
 def test_batch_against_oracle():
-    """One iteration of every scan in one batch; scan 0 (FP32) and scan 1 (BF16) against the
-    oracle's iteration."""
+    """One iteration of every scan in one batch, without and with the fit (two batches);
+    the FP32, BF16 and TF32 scans against the oracle with the full criterion."""
     import torch
     import paper_2003_12726_gb300 as px
     scans = _scans()
-    recs = [_rec(s, f) for s, f in scans]
-    b = px.Batch(recs, n_iter=1, n_branches=4)
-    b.run()
-    torch.cuda.synchronize()
-    for k in (0, 1):
+    recs = {q: [_rec(s, f, q) for s, f in scans] for q in (False, True)}
+    for q in (False, True):
+        b = px.Batch(recs[q], n_iter=1, n_branches=4)
+        b.run()
+        torch.cuda.synchronize()
+        b.close()
+    for k in (0, 1, 4):
         s = scans[k][0]
-        uo, Io, wo, eo = oracle.iterate(s.frames, s.W, s.M, s.delta, s.u_init, s.ref_shape, s.window, 1)
-        parity.check_omap(recs[k].I_ref.cpu().numpy(), recs[k].w.cpu().numpy(), Io, wo)
-        ug = recs[k].u.cpu().numpy()
-        same = np.all(np.abs(ug - uo) <= parity.U_TOL, axis=0)[s.M > 0]
-        assert same.mean() >= parity.ARGMIN_AGREE - 0.004, (k, same.mean())
-    b.close()
+        rep = parity.check_iteration(s, s.u_init, _host(recs[False][k]), _host(recs[True][k]))
+        print(s.name, "form", scans[k][1], rep["update"])
 
 
 @pytest.mark.parametrize("form", [0, 1], ids=["fp32", "bf16"])
@@ -102,13 +106,17 @@ def test_autotune(form):
     else:
         assert tile in (0, 1, 2) and ms > 0
     assert torch.equal(r.u, u0)               # the map is restored
-    # the tuned shape keeps parity: one iteration from the restored state vs the oracle's
+    # the tuned shape keeps parity: one iteration from the restored state, without and with
+    # the fit, against the oracle with the full criterion
     u_start = u0.cpu().numpy()
-    r.run(1)
-    uo, *_ = oracle.iterate(s.frames, s.W, s.M, s.delta, u_start, s.ref_shape, s.window, 1)
-    same = np.all(np.abs(r.u.cpu().numpy() - uo) <= parity.U_TOL, axis=0)[s.M > 0]
-    assert same.mean() >= parity.ARGMIN_AGREE - 0.004, same.mean()
-    print("form", form, "tuned tile", tile, "ms", ms)
+    res = {}
+    for q in (False, True):
+        r.u.copy_(u0)
+        r.opts.quadratic = q
+        r.run(1)
+        res[q] = _host(r)
+    rep = parity.check_iteration(s, u_start, res[False], res[True])
+    print("form", form, "tuned tile", tile, "ms", ms, rep["update"])
 
 
 def test_host_stream_matches_plain_steps():

@@ -27,16 +27,28 @@ def _sample(M, k, seed):
 _CACHE = {}
 
 
+def nonsep_stripe():
+    """24 rows of the 2-D precision scan's geometry at its full width, 400 frames on the
+    20 x 20 grid of 4 px steps, window +-16 x +-16, with a map that couples the axes (a
+    0.01 rad rotation and a shear of 1 px amplitude on top of the magnification 1.02 and the
+    +-8 px cubic) and 1 % isolated bad pixels."""
+    return gen.nonsep2d(n_side=20, step=4, ny=24, nx=1024, ref=(180, 1200), sigma=1.5, mag=1.02, offset=104.0,
+                        theta=0.01, curl=1.0, aberr=8.0, window=16, w_sigma=400.0, seed=gen.BASE_SEED + 32,
+                        name="precision2d-nonsep-24x1024")
+
+
 def _scan(name):
     if name not in _CACHE:
         _CACHE.clear()
-        _CACHE[name] = gen.CONFIGS[name]()
+        _CACHE[name] = nonsep_stripe() if name == "precision2d-nonsep" else gen.CONFIGS[name]()
     return _CACHE[name]
 
 
 @pytest.mark.parametrize("name,k,form", [("lens1d", 3000, 0), ("precision2d", 600, 0), ("precision2d", 600, 1),
-                                         ("precision2d", 600, 2)], ids=["lens1d-fp32", "precision2d-fp32",
-                                                                        "precision2d-bf16", "precision2d-tf32"])
+                                         ("precision2d", 600, 2), ("precision2d-nonsep", 2000, 0),
+                                         ("precision2d-nonsep", 2000, 1), ("precision2d-nonsep", 2000, 2)],
+                         ids=["lens1d-fp32", "precision2d-fp32", "precision2d-bf16", "precision2d-tf32",
+                              "precision2d-nonsep-fp32", "precision2d-nonsep-bf16", "precision2d-nonsep-tf32"])
 def test_full_size(name, k, form):
     s = _scan(name)
     Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)

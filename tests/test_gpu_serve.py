@@ -4,7 +4,6 @@ FP64-atomic rounding); one GPU-rendered scan served in the mix matches the oracl
 import numpy as np
 import pytest
 
-import oracle
 import parity
 
 pytestmark = pytest.mark.gpu
@@ -19,15 +18,16 @@ def _specs():
             dict(kind="2d", n_side=3, det=48, window=3, seed=906)]
 
 
-def _requests(specs, forms, arrivals, n_iter=3):
+def _requests(specs, forms, arrivals, n_iter=3, quadratic=None):
     import gen.gpu as gg
     from paper_2003_12726_gb300.serve import Request, estimate_bytes
     out = []
-    for k, (sp, f, t) in enumerate(zip(specs, forms, arrivals)):
+    quadratic = quadratic or [True] * len(specs)
+    for k, (sp, f, t, q) in enumerate(zip(specs, forms, arrivals, quadratic)):
         sc = gg.render(sp)                     # once, to size the request
         est = estimate_bytes(sc.dims, sc.window, f)
         out.append(Request(rid=k, arrival=float(t), make=(lambda sp=sp: gg.render(sp)), est_bytes=est,
-                           n_iter=n_iter, form=f, keep_result=True))
+                           n_iter=n_iter, form=f, quadratic=q, keep_result=True))
     return out
 
 
@@ -58,20 +58,24 @@ def test_serve_mix_equals_alone():
 
 
 def test_served_scan_against_oracle():
-    """A GPU-rendered scan served among others: one iteration against the oracle's."""
+    """GPU-rendered scans served among others, each also served without the fit: one
+    iteration of the FP32, BF16 and TF32 ones against the oracle with the full criterion
+    (reference image against the oracle's; the map update against the oracle's update on
+    the GPU's own reference image)."""
+    from types import SimpleNamespace
     import gen.gpu as gg
     from paper_2003_12726_gb300.serve import Server
     specs = _specs()
-    reqs = _requests(specs, [0, 1, 0, 1, 2, 0], [0.0] * 6, n_iter=1)
+    forms = [0, 1, 0, 1, 2, 0]
+    # every scan twice: with the fit and without it, in one mix
+    reqs = _requests(specs + specs, forms + forms, [0.0] * 12, n_iter=1, quadratic=[True] * 6 + [False] * 6)
     Server(mem_budget=1 << 34, n_streams=3).run(reqs, realtime=False)
-    for k in (0, 1):
+    for k in (0, 1, 4):
         sc = gg.render(specs[k])
-        fr, W, M = sc.frames.cpu().numpy(), sc.W.cpu().numpy(), sc.M.cpu().numpy()
-        delta, u0 = sc.delta.cpu().numpy(), sc.u_init.cpu().numpy()
-        uo, Io, wo, eo = oracle.iterate(fr, W, M, delta, u0, sc.ref_shape, sc.window, 1)
-        ug = reqs[k].result["u"].cpu().numpy()
-        same = np.all(np.abs(ug - uo) <= parity.U_TOL, axis=0)[M > 0]
-        assert same.mean() >= parity.ARGMIN_AGREE - 0.004, (k, same.mean())
-        Ig = reqs[k].result["I_ref"].cpu().numpy().astype(np.float64)
-        good = wo > 1e-4 * wo.max()
-        assert parity.rel_l2(Ig[good], Io[good]) <= 1e-5
+        s = SimpleNamespace(frames=sc.frames.cpu().numpy(), W=sc.W.cpu().numpy(), M=sc.M.cpu().numpy(),
+                            delta=sc.delta.cpu().numpy(), ref_shape=sc.ref_shape, window=sc.window)
+        u0 = sc.u_init.cpu().numpy()
+        host = lambda r: (r.result["u"].cpu().numpy(), r.result["err"].cpu().numpy().astype(np.float64),
+                          r.result["I_ref"].cpu().numpy(), r.result["w"].cpu().numpy())
+        rep = parity.check_iteration(s, u0, host(reqs[k + 6]), host(reqs[k]))
+        print(specs[k], "form", forms[k], rep["update"])

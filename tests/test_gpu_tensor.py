@@ -43,6 +43,12 @@ SCANS = {
     "2d-100x96": lambda: __import__("gen").tiny2d(n_side=10, det=96, step=4, ref=200, sigma=1.5, mag=1.02,
                                                   offset=50.0, aberr=3.0, window=8,
                                                   seed=__import__("gen").BASE_SEED + 61),
+    # axes coupled by a rotation and a shear (a tile's union of windows grows past its rows
+    # and columns) with 1 % isolated bad pixels; fractional translations on both axes
+    "nonsep2d": lambda: __import__("gen").nonsep2d(),
+    "nonsep2d-100x96": lambda: __import__("gen").nonsep2d(n_side=10, det=96, step=4, ref=230, sigma=1.5, mag=1.02,
+                                                          offset=60.0, theta=0.08, curl=1.5, aberr=3.0, window=8,
+                                                          jitter=0.7, seed=__import__("gen").BASE_SEED + 63),
     # more frames than the rescore stages per slice (512)
     "2d-625x40": lambda: __import__("gen").tiny2d(n_side=25, det=40, step=2, ref=160, sigma=1.5, mag=1.02,
                                                   offset=60.0, aberr=2.0, window=5,
@@ -123,3 +129,15 @@ def test_tensor_tile_shapes(tscan, tile):
     rep = parity.check_update(inp, pix, ug_i.reshape(2, -1)[:, pix], eg_i.ravel()[pix],
                               ug_q.reshape(2, -1)[:, pix], eg_q.ravel()[pix])
     print(s.name, "tile", tile, rep)
+
+
+@pytest.mark.parametrize("form", [1, 2], ids=["bf16", "tf32"])
+def test_tensor_iterate_parity(tscan, form):
+    """A whole iteration in a tensor form (pxst_iterate) with the full criterion: the
+    reference image against the oracle's, the map update against the oracle's update on the
+    GPU's own reference image."""
+    import parity
+    from gpu_util import gpu_iteration_pair
+    s = tscan
+    g_int, g_q = gpu_iteration_pair(s, s.u_init, form=form)
+    print(s.name, "form", form, parity.check_iteration(s, s.u_init, g_int, g_q))
