@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     // the weights of pixels whose zero-shift corners stay on the grid for every fraction
     // class are formed per class (k_dscatter, k_dgather); only the others add them here
     const bool split = a.dcls != nullptr && a.hdr->n_classes <= kMaxClasses;
+    // one fraction class for every frame (set by k_prepare from the translations)
+    const bool uniform = a.hdr->n_classes == 1;
     const bool dom = act && iy >= 0 && iy <= a.Ry - 3 && ix >= 0 && ix <= a.Rx - 3;
     const float WW = (split && dom) ? 0.0f : Wv * Wv;
 
@@ -298,10 +300,80 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 }
             }
         };
-        if (warp_den)
+        // every frame with the same fraction (one class): each pixel's corners, weights and
+        // the hand-over to the next lane are the same for every frame, and only the group's
+        // integer shift moves them
+        auto frames_loop_uniform = [&](auto den_tag) {
+            constexpr bool DEN = decltype(den_tag)::value;
+            int by = iy, bx = ix;
+            float sy = fy + a.hdr->cls_fy[0], sx = fx + a.hdr->cls_fx[0];
+            if (sy >= 1.0f) { sy -= 1.0f; by += 1; }
+            if (sx >= 1.0f) { sx -= 1.0f; bx += 1; }
+            if (!act) { by = INT_MIN; bx = INT_MIN; }
+            // right corners (top, bottom) and left corners, per unit frame value and weight
+            const float wr0 = (1.0f - sy) * sx * Wv, wr1 = sy * sx * Wv;
+            const float wl0 = (1.0f - sy) * (1.0f - sx) * Wv, wl1 = sy * (1.0f - sx) * Wv;
+            const float dr0 = DEN ? (1.0f - sy) * sx * WW : 0.0f, dr1 = DEN ? sy * sx * WW : 0.0f;
+            const float dl0 = DEN ? (1.0f - sy) * (1.0f - sx) * WW : 0.0f, dl1 = DEN ? sy * (1.0f - sx) * WW : 0.0f;
+            const int pbx = __shfl_up_sync(0xffffffffu, bx, 1), pby = __shfl_up_sync(0xffffffffu, by, 1);
+            const float pwr0 = __shfl_up_sync(0xffffffffu, wr0, 1), pwr1 = __shfl_up_sync(0xffffffffu, wr1, 1);
+            const float pdr0 = __shfl_up_sync(0xffffffffu, dr0, 1), pdr1 = __shfl_up_sync(0xffffffffu, dr1, 1);
+            const bool take = act && lane > 0 && pby == by && pbx != INT_MIN && pbx + 1 == bx;
+            const bool given = __shfl_down_sync(0xffffffffu, take ? 1 : 0, 1) && lane < 31;
+            const float tw0 = take ? pwr0 : 0.0f, tw1 = take ? pwr1 : 0.0f;
+            const float td0 = take ? pdr0 : 0.0f, td1 = take ? pdr1 : 0.0f;
+            const bool row1 = sy != 0.0f, right = sx != 0.0f && !given;
+            const bool low = row1 || (take && (pwr1 != 0.0f || pdr1 != 0.0f));
+            // the den terms of a frame do not depend on the frame: the per-frame sums
+            const float D0 = dl0 + td0, D1 = dl1 + td1;
+            const int cb = act ? (by - r0) * Wd + (bx - c0) : 0;
+            float In[SC_PREFETCH];
+#pragma unroll
+            for (int jf = 0; jf < SC_PREFETCH; ++jf)
+                In[jf] = (act && g0 + jf < g1) ? __ldcs(a.frames + (size_t)(g0 + jf) * P + pix) : 0.0f;
+            for (int n = g0; n < g1; n += SC_PREFETCH) {
+                float I[SC_PREFETCH];
+#pragma unroll
+                for (int jf = 0; jf < SC_PREFETCH; ++jf) {
+                    I[jf] = In[jf];
+                    const int m = n + SC_PREFETCH + jf;
+                    In[jf] = (act && m < g1) ? __ldcs(a.frames + (size_t)m * P + pix) : 0.0f;
+                }
+#pragma unroll
+                for (int jf = 0; jf < SC_PREFETCH; ++jf) {
+                    if (n + jf >= g1) break;                    // uniform over the CTA
+                    const FrameShift S = s_sh[n + jf - g0];
+                    const float Iv = I[jf];
+                    const float Ip = __shfl_up_sync(0xffffffffu, Iv, 1);
+                    if (!act) continue;
+                    const int c00 = cb + S.ky * Wd + S.kx;
+                    atomicAdd(&s_num[c00], fmaf(Ip, tw0, Iv * wl0));
+                    if (DEN && D0 != 0.0f) atomicAdd(&s_den[c00], D0);
+                    if (right) {
+                        atomicAdd(&s_num[c00 + 1], Iv * wr0);
+                        if (DEN && dr0 != 0.0f) atomicAdd(&s_den[c00 + 1], dr0);
+                    }
+                    if (low) {
+                        atomicAdd(&s_num[c00 + Wd], fmaf(Ip, tw1, Iv * wl1));
+                        if (DEN && D1 != 0.0f) atomicAdd(&s_den[c00 + Wd], D1);
+                    }
+                    if (row1 && right) {
+                        atomicAdd(&s_num[c00 + Wd + 1], Iv * wr1);
+                        if (DEN && dr1 != 0.0f) atomicAdd(&s_den[c00 + Wd + 1], dr1);
+                    }
+                }
+            }
+        };
+        if (uniform && fits) {
+            if (warp_den)
+                frames_loop_uniform(std::true_type{});
+            else
+                frames_loop_uniform(std::false_type{});
+        } else if (warp_den) {
             frames_loop(std::true_type{});
-        else
+        } else {
             frames_loop(std::false_type{});
+        }
         __syncthreads();
         if (fits)
             for (int c = threadIdx.x; c < H * Wd; c += SC_THREADS) {

@@ -20,8 +20,9 @@
 // masked renormalised reads from global memory, lexicographic warp argmin, FP64 fit.
 // It serves tiles whose reference window does not fit in shared memory and scans with
 // too many frames to stage.
-// Rescore (k_rescore_lean, k_rescore_general): the exact stage of the tensor-core forms,
+// Rescore (k_rescore_tile, k_rescore_general): the exact stage of the tensor-core forms,
 // one thread per pixel.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 
@@ -936,7 +937,6 @@ __device__ void eval_batch(const RescoreArgs &a, size_t pix, float Wv, const int
 
 constexpr int RS_F = 16;      // frames per pipeline stage
 constexpr int RS_S = 3;       // pipeline stages
-constexpr int RL_T = 64;      // lean kernel: pixels per block
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -964,13 +964,13 @@ struct PixCands {
 };
 
 template <int XK>
-__device__ __forceinline__ void pix_setup(const RescoreArgs &a, size_t pix, PixCands<XK> &pc) {
+__device__ __forceinline__ void pix_setup(const RescoreArgs &a, size_t pix, bool inb, PixCands<XK> &pc) {
     const size_t P = (size_t)a.ny * a.nx;
     const int wxn = 2 * a.Sx + 1;
     pc.act = false;
     pc.ci = pc.cj = 0;
     pc.Wv = 0.0f;
-    if (pix < P) {
+    if (inb) {
         if (!a.mask[pix]) {
             if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
         } else {
@@ -1097,27 +1097,107 @@ __device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, con
     if (a.err_out) a.err_out[pix] = be;
 }
 
-// Lean rescore: one block per 64 consecutive pixels, one thread per pixel, for warps whose
-// every pixel passes pix_lean; a warp that does not is appended to the list of
-// k_rescore_general and leaves. Each thread streams its own pixel's frames through a
-// 3-stage cp.async pipeline in shared memory (the copies a thread waits for are its own:
-// no block barrier). For a whole-pixel shift the 3x3 is read as three rows of three from
-// one row pointer each; every 3x3 point is summed (those outside the window are dropped at
-// the end) and the variance is the pixel's own over all frames.
-template <int XK>
-__global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
-    __shared__ __align__(16) float sfr[RS_S][RS_F][RL_T];    // column t: thread t's pixel only
-    const size_t P = (size_t)a.ny * a.nx;
-    const int t = threadIdx.x;
-    const size_t pix = (size_t)blockIdx.x * RL_T + t;
-    PixCands<XK> pc;
-    pix_setup<XK>(a, pix, pc);
-    if (!__all_sync(0xffffffffu, pix_lean<XK>(a, pc))) {
-        if ((t & 31) == 0) a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)(pix >> 5);
-        return;
+// Lean rescore: one CTA per tile of RT_TY detector rows x 32 columns, one thread per pixel,
+// for the warps (one row of 32 pixels each) whose every pixel passes pix_lean; a warp that
+// does not is appended to the list of k_rescore_general (by its first pixel) and only waits
+// at the CTA's barriers. The reference the tile's evaluated candidates read (their bounding
+// box, widened by the range of the integer frame shifts and one corner) is staged once in
+// shared memory when it fits the CTA's share, so that each frame's reads of the 3x3 and of
+// the other kept candidates are shared-memory loads rather than L1 hits; otherwise they are
+// read from the masked reference through the cache, as before. Each thread streams its own
+// pixel's frames through an 8-deep register double buffer. For a whole-pixel shift the 3x3
+// is read as three rows of three about one index; every 3x3 point is summed (those outside
+// the window are dropped at the end) and the variance is the pixel's own over all frames.
+constexpr int RT_TY = 8;                      // detector rows per tile (one warp each)
+constexpr int RT_THREADS = 32 * RT_TY;
+constexpr int RT_PREFETCH = 8;                // frames in flight per thread
+constexpr int RT_SMEM = 110 * 1024;           // dynamic shared memory per CTA: two CTAs per SM
+
+// R at window index q for the shift's fraction (fy, fx), by the masked renormalised rule with
+// the arithmetic of gather_rm (corners NaN where uncovered); false: no valid corner.
+__device__ __forceinline__ bool gather_win(const float *__restrict__ src, int stride, int q, float fy, float fx,
+                                           float &R) {
+    const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx), fy * fx};
+    const int off[4] = {0, 1, stride, stride + 1};
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (wt[k] == 0.0f) continue;
+        const float r = src[q + off[k]];
+        if (r != r) continue;
+        num = fmaf(wt[k], r, num);
+        den += wt[k];
     }
-    // other kept candidates: as many as the warp's longest list (the rest read c0)
-    const int nxw = __reduce_max_sync(0xffffffffu, pc.nxk);
+    if (!(den > 0.0f)) return false;
+    R = num / den;
+    return true;
+}
+
+template <int XK>
+__global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
+    extern __shared__ __align__(16) unsigned char rt_raw[];
+    FrameShift *s_sh = reinterpret_cast<FrameShift *>(rt_raw);
+    float *s_win = reinterpret_cast<float *>(s_sh + (sh_staged ? a.N : 0));
+    const FrameShift *sh = sh_staged ? s_sh : a.shifts;
+    __shared__ int s_box[4];
+    const size_t P = (size_t)a.ny * a.nx;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane, y = blockIdx.y * RT_TY + wid;
+    const bool inb = x < a.nx && y < a.ny;
+    const size_t pix = inb ? (size_t)y * a.nx + x : 0;
+    if (threadIdx.x < 4) s_box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    if (sh_staged)
+        for (int n = threadIdx.x; n < a.N; n += RT_THREADS) s_sh[n] = a.shifts[n];
+    PixCands<XK> pc;
+    pix_setup<XK>(a, pix, inb, pc);
+    const bool lean = __all_sync(0xffffffffu, pix_lean<XK>(a, pc));
+    if (!lean) {
+        // the per-frame rule is needed somewhere in this row segment: the general kernel
+        if (lane == 0 && y < a.ny)
+            a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)((size_t)y * a.nx + blockIdx.x * 32);
+        pc.act = pc.run = false;
+    }
+    __syncthreads();
+    // the box of every candidate the tile's lean pixels evaluate
+    if (pc.run) {
+        int y0 = pc.y0 - 1, y1 = pc.y0 + 1, x0 = pc.x0 - 1, x1 = pc.x0 + 1;
+#pragma unroll
+        for (int q = 0; q < XK; ++q)
+            if (q < pc.nxk) {
+                y0 = min(y0, pc.xy[q]); y1 = max(y1, pc.xy[q]);
+                x0 = min(x0, pc.xx[q]); x1 = max(x1, pc.xx[q]);
+            }
+        atomicMin(&s_box[0], y0); atomicMax(&s_box[1], y1);
+        atomicMin(&s_box[2], x0); atomicMax(&s_box[3], x1);
+    }
+    __syncthreads();
+    const bool any = s_box[0] != INT_MAX;
+    // the window: the box widened by the shifts' integer range (+1 row and column for the
+    // second corner of a fractional shift); lean pixels read only on the grid
+    const int wy0 = any ? s_box[0] + a.hdr->kmin_y : 0, wy1 = any ? s_box[1] + a.hdr->kmax_y + 1 : 0;
+    const int wx0 = any ? s_box[2] + a.hdr->kmin_x : 0, wx1 = any ? s_box[3] + a.hdr->kmax_x + 1 : 0;
+    long long WSl = (long long)wx1 - wx0 + 1;
+    WSl += (WSl & 1) ? 0 : 1;                       // odd row pitch: rows read by a warp spread over banks
+    const long long WHl = (long long)wy1 - wy0 + 1;
+    const bool staged = any && WSl * WHl <= win_cap;
+    const int WS = staged ? (int)WSl : a.Rx;
+    if (staged) {
+        const int WN = (int)(WSl * WHl);
+        const float qnan = __int_as_float(0x7fc00000);
+        for (int idx = threadIdx.x; idx < WN; idx += RT_THREADS) {
+            const int gy = wy0 + idx / WS, gx = wx0 + idx % WS;
+            s_win[idx] = (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) ? __ldg(a.Rm + (size_t)gy * a.Rx + gx) : qnan;
+        }
+    }
+    __syncthreads();
+    if (!pc.act) return;
+    const float *src = staged ? s_win : a.Rm;
+    // window indices of c0 and of the other kept candidates for a zero shift
+    const int base0 = staged ? (pc.y0 - wy0) * WS + (pc.x0 - wx0) : pc.base0;
+    int xb[PixCands<XK>::NX];
+#pragma unroll
+    for (int q = 0; q < XK; ++q) xb[q] = staged ? (pc.xy[q] - wy0) * WS + (pc.xx[q] - wx0) : pc.xbase[q];
+    const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
     // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
     // packed FMA advances two sums
     float2 acc[5];
@@ -1127,80 +1207,71 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
 #pragma unroll
     for (int q = 0; q < XK; ++q) ex[q] = 0.0f;
     const float Wv = pc.Wv;
-    const int nst = (a.N + RS_F - 1) / RS_F;
-    auto issue = [&](int st) {
-        if (st < nst && pc.run) {
-            const int buf = st % RS_S;
+    const float2 nW2 = make_float2(-Wv, -Wv);
+    const bool run = pc.run;
+    const float *fp = a.frames + pix;
+    float In[RT_PREFETCH];
 #pragma unroll
-            for (int f = 0; f < RS_F; ++f) {
-                const int n = st * RS_F + f;
-                if (n < a.N) cp_async4(&sfr[buf][f][t], a.frames + (size_t)n * P + pix);
-            }
+    for (int jf = 0; jf < RT_PREFETCH; ++jf) In[jf] = (run && jf < a.N) ? __ldcs(fp + (size_t)jf * P) : 0.0f;
+    for (int n0 = 0; n0 < a.N; n0 += RT_PREFETCH) {
+        float Iv[RT_PREFETCH];
+#pragma unroll
+        for (int jf = 0; jf < RT_PREFETCH; ++jf) {
+            Iv[jf] = In[jf];
+            const int m = n0 + RT_PREFETCH + jf;
+            In[jf] = (run && m < a.N) ? __ldcs(fp + (size_t)m * P) : 0.0f;
         }
-        cp_async_commit();
-    };
+        if (!run) continue;
 #pragma unroll
-    for (int st = 0; st < RS_S - 1; ++st) issue(st);
-    for (int st = 0; st < nst; ++st) {
-        issue(st + RS_S - 1);
-        cp_async_wait<RS_S - 1>();
-        const int buf = st % RS_S;
-        if (pc.run) {
-            const int nf = min(RS_F, a.N - st * RS_F);
-#pragma unroll 2
-            for (int f = 0; f < nf; ++f) {
-                const FrameShift s = a.shifts[st * RS_F + f];
-                const float I = sfr[buf][f][t];
-                const float2 I2 = make_float2(I, I), nW2 = make_float2(-Wv, -Wv);
-                if (s.fy == 0.0f && s.fx == 0.0f) {          // the same for every lane
-                    const int off = s.ky * a.Rx + s.kx;
-                    const float *r0 = a.Rm + (pc.base0 + off);
-                    const float *rm = r0 - a.Rx, *rp = r0 + a.Rx;
-                    const float R[9] = {__ldg(rm - 1), __ldg(rm), __ldg(rm + 1), __ldg(r0 - 1), __ldg(r0),
-                                        __ldg(r0 + 1), __ldg(rp - 1), __ldg(rp), __ldg(rp + 1)};
+        for (int jf = 0; jf < RT_PREFETCH; ++jf) {
+            if (n0 + jf >= a.N) break;                      // uniform over the CTA
+            const FrameShift sft = sh[n0 + jf];
+            const float I = Iv[jf];
+            const float2 I2 = make_float2(I, I);
+            const int off = sft.ky * WS + sft.kx;
+            if (sft.fy == 0.0f && sft.fx == 0.0f) {         // the same for every lane
+                const float *r0 = src + (base0 + off);
+                const float *rm = r0 - WS, *rp = r0 + WS;
+                const float R[9] = {rm[-1], rm[0], rm[1], r0[-1], r0[0], r0[1], rp[-1], rp[0], rp[1]};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float2 d = __ffma2_rn(nW2, make_float2(R[2 * k], R[2 * k + 1]), I2);
-                        acc[k] = __ffma2_rn(d, d, acc[k]);
+                for (int k = 0; k < 4; ++k) {
+                    const float2 d = __ffma2_rn(nW2, make_float2(R[2 * k], R[2 * k + 1]), I2);
+                    acc[k] = __ffma2_rn(d, d, acc[k]);
+                }
+                // (I - W R8, I - W): the last point and the variance term
+                const float2 d8 = __ffma2_rn(nW2, make_float2(R[8], 1.0f), I2);
+                acc[4] = __ffma2_rn(d8, d8, acc[4]);
+#pragma unroll
+                for (int q = 0; q < XK; ++q) {
+                    if (q >= nxw) break;
+                    const float d = fmaf(-Wv, src[xb[q] + off], I);
+                    ex[q] = fmaf(d, d, ex[q]);
+                }
+            } else {
+                const float tt = I - Wv;
+                acc[4].y = fmaf(tt, tt, acc[4].y);
+                // a fractional shift: the masked bilinear read (valid: the counts are N)
+#pragma unroll
+                for (int jn = 0; jn < 9; ++jn) {
+                    float R;
+                    if (gather_win(src, WS, base0 + off + (jn / 3 - 1) * WS + (jn % 3 - 1), sft.fy, sft.fx, R)) {
+                        const float d = fmaf(-Wv, R, I);
+                        float &e = (jn & 1) ? acc[jn >> 1].y : acc[jn >> 1].x;
+                        e = fmaf(d, d, e);
                     }
-                    // (I - W R8, I - W): the last point and the variance term
-                    const float2 d8 = __ffma2_rn(nW2, make_float2(R[8], 1.0f), I2);
-                    acc[4] = __ffma2_rn(d8, d8, acc[4]);
+                }
 #pragma unroll
-                    for (int q = 0; q < XK; ++q) {
-                        if (q >= nxw) break;
-                        const float d = fmaf(-Wv, __ldg(a.Rm + (pc.xbase[q] + off)), I);
+                for (int q = 0; q < XK; ++q) {
+                    if (q >= nxw) break;
+                    float R;
+                    if (gather_win(src, WS, xb[q] + off, sft.fy, sft.fx, R)) {
+                        const float d = fmaf(-Wv, R, I);
                         ex[q] = fmaf(d, d, ex[q]);
-                    }
-                } else {
-                    const float tt = I - Wv;
-                    acc[4].y = fmaf(tt, tt, acc[4].y);
-                    // a fractional shift: the masked bilinear read (valid: the counts are N)
-#pragma unroll
-                    for (int jn = 0; jn < 9; ++jn) {
-                        float R;
-                        if (gather_rm(a.Rm, a.Ry, a.Rx, pc.y0 + jn / 3 - 1 + s.ky, pc.x0 + jn % 3 - 1 + s.kx, s.fy,
-                                      s.fx, R)) {
-                            const float d = fmaf(-Wv, R, I);
-                            float &e = (jn & 1) ? acc[jn >> 1].y : acc[jn >> 1].x;
-                            e = fmaf(d, d, e);
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < XK; ++q) {
-                        if (q >= nxw) break;
-                        float R;
-                        if (gather_rm(a.Rm, a.Ry, a.Rx, pc.xy[q] + s.ky, pc.xx[q] + s.kx, s.fy, s.fx, R)) {
-                            const float d = fmaf(-Wv, R, I);
-                            ex[q] = fmaf(d, d, ex[q]);
-                        }
                     }
                 }
             }
         }
     }
-    cp_async_wait<0>();
-    if (!pc.act) return;
     // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
     const float var = acc[4].y;
     float f9[9], fxe[PixCands<XK>::NX];
@@ -1214,8 +1285,9 @@ __global__ void __launch_bounds__(RL_T, 16) k_rescore_lean(RescoreArgs a) {
     pix_finish<XK>(a, pix, pc, f9, fxe);
 }
 
-// General rescore: one block per warp listed by k_rescore_lean (blocks beyond the list's
-// length return at once), with the per-frame rule of the masked renormalised reads: each
+// General rescore: one block per row segment of 32 pixels listed by k_rescore_tile (its
+// first pixel; blocks beyond the list's length return at once), with the per-frame rule of
+// the masked renormalised reads: each
 // candidate sums its error and variance over the frames where it is valid. The block's 4
 // warps take the same 32 pixels and a quarter of the frames each (so that the few listed
 // warps still fill the GPU); their sums are added in warp order and warp 0 finishes.
@@ -1229,9 +1301,11 @@ __global__ void __launch_bounds__(32 * RG_W) k_rescore_general(RescoreArgs a) {
     if ((int)blockIdx.x >= a.hdr->n_rescore_warps) return;
     const size_t P = (size_t)a.ny * a.nx;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t pix = (size_t)a.wlist[blockIdx.x] * 32 + lane;
+    const size_t first = (size_t)a.wlist[blockIdx.x];
+    const bool inb = (int)(first % a.nx) + lane < a.nx;
+    const size_t pix = inb ? first + lane : first;
     PixCands<XK> pc;
-    pix_setup<XK>(a, pix, pc);
+    pix_setup<XK>(a, pix, inb, pc);
     CandSums s9[9], sx[PixCands<XK>::NX];
 #pragma unroll
     for (int jn = 0; jn < 9; ++jn) s9[jn].zero();
@@ -1426,18 +1500,24 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0; a.ncand = ncand;
     a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.nvalid = nvalid; a.shifts = shifts;
     a.cand = cand; a.hdr = hdr; a.wlist = wlist; a.u = u; a.err_out = err_out;
-    const size_t P = (size_t)d.ny * d.nx;
-    const unsigned lblocks = (unsigned)((P + RL_T - 1) / RL_T), gblocks = (unsigned)((P + 31) / 32);
+    const dim3 tgrid((unsigned)((d.nx + 31) / 32), (unsigned)((d.ny + RT_TY - 1) / RT_TY));
+    const unsigned gblocks = tgrid.x * (unsigned)d.ny;          // at most one per row segment
+    // the shift table (when it leaves room) and the window share the CTA's part of shared
+    // memory; a window that does not fit is read through the cache
+    const long long shifts_b = (long long)sizeof(FrameShift) * d.n_frames;
+    const int sh_staged = shifts_b <= RT_SMEM / 2 ? 1 : 0;
+    const int smem = RT_SMEM;
+    const int win_cap = (int)((smem - (sh_staged ? shifts_b : 0)) / 4);
     cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_warps, 0, sizeof(int), stream);
     if (e != cudaSuccess) return e;
-    if (ncand <= 4) {
-        k_rescore_lean<3><<<lblocks, RL_T, 0, stream>>>(a); note_launch();
-        k_rescore_general<3><<<gblocks, 32 * RG_W, 0, stream>>>(a); note_launch();
-    } else {
-        k_rescore_lean<7><<<lblocks, RL_T, 0, stream>>>(a); note_launch();
-        k_rescore_general<7><<<gblocks, 32 * RG_W, 0, stream>>>(a); note_launch();
-    }
-    return cudaGetLastError();
+    auto go = [&](auto tile_kernel, auto general_kernel) {
+        cudaError_t r = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (r != cudaSuccess) return r;
+        tile_kernel<<<tgrid, RT_THREADS, smem, stream>>>(a, win_cap, sh_staged); note_launch();
+        general_kernel<<<gblocks, 32 * RG_W, 0, stream>>>(a); note_launch();
+        return cudaGetLastError();
+    };
+    return ncand <= 4 ? go(k_rescore_tile<3>, k_rescore_general<3>) : go(k_rescore_tile<7>, k_rescore_general<7>);
 }
 
 }  // namespace pxst
