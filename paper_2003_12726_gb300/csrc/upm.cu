@@ -1110,7 +1110,7 @@ __device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, con
 // the window are dropped at the end) and the variance is the pixel's own over all frames.
 constexpr int RT_TY = 8;                      // detector rows per tile (one warp each)
 constexpr int RT_THREADS = 32 * RT_TY;
-constexpr int RT_PREFETCH = 8;                // frames in flight per thread
+constexpr int RT_PREFETCH = 16;               // frames in flight per thread
 constexpr int RT_SMEM = 110 * 1024;           // dynamic shared memory per CTA: two CTAs per SM
 
 // R at window index q for the shift's fraction (fy, fx), by the masked renormalised rule with
@@ -1133,77 +1133,20 @@ __device__ __forceinline__ bool gather_win(const float *__restrict__ src, int st
     return true;
 }
 
+// The frame loop of k_rescore_tile: sums, over every frame, the errors of the 3x3 about c0
+// (acc[0..3] in pairs, acc[4] = (ninth point, variance)) and of the other kept candidates
+// (ex), reading the reference at window index base + the frame's shift from `src` (the
+// staged window, pitch WS, or the masked reference, pitch Rx). Frames stream through a
+// register double buffer RT_PREFETCH deep.
 template <int XK>
-__global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
-    extern __shared__ __align__(16) unsigned char rt_raw[];
-    FrameShift *s_sh = reinterpret_cast<FrameShift *>(rt_raw);
-    float *s_win = reinterpret_cast<float *>(s_sh + (sh_staged ? a.N : 0));
-    const FrameShift *sh = sh_staged ? s_sh : a.shifts;
-    __shared__ int s_box[4];
+__device__ __forceinline__ void rescore_frames(const RescoreArgs &a, const PixCands<XK> &pc,
+                                               const float *__restrict__ src, int WS, int base0,
+                                               const int (&xb)[PixCands<XK>::NX], int nxw,
+                                               const FrameShift *__restrict__ sh, size_t pix, float2 (&acc)[5],
+                                               float (&ex)[PixCands<XK>::NX]) {
     const size_t P = (size_t)a.ny * a.nx;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + lane, y = blockIdx.y * RT_TY + wid;
-    const bool inb = x < a.nx && y < a.ny;
-    const size_t pix = inb ? (size_t)y * a.nx + x : 0;
-    if (threadIdx.x < 4) s_box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
-    if (sh_staged)
-        for (int n = threadIdx.x; n < a.N; n += RT_THREADS) s_sh[n] = a.shifts[n];
-    PixCands<XK> pc;
-    pix_setup<XK>(a, pix, inb, pc);
-    const bool lean = __all_sync(0xffffffffu, pix_lean<XK>(a, pc));
-    if (!lean) {
-        // the per-frame rule is needed somewhere in this row segment: the general kernel
-        if (lane == 0 && y < a.ny)
-            a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)((size_t)y * a.nx + blockIdx.x * 32);
-        pc.act = pc.run = false;
-    }
-    __syncthreads();
-    // the box of every candidate the tile's lean pixels evaluate
-    if (pc.run) {
-        int y0 = pc.y0 - 1, y1 = pc.y0 + 1, x0 = pc.x0 - 1, x1 = pc.x0 + 1;
-#pragma unroll
-        for (int q = 0; q < XK; ++q)
-            if (q < pc.nxk) {
-                y0 = min(y0, pc.xy[q]); y1 = max(y1, pc.xy[q]);
-                x0 = min(x0, pc.xx[q]); x1 = max(x1, pc.xx[q]);
-            }
-        atomicMin(&s_box[0], y0); atomicMax(&s_box[1], y1);
-        atomicMin(&s_box[2], x0); atomicMax(&s_box[3], x1);
-    }
-    __syncthreads();
-    const bool any = s_box[0] != INT_MAX;
-    // the window: the box widened by the shifts' integer range (+1 row and column for the
-    // second corner of a fractional shift); lean pixels read only on the grid
-    const int wy0 = any ? s_box[0] + a.hdr->kmin_y : 0, wy1 = any ? s_box[1] + a.hdr->kmax_y + 1 : 0;
-    const int wx0 = any ? s_box[2] + a.hdr->kmin_x : 0, wx1 = any ? s_box[3] + a.hdr->kmax_x + 1 : 0;
-    long long WSl = (long long)wx1 - wx0 + 1;
-    WSl += (WSl & 1) ? 0 : 1;                       // odd row pitch: rows read by a warp spread over banks
-    const long long WHl = (long long)wy1 - wy0 + 1;
-    const bool staged = any && WSl * WHl <= win_cap;
-    const int WS = staged ? (int)WSl : a.Rx;
-    if (staged) {
-        const int WN = (int)(WSl * WHl);
-        const float qnan = __int_as_float(0x7fc00000);
-        for (int idx = threadIdx.x; idx < WN; idx += RT_THREADS) {
-            const int gy = wy0 + idx / WS, gx = wx0 + idx % WS;
-            s_win[idx] = (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) ? __ldg(a.Rm + (size_t)gy * a.Rx + gx) : qnan;
-        }
-    }
-    __syncthreads();
-    if (!pc.act) return;
-    const float *src = staged ? s_win : a.Rm;
-    // window indices of c0 and of the other kept candidates for a zero shift
-    const int base0 = staged ? (pc.y0 - wy0) * WS + (pc.x0 - wx0) : pc.base0;
-    int xb[PixCands<XK>::NX];
-#pragma unroll
-    for (int q = 0; q < XK; ++q) xb[q] = staged ? (pc.xy[q] - wy0) * WS + (pc.xx[q] - wx0) : pc.xbase[q];
-    const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
-    // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
-    // packed FMA advances two sums
-    float2 acc[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) acc[k] = make_float2(0.0f, 0.0f);
-    float ex[PixCands<XK>::NX];
 #pragma unroll
     for (int q = 0; q < XK; ++q) ex[q] = 0.0f;
     const float Wv = pc.Wv;
@@ -1272,6 +1215,81 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
             }
         }
     }
+}
+
+template <int XK>
+__global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
+    extern __shared__ __align__(16) unsigned char rt_raw[];
+    FrameShift *s_sh = reinterpret_cast<FrameShift *>(rt_raw);
+    float *s_win = reinterpret_cast<float *>(s_sh + (sh_staged ? a.N : 0));
+    const FrameShift *sh = sh_staged ? s_sh : a.shifts;
+    __shared__ int s_box[4];
+    const size_t P = (size_t)a.ny * a.nx;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane, y = blockIdx.y * RT_TY + wid;
+    const bool inb = x < a.nx && y < a.ny;
+    const size_t pix = inb ? (size_t)y * a.nx + x : 0;
+    if (threadIdx.x < 4) s_box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    if (sh_staged)
+        for (int n = threadIdx.x; n < a.N; n += RT_THREADS) s_sh[n] = a.shifts[n];
+    PixCands<XK> pc;
+    pix_setup<XK>(a, pix, inb, pc);
+    const bool lean = __all_sync(0xffffffffu, pix_lean<XK>(a, pc));
+    if (!lean) {
+        // the per-frame rule is needed somewhere in this row segment: the general kernel
+        if (lane == 0 && y < a.ny)
+            a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)((size_t)y * a.nx + blockIdx.x * 32);
+        pc.act = pc.run = false;
+    }
+    __syncthreads();
+    // the box of every candidate the tile's lean pixels evaluate
+    if (pc.run) {
+        int y0 = pc.y0 - 1, y1 = pc.y0 + 1, x0 = pc.x0 - 1, x1 = pc.x0 + 1;
+#pragma unroll
+        for (int q = 0; q < XK; ++q)
+            if (q < pc.nxk) {
+                y0 = min(y0, pc.xy[q]); y1 = max(y1, pc.xy[q]);
+                x0 = min(x0, pc.xx[q]); x1 = max(x1, pc.xx[q]);
+            }
+        atomicMin(&s_box[0], y0); atomicMax(&s_box[1], y1);
+        atomicMin(&s_box[2], x0); atomicMax(&s_box[3], x1);
+    }
+    __syncthreads();
+    const bool any = s_box[0] != INT_MAX;
+    // the window: the box widened by the shifts' integer range (+1 row and column for the
+    // second corner of a fractional shift); lean pixels read only on the grid
+    const int wy0 = any ? s_box[0] + a.hdr->kmin_y : 0, wy1 = any ? s_box[1] + a.hdr->kmax_y + 1 : 0;
+    const int wx0 = any ? s_box[2] + a.hdr->kmin_x : 0, wx1 = any ? s_box[3] + a.hdr->kmax_x + 1 : 0;
+    long long WSl = (long long)wx1 - wx0 + 1;
+    WSl += (WSl & 1) ? 0 : 1;                       // odd row pitch: rows read by a warp spread over banks
+    const long long WHl = (long long)wy1 - wy0 + 1;
+    const bool staged = any && WSl * WHl <= win_cap;
+    const int WS = staged ? (int)WSl : a.Rx;
+    if (staged) {
+        const int WN = (int)(WSl * WHl);
+        const float qnan = __int_as_float(0x7fc00000);
+        for (int idx = threadIdx.x; idx < WN; idx += RT_THREADS) {
+            const int gy = wy0 + idx / WS, gx = wx0 + idx % WS;
+            s_win[idx] = (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) ? __ldg(a.Rm + (size_t)gy * a.Rx + gx) : qnan;
+        }
+    }
+    __syncthreads();
+    if (!pc.act) return;
+    // window indices of c0 and of the other kept candidates for a zero shift
+    const int base0 = staged ? (pc.y0 - wy0) * WS + (pc.x0 - wx0) : pc.base0;
+    int xb[PixCands<XK>::NX];
+#pragma unroll
+    for (int q = 0; q < XK; ++q) xb[q] = staged ? (pc.xy[q] - wy0) * WS + (pc.xx[q] - wx0) : pc.xbase[q];
+    const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
+    // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
+    // packed FMA advances two sums
+    float2 acc[5];
+    float ex[PixCands<XK>::NX];
+    // staged: shared-memory loads from the window (a pointer the compiler knows is shared)
+    if (staged)
+        rescore_frames<XK>(a, pc, s_win, WS, base0, xb, nxw, sh, pix, acc, ex);
+    else
+        rescore_frames<XK>(a, pc, a.Rm, WS, base0, xb, nxw, sh, pix, acc, ex);
     // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
     const float var = acc[4].y;
     float f9[9], fxe[PixCands<XK>::NX];
