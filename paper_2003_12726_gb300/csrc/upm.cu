@@ -1217,14 +1217,142 @@ __device__ __forceinline__ void rescore_frames(const RescoreArgs &a, const PixCa
     }
 }
 
+// The frame loop for scans whose translations are all whole pixels, reading the staged
+// window: per frame one shared-memory offset and the reads at c0's 3x3 and the other kept
+// candidates, no per-frame test; 16 frames per chunk without a bound check inside it, so
+// the compiler can overlap one frame's reads with the previous frame's arithmetic.
+template <int XK>
+__device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const PixCands<XK> &pc,
+                                                   const float *__restrict__ win, const int *__restrict__ offs,
+                                                   int WS, int base0, const int (&xb)[PixCands<XK>::NX], int nxw,
+                                                   size_t pix, float2 (&acc)[5], float (&ex)[PixCands<XK>::NX]) {
+    const size_t P = (size_t)a.ny * a.nx;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < XK; ++q) ex[q] = 0.0f;
+    const float Wv = pc.Wv;
+    const float2 nW2 = make_float2(-Wv, -Wv);
+    const bool run = pc.run;
+    const float *fp = a.frames + pix;
+    const float *c0 = win + base0;
+    auto one = [&](float I, int off) {
+        const float2 I2 = make_float2(I, I);
+        const float *r0 = c0 + off;
+        const float R[9] = {r0[-WS - 1], r0[-WS], r0[-WS + 1], r0[-1], r0[0], r0[1], r0[WS - 1], r0[WS], r0[WS + 1]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 d = __ffma2_rn(nW2, make_float2(R[2 * k], R[2 * k + 1]), I2);
+            acc[k] = __ffma2_rn(d, d, acc[k]);
+        }
+        const float2 d8 = __ffma2_rn(nW2, make_float2(R[8], 1.0f), I2);
+        acc[4] = __ffma2_rn(d8, d8, acc[4]);
+#pragma unroll
+        for (int q = 0; q < XK; ++q) {
+            if (q >= nxw) break;
+            const float d = fmaf(-Wv, win[xb[q] + off], I);
+            ex[q] = fmaf(d, d, ex[q]);
+        }
+    };
+    float In[RT_PREFETCH];
+#pragma unroll
+    for (int jf = 0; jf < RT_PREFETCH; ++jf) In[jf] = (run && jf < a.N) ? __ldcs(fp + (size_t)jf * P) : 0.0f;
+    int n0 = 0;
+    for (; n0 + RT_PREFETCH <= a.N; n0 += RT_PREFETCH) {
+        float Iv[RT_PREFETCH];
+#pragma unroll
+        for (int jf = 0; jf < RT_PREFETCH; ++jf) {
+            Iv[jf] = In[jf];
+            const int m = n0 + RT_PREFETCH + jf;
+            In[jf] = (run && m < a.N) ? __ldcs(fp + (size_t)m * P) : 0.0f;
+        }
+        if (!run) continue;
+#pragma unroll
+        for (int jf = 0; jf < RT_PREFETCH; ++jf) one(Iv[jf], offs[n0 + jf]);
+    }
+    if (run)
+        for (int jf = 0; n0 + jf < a.N; ++jf) one(In[jf], offs[n0 + jf]);
+}
+
+// The per-frame rule on the staged window (for the row segments with a candidate that is
+// not valid in every frame): every candidate sums its error and variance over the frames
+// in which its masked renormalised read is valid (window cells off the grid or uncovered
+// are NaN); e = err / var (err if var = 0, +inf with no valid frame).
+template <int XK>
+__device__ __forceinline__ void rescore_frames_rule(const RescoreArgs &a, const PixCands<XK> &pc,
+                                                    const float *__restrict__ win, int WS, int base0,
+                                                    const int (&xb)[PixCands<XK>::NX],
+                                                    const FrameShift *__restrict__ sh, size_t pix, float (&f9)[9],
+                                                    float (&fxe)[PixCands<XK>::NX]) {
+    const size_t P = (size_t)a.ny * a.nx;
+    CandSums s9[9], sx[PixCands<XK>::NX];
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) s9[jn].zero();
+#pragma unroll
+    for (int q = 0; q < XK; ++q) sx[q].zero();
+    const float Wv = pc.Wv;
+    const bool run = pc.run;
+    const float *fp = a.frames + pix;
+    float In[RT_PREFETCH];
+#pragma unroll
+    for (int jf = 0; jf < RT_PREFETCH; ++jf) In[jf] = (run && jf < a.N) ? __ldcs(fp + (size_t)jf * P) : 0.0f;
+    for (int n0 = 0; n0 < a.N; n0 += RT_PREFETCH) {
+        float Iv[RT_PREFETCH];
+#pragma unroll
+        for (int jf = 0; jf < RT_PREFETCH; ++jf) {
+            Iv[jf] = In[jf];
+            const int m = n0 + RT_PREFETCH + jf;
+            In[jf] = (run && m < a.N) ? __ldcs(fp + (size_t)m * P) : 0.0f;
+        }
+        if (!run) continue;
+        for (int jf = 0; jf < RT_PREFETCH && n0 + jf < a.N; ++jf) {
+            const FrameShift sft = sh[n0 + jf];
+            const float I = Iv[jf], tt = I - Wv;
+            const int off = sft.ky * WS + sft.kx;
+            const bool whole = sft.fy == 0.0f && sft.fx == 0.0f;
+#pragma unroll
+            for (int jn = 0; jn < 9; ++jn) {
+                if (!pc.in9[jn]) continue;
+                const int q = base0 + off + (jn / 3 - 1) * WS + (jn % 3 - 1);
+                float R = 0.0f;
+                bool ok;
+                if (whole) {
+                    R = win[q];
+                    ok = R == R;
+                } else {
+                    ok = gather_win(win, WS, q, sft.fy, sft.fx, R);
+                }
+                s9[jn].add(ok, R, I, tt, Wv);
+            }
+#pragma unroll
+            for (int q = 0; q < XK; ++q) {
+                if (q >= pc.nxk) continue;
+                float R = 0.0f;
+                bool ok;
+                if (whole) {
+                    R = win[xb[q] + off];
+                    ok = R == R;
+                } else {
+                    ok = gather_win(win, WS, xb[q] + off, sft.fy, sft.fx, R);
+                }
+                sx[q].add(ok, R, I, tt, Wv);
+            }
+        }
+    }
+#pragma unroll
+    for (int jn = 0; jn < 9; ++jn) f9[jn] = pc.in9[jn] ? s9[jn].e() : INFINITY;
+#pragma unroll
+    for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? sx[q].e() : INFINITY;
+}
+
 template <int XK>
 __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
     extern __shared__ __align__(16) unsigned char rt_raw[];
     FrameShift *s_sh = reinterpret_cast<FrameShift *>(rt_raw);
-    float *s_win = reinterpret_cast<float *>(s_sh + (sh_staged ? a.N : 0));
+    int *s_off = reinterpret_cast<int *>(s_sh + (sh_staged ? a.N : 0));     // whole-pixel shifts: window offsets
+    float *s_win = reinterpret_cast<float *>(s_off + (sh_staged ? a.N : 0));
     const FrameShift *sh = sh_staged ? s_sh : a.shifts;
     __shared__ int s_box[4];
-    const size_t P = (size_t)a.ny * a.nx;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int x = blockIdx.x * 32 + lane, y = blockIdx.y * RT_TY + wid;
     const bool inb = x < a.nx && y < a.ny;
@@ -1235,14 +1363,8 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
     PixCands<XK> pc;
     pix_setup<XK>(a, pix, inb, pc);
     const bool lean = __all_sync(0xffffffffu, pix_lean<XK>(a, pc));
-    if (!lean) {
-        // the per-frame rule is needed somewhere in this row segment: the general kernel
-        if (lane == 0 && y < a.ny)
-            a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)((size_t)y * a.nx + blockIdx.x * 32);
-        pc.act = pc.run = false;
-    }
     __syncthreads();
-    // the box of every candidate the tile's lean pixels evaluate
+    // the box of every candidate the tile's pixels evaluate
     if (pc.run) {
         int y0 = pc.y0 - 1, y1 = pc.y0 + 1, x0 = pc.x0 - 1, x1 = pc.x0 + 1;
 #pragma unroll
@@ -1257,14 +1379,20 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
     __syncthreads();
     const bool any = s_box[0] != INT_MAX;
     // the window: the box widened by the shifts' integer range (+1 row and column for the
-    // second corner of a fractional shift); lean pixels read only on the grid
+    // second corner of a fractional shift); cells off the grid are NaN (not valid)
     const int wy0 = any ? s_box[0] + a.hdr->kmin_y : 0, wy1 = any ? s_box[1] + a.hdr->kmax_y + 1 : 0;
     const int wx0 = any ? s_box[2] + a.hdr->kmin_x : 0, wx1 = any ? s_box[3] + a.hdr->kmax_x + 1 : 0;
     long long WSl = (long long)wx1 - wx0 + 1;
     WSl += (WSl & 1) ? 0 : 1;                       // odd row pitch: rows read by a warp spread over banks
     const long long WHl = (long long)wy1 - wy0 + 1;
-    const bool staged = any && WSl * WHl <= win_cap;
+    const bool staged = sh_staged && any && WSl * WHl <= win_cap;
     const int WS = staged ? (int)WSl : a.Rx;
+    if (!lean && !staged) {
+        // the per-frame rule without a staged window: the general kernel takes this segment
+        if (lane == 0 && y < a.ny)
+            a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)((size_t)y * a.nx + blockIdx.x * 32);
+        pc.act = pc.run = false;
+    }
     if (staged) {
         const int WN = (int)(WSl * WHl);
         const float qnan = __int_as_float(0x7fc00000);
@@ -1272,6 +1400,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
             const int gy = wy0 + idx / WS, gx = wx0 + idx % WS;
             s_win[idx] = (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) ? __ldg(a.Rm + (size_t)gy * a.Rx + gx) : qnan;
         }
+        for (int n = threadIdx.x; n < a.N; n += RT_THREADS) s_off[n] = s_sh[n].ky * WS + s_sh[n].kx;
     }
     __syncthreads();
     if (!pc.act) return;
@@ -1280,26 +1409,34 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
     int xb[PixCands<XK>::NX];
 #pragma unroll
     for (int q = 0; q < XK; ++q) xb[q] = staged ? (pc.xy[q] - wy0) * WS + (pc.xx[q] - wx0) : pc.xbase[q];
-    const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
-    // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
-    // packed FMA advances two sums
-    float2 acc[5];
-    float ex[PixCands<XK>::NX];
-    // staged: shared-memory loads from the window (a pointer the compiler knows is shared)
-    if (staged)
-        rescore_frames<XK>(a, pc, s_win, WS, base0, xb, nxw, sh, pix, acc, ex);
-    else
-        rescore_frames<XK>(a, pc, a.Rm, WS, base0, xb, nxw, sh, pix, acc, ex);
-    // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
-    const float var = acc[4].y;
     float f9[9], fxe[PixCands<XK>::NX];
+    if (lean) {
+        const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
+        // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
+        // packed FMA advances two sums
+        float2 acc[5];
+        float ex[PixCands<XK>::NX];
+        // whole-pixel translations only (one fraction class, zero): the loop without tests
+        const bool whole = a.hdr->n_classes == 1 && a.hdr->cls_fy[0] == 0.0f && a.hdr->cls_fx[0] == 0.0f;
+        // staged: shared-memory loads from the window (a pointer the compiler knows is shared)
+        if (staged && whole)
+            rescore_frames_int<XK>(a, pc, s_win, s_off, WS, base0, xb, nxw, pix, acc, ex);
+        else if (staged)
+            rescore_frames<XK>(a, pc, s_win, WS, base0, xb, nxw, sh, pix, acc, ex);
+        else
+            rescore_frames<XK>(a, pc, a.Rm, WS, base0, xb, nxw, sh, pix, acc, ex);
+        // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
+        const float var = acc[4].y;
 #pragma unroll
-    for (int jn = 0; jn < 9; ++jn) {
-        const float e = (jn & 1) ? acc[jn >> 1].y : acc[jn >> 1].x;
-        f9[jn] = pc.in9[jn] ? (var > 0.0f ? e / var : e) : INFINITY;
+        for (int jn = 0; jn < 9; ++jn) {
+            const float e = (jn & 1) ? acc[jn >> 1].y : acc[jn >> 1].x;
+            f9[jn] = pc.in9[jn] ? (var > 0.0f ? e / var : e) : INFINITY;
+        }
+#pragma unroll
+        for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? (var > 0.0f ? ex[q] / var : ex[q]) : INFINITY;
+    } else {
+        rescore_frames_rule<XK>(a, pc, s_win, WS, base0, xb, sh, pix, f9, fxe);
     }
-#pragma unroll
-    for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? (var > 0.0f ? ex[q] / var : ex[q]) : INFINITY;
     pix_finish<XK>(a, pix, pc, f9, fxe);
 }
 
@@ -1522,7 +1659,7 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
     const unsigned gblocks = tgrid.x * (unsigned)d.ny;          // at most one per row segment
     // the shift table (when it leaves room) and the window share the CTA's part of shared
     // memory; a window that does not fit is read through the cache
-    const long long shifts_b = (long long)sizeof(FrameShift) * d.n_frames;
+    const long long shifts_b = (long long)(sizeof(FrameShift) + sizeof(int)) * d.n_frames;
     const int sh_staged = shifts_b <= RT_SMEM / 2 ? 1 : 0;
     const int smem = RT_SMEM;
     const int win_cap = (int)((smem - (sh_staged ? shifts_b : 0)) / 4);
