@@ -92,7 +92,8 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
         L.Rm = off;     off += align256(sizeof(float) * R);
         L.cand = off;   off += align256(sizeof(int) * kTopK * P);
         L.edge = off;   off += align256(P);
-        L.wlist = off;  off += align256(sizeof(int) * (P / 32 + 1));   // warps for the general rescore
+        // row segments of 32 pixels left to the general rescore (one per row and 32 columns)
+        L.wlist = off;  off += align256(sizeof(int) * ((size_t)d.ny * ((d.nx + 31) / 32) + 1));
     }
     L.total = off;
     return L;
