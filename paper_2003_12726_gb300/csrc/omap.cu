@@ -97,8 +97,6 @@ constexpr int SC_THREADS = SC_TX * SC_TY;
 constexpr int SC_CAP = 12288;                          // cells (num + den: 96 KB): 2 CTAs per SM
 constexpr int SC_PREFETCH = 8;                         // frames in flight while the previous 8 scatter
 constexpr int SC_GROUP_MAX = 512;                      // frames per group (their shifts in shared memory)
-constexpr int SC_OWN = 2;                              // gather form: footprint cells per thread
-constexpr int SC_K = 4;                                // gather form: contributions per cell
 
 struct ScatterArgs {
     int N, ny, nx, Ry, Rx, chunk;
@@ -123,7 +121,6 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     __shared__ int s_rng[4];
     __shared__ int s_grp[6];       // group [start, end), footprint origin r0, c0, height, width
     __shared__ __align__(16) FrameShift s_sh[SC_GROUP_MAX];   // the group's shifts
-    __shared__ float s_frb[2 * SC_THREADS];                   // gather form: the tile's frame values
 
     const int x = blockIdx.x * SC_TX + (threadIdx.x % SC_TX);
     const int y = blockIdx.y * SC_TY + (threadIdx.x / SC_TX);
@@ -170,104 +167,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     const bool dom = act && iy >= 0 && iy <= a.Ry - 3 && ix >= 0 && ix <= a.Rx - 3;
     const float WW = (split && dom) ? 0.0f : Wv * Wv;
     const int lane = threadIdx.x & 31;
-    // some pixel of the CTA adds its weights in the scatter (the gather form then adds them too)
-    const bool warp_den_cta = __syncthreads_or(act && WW != 0.0f) != 0;
 
-    // ---- gather form (one fraction class): the scatter turned around inside the tile ----------
-    // With every frame's fraction the same, pixel p adds b_k W I_n(p) (and b_k W^2) at the
-    // corners corner_k(p) + k_n, where corner_k and b_k do not depend on the frame. So the
-    // tile's zero-shift footprint F0 (the corners of all its pixels) receives, at each cell,
-    // the same few (pixel, weight) contributions in every frame, moved by the frame's shift.
-    // Each thread owns up to SC_OWN cells of F0 and keeps their contributions (at most SC_K,
-    // in pixel order) in registers; per frame it sums them from the tile's frame values (in
-    // shared memory) and adds the sum to its cells moved by the shift: one plain read-modify-
-    // write per cell, no atomics (distinct cells of F0 stay distinct after one shift; the
-    // frames are separated by a barrier).
-    int gby = 0, gbx = 0;
-    float gw[4] = {0.0f, 0.0f, 0.0f, 0.0f}, gd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (uniform) {
-        float sy = fy + a.hdr->cls_fy[0], sx = fx + a.hdr->cls_fx[0];
-        gby = iy; gbx = ix;
-        if (sy >= 1.0f) { sy -= 1.0f; gby += 1; }
-        if (sx >= 1.0f) { sx -= 1.0f; gbx += 1; }
-        const float b[4] = {(1.0f - sy) * (1.0f - sx), (1.0f - sy) * sx, sy * (1.0f - sx), sy * sx};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            gw[k] = act ? b[k] * Wv : 0.0f;
-            gd[k] = act ? b[k] * WW : 0.0f;
-        }
-    }
-    // F0's origin and size: s_rng holds the range of floor(u); a carry adds one, a corner one
-    const int f_y0 = s_rng[0], f_x0 = s_rng[2];
-    const int f_w = s_rng[3] - s_rng[2] + 3, f_h = s_rng[1] - s_rng[0] + 3;
-    const bool gather_fit = uniform && (long long)f_w * f_h <= (long long)SC_OWN * SC_THREADS &&
-                            2 * SC_CAP >= f_w * f_h * SC_K * 3;
-    int own_n[SC_OWN];
-    unsigned own_p[SC_OWN][SC_K / 2];                  // contributing pixels, two 16-bit indices each
-    float own_w[SC_OWN][SC_K], own_d[SC_OWN];
-    __shared__ int s_over;
-    bool gather = false;
-    if (gather_fit) {
-        // build the contribution lists in the accumulators' space (cleared before the groups)
-        int *cnt = reinterpret_cast<int *>(s_num);                 // [f_h * f_w]
-        int *lp = cnt + f_w * f_h;                                  // [cell][SC_K] pixel
-        float *lw = reinterpret_cast<float *>(lp + f_w * f_h * SC_K);   // weight b W
-        float *ld = s_den;                                          // [cell][SC_K] weight b W^2
-        for (int c = threadIdx.x; c < f_w * f_h; c += SC_THREADS) cnt[c] = 0;
-        if (threadIdx.x == 0) s_over = 0;
-        __syncthreads();
-        if (act)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (gw[k] == 0.0f && gd[k] == 0.0f) continue;
-                const int c = (gby + (k >> 1) - f_y0) * f_w + (gbx + (k & 1) - f_x0);
-                const int slot = atomicAdd(&cnt[c], 1);
-                if (slot < SC_K) {
-                    lp[c * SC_K + slot] = threadIdx.x;
-                    lw[c * SC_K + slot] = gw[k];
-                    ld[c * SC_K + slot] = gd[k];
-                } else {
-                    s_over = 1;
-                }
-            }
-        __syncthreads();
-        gather = s_over == 0;
-#pragma unroll
-        for (int o = 0; o < SC_OWN; ++o) {
-            const int c = threadIdx.x + o * SC_THREADS;
-            const int m = (gather && c < f_w * f_h) ? min(cnt[c], SC_K) : 0;
-            own_n[o] = m;
-            // the cell's contributions in pixel order (the same sum whatever order they arrived in)
-            int pp[SC_K];
-            float ww[SC_K], dd[SC_K];
-#pragma unroll
-            for (int j = 0; j < SC_K; ++j) {
-                pp[j] = j < m ? lp[c * SC_K + j] : INT_MAX;
-                ww[j] = j < m ? lw[c * SC_K + j] : 0.0f;
-                dd[j] = j < m ? ld[c * SC_K + j] : 0.0f;
-            }
-#pragma unroll
-            for (int i = 1; i < SC_K; ++i)
-#pragma unroll
-                for (int j = SC_K - 1; j >= i; --j)
-                    if (pp[j] < pp[j - 1]) {
-                        const int tp = pp[j]; pp[j] = pp[j - 1]; pp[j - 1] = tp;
-                        const float tw = ww[j]; ww[j] = ww[j - 1]; ww[j - 1] = tw;
-                        const float td = dd[j]; dd[j] = dd[j - 1]; dd[j - 1] = td;
-                    }
-            float dsum = 0.0f;
-#pragma unroll
-            for (int j = 0; j < SC_K; ++j) {
-                own_w[o][j] = ww[j];
-                dsum += dd[j];
-            }
-#pragma unroll
-            for (int j = 0; j < SC_K / 2; ++j)
-                own_p[o][j] = (unsigned)(2 * j < m ? pp[2 * j] : 0) | ((unsigned)(2 * j + 1 < m ? pp[2 * j + 1] : 0) << 16);
-            own_d[o] = dsum;
-        }
-        __syncthreads();                                  // the lists leave the accumulators' space
-    }
 
     for (int gs = n0; gs < n1;) {
         if (threadIdx.x == 0) {
@@ -465,57 +365,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 }
             }
         };
-        // the gather form: per frame, the tile's frame values go to shared memory (two
-        // buffers), then every thread adds its cells' sums at the frame's shift
-        auto frames_loop_gather = [&](auto den_tag) {
-            constexpr bool DEN = decltype(den_tag)::value;
-            float *s_fr = s_frb;                                   // [2][SC_THREADS]
-            int cb[SC_OWN];
-#pragma unroll
-            for (int o = 0; o < SC_OWN; ++o) {
-                const int c = threadIdx.x + o * SC_THREADS;
-                cb[o] = (f_y0 + c / f_w - r0) * Wd + (f_x0 + c % f_w - c0);
-            }
-            float In[SC_PREFETCH];
-#pragma unroll
-            for (int jf = 0; jf < SC_PREFETCH; ++jf)
-                In[jf] = (act && g0 + jf < g1) ? __ldcs(a.frames + (size_t)(g0 + jf) * P + pix) : 0.0f;
-            for (int n = g0; n < g1; n += SC_PREFETCH) {
-                float I[SC_PREFETCH];
-#pragma unroll
-                for (int jf = 0; jf < SC_PREFETCH; ++jf) {
-                    I[jf] = In[jf];
-                    const int m = n + SC_PREFETCH + jf;
-                    In[jf] = (act && m < g1) ? __ldcs(a.frames + (size_t)m * P + pix) : 0.0f;
-                }
-#pragma unroll
-                for (int jf = 0; jf < SC_PREFETCH; ++jf) {
-                    if (n + jf >= g1) break;                    // uniform over the CTA
-                    float *fb = s_fr + ((n + jf) & 1) * SC_THREADS;
-                    fb[threadIdx.x] = I[jf];
-                    __syncthreads();
-                    const FrameShift S = s_sh[n + jf - g0];
-                    const int off = S.ky * Wd + S.kx;
-#pragma unroll
-                    for (int o = 0; o < SC_OWN; ++o) {
-                        if (own_n[o] == 0) continue;
-                        // unused slots have weight 0 and read pixel 0
-                        float v = own_w[o][0] * fb[own_p[o][0] & 0xffffu];
-#pragma unroll
-                        for (int j = 1; j < SC_K; ++j)
-                            v = fmaf(own_w[o][j], fb[(own_p[o][j >> 1] >> (16 * (j & 1))) & 0xffffu], v);
-                        s_num[cb[o] + off] += v;
-                        if (DEN && own_d[o] != 0.0f) s_den[cb[o] + off] += own_d[o];
-                    }
-                }
-            }
-        };
-        if (gather && fits) {
-            if (warp_den_cta)
-                frames_loop_gather(std::true_type{});
-            else
-                frames_loop_gather(std::false_type{});
-        } else if (uniform && fits) {
+        if (uniform && fits) {
             if (warp_den)
                 frames_loop_uniform(std::true_type{});
             else
