@@ -1110,8 +1110,8 @@ __device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, con
 // the window are dropped at the end) and the variance is the pixel's own over all frames.
 constexpr int RT_TY = 8;                      // detector rows per tile (one warp each)
 constexpr int RT_THREADS = 32 * RT_TY;
-constexpr int RT_PREFETCH = 16;               // frames in flight per thread
-constexpr int RT_SMEM = 110 * 1024;           // dynamic shared memory per CTA: two CTAs per SM
+constexpr int RT_PREFETCH = 8;                // frames in flight per thread
+constexpr int RT_SMEM = 72 * 1024;            // dynamic shared memory per CTA: three CTAs per SM
 
 // R at window index q for the shift's fraction (fy, fx), by the masked renormalised rule with
 // the arithmetic of gather_rm (corners NaN where uncovered); false: no valid corner.
@@ -1140,8 +1140,7 @@ __device__ __forceinline__ bool gather_win(const float *__restrict__ src, int st
 // register double buffer RT_PREFETCH deep.
 template <int XK>
 __device__ __forceinline__ void rescore_frames(const RescoreArgs &a, const PixCands<XK> &pc,
-                                               const float *__restrict__ src, int WS, int base0,
-                                               const int (&xb)[PixCands<XK>::NX], int nxw,
+                                               const float *__restrict__ src, int WS, int base0, int nxw,
                                                const FrameShift *__restrict__ sh, size_t pix, float2 (&acc)[5],
                                                float (&ex)[PixCands<XK>::NX]) {
     const size_t P = (size_t)a.ny * a.nx;
@@ -1187,7 +1186,7 @@ __device__ __forceinline__ void rescore_frames(const RescoreArgs &a, const PixCa
 #pragma unroll
                 for (int q = 0; q < XK; ++q) {
                     if (q >= nxw) break;
-                    const float d = fmaf(-Wv, src[xb[q] + off], I);
+                    const float d = fmaf(-Wv, __ldg(a.Rm + (pc.xbase[q] + sft.ky * a.Rx + sft.kx)), I);
                     ex[q] = fmaf(d, d, ex[q]);
                 }
             } else {
@@ -1207,7 +1206,7 @@ __device__ __forceinline__ void rescore_frames(const RescoreArgs &a, const PixCa
                 for (int q = 0; q < XK; ++q) {
                     if (q >= nxw) break;
                     float R;
-                    if (gather_win(src, WS, xb[q] + off, sft.fy, sft.fx, R)) {
+                    if (gather_rm(a.Rm, a.Ry, a.Rx, pc.xy[q] + sft.ky, pc.xx[q] + sft.kx, sft.fy, sft.fx, R)) {
                         const float d = fmaf(-Wv, R, I);
                         ex[q] = fmaf(d, d, ex[q]);
                     }
@@ -1224,7 +1223,7 @@ __device__ __forceinline__ void rescore_frames(const RescoreArgs &a, const PixCa
 template <int XK>
 __device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const PixCands<XK> &pc,
                                                    const float *__restrict__ win, const int *__restrict__ offs,
-                                                   int WS, int base0, const int (&xb)[PixCands<XK>::NX], int nxw,
+                                                   const int *__restrict__ offg, int WS, int base0, int nxw,
                                                    size_t pix, float2 (&acc)[5], float (&ex)[PixCands<XK>::NX]) {
     const size_t P = (size_t)a.ny * a.nx;
 #pragma unroll
@@ -1236,7 +1235,7 @@ __device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const P
     const bool run = pc.run;
     const float *fp = a.frames + pix;
     const float *c0 = win + base0;
-    auto one = [&](float I, int off) {
+    auto one = [&](float I, int off, int og) {
         const float2 I2 = make_float2(I, I);
         const float *r0 = c0 + off;
         const float R[9] = {r0[-WS - 1], r0[-WS], r0[-WS + 1], r0[-1], r0[0], r0[1], r0[WS - 1], r0[WS], r0[WS + 1]};
@@ -1250,7 +1249,7 @@ __device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const P
 #pragma unroll
         for (int q = 0; q < XK; ++q) {
             if (q >= nxw) break;
-            const float d = fmaf(-Wv, win[xb[q] + off], I);
+            const float d = fmaf(-Wv, __ldg(a.Rm + (pc.xbase[q] + og)), I);
             ex[q] = fmaf(d, d, ex[q]);
         }
     };
@@ -1268,10 +1267,10 @@ __device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const P
         }
         if (!run) continue;
 #pragma unroll
-        for (int jf = 0; jf < RT_PREFETCH; ++jf) one(Iv[jf], offs[n0 + jf]);
+        for (int jf = 0; jf < RT_PREFETCH; ++jf) one(Iv[jf], offs[n0 + jf], offg[n0 + jf]);
     }
     if (run)
-        for (int jf = 0; n0 + jf < a.N; ++jf) one(In[jf], offs[n0 + jf]);
+        for (int jf = 0; n0 + jf < a.N; ++jf) one(In[jf], offs[n0 + jf], offg[n0 + jf]);
 }
 
 // The per-frame rule on the staged window (for the row segments with a candidate that is
@@ -1281,7 +1280,6 @@ __device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const P
 template <int XK>
 __device__ __forceinline__ void rescore_frames_rule(const RescoreArgs &a, const PixCands<XK> &pc,
                                                     const float *__restrict__ win, int WS, int base0,
-                                                    const int (&xb)[PixCands<XK>::NX],
                                                     const FrameShift *__restrict__ sh, size_t pix, float (&f9)[9],
                                                     float (&fxe)[PixCands<XK>::NX]) {
     const size_t P = (size_t)a.ny * a.nx;
@@ -1328,13 +1326,7 @@ __device__ __forceinline__ void rescore_frames_rule(const RescoreArgs &a, const 
             for (int q = 0; q < XK; ++q) {
                 if (q >= pc.nxk) continue;
                 float R = 0.0f;
-                bool ok;
-                if (whole) {
-                    R = win[xb[q] + off];
-                    ok = R == R;
-                } else {
-                    ok = gather_win(win, WS, xb[q] + off, sft.fy, sft.fx, R);
-                }
+                const bool ok = read_any(a, pc.xy[q], pc.xx[q], pc.xbase[q], pc.xsafe[q], sft, R);
                 sx[q].add(ok, R, I, tt, Wv);
             }
         }
@@ -1346,11 +1338,12 @@ __device__ __forceinline__ void rescore_frames_rule(const RescoreArgs &a, const 
 }
 
 template <int XK>
-__global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
+__global__ void __launch_bounds__(RT_THREADS, XK <= 3 ? 3 : 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
     extern __shared__ __align__(16) unsigned char rt_raw[];
     FrameShift *s_sh = reinterpret_cast<FrameShift *>(rt_raw);
     int *s_off = reinterpret_cast<int *>(s_sh + (sh_staged ? a.N : 0));     // whole-pixel shifts: window offsets
-    float *s_win = reinterpret_cast<float *>(s_off + (sh_staged ? a.N : 0));
+    int *s_offg = s_off + (sh_staged ? a.N : 0);                             // ... and offsets in the reference
+    float *s_win = reinterpret_cast<float *>(s_offg + (sh_staged ? a.N : 0));
     const FrameShift *sh = sh_staged ? s_sh : a.shifts;
     __shared__ int s_box[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1364,17 +1357,11 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
     pix_setup<XK>(a, pix, inb, pc);
     const bool lean = __all_sync(0xffffffffu, pix_lean<XK>(a, pc));
     __syncthreads();
-    // the box of every candidate the tile's pixels evaluate
+    // the box of the 3x3s about the tile's first candidates (the other kept candidates, a
+    // few per pixel anywhere in the window, are read through the cache)
     if (pc.run) {
-        int y0 = pc.y0 - 1, y1 = pc.y0 + 1, x0 = pc.x0 - 1, x1 = pc.x0 + 1;
-#pragma unroll
-        for (int q = 0; q < XK; ++q)
-            if (q < pc.nxk) {
-                y0 = min(y0, pc.xy[q]); y1 = max(y1, pc.xy[q]);
-                x0 = min(x0, pc.xx[q]); x1 = max(x1, pc.xx[q]);
-            }
-        atomicMin(&s_box[0], y0); atomicMax(&s_box[1], y1);
-        atomicMin(&s_box[2], x0); atomicMax(&s_box[3], x1);
+        atomicMin(&s_box[0], pc.y0 - 1); atomicMax(&s_box[1], pc.y0 + 1);
+        atomicMin(&s_box[2], pc.x0 - 1); atomicMax(&s_box[3], pc.x0 + 1);
     }
     __syncthreads();
     const bool any = s_box[0] != INT_MAX;
@@ -1400,15 +1387,15 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
             const int gy = wy0 + idx / WS, gx = wx0 + idx % WS;
             s_win[idx] = (gy >= 0 && gy < a.Ry && gx >= 0 && gx < a.Rx) ? __ldg(a.Rm + (size_t)gy * a.Rx + gx) : qnan;
         }
-        for (int n = threadIdx.x; n < a.N; n += RT_THREADS) s_off[n] = s_sh[n].ky * WS + s_sh[n].kx;
+        for (int n = threadIdx.x; n < a.N; n += RT_THREADS) {
+            s_off[n] = s_sh[n].ky * WS + s_sh[n].kx;
+            s_offg[n] = s_sh[n].ky * a.Rx + s_sh[n].kx;
+        }
     }
     __syncthreads();
     if (!pc.act) return;
-    // window indices of c0 and of the other kept candidates for a zero shift
+    // window index of c0 for a zero shift
     const int base0 = staged ? (pc.y0 - wy0) * WS + (pc.x0 - wx0) : pc.base0;
-    int xb[PixCands<XK>::NX];
-#pragma unroll
-    for (int q = 0; q < XK; ++q) xb[q] = staged ? (pc.xy[q] - wy0) * WS + (pc.xx[q] - wx0) : pc.xbase[q];
     float f9[9], fxe[PixCands<XK>::NX];
     if (lean) {
         const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
@@ -1420,11 +1407,11 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
         const bool whole = a.hdr->n_classes == 1 && a.hdr->cls_fy[0] == 0.0f && a.hdr->cls_fx[0] == 0.0f;
         // staged: shared-memory loads from the window (a pointer the compiler knows is shared)
         if (staged && whole)
-            rescore_frames_int<XK>(a, pc, s_win, s_off, WS, base0, xb, nxw, pix, acc, ex);
+            rescore_frames_int<XK>(a, pc, s_win, s_off, s_offg, WS, base0, nxw, pix, acc, ex);
         else if (staged)
-            rescore_frames<XK>(a, pc, s_win, WS, base0, xb, nxw, sh, pix, acc, ex);
+            rescore_frames<XK>(a, pc, s_win, WS, base0, nxw, sh, pix, acc, ex);
         else
-            rescore_frames<XK>(a, pc, a.Rm, WS, base0, xb, nxw, sh, pix, acc, ex);
+            rescore_frames<XK>(a, pc, a.Rm, WS, base0, nxw, sh, pix, acc, ex);
         // every evaluated candidate was valid in all N frames: e = err / var (err if var = 0)
         const float var = acc[4].y;
 #pragma unroll
@@ -1435,7 +1422,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_rescore_tile(RescoreArgs a, i
 #pragma unroll
         for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? (var > 0.0f ? ex[q] / var : ex[q]) : INFINITY;
     } else {
-        rescore_frames_rule<XK>(a, pc, s_win, WS, base0, xb, sh, pix, f9, fxe);
+        rescore_frames_rule<XK>(a, pc, s_win, WS, base0, sh, pix, f9, fxe);
     }
     pix_finish<XK>(a, pix, pc, f9, fxe);
 }
@@ -1659,7 +1646,7 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
     const unsigned gblocks = tgrid.x * (unsigned)d.ny;          // at most one per row segment
     // the shift table (when it leaves room) and the window share the CTA's part of shared
     // memory; a window that does not fit is read through the cache
-    const long long shifts_b = (long long)(sizeof(FrameShift) + sizeof(int)) * d.n_frames;
+    const long long shifts_b = (long long)(sizeof(FrameShift) + 2 * sizeof(int)) * d.n_frames;
     const int sh_staged = shifts_b <= RT_SMEM / 2 ? 1 : 0;
     const int smem = RT_SMEM;
     const int win_cap = (int)((smem - (sh_staged ? shifts_b : 0)) / 4);
