@@ -46,11 +46,19 @@ typedef int32_t pxst_status;
 #define PXST_ERR_CUDA     (-4)   /* a CUDA runtime call failed                         */
 #define PXST_ERR_NOMEM    (-5)   /* workspace smaller than pxst_workspace_size()       */
 #define PXST_ERR_TIMEOUT  (-6)   /* a device-side wait gave up                         */
+#define PXST_ERR_INPUT    (-7)   /* device saw a non-finite frame value, or a whitefield
+                                    value that is not finite and positive, at a pixel
+                                    with M = 1                                          */
 
 /* Device status bits (pxst_get_status reports the most severe as a pxst_status). */
 #define PXST_DEV_NONFINITE_U  0x1
 #define PXST_DEV_U_RANGE      0x2
 #define PXST_DEV_TIMEOUT      0x4
+#define PXST_DEV_BAD_INPUT    0x8   /* see PXST_ERR_INPUT. A pixel with a bad whitefield value
+                                       is treated as masked (keeps its map, error NaN, adds
+                                       nothing to the reference image); a non-finite frame value
+                                       adds nothing to the reference image, and its pixel keeps
+                                       its map with error +inf (no candidate has a finite error) */
 
 typedef struct {
     int32_t n_frames;   /* N  >= 1 */
@@ -82,7 +90,9 @@ typedef struct {
                               columns per strip. Tensor forms: 0 = 8 x 16 pixels
                               against 8 x 32 candidates, 1 = 4 x 32 / 4 x 64, 2 = 2 x 64 /
                               2 x 128. Any other value is PXST_ERR_ARG. */
-    int64_t timeout_ns;    /* reserved for device-side waits (0 = default) */
+    int64_t timeout_ns;    /* limit of every device-side wait of the call, in ns (the
+                              tensor forms' pipeline waits); 0 = 1 s. A wait that runs out
+                              sets PXST_DEV_TIMEOUT and the kernel returns without hanging */
 } pxst_options;
 
 /* Bytes of workspace needed by every entry point below for these sizes. */
@@ -171,8 +181,25 @@ pxst_status pxst_reference_terms(const pxst_dims *dims, const float *I_ref, cons
                                  const double *delta, float *T, int32_t *n_valid,
                                  void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * wait_flag -- a stream-ordered wait for an external producer, for reconstructions that
+ * start while the scan is still being acquired: the kernels queued on `stream` after this
+ * call run once the 32-bit value at `flag` is >= `target` (the producer -- a host thread
+ * writing pinned host memory, which is device-accessible under unified addressing, or a
+ * copy into device memory -- raises it, for instance to the number of frames it has
+ * written). One GPU thread polls it, with back-off, for at most timeout_ns (> 0; 0 = 1 s);
+ * if the value has not arrived by then it sets PXST_DEV_TIMEOUT in the workspace's status
+ * word and returns, so the stream never hangs: pxst_get_status then reports
+ * PXST_ERR_TIMEOUT (the work queued after the wait has run on whatever the inputs held).
+ * The producer must not be a kernel that could be waiting for a slot on the GPU.
+ * Not described in the paper: it serves the acquisition loop around the method.
+ */
+pxst_status pxst_wait_flag(const int32_t *flag, int32_t target, int64_t timeout_ns, void *workspace,
+                           size_t ws_bytes, void *stream);
+
 /* Synchronise `stream`, then return (and clear) the device status word in `workspace`:
- * PXST_OK, PXST_ERR_RANGE or PXST_ERR_TIMEOUT. `bits_out` (nullable) gets the raw bits. */
+ * PXST_OK, PXST_ERR_RANGE, PXST_ERR_INPUT or PXST_ERR_TIMEOUT (the most severe, in the
+ * order timeout, range, input). `bits_out` (nullable) gets the raw bits. */
 pxst_status pxst_get_status(void *workspace, void *stream, int32_t *bits_out);
 
 /* Number of pixels of the last update on this workspace that needed the per-frame

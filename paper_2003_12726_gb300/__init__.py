@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "invalid shape", -3: "range", -4: "cuda error",
-          -5: "workspace too small", -6: "timeout"}
+          -5: "workspace too small", -6: "timeout", -7: "bad input"}
 FORM_FP32 = 0
 FORM_BF16 = 1
 FORM_TF32 = 2
@@ -97,6 +97,8 @@ def lib():
         L.pxst_version.restype = C.c_char_p
         L.pxst_launch_count.argtypes = [C.POINTER(i64)]
         L.pxst_launch_count.restype = i32
+        L.pxst_wait_flag.argtypes = [P, i32, i64, P, sz, P]
+        L.pxst_wait_flag.restype = i32
         L.pxst_tensor_check.argtypes = [i32, i32, P, P, P, P, P]
         L.pxst_tensor_check.restype = i32
         S = C.POINTER(_Scan)
@@ -130,7 +132,8 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_timing_enable", "pxst_timing_read", "pxst_kernel_name", "pxst_status_string",
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
             "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations",
-            "pxst_filter_map", "pxst_update_pixel_map_fractional", "pxst_defocus_sweep", "pxst_launch_count"]
+            "pxst_filter_map", "pxst_update_pixel_map_fractional", "pxst_defocus_sweep", "pxst_launch_count",
+            "pxst_wait_flag"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -184,9 +187,11 @@ class Options:
     form: int = FORM_FP32
     rescore_k: int = 0      # tensor forms: 4 or 8 (0: 8 below 128 frames, else 4)
     tile: int = 0           # tile shape (0: automatic); see pxst_options.tile
+    timeout_ns: int = 0     # limit of the device-side waits (0: 1 s)
 
     def c(self):
-        return _Opts(self.win_y, self.win_x, 1 if self.quadratic else 0, self.form, self.rescore_k, self.tile, 0)
+        return _Opts(self.win_y, self.win_x, 1 if self.quadratic else 0, self.form, self.rescore_k, self.tile,
+                     self.timeout_ns)
 
 
 def workspace_size(dims: Dims, opts: Options | None = None):
@@ -303,6 +308,19 @@ def timing_read():
 
 def version():
     return lib().pxst_version().decode()
+
+
+def wait_flag(flag, target, timeout_ns, ws, stream=None):
+    """pxst_wait_flag: the work queued on `stream` after this call runs once the int32 at
+    `flag` (a CUDA tensor, or a pinned CPU tensor, which the GPU reads through unified
+    addressing) is >= target; gives up after timeout_ns (the status then reports a timeout)."""
+    torch = _torch()
+    if not isinstance(flag, torch.Tensor) or flag.dtype != torch.int32 or flag.numel() < 1:
+        raise TypeError("flag must be an int32 tensor")
+    if not flag.is_cuda and not flag.is_pinned():
+        raise ValueError("flag must be on a CUDA device or in pinned host memory")
+    _raise(lib().pxst_wait_flag(C.c_void_p(flag.data_ptr()), int(target), int(timeout_ns), C.c_void_p(ws.data_ptr()),
+                                ws.numel(), _stream(stream)), "wait_flag")
 
 
 def launch_count():

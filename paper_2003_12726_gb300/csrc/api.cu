@@ -29,6 +29,7 @@ bool opts_ok(const pxst_options *o) {
     if (o->quadratic != 0 && o->quadratic != 1) return false;
     if (o->form != PXST_FORM_FP32 && o->form != PXST_FORM_BF16 && o->form != PXST_FORM_TF32) return false;
     if (o->rescore_k != 0 && o->rescore_k != 4 && o->rescore_k != 8) return false;
+    if (o->timeout_ns < 0) return false;
     const int ty = o->tile & 15, ls = o->tile >> 4;
     if (o->form == PXST_FORM_FP32 ? (o->tile < 0 || ls > 3 || (ty != 0 && ty != 1 && ty != 2 && ty != 4 && ty != 8))
                                   : (o->tile < 0 || o->tile > 2))
@@ -223,7 +224,7 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
         // best few per pixel and of the 3x3 about the minimum
         if (!operands_ready) {
             Timed t(PXST_K_TPREP, s);
-            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, s));
+            PXST_TRY(launch_tprep(d, o.form, w.Npad, frames, W, mask, w.At, w.hdr, s));
         }
         {
             Timed t(PXST_K_GTABLE, s);
@@ -337,7 +338,7 @@ pxst_status pxst_iterate(const pxst_dims *dims, const pxst_options *opts, int32_
     if (st != PXST_OK) return st;
     if (opts->form != PXST_FORM_FP32 && n_iter > 0) {
         Timed t(PXST_K_TPREP, s);
-        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, s));
+        PXST_TRY(launch_tprep(*dims, opts->form, ws.Npad, frames, W, mask, ws.At, ws.hdr, s));
     }
     for (int it = 0; it < n_iter; ++it) {
         st = run_omap(*dims, frames, W, mask, u_inout, I_ref, w, ws, s);
@@ -486,6 +487,7 @@ pxst_status pxst_get_status(void *workspace, void *stream, int32_t *bits_out) {
     if (bits_out) *bits_out = bits;
     if (bits & PXST_DEV_TIMEOUT) return PXST_ERR_TIMEOUT;
     if (bits & (PXST_DEV_NONFINITE_U | PXST_DEV_U_RANGE)) return PXST_ERR_RANGE;
+    if (bits & PXST_DEV_BAD_INPUT) return PXST_ERR_INPUT;
     return PXST_OK;
 }
 
@@ -562,6 +564,7 @@ const char *pxst_status_string(pxst_status s) {
         case PXST_ERR_CUDA: return "CUDA runtime error";
         case PXST_ERR_NOMEM: return "workspace too small";
         case PXST_ERR_TIMEOUT: return "device-side wait timed out";
+        case PXST_ERR_INPUT: return "non-finite frame value or non-positive whitefield at a good pixel";
         default: return "unknown status";
     }
 }

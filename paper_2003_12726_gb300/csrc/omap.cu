@@ -151,9 +151,15 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 if (fy >= 1.0f) { fy = 0.0f; iy += 1; }
                 if (fx >= 1.0f) { fx = 0.0f; ix += 1; }
                 Wv = a.W[pix];
-                act = true;
-                atomicMin(&s_rng[0], iy); atomicMax(&s_rng[1], iy);
-                atomicMin(&s_rng[2], ix); atomicMax(&s_rng[3], ix);
+                if (!(Wv > 0.0f) || !isfinite(Wv)) {
+                    // the forward model needs a positive whitefield: the pixel adds nothing
+                    atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
+                    Wv = 0.0f;
+                } else {
+                    act = true;
+                    atomicMin(&s_rng[0], iy); atomicMax(&s_rng[1], iy);
+                    atomicMin(&s_rng[2], ix); atomicMax(&s_rng[3], ix);
+                }
             }
         }
     }
@@ -164,6 +170,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
     const bool split = a.dcls != nullptr && a.hdr->n_classes <= kMaxClasses;
     // one fraction class for every frame (set by k_prepare from the translations)
     const bool uniform = a.hdr->n_classes == 1;
+    bool bad_frame = false;
     const bool dom = act && iy >= 0 && iy <= a.Ry - 3 && ix >= 0 && ix <= a.Rx - 3;
     const float WW = (split && dom) ? 0.0f : Wv * Wv;
     const int lane = threadIdx.x & 31;
@@ -223,7 +230,9 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 float I[SC_PREFETCH];
 #pragma unroll
                 for (int jf = 0; jf < SC_PREFETCH; ++jf) {
-                    I[jf] = In[jf];
+                    // a non-finite frame value adds nothing (and is reported below)
+                    bad_frame |= !isfinite(In[jf]);
+                    I[jf] = isfinite(In[jf]) ? In[jf] : 0.0f;
                     const int m = n + SC_PREFETCH + jf;
                     In[jf] = (act && m < g1) ? __ldcs(a.frames + (size_t)m * P + pix) : 0.0f;
                 }
@@ -336,7 +345,9 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
                 float I[SC_PREFETCH];
 #pragma unroll
                 for (int jf = 0; jf < SC_PREFETCH; ++jf) {
-                    I[jf] = In[jf];
+                    // a non-finite frame value adds nothing (and is reported below)
+                    bad_frame |= !isfinite(In[jf]);
+                    I[jf] = isfinite(In[jf]) ? In[jf] : 0.0f;
                     const int m = n + SC_PREFETCH + jf;
                     In[jf] = (act && m < g1) ? __ldcs(a.frames + (size_t)m * P + pix) : 0.0f;
                 }
@@ -389,6 +400,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_scatter(ScatterArgs a) {
         __syncthreads();
         gs = g1;
     }
+    if (bad_frame) atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
 }
 
 // ------------------------------------------------------------------------------------
@@ -426,6 +438,7 @@ __global__ void __launch_bounds__(256) k_dscatter(int ny, int nx, int Ry, int Rx
     if (fx >= 1.0f) { fx = 0.0f; ix += 1; }
     if (iy < 0 || iy > Ry - 3 || ix < 0 || ix > Rx - 3) return;      // k_scatter adds these
     const float Wv = W[pix], WW = Wv * Wv;
+    if (!(Wv > 0.0f) || !isfinite(Wv)) return;                       // reported by k_scatter
     int by = iy, bx = ix;
     float sy = fy + hdr->cls_fy[f], sx = fx + hdr->cls_fx[f];
     if (sy >= 1.0f) { sy -= 1.0f; by += 1; }

@@ -148,7 +148,7 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
                            float *err_out, cudaStream_t stream);
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
-                         const uint8_t *mask, void *At, cudaStream_t stream);
+                         const uint8_t *mask, void *At, WsHeader *hdr, cudaStream_t stream);
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
                           const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
                           cudaStream_t stream);

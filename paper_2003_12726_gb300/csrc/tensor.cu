@@ -143,7 +143,8 @@ constexpr int TP_PIX = 64;
 template <typename T>
 __global__ void __launch_bounds__(256) k_tprep(int N, int ny, int nx, const float *__restrict__ frames,
                                                const float *__restrict__ W,
-                                               const uint8_t *__restrict__ mask, T *__restrict__ At) {
+                                               const uint8_t *__restrict__ mask, T *__restrict__ At,
+                                               WsHeader *__restrict__ hdr) {
     constexpr int KB = 128 / sizeof(T);       // frames per operand row
     constexpr int EPP = 16 / sizeof(T);       // elements per 16-byte piece
     __shared__ float tile[KB][TP_PIX + 1];
@@ -152,15 +153,20 @@ __global__ void __launch_bounds__(256) k_tprep(int N, int ny, int nx, const floa
     const int kb = blockIdx.y, n0 = kb * KB;
     const int col = threadIdx.x & (TP_PIX - 1), r0 = threadIdx.x / TP_PIX;   // 4 rows of 64
     const size_t p = p0 + col;
-    const bool on = p < P && mask[p];
+    const float Wp = p < P ? __ldg(W + p) : 0.0f;
+    const bool on = p < P && mask[p] && Wp > 0.0f && isfinite(Wp);   // usable pixels only
     // the operand only ranks candidates, so I * (1/W) stands in for I / W
-    const float rw = on ? __frcp_rn(__ldg(W + p)) : 0.0f;
+    const float rw = on ? __frcp_rn(Wp) : 0.0f;
     float f[KB / 4];
 #pragma unroll
     for (int i = 0; i < KB / 4; ++i) {            // every load in flight before the first use
         const int n = n0 + r0 + 4 * i;
         f[i] = (on && n < N) ? __ldcs(frames + (size_t)n * P + p) : 0.0f;
     }
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < KB / 4; ++i) bad |= !isfinite(f[i]);
+    if (bad) atomicOr(&hdr->status, PXST_DEV_BAD_INPUT);
 #pragma unroll
     for (int i = 0; i < KB / 4; ++i) {
         const int n = n0 + r0 + 4 * i;
@@ -313,6 +319,7 @@ struct TSearchArgs {
     int tiles_x;        // tiles per detector row (to decode a listed tile)
     const float *W;     // masked ranking: the whitefield (the key of a zero-variance candidate)
     int ares;           // first pass: 0 = A~ streams with G~; k > 0 = A~ resident, k G~ stages
+    unsigned long long limit_ns;   // bound of every pipeline wait (pxst_options.timeout_ns)
 };
 
 // Insert (qv, idx) into the ascending list bq/bi when it beats an entry (strict <, so of
@@ -460,7 +467,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
         if (x < a.nx && y < a.ny) {
             const size_t pix = (size_t)y * a.nx + x;
             const double u0 = a.u[pix], u1 = a.u[P + pix];
-            if (a.mask[pix] && isfinite(u0) && isfinite(u1) && fabs(u0) <= kMaxCoord && fabs(u1) <= kMaxCoord) {
+            const float Wp = a.W[pix];
+            if (a.mask[pix] && isfinite(u0) && isfinite(u1) && fabs(u0) <= kMaxCoord && fabs(u1) <= kMaxCoord &&
+                Wp > 0.0f && isfinite(Wp)) {
                 ci = (int)floor(u0 + 0.5);
                 cj = (int)floor(u1 + 0.5);
                 act = 1;
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                 chunk_origin(j, row0, col0);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % NS;
-                    if (!tc::mbar_wait(&bar_empty[s], ((it / NS) & 1) ^ 1, abortp)) {
+                    if (!tc::mbar_wait(&bar_empty[s], ((it / NS) & 1) ^ 1, abortp, a.limit_ns)) {
                         *abortp = 1;
                         break;
                     }
@@ -559,21 +568,21 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             for (int k = 0; k < NS && k < it; ++k) {
                 const int i2 = it - 1 - k, s = i2 % NS;
                 volatile int never = 0;
-                tc::mbar_wait(&bar_full[s], (i2 / NS) & 1, &never);
+                tc::mbar_wait(&bar_full[s], (i2 / NS) & 1, &never, a.limit_ns);
             }
             if (ares) {
                 volatile int never = 0;
-                tc::mbar_wait(&bar_afull, 0, &never);
+                tc::mbar_wait(&bar_afull, 0, &never, a.limit_ns);
             }
         }
     } else if (warp == 1) {
         // ---- MMA issuer -------------------------------------------------------------------
         if (lane == 0) {
             int it = 0;
-            if (ares && !tc::mbar_wait(&bar_afull, 0, abortp)) *abortp = 1;
+            if (ares && !tc::mbar_wait(&bar_afull, 0, abortp, a.limit_ns)) *abortp = 1;
             for (int j = 0; j < nchunks && !*abortp; ++j) {
                 const int buf = j % NBUF;
-                if (!tc::mbar_wait(&bar_tempty[buf], ((j / NBUF) & 1) ^ 1, abortp)) {
+                if (!tc::mbar_wait(&bar_tempty[buf], ((j / NBUF) & 1) ^ 1, abortp, a.limit_ns)) {
                     *abortp = 1;
                     break;
                 }
@@ -581,7 +590,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
                 const uint32_t d = tmem + buf * 256;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % NS;
-                    if (!tc::mbar_wait(&bar_full[s], (it / NS) & 1, abortp)) {
+                    if (!tc::mbar_wait(&bar_full[s], (it / NS) & 1, abortp, a.limit_ns)) {
                         *abortp = 1;
                         break;
                     }
@@ -661,7 +670,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
             bool okn = false;
             if (j + 1 < nchunks && ew < 8) fetch(j + 1, tn, okn);
             // a wait that ran out stops every epilogue warp after the same barrier below
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], (j / NBUF) & 1, abortp));
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], (j / NBUF) & 1, abortp, a.limit_ns));
             if (!ok) *abortp = 1;
             tc::tc_fence_after();
             if (ok) {
@@ -752,15 +761,16 @@ __global__ void __launch_bounds__(TS_THREADS, 1) k_tsearch(const __grid_constant
 // ---- host launchers for the precision form --------------------------------------------------
 
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
-                         const uint8_t *mask, void *At, cudaStream_t stream) {
+                         const uint8_t *mask, void *At, WsHeader *hdr, cudaStream_t stream) {
     const size_t P = (size_t)d.ny * d.nx;
     const int KB = form == PXST_FORM_TF32 ? 32 : 64;
     dim3 grid((unsigned)((P + TP_PIX - 1) / TP_PIX), (unsigned)(Npad / KB));
     if (form == PXST_FORM_TF32)
-        k_tprep<float><<<grid, 256, 0, stream>>>(d.n_frames, d.ny, d.nx, frames, W, mask, static_cast<float *>(At));
+        k_tprep<float><<<grid, 256, 0, stream>>>(d.n_frames, d.ny, d.nx, frames, W, mask, static_cast<float *>(At),
+                                                 hdr);
     else
         k_tprep<__nv_bfloat16><<<grid, 256, 0, stream>>>(d.n_frames, d.ny, d.nx, frames, W, mask,
-                                                         static_cast<__nv_bfloat16 *>(At));
+                                                         static_cast<__nv_bfloat16 *>(At), hdr);
     note_launch();
     return cudaGetLastError();
 }
@@ -810,6 +820,7 @@ cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, 
     a.N = d.n_frames; a.Npad = Npad; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.mask = mask; a.u = u; a.Tt = Tt; a.nvalid = nvalid; a.hdr = hdr;
     a.cand = cand; a.edge = edge; a.tile_list = tile_list; a.W = W;
+    a.limit_ns = o.timeout_ns > 0 ? (unsigned long long)o.timeout_ns : 1000000000ull;
     const unsigned gx = (d.nx + 128 / pty - 1) / (128 / pty), gy = (d.ny + pty - 1) / pty;
     a.tiles_x = (int)gx;
     // list length: the candidates the rescore reads (4 unless more are asked for)

@@ -365,6 +365,10 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
                     atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
                 } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
                     atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
+                } else if (!(a.W[pix] > 0.0f) || !isfinite(a.W[pix])) {
+                    // not a usable whitefield value: the pixel is left as a masked one
+                    atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
+                    if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
                 } else {
                     ci = (int)floor(u0 + 0.5);
                     cj = (int)floor(u1 + 0.5);
@@ -397,6 +401,8 @@ __global__ void __launch_bounds__(kSearchThreads, (L <= 9 ? 3 : 2)) k_search(Sea
             v = fmaf(t, t, v);
         }
         s_var[p] = v;
+        // a non-finite frame value: every candidate's error is NaN, so the pixel keeps its map
+        if (!isfinite(v)) atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
     }
     for (int g = tid; g < NG; g += NT) {
         int mn_i = INT_MAX, mx_i = INT_MIN, mn_j = INT_MAX, mx_j = INT_MIN;
@@ -722,6 +728,13 @@ __global__ void __launch_bounds__(256) k_exact(ExactArgs a) {
                                                                              : PXST_DEV_U_RANGE);
                 continue;
             }
+            if (!(a.W[pix] > 0.0f) || !isfinite(a.W[pix])) {
+                if (lane == 0) {
+                    atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
+                    if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
+                }
+                continue;
+            }
         }
         const double u0 = a.u[pix], u1 = a.u[P + pix];
         const int ci = (int)floor(u0 + 0.5), cj = (int)floor(u1 + 0.5);
@@ -979,6 +992,10 @@ __device__ __forceinline__ void pix_setup(const RescoreArgs &a, size_t pix, bool
                 atomicOr(&a.hdr->status, PXST_DEV_NONFINITE_U);
             } else if (fabs(u0) > kMaxCoord || fabs(u1) > kMaxCoord) {
                 atomicOr(&a.hdr->status, PXST_DEV_U_RANGE);
+            } else if (!(a.W[pix] > 0.0f) || !isfinite(a.W[pix])) {
+                // not a usable whitefield value: the pixel is left as a masked one
+                atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
+                if (a.err_out) a.err_out[pix] = __int_as_float(0x7fc00000);
             } else {
                 pc.ci = (int)floor(u0 + 0.5);
                 pc.cj = (int)floor(u1 + 0.5);
@@ -1061,6 +1078,8 @@ __device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, con
     }
     const float be = __uint_as_float((unsigned int)(key >> 32));
     if (!(be < INFINITY)) {
+        // NaN errors of evaluated candidates come only from a non-finite frame value
+        if (pc.run && be != be) atomicOr(&a.hdr->status, PXST_DEV_BAD_INPUT);
         if (a.err_out) a.err_out[pix] = INFINITY;
         return;
     }

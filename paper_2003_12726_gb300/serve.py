@@ -8,7 +8,11 @@ through pxst_iterate) of each scan whose previous iteration has completed, on a 
 streams, so the iterations of scans admitted at different times run side by side on the
 GPU and a new scan joins at the next pass instead of waiting for the others to finish.
 A scan's completion time is a CUDA event after its last iteration; its latency is that
-time minus its arrival.
+time minus its arrival. A request whose scan is returned on the host (pinned CPU tensors) is
+copied to the device at admission, on the admission stream, so the copy counts in its
+latency. A request larger than the whole memory budget is rejected at once (it could never
+be admitted); a request can be cancelled at any time: it is dropped if still waiting, or its
+slot is freed after its iteration in flight, and the other scans are not affected.
 """
 from __future__ import annotations
 
@@ -37,6 +41,14 @@ class Request:
     done: float | None = None
     evals: int = 0
     result: dict | None = None
+    iterations_done: int = 0
+    cancelled: bool = False
+    rejected: str | None = None         # why the request was not admitted
+    charged_bytes: int = 0              # device bytes charged against the budget
+
+    def cancel(self):
+        """Drop the request: no further iteration is launched for it (safe from any thread)."""
+        self.cancelled = True
 
 
 @dataclass
@@ -83,18 +95,29 @@ class Server:
         torch.cuda.synchronize(self.device)
         t0 = time.perf_counter()
         peak_active = 0
+        peak_used = 0
         while pending or active:
             now = time.perf_counter() - t0
-            # admission: arrived, a slot free, memory available (one scan always fits)
+            # admission: arrived, a slot free, memory available
             while pending and (not realtime or pending[0].arrival <= now) and len(active) < self.max_active:
                 r = pending[0]
-                if active and used + r.est_bytes > self.budget:
+                if r.cancelled:
+                    pending.pop(0)
+                    continue
+                if r.est_bytes > self.budget:
+                    # it could never fit: rejected, and it does not hold up the requests behind it
+                    pending.pop(0)
+                    r.rejected = f"needs {r.est_bytes} B of device memory, the budget is {self.budget} B"
+                    continue
+                if used + r.est_bytes > self.budget:
                     break
                 pending.pop(0)
                 with torch.cuda.stream(self.admit_stream):
                     sc = r.make()
-                    rec = Reconstruction.from_device(sc.frames, sc.W, sc.M, sc.delta, sc.u_init, sc.ref_shape,
-                                                     sc.window, quadratic=r.quadratic, form=r.form, tile=r.tile)
+                    dev = lambda t: t.to(self.device, non_blocking=True) if not t.is_cuda else t
+                    rec = Reconstruction.from_device(dev(sc.frames), dev(sc.W), dev(sc.M), dev(sc.delta),
+                                                     dev(sc.u_init), sc.ref_shape, sc.window, quadratic=r.quadratic,
+                                                     form=r.form, tile=r.tile)
                 ready = torch.cuda.Event()
                 ready.record(self.admit_stream)
                 st = self.streams[nxt % len(self.streams)]
@@ -103,8 +126,12 @@ class Server:
                 r.admitted = time.perf_counter() - t0
                 r.evals = int(sc.M.sum().item()) * (2 * sc.window[0] + 1) * (2 * sc.window[1] + 1) * \
                     int(sc.frames.shape[0]) * r.n_iter
-                slot = _Slot(r, rec, st, torch.cuda.Event(enable_timing=True), nbytes=rec.device_bytes())
+                # charged: the larger of the estimate and what the scan holds
+                slot = _Slot(r, rec, st, torch.cuda.Event(enable_timing=True),
+                             nbytes=max(int(r.est_bytes), rec.device_bytes()))
+                r.charged_bytes = slot.nbytes
                 used += slot.nbytes
+                peak_used = max(peak_used, used)
                 active.append(slot)
             peak_active = max(peak_active, len(active))
             # one iteration of every scan whose previous one has finished
@@ -113,6 +140,12 @@ class Server:
                 if slot.inflight and not slot.event.query():
                     continue
                 slot.inflight = False
+                slot.req.iterations_done = slot.iters
+                if slot.req.cancelled:
+                    active.remove(slot)
+                    used -= slot.nbytes
+                    del slot
+                    continue
                 if slot.iters == slot.req.n_iter:
                     r = slot.req
                     r.done = t_start.elapsed_time(slot.event) / 1e3
@@ -136,12 +169,18 @@ class Server:
                     time.sleep(idle_sleep)
         torch.cuda.synchronize(self.device)
         wall = time.perf_counter() - t0
-        lat = np.array([r.done - r.arrival for r in requests])
-        span = max(r.done for r in requests) - min(r.arrival for r in requests)
-        return dict(scans=len(requests), wall_s=wall, span_s=span, scans_per_s=len(requests) / span,
-                    evals_per_s=sum(r.evals for r in requests) / span,
+        done = [r for r in requests if r.done is not None]
+        if not done:
+            return dict(scans=0, rejected=sum(r.rejected is not None for r in requests),
+                        cancelled=sum(r.cancelled for r in requests), wall_s=wall, peak_active=peak_active,
+                        peak_bytes=peak_used)
+        lat = np.array([r.done - r.arrival for r in done])
+        span = max(r.done for r in done) - min(r.arrival for r in done)
+        return dict(scans=len(done), rejected=sum(r.rejected is not None for r in requests),
+                    cancelled=sum(r.cancelled for r in requests), wall_s=wall, span_s=span,
+                    scans_per_s=len(done) / span, evals_per_s=sum(r.evals for r in done) / span,
                     p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
-                    mean_s=float(lat.mean()), peak_active=peak_active)
+                    mean_s=float(lat.mean()), peak_active=peak_active, peak_bytes=peak_used)
 
 
 def poisson_arrivals(n, rate, seed):
