@@ -62,6 +62,8 @@ def _bind(L):
     L.pxst_oracle_contrast.argtypes = [i64, P, P]
     L.pxst_oracle_contrast.restype = dbl
     L.pxst_oracle_defocus_sweep.argtypes = [i32] * 5 + [P] * 5 + [i32, P, i32, P, P]
+    L.pxst_oracle_integrate_map.argtypes = [i32, i32, P, P, i32, dbl, P, P]
+    L.pxst_oracle_integrate_map.restype = i32
     return L
 
 
@@ -291,3 +293,17 @@ def defocus_sweep(frames, W, M, u, delta, ref_shape, sy, sx, L=None):
     (L or lib()).pxst_oracle_defocus_sweep(N, ny, nx, ref_shape[0], ref_shape[1], _p(frames), _p(W), _p(M), _p(u),
                                            _p(delta), sy.size, _p(sy), sx.size, _p(sx), _p(out))
     return out
+
+
+def integrate_map(M, u, max_iter=100000, tol=1e-12, L=None):
+    """The "integrate" option (R17): least-squares integration of the map u [2][ny][nx] over
+    the good pixels by conjugate gradients and re-differentiation. Returns (u_out, steps,
+    relative residual)."""
+    L = L or lib()
+    ny, nx = M.shape
+    Mu = _u8(M)
+    uin = _f64(u)
+    out = np.empty_like(uin)
+    res = C.c_double(0.0)
+    it = L.pxst_oracle_integrate_map(ny, nx, _p(Mu), _p(uin), int(max_iter), float(tol), _p(out), C.byref(res))
+    return out, int(it), float(res.value)

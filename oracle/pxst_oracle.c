@@ -28,7 +28,9 @@
  *     the error evaluated at non-integer candidates (bilinear reads, section "Sub-pixel
  *     interpolation") instead of the paraboloid;
  *   - defocus_sweep, fit_defocus_registration of section "Initialisation": a reference
- *     image built for a range of magnifications, scored by its contrast.
+ *     image built for a range of magnifications, scored by its contrast;
+ *   - integrate_map, the "integrate" option of section "Update pixel mapping": the map made
+ *     irrotational by least-squares integration (conjugate gradients) and re-differentiation.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   R1  the bilinear weight multiplies both the M*W*I term and the M*W^2 term;
@@ -64,6 +66,11 @@
  *       u(x) - Delta_n - (a, b), of (I_n(x) - W(x) R)^2 / var(x) (a mean, not a sum, so
  *       that shifting pixels off the reference is not rewarded); +inf with no such pixel;
  *       argmin as R8, the fit as R10; Delta_n <- Delta_n + (a*, b*) + fit.
+ *   R17 integrate: the least-squares projection of the map onto discrete gradient fields
+ *       over the good pixels (central differences where both neighbours along an axis are
+ *       good, second-order one-sided ones where two on one side are, first-order where
+ *       only one is), solved by conjugate gradients on the normal equations; see
+ *       pxst_oracle_integrate_map.
  *
  * Array conventions: frames float32 [N][ny][nx]; W float32 [ny][nx]; M uint8 [ny][nx];
  * u float64 [2][ny][nx] (u[0] rows, u[1] columns, reference-pixel units);
@@ -526,6 +533,131 @@ void pxst_oracle_update_pixel_map_frac(int N, int ny, int nx, int Ry, int Rx, in
         }
         free(e);
     }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* the irrotational constraint (the "integrate" option of the update)                 */
+/* ---------------------------------------------------------------------------------- */
+
+/* R17 u is the gradient of a scalar (u = x - lambda z / (2 pi) grad Phi, section "Update
+ *     pixel mapping"): the map is integrated by least squares and differentiated again.
+ *     Equations, one per good pixel p and axis a (e = the unit step along a), each the
+ *     derivative of Psi at p along a set equal to u_a[p], by the first of these stencils
+ *     whose pixels are all good:
+ *        central          (Psi[p+e] - Psi[p-e]) / 2
+ *        forward, 2nd ord (-3 Psi[p] + 4 Psi[p+e] - Psi[p+2e]) / 2
+ *        backward, 2nd ord (3 Psi[p] - 4 Psi[p-e] + Psi[p-2e]) / 2
+ *        forward          Psi[p+e] - Psi[p]
+ *        backward         Psi[p] - Psi[p-e]
+ *     (none if p has no good neighbour along a). Psi on the good pixels minimises the sum of
+ *     squared residuals, by conjugate gradients on the normal equations G^T G Psi = G^T u
+ *     from Psi = 0, until |G^T (u - G Psi)| <= tol |G^T u| or max_iter steps; the output is
+ *     u_a[p] = (G Psi) of each equation (a pixel and axis with no equation, and every M = 0
+ *     pixel, keep u). Every stencil but the last two is exact for a quadratic Psi. Returns
+ *     the steps taken; *resid gets the final relative residual. */
+
+/* the stencil of pixel (i, j) on axis a: n taps at offsets off[k] (in steps along a) with
+ * coefficients c[k]; n = 0: no equation */
+static int integ_stencil(int ny, int nx, const uint8_t *M, int i, int j, int a, int off[3], double c[3]) {
+    if (!M[(size_t)i * nx + j]) return 0;
+    const int len = a == 0 ? ny : nx, pos = a == 0 ? i : j;
+#define GOOD(k) (pos + (k) >= 0 && pos + (k) < len && M[(size_t)(a == 0 ? i + (k) : i) * nx + (a == 0 ? j : j + (k))])
+    if (GOOD(1) && GOOD(-1)) { off[0] = 1; c[0] = 0.5; off[1] = -1; c[1] = -0.5; return 2; }
+    if (GOOD(1) && GOOD(2)) { off[0] = 0; c[0] = -1.5; off[1] = 1; c[1] = 2.0; off[2] = 2; c[2] = -0.5; return 3; }
+    if (GOOD(-1) && GOOD(-2)) { off[0] = 0; c[0] = 1.5; off[1] = -1; c[1] = -2.0; off[2] = -2; c[2] = 0.5; return 3; }
+    if (GOOD(1)) { off[0] = 1; c[0] = 1.0; off[1] = 0; c[1] = -1.0; return 2; }
+    if (GOOD(-1)) { off[0] = 0; c[0] = 1.0; off[1] = -1; c[1] = -1.0; return 2; }
+#undef GOOD
+    return 0;
+}
+
+/* g = G psi: one value per pixel and axis (0 where there is no equation) */
+static void integ_apply_G(int ny, int nx, const uint8_t *M, const double *psi, double *g) {
+    const size_t P = (size_t)ny * nx;
+    for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                const size_t p = (size_t)i * nx + j;
+                const long step = a == 0 ? nx : 1;
+                int off[3];
+                double c[3];
+                const int n = integ_stencil(ny, nx, M, i, j, a, off, c);
+                double v = 0.0;
+                for (int k = 0; k < n; ++k) v += c[k] * psi[(long)p + off[k] * step];
+                g[a * P + p] = v;
+            }
+}
+
+/* y = G^T g: every equation adds its coefficients times its value to the pixels it reads */
+static void integ_apply_GT(int ny, int nx, const uint8_t *M, const double *g, double *y) {
+    const size_t P = (size_t)ny * nx;
+    for (size_t p = 0; p < P; ++p) y[p] = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                const size_t p = (size_t)i * nx + j;
+                const long step = a == 0 ? nx : 1;
+                int off[3];
+                double c[3];
+                const int n = integ_stencil(ny, nx, M, i, j, a, off, c);
+                for (int k = 0; k < n; ++k) y[(long)p + off[k] * step] += c[k] * g[a * P + p];
+            }
+}
+
+static double integ_dot(size_t n, const double *x, const double *y) {
+    double s = 0.0;
+    for (size_t k = 0; k < n; ++k) s += x[k] * y[k];
+    return s;
+}
+
+int pxst_oracle_integrate_map(int ny, int nx, const uint8_t *M, const double *u_in, int max_iter, double tol,
+                              double *u_out, double *resid) {
+    const size_t P = (size_t)ny * nx;
+    double *psi = calloc(P, sizeof(double)), *r = calloc(P, sizeof(double)), *d = calloc(P, sizeof(double));
+    double *q = calloc(P, sizeof(double)), *g = calloc(2 * P, sizeof(double)), *b = calloc(P, sizeof(double));
+    double *ue = calloc(2 * P, sizeof(double));
+    /* the data of each equation (0 where there is none) */
+    for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                const size_t p = (size_t)i * nx + j;
+                int off[3];
+                double c[3];
+                ue[a * P + p] = integ_stencil(ny, nx, M, i, j, a, off, c) ? u_in[a * P + p] : 0.0;
+            }
+    integ_apply_GT(ny, nx, M, ue, b);                      /* b = G^T u */
+    for (size_t p = 0; p < P; ++p) { r[p] = b[p]; d[p] = b[p]; }
+    const double bb = integ_dot(P, b, b);
+    double rr = bb;
+    int it = 0;
+    while (it < max_iter && rr > tol * tol * bb && bb > 0.0) {
+        integ_apply_G(ny, nx, M, d, g);                    /* q = G^T G d */
+        integ_apply_GT(ny, nx, M, g, q);
+        const double dq = integ_dot(P, d, q);
+        if (!(dq > 0.0)) break;
+        const double alpha = rr / dq;
+        for (size_t p = 0; p < P; ++p) {
+            psi[p] += alpha * d[p];
+            r[p] -= alpha * q[p];
+        }
+        const double rr_new = integ_dot(P, r, r);
+        const double beta = rr_new / rr;
+        for (size_t p = 0; p < P; ++p) d[p] = r[p] + beta * d[p];
+        rr = rr_new;
+        ++it;
+    }
+    if (resid) *resid = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    integ_apply_G(ny, nx, M, psi, g);
+    for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                const size_t p = (size_t)i * nx + j;
+                int off[3];
+                double c[3];
+                u_out[a * P + p] = integ_stencil(ny, nx, M, i, j, a, off, c) ? g[a * P + p] : u_in[a * P + p];
+            }
+    free(psi); free(r); free(d); free(q); free(g); free(b); free(ue);
+    return it;
 }
 
 /* ---------------------------------------------------------------------------------- */

@@ -654,4 +654,131 @@ def pin_defocus_recovers_magnification(L):
     assert (sy[ky], sx[kx]) == (1.04, 0.96), (sy[ky], sx[kx], c)
 
 
+# ---- the "integrate" option (R17) ------------------------------------------------------
+def _integ_masks():
+    """A full detector, one with isolated bad pixels and a notch, one with a bad border row."""
+    full = np.ones((18, 23), np.uint8)
+    holes = full.copy()
+    holes[4, 6] = holes[9, 15] = holes[13, 3] = 0
+    holes[0:3, 19:] = 0
+    edge = full.copy()
+    edge[:, 0] = 0
+    edge[17, :] = 0
+    return [full, holes, edge]
+
+
+def pin_integrate_quadratic_potential_unchanged(L):
+    """The gradient of a quadratic potential is a fixed point: every stencil the reading uses
+    where at least two neighbours are good is exact for quadratics."""
+    i, j = np.mgrid[0:18, 0:23].astype(np.float64)
+    # Psi = 104 i + 37 j + 0.51 i^2 + 0.03 i j + 0.49 j^2 (a magnification ~1 and a rotation-free shear)
+    u = np.stack([104.0 + 1.02 * i + 0.03 * j, 37.0 + 0.03 * i + 0.98 * j])
+    for M in _integ_masks():
+        out, it, res = oracle.integrate_map(M, u, tol=1e-13, L=L)
+        assert res < 1e-12
+        assert np.abs(out - u)[:, M > 0].max() < 1e-7, np.abs(out - u)[:, M > 0].max()
+
+
+def pin_integrate_is_an_orthogonal_projection(L):
+    """Least squares onto gradient fields is an orthogonal projection P: P(P u) = P u,
+    <u - P u, P w> = 0 and <P u, w> = <u, P w> for any maps u, w (the entries without an
+    equation, where P leaves the map, cancel on both sides), and P is linear."""
+    rng = np.random.default_rng(12726 + 501)
+    for M in _integ_masks():
+        u = rng.normal(size=(2,) + M.shape)
+        w = rng.normal(size=(2,) + M.shape)
+        Pu, _, r1 = oracle.integrate_map(M, u, tol=1e-13, L=L)
+        Pw, _, r2 = oracle.integrate_map(M, w, tol=1e-13, L=L)
+        PPu, _, _ = oracle.integrate_map(M, Pu, tol=1e-13, L=L)
+        assert r1 < 1e-12 and r2 < 1e-12
+        assert np.abs(PPu - Pu).max() < 1e-8
+        assert abs(np.sum((u - Pu) * Pw)) < 1e-8 * np.sum(u * u) ** 0.5 * np.sum(w * w) ** 0.5
+        assert abs(np.sum(Pu * w) - np.sum(u * Pw)) < 1e-8 * np.sum(u * u) ** 0.5 * np.sum(w * w) ** 0.5
+        Pl, _, _ = oracle.integrate_map(M, 2.0 * u - 3.0 * w, tol=1e-13, L=L)
+        assert np.abs(Pl - (2.0 * Pu - 3.0 * Pw)).max() < 1e-8
+
+
+def pin_integrate_output_is_curl_free(L):
+    """On a full detector the output's curl by central differences vanishes at every pixel
+    two or more from the border (there the output is a central-difference gradient, and
+    central differences along the two axes commute)."""
+    rng = np.random.default_rng(12726 + 502)
+    M = np.ones((20, 26), np.uint8)
+    u = rng.normal(size=(2, 20, 26)) * 3.0
+    out, _, res = oracle.integrate_map(M, u, tol=1e-13, L=L)
+    assert res < 1e-12
+    d_u1_di = 0.5 * (out[1][2:, 1:-1] - out[1][:-2, 1:-1])
+    d_u0_dj = 0.5 * (out[0][1:-1, 2:] - out[0][1:-1, :-2])
+    curl = (d_u1_di - d_u0_dj)[1:-1, 1:-1]
+    assert np.abs(curl).max() < 1e-8
+    # and the input had a curl of order one
+    raw = 0.5 * (u[1][2:, 1:-1] - u[1][:-2, 1:-1]) - 0.5 * (u[0][1:-1, 2:] - u[0][1:-1, :-2])
+    assert np.abs(raw).max() > 1.0
+
+
+def pin_integrate_removes_a_pure_curl(L):
+    """A divergence-free field with no flux through the border (the rotated gradient of a
+    stream function that vanishes there) is orthogonal to every gradient field: the
+    projection removes it, up to the discretisation of the stencils."""
+    ny, nx = 40, 48
+    i, j = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    # stream function s = sin(pi i / (ny - 1))^2 sin(pi j / (nx - 1))^2; u = (ds/dj, -ds/di)
+    a, b = np.pi / (ny - 1), np.pi / (nx - 1)
+    ds_di = 2 * a * np.sin(a * i) * np.cos(a * i) * np.sin(b * j) ** 2
+    ds_dj = 2 * b * np.sin(b * j) * np.cos(b * j) * np.sin(a * i) ** 2
+    u = np.stack([ds_dj, -ds_di]) * 50.0
+    M = np.ones((ny, nx), np.uint8)
+    out, _, res = oracle.integrate_map(M, u, tol=1e-13, L=L)
+    assert res < 1e-12
+    assert np.sqrt(np.mean(out ** 2)) < 0.03 * np.sqrt(np.mean(u ** 2)), np.sqrt(np.mean(out ** 2))
+
+
+def pin_integrate_bruteforce(L):
+    """A tiny detector with holes: the output equals the least-squares solution computed by
+    numpy.linalg.lstsq on the equations written out as a dense matrix, one row per good pixel
+    and axis with a good neighbour (central difference, else the second-order one-sided
+    difference forward then backward, else the first-order one forward then backward)."""
+    rng = np.random.default_rng(12726 + 503)
+    M = np.ones((6, 7), np.uint8)
+    M[2, 3] = 0
+    M[0, 0] = 0
+    M[5, 5:] = 0
+    ny, nx = M.shape
+    u = rng.normal(size=(2, ny, nx)) * 2.0 + 5.0
+    good = lambda y, x: 0 <= y < ny and 0 <= x < nx and M[y, x] > 0
+    rows, rhs, where = [], [], []
+    for a in (0, 1):
+        for y in range(ny):
+            for x in range(nx):
+                if not M[y, x]:
+                    continue
+                e = (1, 0) if a == 0 else (0, 1)
+                at = lambda k: (y + k * e[0], x + k * e[1])
+                if good(*at(1)) and good(*at(-1)):
+                    taps = [(at(1), 0.5), (at(-1), -0.5)]
+                elif good(*at(1)) and good(*at(2)):
+                    taps = [(at(0), -1.5), (at(1), 2.0), (at(2), -0.5)]
+                elif good(*at(-1)) and good(*at(-2)):
+                    taps = [(at(0), 1.5), (at(-1), -2.0), (at(-2), 0.5)]
+                elif good(*at(1)):
+                    taps = [(at(1), 1.0), (at(0), -1.0)]
+                elif good(*at(-1)):
+                    taps = [(at(0), 1.0), (at(-1), -1.0)]
+                else:
+                    continue
+                row = np.zeros(ny * nx)
+                for (yy, xx), c in taps:
+                    row[yy * nx + xx] += c
+                rows.append(row)
+                rhs.append(u[a, y, x])
+                where.append((a, y, x))
+    G = np.array(rows)
+    psi = np.linalg.lstsq(G, np.array(rhs), rcond=None)[0]
+    want = u.copy()
+    for k, (a, y, x) in enumerate(where):
+        want[a, y, x] = G[k] @ psi
+    out, _, res = oracle.integrate_map(M, u, tol=1e-14, L=L)
+    assert np.abs(out - want).max() < 1e-8, np.abs(out - want).max()
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

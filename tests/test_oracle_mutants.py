@@ -66,6 +66,18 @@ MUTANTS = {
                                  "e[(a + Ty) * wx + (b + Tx)] = cnt > 0 ? sum : INFINITY;"),
     "translation_update_sign": ("delta_out[2 * n + 1] = delta_in[2 * n + 1] + (double)(ib - Tx) + db;",
                                 "delta_out[2 * n + 1] = delta_in[2 * n + 1] - (double)(ib - Tx) + db;"),
+    "integrate_central_not_halved": ("off[0] = 1; c[0] = 0.5; off[1] = -1; c[1] = -0.5; return 2;",
+                                     "off[0] = 1; c[0] = 1.0; off[1] = -1; c[1] = -1.0; return 2;"),
+    "integrate_second_order_wrong": ("off[0] = 0; c[0] = -1.5; off[1] = 1; c[1] = 2.0; off[2] = 2; c[2] = -0.5; return 3;",
+                                     "off[0] = 0; c[0] = -1.0; off[1] = 1; c[1] = 1.0; off[2] = 2; c[2] = 0.0; return 3;"),
+    "integrate_backward_sign": ("off[0] = 0; c[0] = 1.5; off[1] = -1; c[1] = -2.0; off[2] = -2; c[2] = 0.5; return 3;",
+                                "off[0] = 0; c[0] = -1.5; off[1] = -1; c[1] = 2.0; off[2] = -2; c[2] = -0.5; return 3;"),
+    "integrate_transposed_gradient": ("const long step = a == 0 ? nx : 1;\n                int off[3];\n                double c[3];\n                const int n = integ_stencil(ny, nx, M, i, j, a, off, c);\n                double v = 0.0;",
+                                      "const long step = a == 0 ? 1 : nx;\n                int off[3];\n                double c[3];\n                const int n = integ_stencil(ny, nx, M, i, j, a, off, c);\n                double v = 0.0;"),
+    "integrate_cg_beta_sign": ("for (size_t p = 0; p < P; ++p) d[p] = r[p] + beta * d[p];",
+                               "for (size_t p = 0; p < P; ++p) d[p] = r[p] - beta * d[p];"),
+    "integrate_keeps_input": ("u_out[a * P + p] = integ_stencil(ny, nx, M, i, j, a, off, c) ? g[a * P + p] : u_in[a * P + p];",
+                              "u_out[a * P + p] = u_in[a * P + p];"),
 }
 
 
