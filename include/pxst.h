@@ -295,6 +295,27 @@ pxst_status pxst_defocus_sweep(const pxst_dims *dims, const float *frames, const
                                const double *sx, double *contrast, float *I_ref, float *w, void *workspace,
                                size_t ws_bytes, void *stream);
 
+/* pxst_integrate_map: the "integrate" option named at the end of section "Update pixel
+ * mapping". The map is the gradient of a scalar (u = x - lambda z / (2 pi) grad Phi), so it
+ * is integrated by least squares and differentiated again, which makes it irrotational.
+ * Equations, one per pixel with M = 1 and axis a: the derivative of Psi along a at the
+ * pixel equals u_a there, by the first of these stencils whose pixels all have M = 1:
+ * central, (Psi[p+e] - Psi[p-e]) / 2; second-order forward, (-3 Psi[p] + 4 Psi[p+e] -
+ * Psi[p+2e]) / 2; second-order backward, (3 Psi[p] - 4 Psi[p-e] + Psi[p-2e]) / 2; forward,
+ * Psi[p+e] - Psi[p]; backward, Psi[p] - Psi[p-e] (no equation where the pixel has no good
+ * neighbour along a). Psi minimises the squared residuals, by conjugate gradients on the
+ * normal equations from Psi = 0, stopping when the residual of the normal equations falls
+ * to tol times its start or after max_iter steps; u_inout then becomes G Psi at every
+ * equation (the pixels and axes without one, and every M = 0 pixel, keep u). FP64. The
+ * result is the orthogonal projection of the map onto these discrete gradient fields: a
+ * map that is one (the gradient of a quadratic Psi, for instance) is returned unchanged.
+ * info_out (device double[2], nullable): the steps taken and the final relative residual.
+ * One cooperative launch (every block resident) runs the solve; its grid barriers give up
+ * after timeout_ns (0 = 10 s), set PXST_DEV_TIMEOUT and leave u unchanged. */
+pxst_status pxst_integrate_map(const pxst_dims *dims, const uint8_t *mask, double *u_inout, int32_t max_iter,
+                               double tol, int64_t timeout_ns, double *info_out, void *workspace, size_t ws_bytes,
+                               void *stream);
+
 /* pxst_filter_map: the "sigma" regularisation of the pixel map named at the end of section
  * "Update pixel mapping": u(x) <- sum_y g(x - y) M(y) u(y) / sum_y g(x - y) M(y) for pixels
  * with M = 1, g(d) = exp(-|d|^2 / (2 sigma^2)) on a square support of radius floor(4 sigma +

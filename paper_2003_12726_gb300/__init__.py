@@ -99,6 +99,8 @@ def lib():
         L.pxst_launch_count.restype = i32
         L.pxst_wait_flag.argtypes = [P, i32, i64, P, sz, P]
         L.pxst_wait_flag.restype = i32
+        L.pxst_integrate_map.argtypes = [D, P, P, i32, C.c_double, i64, P, P, sz, P]
+        L.pxst_integrate_map.restype = i32
         L.pxst_tensor_check.argtypes = [i32, i32, P, P, P, P, P]
         L.pxst_tensor_check.restype = i32
         S = C.POINTER(_Scan)
@@ -133,7 +135,7 @@ EXPORTED = ["pxst_workspace_size", "pxst_make_object_map", "pxst_make_object_map
             "pxst_version", "pxst_tensor_check", "pxst_batch_plan", "pxst_batch_run", "pxst_batch_branch",
             "pxst_batch_destroy", "pxst_autotune", "pxst_calc_error", "pxst_update_translations",
             "pxst_filter_map", "pxst_update_pixel_map_fractional", "pxst_defocus_sweep", "pxst_launch_count",
-            "pxst_wait_flag"]
+            "pxst_wait_flag", "pxst_integrate_map"]
 
 
 # ---------------------------------------------------------------------------------------
@@ -570,6 +572,19 @@ def update_translations(dims: Dims, twindow, frames, W, M, I_ref, w, u, delta, w
                                           if frame_err is not None else None,
                                           C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)),
            "update_translations")
+
+
+def integrate_map(dims: Dims, M, u, ws, max_iter=100000, tol=1e-12, timeout_ns=0, stream=None):
+    """pxst_integrate_map: the "integrate" option -- u (float64 [2][ny][nx], CUDA) made
+    irrotational in place by least-squares integration and re-differentiation. Returns a CUDA
+    float64 tensor [2]: the conjugate-gradient steps taken and the final relative residual."""
+    torch = _torch()
+    info = torch.zeros(2, dtype=torch.float64, device=u.device)
+    _raise(lib().pxst_integrate_map(C.byref(dims.c()), _check(M, torch.uint8, (dims.ny, dims.nx), "M"),
+                                    _check(u, torch.float64, (2, dims.ny, dims.nx), "u"), int(max_iter), float(tol),
+                                    int(timeout_ns), C.c_void_p(info.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                    ws.numel(), _stream(stream)), "integrate_map")
+    return info
 
 
 def filter_map(dims: Dims, sigma, M, u, ws, stream=None):

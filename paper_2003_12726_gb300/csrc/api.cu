@@ -447,6 +447,22 @@ pxst_status pxst_defocus_sweep(const pxst_dims *dims, const float *frames, const
     return PXST_OK;
 }
 
+pxst_status pxst_integrate_map(const pxst_dims *dims, const uint8_t *mask, double *u_inout, int32_t max_iter,
+                               double tol, int64_t timeout_ns, double *info_out, void *workspace, size_t ws_bytes,
+                               void *stream) {
+    if (!dims_ok(dims)) return PXST_ERR_SHAPE;
+    if (!mask || !u_inout || max_iter < 0 || !(tol >= 0.0) || timeout_ns < 0) return PXST_ERR_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255) != 0) return PXST_ERR_ARG;
+    const WsLayout L = ws_layout(*dims, PXST_FORM_FP32);
+    if (ws_bytes < L.total) return PXST_ERR_NOMEM;
+    char *b = static_cast<char *>(workspace);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PXST_TRY(launch_integrate(*dims, mask, u_inout, max_iter, tol, info_out, reinterpret_cast<uint8_t *>(b + L.integ_type),
+                              reinterpret_cast<double *>(b + L.integ_buf), reinterpret_cast<unsigned *>(b + L.integ_bar),
+                              reinterpret_cast<WsHeader *>(b + L.header), timeout_ns, s));
+    return PXST_OK;
+}
+
 pxst_status pxst_filter_map(const pxst_dims *dims, double sigma, const uint8_t *mask, double *u_inout,
                             void *workspace, size_t ws_bytes, void *stream) {
     if (!dims_ok(dims)) return PXST_ERR_SHAPE;

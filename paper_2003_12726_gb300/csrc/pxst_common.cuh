@@ -43,9 +43,12 @@ constexpr int kClassFramesMax = 2048;   // frames the class assignment handles (
 constexpr int kTopK = 8;
 constexpr int kTransMax = 17 * 17;     // translation update: shifts within +-8 on each axis
 
+constexpr int kIntegMaxBlocks = 4096;  // integrate: blocks of the cooperative launch (partial sums)
+
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
     size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp, filt_den;
+    size_t integ_buf, integ_type, integ_bar;   // integrate: CG vectors, equation types, barrier
     size_t fclass, dcls;     // class of each frame; one zero-shift weight image per class
     // precision forms only (zero size otherwise)
     size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge, wlist;
@@ -78,6 +81,10 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.filt_den = off;   off += align256(sizeof(double) * P);        // the map filter's row pass
     L.fclass = off;     off += align256(sizeof(int) * (size_t)d.n_frames);
     L.dcls = off;       off += align256(sizeof(float) * kMaxClasses * R);
+    // integrate: psi, r, two directions, q, G d (2 per pixel), per-block partial sums
+    L.integ_buf = off;  off += align256(sizeof(double) * (7 * P + 2 * (size_t)kIntegMaxBlocks));
+    L.integ_type = off; off += align256(2 * P);
+    L.integ_bar = off;  off += align256(2 * sizeof(unsigned));
     L.Npad = 0;
     L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.wlist = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
@@ -184,6 +191,10 @@ cudaError_t launch_contrast_final(int npairs, const double *acc, double *contras
 cudaError_t launch_frac_refine(const pxst_dims &d, int sub, const float *frames, const float *W, const uint8_t *mask,
                                const float *I_ref, const float *w, const FrameShift *shifts, double *u,
                                float *err_out, cudaStream_t s);
+// integrate (integrate.cu): one cooperative launch of the whole conjugate-gradient solve
+cudaError_t launch_integrate(const pxst_dims &d, const uint8_t *mask, double *u, int max_iter, double tol,
+                             double *info, uint8_t *type, double *buf, unsigned *bar, WsHeader *hdr,
+                             long long limit_ns, cudaStream_t s);
 // learn (and cache) the integer shift span of a translation array outside any capture
 void prime_shift_span(const pxst_dims &d, const double *delta, cudaStream_t s);
 cudaError_t launch_refterms(const pxst_dims &d, const float *I_ref, const float *w,
