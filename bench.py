@@ -25,6 +25,7 @@ import subprocess
 import sys
 import threading
 import time
+from types import SimpleNamespace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -523,6 +524,23 @@ def pxst_arm(args, rank, world, local_rank):
     results = {f: time_form(args, s, base, u0, f, dist, world, orc, sampler) for f in forms}
     if sampler:
         sampler.stop()
+    # the batched and served workloads of the same run (one GPU, the default line only)
+    batch = serve = None
+    if world == 1 and args.form == "all" and args.workload == "precision2d" and not args.no_extra:
+        del base
+        torch.cuda.empty_cache()
+        batch = run_batch(FORMS["bf16"], steps=5, warmup=3)
+        batch.pop("_scans")
+        torch.cuda.empty_cache()
+        pool = ServePool()
+        serve = {}
+        for fname, n_req in (("bf16", 120), ("fp32", 60)):
+            cap = run_serve(FORMS[fname], pool, n_req, 0.0, args.mem_gb, realtime=False)
+            sub = run_serve(FORMS[fname], pool, n_req, 0.5 * cap["scans_per_s"], args.mem_gb, realtime=True,
+                            seed_offset=45)
+            serve[fname] = {"capacity": cap, "half_capacity": sub}
+        del pool
+        torch.cuda.empty_cache()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -577,6 +595,12 @@ def pxst_arm(args, rank, world, local_rank):
                            "error back; the next step's copy overlaps this step's compute"},
             "gpu_launches": h["gpu_launches"], "kernel_ms": h["kernel_ms"], "exact_path_pixels": h["exact_path_pixels"],
             "forms": per_form, "iref_error_vs_oracle": iref_err, "clocks": clocks}
+    if batch:
+        line["batch64"] = dict(batch, form="bf16", workload="64 scans of the batched configuration")
+    if serve:
+        line["serve"] = dict(serve, workload="Poisson stream, sizes log-uniform between the small configuration and "
+                                              "the 2-D precision scan, 1-D or 2-D, 10 iterations each; capacity: every "
+                                              "request at t = 0; half_capacity: arrivals at half that rate")
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -590,26 +614,25 @@ def _host_scan(sc):
                            window=sc.window)
 
 
-def batch_arm(args):
+def run_batch(form, steps, warmup, branches=8, n_scans=64):
     """The batched workload: 64 scans of uneven size (frames U[16, 400], sides U[128, 1024],
     windows U{4..16}) iterated together; a step is one iteration of every scan, one graph
-    launch of pxst_batch_run. Tile shapes come from the autotuner."""
+    launch of pxst_batch_run. Tile shapes come from the autotuner. Returns a summary dict."""
     import torch
     import gen.gpu as gg
     import paper_2003_12726_gb300 as px
-    form = FORMS[args.form]
-    specs = gg.batch_specs(64)
+    specs = gg.batch_specs(n_scans)
     scans = [gg.render(sp) for sp in specs]
     torch.cuda.synchronize()
     recs = [px.Reconstruction.from_device(sc.frames, sc.W, sc.M, sc.delta, sc.u_init, sc.ref_shape, sc.window,
                                           form=form) for sc in scans]
     ev_step = sum(sc.evals for sc in scans)
     t_plan = time.time()
-    b = px.Batch(recs, n_iter=1, n_branches=args.branches, autotune=True)
+    b = px.Batch(recs, n_iter=1, n_branches=branches, autotune=True)
     t_plan = time.time() - t_plan
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(0)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run()
     torch.cuda.synchronize()
     for r in recs:
@@ -620,7 +643,7 @@ def batch_arm(args):
     t_wall0 = time.time()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.run()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -630,6 +653,24 @@ def batch_arm(args):
     tiles = {}
     for r in recs:
         tiles[r.opts.tile] = tiles.get(r.opts.tile, 0) + 1
+    out = {"value": ev_step / (ms / 1e3) * steps, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "scans": len(scans), "scan_iterations_per_s": len(scans) * steps / (ms / 1e3),
+           "frames_range": [min(s.frames.shape[0] for s in scans), max(s.frames.shape[0] for s in scans)],
+           "side_range": [min(s.frames.shape[1] for s in scans), max(s.frames.shape[1] for s in scans)],
+           "window_range": [min(s.window[0] for s in scans), max(s.window[0] for s in scans)],
+           "evals_per_step": ev_step, "branches": branches, "plan_s": t_plan,
+           "tiles_chosen": {str(k): v for k, v in sorted(tiles.items())},
+           "step": "one iteration of every scan: one cudaGraphLaunch of pxst_batch_run",
+           "l2": f"inputs larger than L2 (frames {sum(s.frames.numel() for s in scans) * 4 / 1e9:.1f} GB)",
+           "clocks": sampler.summary(t_wall0 - 0.2, t_wall1 + 0.2), "_scans": scans}
+    b.close()
+    return out
+
+
+def batch_arm(args):
+    form = FORMS[args.form]
+    res = run_batch(form, args.steps, args.warmup, args.branches)
+    scans = res.pop("_scans")
     cpu = None
     if not args.no_cpu_baseline:
         small = min(range(len(scans)), key=lambda k: scans[k].evals)
@@ -637,63 +678,113 @@ def batch_arm(args):
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{rows} detector rows of scan {scans[small].name}: make_object_map + update_pixel_map "
                          f"of the stripe, {sec:.1f} s"}
-    line = {"metric": METRIC, "value": ev_step / (ms / 1e3) * args.steps, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form],
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form],
             "data": "synthetic (rendered on the GPU)",
-            "config": {"workload": "batch-64-scans", "scans": len(scans),
-                       "frames_range": [min(s.frames.shape[0] for s in scans), max(s.frames.shape[0] for s in scans)],
-                       "side_range": [min(s.frames.shape[1] for s in scans), max(s.frames.shape[1] for s in scans)],
-                       "window_range": [min(s.window[0] for s in scans), max(s.window[0] for s in scans)],
-                       "form": args.form, "evals_per_step": ev_step, "branches": args.branches,
-                       "tiles_chosen": {str(k): v for k, v in sorted(tiles.items())}, "plan_s": t_plan,
-                       "parallelism": "one graph launch per step",
-                       "l2": f"inputs larger than L2 (frames {sum(s.frames.numel() for s in scans) * 4 / 1e9:.1f} GB)"},
-            "scan_iterations_per_s": len(scans) * args.steps / (ms / 1e3),
-            "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps,
-            "clocks": sampler.summary(t_wall0 - 0.2, t_wall1 + 0.2)}
+            "config": {"workload": "batch-64-scans", "form": args.form,
+                       **{k: res[k] for k in ("scans", "frames_range", "side_range", "window_range", "evals_per_step",
+                                               "branches", "tiles_chosen", "plan_s", "l2")},
+                       "parallelism": "one graph launch per step"},
+            "scan_iterations_per_s": res["scan_iterations_per_s"], "roofline": None, "cpu_baseline": cpu, "e2e": None,
+            "gpu_launches": None, "clocks": res["clocks"]}
     print(json.dumps(line), flush=True)
-    b.close()
 
 
-def serve_arm(args):
-    """The served workload: a Poisson stream of scans (sizes log-uniform between the small
-    configuration and the 2-D precision scan, 1-D or 2-D), 10 iterations each, through the
-    continuous-batching server with admission by device memory."""
-    import torch
+class ServePool:
+    """Host-resident scans for the served workload: the size parameter tau of the stream's
+    log-uniform mix, binned to `levels` values, for each geometry, rendered once on the GPU
+    and kept in pinned host memory; a request takes the template of its bin and geometry, and
+    the server copies it to the device at admission (inside the request's latency)."""
+
+    def __init__(self, levels=8, device="cuda"):
+        import torch
+        import gen.gpu as gg
+        self.levels = levels
+        self.tmpl = {}
+        for kind in ("2d", "1d"):
+            for k in range(levels):
+                tau = k / (levels - 1)
+                sp = self._spec(kind, tau, seed=12726 * 100 + k + (0 if kind == "2d" else 50))
+                sc = gg.render(sp, device=device)
+                pin = lambda t: t.cpu().pin_memory()
+                self.tmpl[(kind, k)] = SimpleNamespace(frames=pin(sc.frames), W=pin(sc.W), M=pin(sc.M),
+                                                       delta=pin(sc.delta), u_init=pin(sc.u_init),
+                                                       ref_shape=sc.ref_shape, window=sc.window, spec=sp)
+                del sc
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    @staticmethod
+    def _spec(kind, tau, seed):
+        frames = int(round(16 * 25 ** tau))
+        side = int(round(64 * 16 ** tau))
+        if kind == "2d":
+            return dict(kind="2d", n_side=max(4, int(round(frames ** 0.5))), det=side, window=int(round(4 + 12 * tau)),
+                        seed=seed)
+        return dict(kind="1d", n_frames=frames, ny=max(16, side // 2), nx=max(96, (3 * side) // 2), seed=seed)
+
+    def template(self, spec):
+        # the bin of the spec's size parameter: 16 * 25^tau frames and 64 * 16^tau pixels
+        import math
+        if spec["kind"] == "2d":
+            tau = math.log(max(spec["det"], 64) / 64.0) / math.log(16.0)
+        else:
+            tau = math.log(max(spec["nx"] * 2 // 3, 64) / 64.0) / math.log(16.0)
+        k = min(self.levels - 1, max(0, int(round(tau * (self.levels - 1)))))
+        return self.tmpl[(spec["kind"], k)]
+
+
+def run_serve(form, pool, n_requests, rate, mem_gb, realtime=True, seed_offset=44):
+    """The served workload: a Poisson stream (rate per second; realtime=False: every request
+    arrives at once, so the throughput is the capacity) of scans drawn from the log-uniform
+    mix between the small configuration and the 2-D precision scan, 10 iterations each,
+    through the continuous-batching server with admission by device memory; each request's
+    data is copied from pinned host memory at admission."""
     import gen.gpu as gg
-    import paper_2003_12726_gb300 as px
     from paper_2003_12726_gb300.serve import Request, Server, estimate_bytes, poisson_arrivals
-    form = FORMS[args.form]
-    specs = gg.serve_specs(args.requests)
-    arr = poisson_arrivals(len(specs), args.rate, seed=gen.BASE_SEED + 44)
+    specs = gg.serve_specs(n_requests)
+    arr = poisson_arrivals(len(specs), rate, seed=gen.BASE_SEED + seed_offset) if realtime else [0.0] * len(specs)
 
     def reqs(sp_list, times):
         out = []
         for k, (sp, t) in enumerate(zip(sp_list, times)):
-            dims, wnd = gg.spec_dims(sp)
-            out.append(Request(rid=k, arrival=float(t), make=(lambda sp=sp: gg.render(sp)),
-                               est_bytes=estimate_bytes(dims, wnd, form), n_iter=10, form=form))
+            tp = pool.template(sp)
+            n, ny, nx = (int(v) for v in tp.frames.shape)
+            dims = (n, ny, nx, int(tp.ref_shape[0]), int(tp.ref_shape[1]))
+            out.append(Request(rid=k, arrival=float(t), make=(lambda tp=tp: tp),
+                               est_bytes=estimate_bytes(dims, tp.window, form), n_iter=10, form=form))
         return out
-    server = Server(mem_budget=int(args.mem_gb * (1 << 30)), n_streams=8, max_active=32)
+    server = Server(mem_budget=int(mem_gb * (1 << 30)), n_streams=8, max_active=32)
     server.run(reqs(specs[:8], [0.0] * 8), realtime=False)          # warm-up
     sampler = ClockSampler(0)
     t_wall0 = time.time()
     R = reqs(specs, arr)
-    st = server.run(R, realtime=True)
+    st = server.run(R, realtime=realtime)
     t_wall1 = time.time()
     sampler.stop()
-    line = {"metric": METRIC, "value": st["scans_per_s"], "unit": "scans/s", "n_gpus": 1, "steps": len(R),
-            "warmup": 8, "ms_per_step": 1e3 / st["scans_per_s"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form],
-            "data": "synthetic (rendered on the GPU at admission)",
-            "config": {"workload": f"serve-{len(R)}-scans", "rate_per_s": args.rate, "iterations": 10,
-                       "form": args.form, "mem_budget_gb": args.mem_gb, "streams": 8, "max_active": 32,
-                       "parallelism": "continuous batching over streams"},
+    h2d = sum(r.make().frames.numel() * 4 for r in R)
+    return {"scans_per_s": st["scans_per_s"], "requests": len(R), "rate_per_s": rate if realtime else "all at t=0",
             "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},
             "evals_per_s": st["evals_per_s"], "span_s": st["span_s"], "peak_active": st["peak_active"],
-            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+            "peak_bytes": st["peak_bytes"], "h2d_frame_bytes": h2d, "iterations": 10, "mem_budget_gb": mem_gb,
             "clocks": sampler.summary(t_wall0, t_wall1)}
+
+
+def serve_arm(args):
+    form = FORMS[args.form]
+    pool = ServePool()
+    st = run_serve(form, pool, args.requests, args.rate, args.mem_gb)
+    line = {"metric": METRIC, "value": st["scans_per_s"], "unit": "scans/s", "n_gpus": 1, "steps": st["requests"],
+            "warmup": 8, "ms_per_step": 1e3 / st["scans_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16/f32", 2: "tf32/f32"}[form],
+            "data": "synthetic (rendered once on the GPU, kept in pinned host memory, copied at admission)",
+            "config": {"workload": f"serve-{st['requests']}-scans", "rate_per_s": args.rate, "iterations": 10,
+                       "form": args.form, "mem_budget_gb": args.mem_gb, "streams": 8, "max_active": 32,
+                       "parallelism": "continuous batching over streams"},
+            "latency_s": st["latency_s"], "evals_per_s": st["evals_per_s"], "span_s": st["span_s"],
+            "peak_active": st["peak_active"], "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": None, "clocks": st["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -711,6 +802,8 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default line without the batched and served workloads")
     ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic tile shape")
     ap.add_argument("--frac", type=int, default=0, help="fractional candidates on a 1/FRAC grid instead of the fit")
