@@ -228,7 +228,7 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
         }
         {
             Timed t(PXST_K_GTABLE, s);
-            PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.G, w.V, w.Tt, w.nvalid, w.Rm, s));
+            PXST_TRY(launch_gtable(d, o.form, w.Npad, I_ref, wref, w.shifts, w.hdr, w.G, w.V, w.Tt, w.nvalid, w.Rm, s));
         }
         {
             Timed t(PXST_K_TSEARCH, s);

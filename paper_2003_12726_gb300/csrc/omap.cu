@@ -450,80 +450,99 @@ __global__ void __launch_bounds__(256) k_dscatter(int ny, int nx, int Ry, int Rx
         if (b[k] != 0.0f) atomicAdd(D + (size_t)(by + (k >> 1)) * Rx + (bx + (k & 1)), b[k]);
 }
 
-// den(c) += sum_n D_class(n)(c - k_n), FP32 over runs of 32 frames, FP64 across them. Each
-// warp covers 128 consecutive cells, a thread the cells lane, lane + 32, lane + 64, lane + 96
-// (every read of the warp one coalesced line); the block stages 256 frames' shifts and
-// classes at a time in shared memory, and each thread keeps 4 frames x 4 cells of reads in
-// flight.
+// den(c) += sum_n D_class(n)(c - k_n), FP32 over runs of 32 frames, FP64 across them: a
+// correlation of each class's zero-shift weight image with the frames' integer shifts. One
+// block per tile of DT_TY x DT_TX cells; thread t takes column t mod 64 of rows t / 64 + 4 j.
+// When the tile's window (the tile widened by the range of the integer shifts) fits the
+// block's shared memory, each class's D is staged there once (zero off the grid), and every
+// frame's reads are shared-memory loads along a row (consecutive lanes, consecutive words);
+// otherwise the reads go through the cache. The block stages 256 frames' window offsets at
+// a time; a frame of another class than the one staged is skipped.
 constexpr int DG_FRAMES = 256;
-constexpr int DG_CELLS = 4;
-__global__ void __launch_bounds__(256) k_dgather(int N, int Ry, int Rx, const FrameShift *__restrict__ shifts,
-                                                 const int *__restrict__ fclass, const WsHeader *__restrict__ hdr,
-                                                 const float *__restrict__ dcls, double *__restrict__ den) {
-    __shared__ int s_cls[DG_FRAMES], s_ky[DG_FRAMES], s_kx[DG_FRAMES];   // the frames' class and shift
-    if (hdr->n_classes > kMaxClasses) return;
+constexpr int DT_TY = 32, DT_TX = 64, DT_THREADS = 256;
+constexpr int DT_RPT = DT_TY * DT_TX / DT_THREADS;       // cells (rows) per thread: 8
+constexpr int DT_SMEM = 64 * 1024;                       // the staged window: three blocks per SM
+constexpr int DT_CAP = DT_SMEM / 4;
+__global__ void __launch_bounds__(DT_THREADS, 3) k_dgather(int N, int Ry, int Rx, const FrameShift *__restrict__ shifts,
+                                                          const int *__restrict__ fclass,
+                                                          const WsHeader *__restrict__ hdr,
+                                                          const float *__restrict__ dcls, double *__restrict__ den) {
+    extern __shared__ float s_win[];
+    __shared__ int s_off[DG_FRAMES], s_ky[DG_FRAMES], s_kx[DG_FRAMES];
+    const int ncls = hdr->n_classes;
+    if (ncls > kMaxClasses) return;
     const size_t R = (size_t)Ry * Rx;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t cbase = ((size_t)blockIdx.x * 8 + warp) * (32 * DG_CELLS) + lane;
-    int cy[DG_CELLS], cx[DG_CELLS];
-    bool in[DG_CELLS];
+    const int gx = (Rx + DT_TX - 1) / DT_TX;               // tiles per row (a 1-D grid of tiles)
+    const int ty0 = (int)(blockIdx.x / gx) * DT_TY, tx0 = (int)(blockIdx.x % gx) * DT_TX;
+    const int lx = threadIdx.x % DT_TX, ly0 = threadIdx.x / DT_TX;
+    const int ky0 = hdr->kmin_y, ky1 = hdr->kmax_y, kx0 = hdr->kmin_x, kx1 = hdr->kmax_x;
+    const long long HHl = (long long)DT_TY + ky1 - ky0, HWl = (long long)DT_TX + kx1 - kx0;
+    const bool staged = HHl * HWl <= DT_CAP;
+    const int HH = staged ? (int)HHl : 0, HW = staged ? (int)HWl : 0;
+    const int cx = tx0 + lx;
+    double acc[DT_RPT];
+    float part[DT_RPT];
 #pragma unroll
-    for (int k = 0; k < DG_CELLS; ++k) {
-        const size_t c = cbase + 32 * k;
-        in[k] = c < R;
-        cy[k] = in[k] ? (int)(c / Rx) : -1;
-        cx[k] = in[k] ? (int)(c % Rx) : 0;
+    for (int j = 0; j < DT_RPT; ++j) {
+        acc[j] = 0.0;
+        part[j] = 0.0f;
     }
-    double acc[DG_CELLS];
-    float part[DG_CELLS];
-#pragma unroll
-    for (int k = 0; k < DG_CELLS; ++k) {
-        acc[k] = 0.0;
-        part[k] = 0.0f;
-    }
-    for (int n0 = 0; n0 < N; n0 += DG_FRAMES) {
-        const int nf = min(DG_FRAMES, N - n0);
-        __syncthreads();
-        for (int q = threadIdx.x; q < nf; q += blockDim.x) {
-            const FrameShift f = shifts[n0 + q];
-            s_ky[q] = f.ky;
-            s_kx[q] = f.kx;
-            s_cls[q] = fclass[n0 + q];
-        }
-        __syncthreads();
-        for (int q0 = 0; q0 < nf; q0 += 4) {
-            float v[4][DG_CELLS];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int q = q0 + e;
-                const bool fr = q < nf;
-                const int ky = fr ? s_ky[q] : 0, kx = fr ? s_kx[q] : 0;
-                const float *D = dcls + (size_t)(fr ? s_cls[q] : 0) * R;
-#pragma unroll
-                for (int k = 0; k < DG_CELLS; ++k) {
-                    const int ty = cy[k] - ky, tx = cx[k] - kx;
-                    v[e][k] = (fr && in[k] && (unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
-                                  ? __ldg(D + (size_t)ty * Rx + tx)
-                                  : 0.0f;
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-#pragma unroll
-                for (int k = 0; k < DG_CELLS; ++k) part[k] += v[e][k];
-            if (((n0 + q0) & 31) == 28) {       // every 32 frames
-#pragma unroll
-                for (int k = 0; k < DG_CELLS; ++k) {
-                    acc[k] += part[k];
-                    part[k] = 0.0f;
-                }
+    int run = 0;                                          // frames in the FP32 partial sums
+    for (int c = 0; c < ncls; ++c) {
+        const float *D = dcls + (size_t)c * R;
+        if (staged) {
+            __syncthreads();                              // the previous class's reads are done
+            const int gy0 = ty0 - ky1, gx0 = tx0 - kx1;
+            for (int i = threadIdx.x; i < HH * HW; i += DT_THREADS) {
+                const int gy = gy0 + i / HW, gx = gx0 + i % HW;
+                s_win[i] = ((unsigned)gy < (unsigned)Ry && (unsigned)gx < (unsigned)Rx) ? __ldg(D + (size_t)gy * Rx + gx)
+                                                                                       : 0.0f;
             }
         }
+        for (int n0 = 0; n0 < N; n0 += DG_FRAMES) {
+            const int nf = min(DG_FRAMES, N - n0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < nf; q += DT_THREADS) {
+                const FrameShift f = shifts[n0 + q];
+                s_ky[q] = f.ky;
+                s_kx[q] = f.kx;
+                // the frame's offset in the window; INT_MIN: another class
+                s_off[q] = fclass[n0 + q] == c ? (staged ? (ky1 - f.ky) * HW + (kx1 - f.kx) : 0) : INT_MIN;
+            }
+            __syncthreads();
+            for (int q = 0; q < nf; ++q) {
+                const int off = s_off[q];
+                if (off == INT_MIN) continue;             // the same for the whole block
+                if (staged) {
+                    const float *p = s_win + ly0 * HW + lx + off;
+#pragma unroll
+                    for (int j = 0; j < DT_RPT; ++j) part[j] += p[j * (DT_THREADS / DT_TX) * HW];
+                } else {
+                    const int ky = s_ky[q], kx = s_kx[q];
+                    const int tx = cx - kx;
+#pragma unroll
+                    for (int j = 0; j < DT_RPT; ++j) {
+                        const int ty = ty0 + ly0 + j * (DT_THREADS / DT_TX) - ky;
+                        if ((unsigned)ty < (unsigned)Ry && (unsigned)tx < (unsigned)Rx)
+                            part[j] += __ldg(D + (size_t)ty * Rx + tx);
+                    }
+                }
+                if (++run == 32) {
+                    run = 0;
+#pragma unroll
+                    for (int j = 0; j < DT_RPT; ++j) {
+                        acc[j] += part[j];
+                        part[j] = 0.0f;
+                    }
+                }
+            }
+        }
     }
 #pragma unroll
-    for (int k = 0; k < DG_CELLS; ++k) {
-        acc[k] += part[k];
-        if (in[k] && acc[k] != 0.0) den[cbase + 32 * k] += acc[k];
+    for (int j = 0; j < DT_RPT; ++j) {
+        acc[j] += part[j];
+        const int cy = ty0 + ly0 + j * (DT_THREADS / DT_TX);
+        if (cy < Ry && cx < Rx && acc[j] != 0.0) den[(size_t)cy * Rx + cx] += acc[j];
     }
 }
 
@@ -615,8 +634,12 @@ cudaError_t launch_scatter(const pxst_dims &d, const float *frames, const float 
         k_dzero<<<device_sms() * 8, 256, 0, stream>>>(R, hdr, dcls); note_launch();
         k_dscatter<<<dim3((unsigned)((P + 255) / 256), kMaxClasses), 256, 0, stream>>>(d.ny, d.nx, d.ref_ny, d.ref_nx,
                                                                                      W, mask, u, hdr, dcls); note_launch();
-        k_dgather<<<(unsigned)((R + 256 * DG_CELLS - 1) / (256 * DG_CELLS)), 256, 0, stream>>>(
-            d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr, dcls, den); note_launch();
+        e = cudaFuncSetAttribute(k_dgather, cudaFuncAttributeMaxDynamicSharedMemorySize, DT_SMEM);
+        if (e != cudaSuccess) return e;
+        const long long tiles = (long long)((d.ref_nx + DT_TX - 1) / DT_TX) * ((d.ref_ny + DT_TY - 1) / DT_TY);
+        k_dgather<<<(unsigned)tiles, DT_THREADS, DT_SMEM, stream>>>(d.n_frames, d.ref_ny, d.ref_nx, shifts, fclass, hdr,
+                                                                    dcls, den);
+        note_launch();
         e = cudaGetLastError();
     }
     return e;

@@ -157,8 +157,8 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
                          const uint8_t *mask, void *At, WsHeader *hdr, cudaStream_t stream);
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
-                          const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
-                          cudaStream_t stream);
+                          const FrameShift *shifts, const WsHeader *hdr, void *G, void *V, float *Tt, int *nvalid,
+                          float *Rm, cudaStream_t stream);
 cudaError_t launch_tsearch(const pxst_dims &d, const pxst_options &o, int Npad, const void *At, void *A2,
                            const void *G, const void *V, const uint8_t *mask, const float *W, const double *u,
                            const float *Tt, const int *nvalid, WsHeader *hdr, int *cand, uint8_t *edge,

@@ -221,18 +221,26 @@ __global__ void __launch_bounds__(256) k_rmask(size_t R, const float *__restrict
 }
 
 // G~ [Npad/KB][Ry][Rx][KB], the validity V (0 or 1) in the same layout, T~ and n_valid,
-// gathered from the NaN-masked reference: one block per 32 consecutive reference pixels. For each frame block
-// the 8 warps gather with lanes over the 32 pixels (one frame's reads coalesce), the values
-// are transposed through shared memory and written as 32 operand rows of 128 bytes
-// (4 KB contiguous per array).
+// gathered from the NaN-masked reference: one block per 32 consecutive reference pixels. For
+// each frame block the block stages the frames' shifts (and, for whole-pixel shifts, the
+// flat offset ky Rx + kx) in shared memory; the 8 warps gather with lanes over the 32 pixels
+// (one frame's reads coalesce), each thread forming one 32-bit word of its pixel's operand
+// row at a time (two BF16 frames or one FP32 frame), and the words are transposed through
+// shared memory and written as 32 operand rows of 128 bytes (4 KB contiguous per array).
+// When every shift is a whole pixel, a pixel whose reads stay on the grid for every frame
+// reads each frame with one load at its flat offset, without bounds tests.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx, const float *__restrict__ Rm,
-                                                const FrameShift *__restrict__ shifts, T *__restrict__ G,
+                                                const FrameShift *__restrict__ shifts,
+                                                const WsHeader *__restrict__ hdr, T *__restrict__ G,
                                                 T *__restrict__ V, float *__restrict__ Tt,
                                                 int *__restrict__ nvalid) {
     constexpr int KB = 128 / sizeof(T);
+    constexpr int EW = 4 / sizeof(T);              // frames per 32-bit word
     constexpr int RW = 33;                         // words per padded shared row (32 + 1)
     __shared__ uint32_t sg[32 * RW], sv[32 * RW];
+    __shared__ int s_off[KB], s_ky[KB], s_kx[KB];
+    __shared__ float s_fy[KB], s_fx[KB];
     __shared__ float s_t[8][32];
     __shared__ int s_n[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -240,28 +248,81 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
     const size_t c0 = (size_t)blockIdx.x * 32, c = c0 + lane;
     const bool inr = c < R;
     const int cy = inr ? (int)(c / Rx) : 0, cx = inr ? (int)(c % Rx) : 0;
-    T *rowg = reinterpret_cast<T *>(sg + lane * RW), *rowv = reinterpret_cast<T *>(sv + lane * RW);
+    // every frame's whole-pixel read of this pixel stays on the grid (then |ky| < Ry and
+    // |kx| < Rx, so c + ky Rx + kx fits an int, as R does)
+    const bool interior = inr && cy + hdr->kmin_y >= 0 && cy + hdr->kmax_y < Ry && cx + hdr->kmin_x >= 0 &&
+                          cx + hdr->kmax_x < Rx;
+    // every frame's shift is a whole pixel (one fraction class, zero)
+    const bool whole = hdr->n_classes == 1 && hdr->cls_fy[0] == 0.0f && hdr->cls_fx[0] == 0.0f;
     float t = 0.0f;
     int nv = 0;
     const int nkb = Npad / KB;
     for (int kb = 0; kb < nkb; ++kb) {
-#pragma unroll
-        for (int jj = 0; jj < KB / 8; ++jj) {
-            const int j = warp + 8 * jj, n = kb * KB + j;
-            float g = 0.0f, vf = 0.0f;
-            if (inr && n < N) {
-                const FrameShift s = shifts[n];
-                float Rv;
-                if (gather_rm(Rm, Ry, Rx, cy + s.ky, cx + s.kx, s.fy, s.fx, Rv)) {
-                    const T gt = T(Rv - 1.0f);
-                    g = float(gt);
-                    t = fmaf(g, g, t);
-                    vf = 1.0f;
-                    ++nv;
-                }
+        if (threadIdx.x < KB) {
+            const int n = kb * KB + threadIdx.x;
+            const FrameShift f = n < N ? shifts[n] : FrameShift{0, 0, 0.0f, 0.0f};
+            s_ky[threadIdx.x] = f.ky;
+            s_kx[threadIdx.x] = f.kx;
+            s_fy[threadIdx.x] = f.fy;
+            s_fx[threadIdx.x] = f.fx;
+            s_off[threadIdx.x] = (int)((long long)f.ky * Rx + f.kx);
+        }
+        __syncthreads();
+        // one word of the pixel's operand row from its frames' reads (g: R - 1, val: valid)
+        auto put = [&](int k, const float (&g)[EW], const bool (&val)[EW]) {
+            uint32_t wg, wv;
+            if constexpr (EW == 2) {
+                const __nv_bfloat162 gb = __floats2bfloat162_rn(g[0], g[1]);
+                const float g0 = __low2float(gb), g1 = __high2float(gb);
+                t = fmaf(g0, g0, t);
+                t = fmaf(g1, g1, t);
+                wg = *reinterpret_cast<const uint32_t *>(&gb);
+                wv = (val[0] ? 0x3f80u : 0u) | (val[1] ? 0x3f800000u : 0u);     // BF16 1.0 in each half
+            } else {
+                t = fmaf(g[0], g[0], t);
+                wg = __float_as_uint(g[0]);
+                wv = val[0] ? 0x3f800000u : 0u;
             }
-            rowg[j] = T(g);
-            rowv[j] = T(vf);
+#pragma unroll
+            for (int e = 0; e < EW; ++e) nv += val[e] ? 1 : 0;
+            sg[lane * RW + k] = wg;
+            sv[lane * RW + k] = wv;
+        };
+        if (whole && interior) {
+            // every shift whole and every read of this pixel on the grid: one load per frame
+#pragma unroll
+            for (int i = 0; i < 32 / 8; ++i) {
+                const int k = warp + 8 * i;
+                float g[EW];
+                bool val[EW];
+#pragma unroll
+                for (int e = 0; e < EW; ++e) {
+                    const int j = k * EW + e;
+                    const float Rv = kb * KB + j < N ? __ldg(Rm + ((int)c + s_off[j])) : __int_as_float(0x7fc00000);
+                    val[e] = Rv == Rv;
+                    g[e] = val[e] ? Rv - 1.0f : 0.0f;
+                }
+                put(k, g, val);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32 / 8; ++i) {
+                const int k = warp + 8 * i;
+                float g[EW];
+                bool val[EW];
+#pragma unroll
+                for (int e = 0; e < EW; ++e) {
+                    const int j = k * EW + e, n = kb * KB + j;
+                    g[e] = 0.0f;
+                    val[e] = false;
+                    if (inr && n < N) {
+                        float Rv = 0.0f;
+                        val[e] = gather_rm(Rm, Ry, Rx, cy + s_ky[j], cx + s_kx[j], s_fy[j], s_fx[j], Rv);
+                        if (val[e]) g[e] = Rv - 1.0f;
+                    }
+                }
+                put(k, g, val);
+            }
         }
         __syncthreads();
         uint32_t *G32 = reinterpret_cast<uint32_t *>(G) + (size_t)kb * R * 32;
@@ -274,7 +335,8 @@ __global__ void __launch_bounds__(256) k_gtable(int N, int Npad, int Ry, int Rx,
                 V32[(c0 + r) * 32 + k] = sv[r * RW + k];
             }
         }
-        __syncthreads();
+        // the next frame block's shifts are written after every thread has read this one's
+        // words (its first barrier)
     }
     s_t[warp][lane] = t;
     s_n[warp][lane] = nv;
@@ -776,16 +838,16 @@ cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *fr
 }
 
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
-                          const FrameShift *shifts, void *G, void *V, float *Tt, int *nvalid, float *Rm,
-                          cudaStream_t stream) {
+                          const FrameShift *shifts, const WsHeader *hdr, void *G, void *V, float *Tt, int *nvalid,
+                          float *Rm, cudaStream_t stream) {
     const size_t R = (size_t)d.ref_ny * d.ref_nx;
     k_rmask<<<(unsigned)std::min<size_t>((R + 255) / 256, (size_t)device_sms() * 16), 256, 0, stream>>>(R, I_ref, w, Rm); note_launch();
     const unsigned blocks = (unsigned)((R + 31) / 32);
     if (form == PXST_FORM_TF32)
-        k_gtable<float><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts,
+        k_gtable<float><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts, hdr,
                                                      static_cast<float *>(G), static_cast<float *>(V), Tt, nvalid);
     else
-        k_gtable<__nv_bfloat16><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts,
+        k_gtable<__nv_bfloat16><<<blocks, 256, 0, stream>>>(d.n_frames, Npad, d.ref_ny, d.ref_nx, Rm, shifts, hdr,
                                                              static_cast<__nv_bfloat16 *>(G),
                                                              static_cast<__nv_bfloat16 *>(V), Tt, nvalid);
     note_launch();
