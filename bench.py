@@ -458,11 +458,29 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(hs.copy)
     hs.compute.wait_stream(hs.copy)
-    hs.run(args.steps)
+    ev_steps = []
+    for _ in range(args.steps):
+        hs.run(1)
+        ev_steps.append(torch.cuda.Event(enable_timing=True))
+        ev_steps[-1].record(hs.compute)
     f1.record(hs.compute)
     hs.synchronize()
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, "cuda")
+    # what bounds it: each step's completion interval, and the inputs' host-to-device copy
+    # alone (no compute beside it)
+    e2e_steps = [f0.elapsed_time(ev_steps[0])] + [ev_steps[k - 1].elapsed_time(ev_steps[k])
+                                                  for k in range(1, len(ev_steps))]
+    h2d_alone = []
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(hs.copy)
+        with torch.cuda.stream(hs.copy):
+            for key in ("frames", "W", "M", "delta", "u"):
+                hs.bufs[1][key].copy_(pinned[key], non_blocking=True)
+        c1.record(hs.copy)
+        c1.synchronize()
+        h2d_alone.append(c0.elapsed_time(c1))
     hs = None
 
     # ---- accuracy on the oracle's stripes: both sides search the oracle's reference --------
@@ -483,6 +501,7 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
         acc = accuracy(s, orc, out[False][0], out[False][1], out[True][0])
     res = {"ms_per_step": ms / args.steps, "ms_per_iteration_10": ms_iter10, "tuned": tuned,
            "ktimes": ktimes, "launches": launches, "exact_pixels": n_exact, "e2e_ms": ms_e2e / args.steps,
+           "e2e_steps_ms": e2e_steps, "h2d_alone_ms": float(np.median(h2d_alone)),
            "h2d": h2d, "d2h": d2h, "t_wall": (t_wall0, t_wall1), "accuracy": acc, "sweep": sweep}
     del rec
     torch.cuda.empty_cache()
@@ -590,6 +609,7 @@ def pxst_arm(args, rank, world, local_rank):
             "roofline": h["roofline"], "cpu_baseline": cpu,
             "e2e": {"value": h["e2e"]["value"], "unit": UNIT, "h2d_bytes_per_step": rh["h2d"],
                     "d2h_bytes_per_step": rh["d2h"], "ms_per_step": h["e2e"]["ms_per_step"],
+                    "step_ms": [round(x, 3) for x in rh["e2e_steps_ms"]], "h2d_alone_ms": rh["h2d_alone_ms"],
                     "api": "HostStream: every step copies the frames, whitefield, mask, translations and initial "
                            "map from pinned host memory, runs pxst_iterate for one iteration and copies the map and "
                            "error back; the next step's copy overlaps this step's compute"},

@@ -440,6 +440,7 @@ class HostStream:
         self.done = [torch.cuda.Event(), torch.cuda.Event()]
         for e in self.done:
             e.record(self.compute)
+        self.k = 0
         self.h2d = sum(pinned[k].numel() * pinned[k].element_size() for k in ("frames", "W", "M", "delta", "u"))
         self.d2h = pinned["u_out"].numel() * 8 + pinned["err_out"].numel() * 4
 
@@ -448,7 +449,9 @@ class HostStream:
         (h2d bytes, d2h bytes) = (self.h2d, self.d2h)."""
         torch = _torch()
         r = self.rec
-        for k in range(steps):
+        for _ in range(steps):
+            k = self.k                                            # steps alternate buffers across calls
+            self.k += 1
             b = self.bufs[k & 1]
             self.copy.wait_event(self.done[k & 1])                # the buffer's previous step is done
             with torch.cuda.stream(self.copy):

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "pxst.h"
@@ -156,6 +157,11 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
                          const uint8_t *mask, void *At, WsHeader *hdr, cudaStream_t stream);
+// A tiled TMA descriptor (rank 2-5, strides in bytes for dimensions 1..rank-1) through the
+// driver entry point; 128-byte swizzle (the tensor-core operands) or none.
+cudaError_t tmap_encode(CUtensorMap *map, CUtensorMapDataType dt, uint32_t rank, void *base,
+                        const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box,
+                        bool swizzle128 = true);
 cudaError_t launch_gtable(const pxst_dims &d, int form, int Npad, const float *I_ref, const float *w,
                           const FrameShift *shifts, const WsHeader *hdr, void *G, void *V, float *Tt, int *nvalid,
                           float *Rm, cudaStream_t stream);

@@ -26,7 +26,7 @@ std::mutex g_enc_mu;
 }  // namespace
 
 cudaError_t tmap_encode(CUtensorMap *map, CUtensorMapDataType dt, uint32_t rank, void *base,
-                        const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box) {
+                        const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box, bool swizzle128) {
     {
         std::lock_guard<std::mutex> g(g_enc_mu);
         if (!g_encode) {
@@ -39,7 +39,8 @@ cudaError_t tmap_encode(CUtensorMap *map, CUtensorMapDataType dt, uint32_t rank,
     }
     uint32_t estride[5] = {1, 1, 1, 1, 1};
     CUresult r = g_encode(map, dt, rank, base, dims, strides_bytes, box, estride,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
