@@ -50,7 +50,7 @@ struct Ws {
     float *dcls;
     void *At, *G, *A2, *V;
     float *Tt, *Rm;
-    int *nvalid, *cand, *wlist;
+    int *nvalid, *cand, *wlist, *second;
     uint8_t *edge;
     int Npad;
 };
@@ -84,6 +84,7 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     w.cand = reinterpret_cast<int *>(b + L.cand);
     w.edge = reinterpret_cast<uint8_t *>(b + L.edge);
     w.wlist = reinterpret_cast<int *>(b + L.wlist);
+    w.second = reinterpret_cast<int *>(b + L.second);
     w.Npad = L.Npad;
     return PXST_OK;
 }
@@ -239,7 +240,7 @@ pxst_status run_update(const pxst_dims &d, const pxst_options &o, const float *f
         // few frames make the reduced-precision ranking noisier: rescore more of it
         const int rk = o.rescore_k ? o.rescore_k : (d.n_frames < 128 ? 8 : 4);
         Timed t(PXST_K_RESCORE, s);
-        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.nvalid, w.shifts, w.cand, w.hdr, w.wlist, u, err_out, s));
+        PXST_TRY(launch_rescore(d, o, rk, frames, W, mask, w.Rm, w.nvalid, w.shifts, w.cand, w.hdr, w.wlist, w.second, u, err_out, s));
     } else if (d.n_frames <= search_max_frames()) {
         int sy, sx;
         shift_span(d, delta, s, sy, sx);

@@ -28,11 +28,12 @@ struct WsHeader {
     int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
     int n_edge_tiles;  // tensor forms: tiles listed for the masked ranking
     int n_rescore_warps;   // tensor forms: warps listed for the general rescore
+    int n_second;      // tensor forms: pixels listed for the rescore's second 3x3 (follows n_rescore_warps)
     // frames grouped by their fractional shift (fy, fx): the reference weights of make_object_map
     // are formed per class (n_classes > kMaxClasses: too many classes, the scatter forms them)
     int n_classes;
     float cls_fy[8], cls_fx[8];
-    int pad[38];
+    int pad[37];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 
@@ -52,7 +53,7 @@ struct WsLayout {
     size_t integ_buf, integ_type, integ_bar;   // integrate: CG vectors, equation types, barrier
     size_t fclass, dcls;     // class of each frame; one zero-shift weight image per class
     // precision forms only (zero size otherwise)
-    size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge, wlist;
+    size_t At, G, A2, V, Tt, nvalid, Rm, cand, edge, wlist, second;
     int Npad;
     size_t total;
 };
@@ -87,7 +88,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.integ_type = off; off += align256(2 * P);
     L.integ_bar = off;  off += align256(2 * sizeof(unsigned));
     L.Npad = 0;
-    L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.wlist = off;
+    L.At = L.G = L.A2 = L.V = L.Tt = L.nvalid = L.Rm = L.cand = L.edge = L.wlist = L.second = off;
     if (form == PXST_FORM_BF16 || form == PXST_FORM_TF32) {
         const size_t es = form == PXST_FORM_TF32 ? 4 : 2;
         L.Npad = tensor_npad(d.n_frames, form);
@@ -102,6 +103,8 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
         L.edge = off;   off += align256(P);
         // row segments of 32 pixels left to the general rescore (one per row and 32 columns)
         L.wlist = off;  off += align256(sizeof(int) * ((size_t)d.ny * ((d.nx + 31) / 32) + 1));
+        // pixels whose minimum left the first 3x3: (pixel, window index, error, 0) each
+        L.second = off; off += align256(4 * sizeof(int) * P);
     }
     L.total = off;
     return L;
@@ -152,8 +155,8 @@ cudaError_t launch_search(const pxst_dims &d, const pxst_options &o, const float
                           cudaStream_t stream);
 cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
                            const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
-                           const FrameShift *shifts, const int *cand, WsHeader *hdr, int *wlist, double *u,
-                           float *err_out, cudaStream_t stream);
+                           const FrameShift *shifts, const int *cand, WsHeader *hdr, int *wlist, int *second,
+                           double *u, float *err_out, cudaStream_t stream);
 // precision forms (tensor.cu)
 cudaError_t launch_tprep(const pxst_dims &d, int form, int Npad, const float *frames, const float *W,
                          const uint8_t *mask, void *At, WsHeader *hdr, cudaStream_t stream);

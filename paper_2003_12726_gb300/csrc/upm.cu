@@ -867,6 +867,7 @@ struct RescoreArgs {
     const int *cand;          // [P][kTopK] window indices, -1 = none
     WsHeader *hdr;
     int *wlist;               // warps (pixel index / 32) left to the general kernel
+    int *second;              // [4 x n_second]: pixel, window index of its minimum, error bits, 0
     double *u;
     float *err_out;
 };
@@ -915,37 +916,6 @@ __device__ __forceinline__ bool read_any(const RescoreArgs &a, int cy, int cx, i
 __device__ __forceinline__ bool span_safe(const RescoreArgs &a, int y0, int y1, int x0, int x1) {
     const WsHeader &h = *a.hdr;
     return y0 + h.kmin_y >= 0 && y1 + h.kmax_y + 1 < a.Ry && x0 + h.kmin_x >= 0 && x1 + h.kmax_x + 1 < a.Rx;
-}
-
-// Errors of up to B candidates (cy[k], cx[k]), k < nb, of pixel `pix`, frames read from
-// global memory (the rare second 3x3).
-template <int B>
-__device__ void eval_batch(const RescoreArgs &a, size_t pix, float Wv, const int (&cy)[B], const int (&cx)[B],
-                           int nb, float (&e)[B]) {
-    const size_t P = (size_t)a.ny * a.nx;
-    CandSums cs[B];
-    int base[B];
-    bool safe[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-        cs[k].zero();
-        base[k] = cy[k] * a.Rx + cx[k];
-        safe[k] = span_safe(a, cy[k], cy[k], cx[k], cx[k]);
-    }
-    for (int n = 0; n < a.N; ++n) {
-        const FrameShift s = a.shifts[n];
-        const float I = __ldcs(a.frames + (size_t)n * P + pix);
-        const float t = I - Wv;
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-            if (k >= nb) continue;
-            float R;
-            const bool ok = read_any(a, cy[k], cx[k], base[k], safe[k], s, R);
-            cs[k].add(ok, R, I, t, Wv);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < B; ++k) e[k] = cs[k].e();
 }
 
 constexpr int RS_F = 16;      // frames per pipeline stage
@@ -1088,26 +1058,12 @@ __device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, con
     double da = 0.0, db = 0.0;
     if (a.quadratic) {
         if (bi != pc.c0) {
-            // the minimum moved off the evaluated 3x3: evaluate the one about it, 4 at a time
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int cy[4], cx[4];
-                float e4[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int k = 4 * h + m, jn = k < 4 ? k : k + 1;
-                    cy[m] = pc.ci + ia + jn / 3 - 1 - a.Sy;
-                    cx[m] = pc.cj + ib + jn % 3 - 1 - a.Sx;
-                }
-                eval_batch<4>(a, pix, pc.Wv, cy, cx, 4, e4);
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int k = 4 * h + m, jn = k < 4 ? k : k + 1;
-                    const int na = ia + jn / 3 - 1, nb = ib + jn % 3 - 1;
-                    f9[jn] = (na < 0 || na > 2 * a.Sy || nb < 0 || nb >= wxn) ? INFINITY : e4[m];
-                }
-            }
-            f9[4] = be;
+            // the minimum moved off the evaluated 3x3: the second pass (k_rescore_second)
+            // evaluates the 3x3 about it, fits and writes the map
+            const int k = atomicAdd(&a.hdr->n_second, 1);
+            reinterpret_cast<int4 *>(a.second)[k] = make_int4((int)pix, bi, __float_as_int(be), 0);
+            if (a.err_out) a.err_out[pix] = be;
+            return;
         }
         refine3x3(f9, da, db);
     }
@@ -1557,6 +1513,77 @@ __global__ void __launch_bounds__(32 * RG_W) k_rescore_general(RescoreArgs a) {
     pix_finish<XK>(a, pix, pc, f9, fxe);
 }
 
+// Second pass of the rescore: the pixels whose minimum left the first 3x3 (a few hundred in a
+// megapixel), one warp per listed pixel. The lanes split the frames (n = lane, lane + 32, ...)
+// and sum, by the per-frame rule, the 8 points of the 3x3 about the minimum; the warp adds
+// the lanes' sums in a fixed butterfly order; lane 0 fits and writes the map. (Evaluated
+// inside the tile kernels instead, one thread running 8 candidates through every frame held
+// its whole CTA for about ten times a typical CTA's duration.)
+__global__ void __launch_bounds__(256) k_rescore_second(RescoreArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const size_t P = (size_t)a.ny * a.nx;
+    const int wxn = 2 * a.Sx + 1;
+    const int n_list = a.hdr->n_second;
+    for (int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n_list; e += nw) {
+        const int4 ent = reinterpret_cast<const int4 *>(a.second)[e];
+        const size_t pix = (size_t)ent.x;
+        const int bi = ent.y;
+        const float be = __int_as_float(ent.z);
+        // the window centre of the map before this update (the map is written below only)
+        const int ci = (int)floor(a.u[pix] + 0.5), cj = (int)floor(a.u[P + pix] + 0.5);
+        const float Wv = a.W[pix];
+        const int ia = bi / wxn, ib = bi % wxn;
+        int cy[8], cx[8], base[8];
+        bool in[8], safe[8];
+        CandSums cs[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int jn = k < 4 ? k : k + 1;
+            const int na = ia + jn / 3 - 1, nb = ib + jn % 3 - 1;
+            in[k] = na >= 0 && na <= 2 * a.Sy && nb >= 0 && nb < wxn;
+            cy[k] = ci + na - a.Sy;
+            cx[k] = cj + nb - a.Sx;
+            base[k] = cy[k] * a.Rx + cx[k];
+            safe[k] = span_safe(a, cy[k], cy[k], cx[k], cx[k]);
+            cs[k].zero();
+        }
+        for (int n = lane; n < a.N; n += 32) {
+            const FrameShift sft = a.shifts[n];
+            const float I = __ldcs(a.frames + (size_t)n * P + pix);
+            const float t = I - Wv;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (!in[k]) continue;
+                float R = 0.0f;
+                const bool ok = read_any(a, cy[k], cx[k], base[k], safe[k], sft, R);
+                cs[k].add(ok, R, I, t, Wv);
+            }
+        }
+        float f9[9];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float er = cs[k].err, va = cs[k].var;
+            int nv = cs[k].nv;
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                er += __shfl_xor_sync(0xffffffffu, er, m);
+                va += __shfl_xor_sync(0xffffffffu, va, m);
+                nv += __shfl_xor_sync(0xffffffffu, nv, m);
+            }
+            const int jn = k < 4 ? k : k + 1;
+            f9[jn] = !in[k] ? INFINITY : (nv == 0 ? INFINITY : (va > 0.0f ? er / va : er));
+        }
+        f9[4] = be;
+        if (lane == 0) {
+            double da = 0.0, db = 0.0;
+            refine3x3(f9, da, db);
+            a.u[pix] = (double)(ci + ia - a.Sy) + da;
+            a.u[P + pix] = (double)(cj + ib - a.Sx) + db;
+        }
+    }
+}
+
 }  // namespace
 
 // Largest frame count the fast path can stage (a 1 x 32 tile in shared memory).
@@ -1654,13 +1681,13 @@ cudaError_t launch_exact(const pxst_dims &d, const pxst_options &o, const float 
 
 cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand, const float *frames,
                            const float *W, const uint8_t *mask, const float *Rm, const int *nvalid,
-                           const FrameShift *shifts, const int *cand, WsHeader *hdr, int *wlist, double *u,
-                           float *err_out, cudaStream_t stream) {
+                           const FrameShift *shifts, const int *cand, WsHeader *hdr, int *wlist, int *second,
+                           double *u, float *err_out, cudaStream_t stream) {
     RescoreArgs a;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.Sy = o.win_y; a.Sx = o.win_x; a.quadratic = o.quadratic ? 1 : 0; a.ncand = ncand;
     a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.nvalid = nvalid; a.shifts = shifts;
-    a.cand = cand; a.hdr = hdr; a.wlist = wlist; a.u = u; a.err_out = err_out;
+    a.cand = cand; a.hdr = hdr; a.wlist = wlist; a.second = second; a.u = u; a.err_out = err_out;
     const dim3 tgrid((unsigned)((d.nx + 31) / 32), (unsigned)((d.ny + RT_TY - 1) / RT_TY));
     const unsigned gblocks = tgrid.x * (unsigned)d.ny;          // at most one per row segment
     // the shift table (when it leaves room) and the window share the CTA's part of shared
@@ -1669,13 +1696,18 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
     const int sh_staged = shifts_b <= RT_SMEM / 2 ? 1 : 0;
     const int smem = RT_SMEM;
     const int win_cap = (int)((smem - (sh_staged ? shifts_b : 0)) / 4);
-    cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_warps, 0, sizeof(int), stream);
+    // n_rescore_warps and n_second
+    cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_warps, 0, 2 * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     auto go = [&](auto tile_kernel, auto general_kernel) {
         cudaError_t r = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (r != cudaSuccess) return r;
         tile_kernel<<<tgrid, RT_THREADS, smem, stream>>>(a, win_cap, sh_staged); note_launch();
         general_kernel<<<gblocks, 32 * RG_W, 0, stream>>>(a); note_launch();
+        if ((r = cudaGetLastError()) != cudaSuccess) return r;
+        if (a.quadratic) {
+            k_rescore_second<<<device_sms() * 2, 256, 0, stream>>>(a); note_launch();
+        }
         return cudaGetLastError();
     };
     return ncand <= 4 ? go(k_rescore_tile<3>, k_rescore_general<3>) : go(k_rescore_tile<7>, k_rescore_general<7>);
