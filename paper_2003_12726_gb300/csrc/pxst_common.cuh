@@ -27,8 +27,8 @@ struct WsHeader {
     int n_exact_cta;   // pixels of the last update with a strip evaluated by the per-frame rule
     int kmin_y, kmax_y, kmin_x, kmax_x;   // range of the integer shifts over all frames
     int n_edge_tiles;  // tensor forms: tiles listed for the masked ranking
-    int n_rescore_warps;   // tensor forms: warps listed for the general rescore
-    int n_second;      // tensor forms: pixels listed for the rescore's second 3x3 (follows n_rescore_warps)
+    int n_rescore_pix;     // tensor forms: pixels listed for the general rescore
+    int n_second;      // tensor forms: pixels listed for the rescore's second 3x3 (follows n_rescore_pix)
     // frames grouped by their fractional shift (fy, fx): the reference weights of make_object_map
     // are formed per class (n_classes > kMaxClasses: too many classes, the scatter forms them)
     int n_classes;
@@ -101,8 +101,8 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
         L.Rm = off;     off += align256(sizeof(float) * R);
         L.cand = off;   off += align256(sizeof(int) * kTopK * P);
         L.edge = off;   off += align256(P);
-        // row segments of 32 pixels left to the general rescore (one per row and 32 columns)
-        L.wlist = off;  off += align256(sizeof(int) * ((size_t)d.ny * ((d.nx + 31) / 32) + 1));
+        // pixels left to the general rescore (those with a candidate not valid in every frame)
+        L.wlist = off;  off += align256(sizeof(int) * (P + 1));
         // pixels whose minimum left the first 3x3: (pixel, window index, error, 0) each
         L.second = off; off += align256(4 * sizeof(int) * P);
     }

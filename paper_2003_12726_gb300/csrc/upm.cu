@@ -1073,13 +1073,12 @@ __device__ __forceinline__ void pix_finish(const RescoreArgs &a, size_t pix, con
 }
 
 // Lean rescore: one CTA per tile of RT_TY detector rows x 32 columns, one thread per pixel,
-// for the warps (one row of 32 pixels each) whose every pixel passes pix_lean; a warp that
-// does not is appended to the list of k_rescore_general (by its first pixel) and only waits
-// at the CTA's barriers. The reference the tile's evaluated candidates read (their bounding
-// box, widened by the range of the integer frame shifts and one corner) is staged once in
-// shared memory when it fits the CTA's share, so that each frame's reads of the 3x3 and of
-// the other kept candidates are shared-memory loads rather than L1 hits; otherwise they are
-// read from the masked reference through the cache, as before. Each thread streams its own
+// for the pixels that pass pix_lean; a pixel that does not is appended to the list of
+// k_rescore_general. The reference the 3x3s of the tile's pixels read (their bounding box,
+// widened by the range of the integer frame shifts and one corner) is staged once in shared
+// memory when it fits the CTA's share, so that each frame's reads of the 3x3 are
+// shared-memory loads rather than L1 hits (the other kept candidates are read through the
+// cache); otherwise the 3x3 is read from the masked reference too. Each thread streams its own
 // pixel's frames through an 8-deep register double buffer. For a whole-pixel shift the 3x3
 // is read as three rows of three about one index; every 3x3 point is summed (those outside
 // the window are dropped at the end) and the variance is the pixel's own over all frames.
@@ -1248,70 +1247,6 @@ __device__ __forceinline__ void rescore_frames_int(const RescoreArgs &a, const P
         for (int jf = 0; n0 + jf < a.N; ++jf) one(In[jf], offs[n0 + jf], offg[n0 + jf]);
 }
 
-// The per-frame rule on the staged window (for the row segments with a candidate that is
-// not valid in every frame): every candidate sums its error and variance over the frames
-// in which its masked renormalised read is valid (window cells off the grid or uncovered
-// are NaN); e = err / var (err if var = 0, +inf with no valid frame).
-template <int XK>
-__device__ __forceinline__ void rescore_frames_rule(const RescoreArgs &a, const PixCands<XK> &pc,
-                                                    const float *__restrict__ win, int WS, int base0,
-                                                    const FrameShift *__restrict__ sh, size_t pix, float (&f9)[9],
-                                                    float (&fxe)[PixCands<XK>::NX]) {
-    const size_t P = (size_t)a.ny * a.nx;
-    CandSums s9[9], sx[PixCands<XK>::NX];
-#pragma unroll
-    for (int jn = 0; jn < 9; ++jn) s9[jn].zero();
-#pragma unroll
-    for (int q = 0; q < XK; ++q) sx[q].zero();
-    const float Wv = pc.Wv;
-    const bool run = pc.run;
-    const float *fp = a.frames + pix;
-    float In[RT_PREFETCH];
-#pragma unroll
-    for (int jf = 0; jf < RT_PREFETCH; ++jf) In[jf] = (run && jf < a.N) ? __ldcs(fp + (size_t)jf * P) : 0.0f;
-    for (int n0 = 0; n0 < a.N; n0 += RT_PREFETCH) {
-        float Iv[RT_PREFETCH];
-#pragma unroll
-        for (int jf = 0; jf < RT_PREFETCH; ++jf) {
-            Iv[jf] = In[jf];
-            const int m = n0 + RT_PREFETCH + jf;
-            In[jf] = (run && m < a.N) ? __ldcs(fp + (size_t)m * P) : 0.0f;
-        }
-        if (!run) continue;
-        for (int jf = 0; jf < RT_PREFETCH && n0 + jf < a.N; ++jf) {
-            const FrameShift sft = sh[n0 + jf];
-            const float I = Iv[jf], tt = I - Wv;
-            const int off = sft.ky * WS + sft.kx;
-            const bool whole = sft.fy == 0.0f && sft.fx == 0.0f;
-#pragma unroll
-            for (int jn = 0; jn < 9; ++jn) {
-                if (!pc.in9[jn]) continue;
-                const int q = base0 + off + (jn / 3 - 1) * WS + (jn % 3 - 1);
-                float R = 0.0f;
-                bool ok;
-                if (whole) {
-                    R = win[q];
-                    ok = R == R;
-                } else {
-                    ok = gather_win(win, WS, q, sft.fy, sft.fx, R);
-                }
-                s9[jn].add(ok, R, I, tt, Wv);
-            }
-#pragma unroll
-            for (int q = 0; q < XK; ++q) {
-                if (q >= pc.nxk) continue;
-                float R = 0.0f;
-                const bool ok = read_any(a, pc.xy[q], pc.xx[q], pc.xbase[q], pc.xsafe[q], sft, R);
-                sx[q].add(ok, R, I, tt, Wv);
-            }
-        }
-    }
-#pragma unroll
-    for (int jn = 0; jn < 9; ++jn) f9[jn] = pc.in9[jn] ? s9[jn].e() : INFINITY;
-#pragma unroll
-    for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? sx[q].e() : INFINITY;
-}
-
 template <int XK>
 __global__ void __launch_bounds__(RT_THREADS, XK <= 3 ? 3 : 2) k_rescore_tile(RescoreArgs a, int win_cap, int sh_staged) {
     extern __shared__ __align__(16) unsigned char rt_raw[];
@@ -1330,7 +1265,13 @@ __global__ void __launch_bounds__(RT_THREADS, XK <= 3 ? 3 : 2) k_rescore_tile(Re
         for (int n = threadIdx.x; n < a.N; n += RT_THREADS) s_sh[n] = a.shifts[n];
     PixCands<XK> pc;
     pix_setup<XK>(a, pix, inb, pc);
-    const bool lean = __all_sync(0xffffffffu, pix_lean<XK>(a, pc));
+    // a pixel with an evaluated candidate that is not valid in every frame (near the edge of
+    // the reference's coverage) is left to the general kernel's per-frame rule, so that every
+    // warp here runs the lean loop and an edge tile takes no longer than any other
+    if (pc.run && !pix_lean<XK>(a, pc)) {
+        a.wlist[atomicAdd(&a.hdr->n_rescore_pix, 1)] = (int)pix;
+        pc.act = pc.run = false;
+    }
     __syncthreads();
     // the box of the 3x3s about the tile's first candidates (the other kept candidates, a
     // few per pixel anywhere in the window, are read through the cache)
@@ -1349,12 +1290,6 @@ __global__ void __launch_bounds__(RT_THREADS, XK <= 3 ? 3 : 2) k_rescore_tile(Re
     const long long WHl = (long long)wy1 - wy0 + 1;
     const bool staged = sh_staged && any && WSl * WHl <= win_cap;
     const int WS = staged ? (int)WSl : a.Rx;
-    if (!lean && !staged) {
-        // the per-frame rule without a staged window: the general kernel takes this segment
-        if (lane == 0 && y < a.ny)
-            a.wlist[atomicAdd(&a.hdr->n_rescore_warps, 1)] = (int)((size_t)y * a.nx + blockIdx.x * 32);
-        pc.act = pc.run = false;
-    }
     if (staged) {
         const int WN = (int)(WSl * WHl);
         const float qnan = __int_as_float(0x7fc00000);
@@ -1372,7 +1307,7 @@ __global__ void __launch_bounds__(RT_THREADS, XK <= 3 ? 3 : 2) k_rescore_tile(Re
     // window index of c0 for a zero shift
     const int base0 = staged ? (pc.y0 - wy0) * WS + (pc.x0 - wx0) : pc.base0;
     float f9[9], fxe[PixCands<XK>::NX];
-    if (lean) {
+    {
         const int nxw = __reduce_max_sync(__activemask(), pc.nxk);
         // the 3x3 errors in pairs, (e9[2k], e9[2k+1]) = acc[k], and acc[4] = (e9[8], var): one
         // packed FMA advances two sums
@@ -1396,18 +1331,15 @@ __global__ void __launch_bounds__(RT_THREADS, XK <= 3 ? 3 : 2) k_rescore_tile(Re
         }
 #pragma unroll
         for (int q = 0; q < XK; ++q) fxe[q] = q < pc.nxk ? (var > 0.0f ? ex[q] / var : ex[q]) : INFINITY;
-    } else {
-        rescore_frames_rule<XK>(a, pc, s_win, WS, base0, sh, pix, f9, fxe);
     }
     pix_finish<XK>(a, pix, pc, f9, fxe);
 }
 
-// General rescore: one block per row segment of 32 pixels listed by k_rescore_tile (its
-// first pixel; blocks beyond the list's length return at once), with the per-frame rule of
-// the masked renormalised reads: each
+// General rescore: one block per 32 pixels listed by k_rescore_tile (blocks beyond the list's
+// length return at once), with the per-frame rule of the masked renormalised reads: each
 // candidate sums its error and variance over the frames where it is valid. The block's 4
 // warps take the same 32 pixels and a quarter of the frames each (so that the few listed
-// warps still fill the GPU); their sums are added in warp order and warp 0 finishes.
+// pixels still fill the GPU); their sums are added in warp order and warp 0 finishes.
 constexpr int RG_W = 4;
 template <int XK>
 __global__ void __launch_bounds__(32 * RG_W) k_rescore_general(RescoreArgs a) {
@@ -1415,12 +1347,13 @@ __global__ void __launch_bounds__(32 * RG_W) k_rescore_general(RescoreArgs a) {
     constexpr int STAGE_BYTES = RG_W * RS_S * RS_F * 32 * 4;       // frames, per warp
     constexpr int SUM_BYTES = (RG_W - 1) * NC * 32 * 12;           // partial sums, warps 1..
     __shared__ __align__(16) uint8_t sraw[STAGE_BYTES > SUM_BYTES ? STAGE_BYTES : SUM_BYTES];
-    if ((int)blockIdx.x >= a.hdr->n_rescore_warps) return;
+    const int n_list = a.hdr->n_rescore_pix;
+    if ((int)blockIdx.x * 32 >= n_list) return;
     const size_t P = (size_t)a.ny * a.nx;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t first = (size_t)a.wlist[blockIdx.x];
-    const bool inb = (int)(first % a.nx) + lane < a.nx;
-    const size_t pix = inb ? first + lane : first;
+    const int idx = blockIdx.x * 32 + lane;
+    const bool inb = idx < n_list;
+    const size_t pix = (size_t)a.wlist[inb ? idx : blockIdx.x * 32];
     PixCands<XK> pc;
     pix_setup<XK>(a, pix, inb, pc);
     CandSums s9[9], sx[PixCands<XK>::NX];
@@ -1689,15 +1622,15 @@ cudaError_t launch_rescore(const pxst_dims &d, const pxst_options &o, int ncand,
     a.frames = frames; a.W = W; a.mask = mask; a.Rm = Rm; a.nvalid = nvalid; a.shifts = shifts;
     a.cand = cand; a.hdr = hdr; a.wlist = wlist; a.second = second; a.u = u; a.err_out = err_out;
     const dim3 tgrid((unsigned)((d.nx + 31) / 32), (unsigned)((d.ny + RT_TY - 1) / RT_TY));
-    const unsigned gblocks = tgrid.x * (unsigned)d.ny;          // at most one per row segment
+    const unsigned gblocks = (unsigned)(((size_t)d.ny * d.nx + 31) / 32);   // at most one per 32 listed pixels
     // the shift table (when it leaves room) and the window share the CTA's part of shared
     // memory; a window that does not fit is read through the cache
     const long long shifts_b = (long long)(sizeof(FrameShift) + 2 * sizeof(int)) * d.n_frames;
     const int sh_staged = shifts_b <= RT_SMEM / 2 ? 1 : 0;
     const int smem = RT_SMEM;
     const int win_cap = (int)((smem - (sh_staged ? shifts_b : 0)) / 4);
-    // n_rescore_warps and n_second
-    cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_warps, 0, 2 * sizeof(int), stream);
+    // n_rescore_pix and n_second
+    cudaError_t e = cudaMemsetAsync(&hdr->n_rescore_pix, 0, 2 * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     auto go = [&](auto tile_kernel, auto general_kernel) {
         cudaError_t r = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
