@@ -5,7 +5,10 @@
     1e-5 * e_min + 1e-7 * (sum_n I^2 / var) of the oracle's minimum;
   * sub-pixel u: within 1e-3 px wherever the integer picks agree;
   * normalised error at the pick: relative 1e-4 (FP32 sums of at most a few hundred positive
-    terms, each rounded at 2^-24, stay well inside it);
+    terms, each rounded at 2^-24, stay well inside it), plus an absolute floor for a pick whose
+    residuals I - W R nearly vanish: a bilinear read in FP32 carries an absolute rounding of a
+    few ulp of W R ~ I, so each squared residual is only known to about (2^-21 max_n |I_n|)^2,
+    i.e. the error to N (2^-21 max_n |I_n|)^2 / var;
   * I_ref: relative L2 <= 1e-5 over reference pixels whose oracle weight exceeds
     1e-4 * max w (a few barely-covered edge pixels would otherwise dominate).
 """
@@ -77,9 +80,15 @@ def check_update(inp, pix, u_gpu_int, err_gpu_int, u_gpu_q, err_gpu_q, check_fit
     max_du = float(du.max()) if du.size else 0.0
     assert max_du <= U_TOL, f"sub-pixel u differs by {max_du:.3e} px"
     fin = same & np.isfinite(eo_int)
-    rel = np.abs(err_gpu_int[fin] - eo_int[fin]) / np.maximum(np.abs(eo_int[fin]), 1e-30)
+    # the absolute floor of the error at the pick (module docstring), per pixel
+    fr = frames.reshape(frames.shape[0], -1)[:, pix].astype(np.float64)
+    Wp = W.ravel()[pix].astype(np.float64)
+    var_all = np.maximum(np.sum((fr - Wp) ** 2, axis=0), 1e-300)
+    floor = fr.shape[0] * (2.0 ** -21 * np.max(np.abs(fr), axis=0)) ** 2 / var_all
+    dev = np.abs(err_gpu_int[fin] - eo_int[fin])
+    rel = np.maximum(dev - floor[fin], 0.0) / np.maximum(np.abs(eo_int[fin]), 1e-30)
     max_rel = float(rel.max()) if rel.size else 0.0
-    assert max_rel <= ERR_RTOL, f"error at the pick differs by {max_rel:.3e} (relative)"
+    assert max_rel <= ERR_RTOL, f"error at the pick differs by {max_rel:.3e} (relative, beyond the rounding floor)"
     # non-finite errors (no valid candidate) must match exactly
     assert np.array_equal(np.isinf(err_gpu_int[same]), np.isinf(eo_int[same]))
     return dict(pixels=int(pix.size), argmin_agree=agree, near_ties=int(bad.size),

@@ -76,7 +76,8 @@ def test_batch_matches_each_scan_alone():
 
 def test_batch_against_oracle():
     """One iteration of every scan in one batch, without and with the fit (two batches);
-    the FP32, BF16 and TF32 scans against the oracle with the full criterion."""
+    2-D scans in FP32, BF16 and TF32 and the 1-D lens scan (FP32, fractional shifts) against
+    the oracle with the full criterion."""
     import torch
     import paper_2003_12726_gb300 as px
     scans = _scans()
@@ -86,7 +87,7 @@ def test_batch_against_oracle():
         b.run()
         torch.cuda.synchronize()
         b.close()
-    for k in (0, 1, 4):
+    for k in (0, 1, 3, 4):
         s = scans[k][0]
         rep = parity.check_iteration(s, s.u_init, _host(recs[False][k]), _host(recs[True][k]))
         print(s.name, "form", scans[k][1], rep["update"])
