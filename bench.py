@@ -410,6 +410,7 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
             rec.run(1)
         if full:
             px.filter_map(rec.dims, 1.0, rec.M, rec.u, rec.ws)
+            px.integrate_map(rec.dims, rec.M, rec.u, rec.ws, max_iter=200, tol=1e-8)
             px.update_translations(rec.dims, tw, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta,
                                    rec.ws, fe_t)
             px.calc_error(rec.dims, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta, rec.ws, pe_t,
@@ -627,8 +628,9 @@ def pxst_arm(args, rank, world, local_rank):
                        "step": "one main-loop iteration (make_object_map, update_pixel_map with the 3x3 fit) from "
                                "the scan's initial map, restored on the device before each step",
                        "subpixel": f"fractional candidates, 1/{args.frac} grid" if args.frac else "3x3 paraboloid",
-                       "loop": "full: reference image, pixel map, map filter (sigma 1), translations, figures of "
-                               "merit" if args.loop == "full" else "reference image, pixel map",
+                       "loop": "full: reference image, pixel map, map filter (sigma 1), integration (at most 200 "
+                               "conjugate-gradient steps, tolerance 1e-8), translations, figures of merit"
+                               if args.loop == "full" else "reference image, pixel map",
                        "l2": f"inputs larger than L2 (frames {s.frames.nbytes / 1e6:.0f} MB per step)"},
             "roofline": h["roofline"], "cpu_baseline": cpu,
             "e2e": {"value": h["e2e"]["value"], "unit": UNIT, "h2d_bytes_per_step": rh["h2d"],

@@ -228,7 +228,8 @@ pxst_status pxst_last_exact_count(void *workspace, void *stream, int64_t *count_
 #define PXST_K_FILTER     12  /* filter_map */
 #define PXST_K_FRAC       13  /* update_pixel_map_fractional: the fractional candidates */
 #define PXST_K_DEFOCUS    14  /* defocus_sweep (includes its make_object_map launches) */
-#define PXST_K_COUNT      15
+#define PXST_K_INTEGRATE  15  /* integrate_map (the stencil codes and the conjugate-gradient solve) */
+#define PXST_K_COUNT      16
 pxst_status pxst_timing_enable(int32_t enable);
 pxst_status pxst_timing_read(int64_t *launches, double *total_ms, int32_t n_kernels);
 const char *pxst_kernel_name(int32_t k);

@@ -26,7 +26,7 @@ FORM_BF16 = 1
 FORM_TF32 = 2
 KERNELS = ["prepare", "omap_scatter", "omap_normalise", "upm_search", "upm_exact", "reference_terms",
            "tensor_prep", "tensor_gtable", "tensor_search", "upm_rescore", "calc_error",
-           "update_translations", "filter_map", "upm_fractional", "defocus_sweep"]
+           "update_translations", "filter_map", "upm_fractional", "defocus_sweep", "integrate"]
 
 
 class PxstError(RuntimeError):

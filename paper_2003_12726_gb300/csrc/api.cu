@@ -458,6 +458,7 @@ pxst_status pxst_integrate_map(const pxst_dims *dims, const uint8_t *mask, doubl
     if (ws_bytes < L.total) return PXST_ERR_NOMEM;
     char *b = static_cast<char *>(workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Timed t(PXST_K_INTEGRATE, s);
     PXST_TRY(launch_integrate(*dims, mask, u_inout, max_iter, tol, info_out, reinterpret_cast<uint8_t *>(b + L.integ_type),
                               reinterpret_cast<double *>(b + L.integ_buf), reinterpret_cast<unsigned *>(b + L.integ_bar),
                               reinterpret_cast<WsHeader *>(b + L.header), timeout_ns, s));
@@ -568,6 +569,7 @@ const char *pxst_kernel_name(int32_t k) {
         case PXST_K_FILTER: return "filter_map";
         case PXST_K_FRAC: return "upm_fractional";
         case PXST_K_DEFOCUS: return "defocus_sweep";
+        case PXST_K_INTEGRATE: return "integrate";
         default: return "?";
     }
 }
