@@ -335,20 +335,25 @@ def accuracy(s, orc, u_int, e_int, u_q):
             "err_max_rel": float(rel.max()) if rel.size else 0.0}
 
 
-def kernel_roofline(name, avg_ms, s, ev_step, form, pk, basis, sms, sm_mhz):
+def kernel_roofline(name, avg_ms, s, ev_step, form, pk, basis, sms, sm_mhz, extra=None):
     """Algorithmic work of one launch of kernel group `name` over its average launch time,
-    against the peak that bounds it."""
+    against the peak that bounds it. extra: the full loop's translation window (tw), map
+    filter radius (filter_r) and conjugate-gradient steps per integration (integ_steps)."""
+    extra = extra or {}
     N = s.frames.shape[0]
     P = s.frames.shape[1] * s.frames.shape[2]
     R = s.ref_shape[0] * s.ref_shape[1]
     n_good = int(s.M.sum())
     alu = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
     alu_basis = f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"
+    # FP64: 2 DFMA per clock per SM on this GPU (the DFMA peak ncu reports for it)
+    fp64 = sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+    fp64_basis = f"{sms} SMs x 2 FP64 FMA x 2 flop x {sm_mhz:.0f} MHz ({basis} max clock)"
     if name == "tensor_search":
         work, unit, bound = 2.0 * ev_step / 1e12, "TFLOP/s", "tensor"        # cross term: one multiply-add per eval
         peak = float(pk["bf16_tflops"]) * (0.5 if form == 2 else 1.0)
         pb = f"{basis} dense bf16 cuBLAS burst" + (" x 0.5 (nominal tf32/bf16 ratio)" if form == 2 else "")
-    elif name in ("upm_search", "upm_exact"):
+    elif name == "upm_search":
         work, unit, bound, peak, pb = 4.0 * ev_step / 1e12, "TFLOP/s", "alu", alu, alu_basis   # 2 FMA per eval
     elif name == "upm_rescore":
         # at least the 3x3 about each pixel's first candidate: 2 FMA per pixel, frame and point
@@ -361,6 +366,26 @@ def kernel_roofline(name, avg_ms, s, ev_step, form, pk, basis, sms, sm_mhz):
     elif name == "tensor_prep":
         es = 4 if form == 2 else 2
         work, unit, bound = (4.0 * N * P + es * N * P + 5.0 * P) / 1e9, "GB/s", "hbm"
+        peak, pb = float(pk["hbm_gbs"]), f"{basis} HBM copy bandwidth"
+    elif name == "integrate":
+        # per pixel and conjugate-gradient step: the 5-point normal operator (5 flop), three
+        # vector updates and two dot products (2 flop each)
+        work = 17.0 * n_good * max(extra.get("integ_steps", 0), 1) / 1e12
+        unit, bound, peak, pb = "TFLOP/s", "fp64", fp64, fp64_basis
+    elif name == "filter_map":
+        # per good pixel: two passes of 2r + 1 taps, 3 FMA each
+        work = 12.0 * (2 * extra.get("filter_r", 4) + 1) * n_good / 1e12
+        unit, bound, peak, pb = "TFLOP/s", "fp64", fp64, fp64_basis
+    elif name == "update_translations":
+        # per pixel, frame and shift: the masked bilinear read (4 FMA) and the squared,
+        # normalised residual added to the shift's sum (2 FMA)
+        ty, tx = extra.get("tw") or (1, 1)
+        work = 12.0 * N * n_good * (2 * ty + 1) * (2 * tx + 1) / 1e12
+        unit, bound, peak, pb = "TFLOP/s", "alu", alu, alu_basis
+    elif name == "calc_error":
+        # frames read twice (var(x), then the errors), the map, W, M, var and the pixel error per
+        # pixel, the reference-plane sums and error per reference pixel
+        work, unit, bound = (8.0 * N * P + 33.0 * P + 12.0 * R) / 1e9, "GB/s", "hbm"
         peak, pb = float(pk["hbm_gbs"]), f"{basis} HBM copy bandwidth"
     else:
         # make_object_map: frames once, the map, W and M per pixel, FP64 flush and the outputs
@@ -391,6 +416,7 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
     # figures of merit (iv); --frac replaces the 3x3 fit by fractional candidates
     full, frac = args.loop == "full", args.frac
     delta0 = rec.delta.clone()
+    tw, integ = None, [None]
     if full:
         tw = (0, 2) if s.window[0] <= 1 else (1, 1)
         pe_t = torch.empty((rec.dims.ny, rec.dims.nx), dtype=torch.float32, device="cuda")
@@ -410,7 +436,7 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
             rec.run(1)
         if full:
             px.filter_map(rec.dims, 1.0, rec.M, rec.u, rec.ws)
-            px.integrate_map(rec.dims, rec.M, rec.u, rec.ws, max_iter=200, tol=1e-8)
+            integ[0] = px.integrate_map(rec.dims, rec.M, rec.u, rec.ws, max_iter=200, tol=1e-8)
             px.update_translations(rec.dims, tw, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta,
                                    rec.ws, fe_t)
             px.calc_error(rec.dims, rec.frames, rec.W, rec.M, rec.I_ref, rec.w, rec.u, rec.delta, rec.ws, pe_t,
@@ -527,7 +553,9 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
     res = {"ms_per_step": ms / args.steps, "ms_per_iteration_10": ms_iter10, "tuned": tuned,
            "ktimes": ktimes, "launches": launches, "exact_pixels": n_exact, "e2e_ms": ms_e2e / args.steps,
            "e2e_steps_ms": e2e_steps, "h2d_alone_ms": float(np.median(h2d_alone)),
-           "h2d": h2d, "d2h": d2h, "t_wall": (t_wall0, t_wall1), "accuracy": acc, "sweep": sweep}
+           "h2d": h2d, "d2h": d2h, "t_wall": (t_wall0, t_wall1), "accuracy": acc, "sweep": sweep,
+           "extra": {"tw": tw, "filter_r": 4,
+                     "integ_steps": int(integ[0][0].item()) if integ[0] is not None else 0}}
     del rec
     torch.cuda.empty_cache()
     return res
@@ -596,8 +624,8 @@ def pxst_arm(args, rank, world, local_rank):
     per_form = {}
     for f, r in results.items():
         kt = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in r["ktimes"].items() if v[0]}
-        roofs = {k: kernel_roofline(k, kt[k], s, ev_step, FORMS[f], pk, basis, sms, sm_mhz)
-                 for k in kt if k not in ("prepare", "omap_normalise")}
+        roofs = {k: kernel_roofline(k, kt[k], s, ev_step, FORMS[f], pk, basis, sms, sm_mhz, r.get("extra"))
+                 for k in kt if k not in ("prepare", "omap_normalise", "upm_exact")}
         dom = max(kt, key=lambda k: kt[k] * r["ktimes"][k][0])
         roofs[dom]["traffic"] = load_traffic(args.workload + ("" if f == "fp32" else "-" + f), dom)
         clocks = sampler.summary(r["t_wall"][0] - 0.2, r["t_wall"][1] + 0.2) if sampler else None

@@ -40,6 +40,7 @@ bool opts_ok(const pxst_options *o) {
 struct Ws {
     WsHeader *hdr;
     float *var_px;
+    PixSplit *usplit;
     double *u_save, *filt_den;
     double *tacc_sum, *delta_tmp;
     unsigned long long *tacc_cnt;
@@ -63,6 +64,7 @@ pxst_status carve(const pxst_dims &d, int form, void *workspace, size_t ws_bytes
     char *b = static_cast<char *>(workspace);
     w.hdr = reinterpret_cast<WsHeader *>(b + L.header);
     w.var_px = reinterpret_cast<float *>(b + L.var_px);
+    w.usplit = reinterpret_cast<PixSplit *>(b + L.usplit);
     w.u_save = reinterpret_cast<double *>(b + L.u_save);
     w.filt_den = reinterpret_cast<double *>(b + L.filt_den);
     w.tacc_sum = reinterpret_cast<double *>(b + L.tacc_sum);
@@ -363,7 +365,7 @@ pxst_status pxst_calc_error(const pxst_dims *dims, const float *frames, const fl
     st = run_prepare(*dims, delta, ws, s);
     if (st != PXST_OK) return st;
     Timed t(PXST_K_ERROR, s);
-    PXST_TRY(launch_pixvar(*dims, frames, W, mask, I_ref, w, u, delta, ws.shifts, ws.var_px, ws.hdr, s));
+    PXST_TRY(launch_pixvar(*dims, frames, W, mask, I_ref, w, u, delta, ws.shifts, ws.var_px, nullptr, ws.hdr, s));
     PXST_TRY(launch_calc_error(*dims, frames, W, mask, I_ref, w, u, delta, ws.shifts, ws.var_px, ws.hdr, pixel_err,
                                frame_err, total_err, ref_err, ws.num, ws.den, s));
     return PXST_OK;
@@ -383,10 +385,13 @@ pxst_status pxst_update_translations(const pxst_dims *dims, int32_t win_y, int32
     st = run_prepare(*dims, delta_inout, ws, s);
     if (st != PXST_OK) return st;
     Timed t(PXST_K_TRANS, s);
-    PXST_TRY(launch_pixvar(*dims, frames, W, mask, I_ref, w, u, delta_inout, ws.shifts, ws.var_px, ws.hdr, s));
-    // every frame's shifts are scored against the translations as they were on entry
+    PXST_TRY(launch_pixvar(*dims, frames, W, mask, I_ref, w, u, delta_inout, ws.shifts, ws.var_px, ws.usplit, ws.hdr,
+                           s));
+    // every frame's shifts are scored against the translations as they were on entry; the
+    // NaN-marked reference goes to the make_object_map accumulators, unused by this call
     PXST_TRY(launch_update_translations(*dims, win_y, win_x, quadratic, frames, W, mask, I_ref, w, u, delta_inout,
-                                        ws.shifts, ws.var_px, ws.hdr, ws.tacc_sum, ws.tacc_cnt, ws.delta_tmp,
+                                        ws.shifts, ws.var_px, ws.usplit, reinterpret_cast<float *>(ws.num), ws.hdr,
+                                        ws.tacc_sum, ws.tacc_cnt, ws.delta_tmp,
                                         frame_err, s));
     PXST_TRY(cudaMemcpyAsync(delta_inout, ws.delta_tmp, sizeof(double) * 2 * dims->n_frames,
                              cudaMemcpyDeviceToDevice, s));

@@ -58,6 +58,8 @@ struct MeritArgs {
     const double *u, *delta;
     const FrameShift *shifts;      // -Delta_n split (prepared from delta)
     float *var;                    // [P] workspace: var(x), -1 where the pixel does not count
+    PixSplit *split;               // [P] workspace: the split map (written by k_pixvar), or null
+    const float *Rm;               // [R] workspace: the NaN-marked reference, or null
     WsHeader *hdr;
 };
 
@@ -66,6 +68,7 @@ __global__ void __launch_bounds__(256) k_pixvar(MeritArgs a) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     float v = -1.0f;
+    PixSplit rec{0, 0, 0.0f, 0.0f, -1.0f, 0.0f, 0, 0};
     if (a.mask[p]) {
         const double u0 = a.u[p], u1 = a.u[P + p];
         if (!isfinite(u0) || !isfinite(u1)) {
@@ -78,12 +81,23 @@ __global__ void __launch_bounds__(256) k_pixvar(MeritArgs a) {
             float uf0, uf1;
             split_coord(u0, ui0, uf0);
             split_coord(u1, ui1, uf1);
+            rec = PixSplit{ui0, ui1, uf0, uf1, -1.0f, Wv, 0, 0};
             float s2 = 0.0f;
             for (int n = 0; n < a.N; ++n) {
                 int i0, j0;
-                float f0, f1, R;
+                float f0, f1;
                 frame_point(ui0, uf0, ui1, uf1, a.shifts[n], 0, 0, i0, f0, j0, f1);
-                if (!gather_masked(a.Iref, a.w, a.Ry, a.Rx, i0, j0, f0, f1, R)) continue;
+                // the frame is valid when gather_masked's weight sum is positive: some corner
+                // with a non-zero bilinear weight is on the grid with w > 0 (the weights are >= 0)
+                const float wt[4] = {(1.0f - f0) * (1.0f - f1), (1.0f - f0) * f1, f0 * (1.0f - f1), f0 * f1};
+                bool valid = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
+                    if (wt[k] == 0.0f || ii < 0 || ii >= a.Ry || jj < 0 || jj >= a.Rx) continue;
+                    valid = valid || __ldg(a.w + (size_t)ii * a.Rx + jj) > 0.0f;
+                }
+                if (!valid) continue;
                 const float t = __ldg(a.frames + (size_t)n * P + p) - Wv;
                 s2 = fmaf(t, t, s2);
             }
@@ -91,6 +105,17 @@ __global__ void __launch_bounds__(256) k_pixvar(MeritArgs a) {
         }
     }
     a.var[p] = v;
+    if (a.split) {
+        rec.var = v;
+        a.split[p] = rec;
+    }
+}
+
+// the record of pixel p, read as two 16-byte loads through the read-only path
+__device__ __forceinline__ PixSplit load_split(const PixSplit *sp, size_t p) {
+    const int4 *q = reinterpret_cast<const int4 *>(sp + p);
+    const int4 x = __ldg(q), y = __ldg(q + 1);
+    return PixSplit{x.x, x.y, __int_as_float(x.z), __int_as_float(x.w), __int_as_float(y.x), __int_as_float(y.y), 0, 0};
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -103,8 +128,16 @@ struct ErrorOut {
     float *pixel_err;      // [P] or null
     double *frame_err;     // [N] or null (accumulated: zeroed by the launcher)
     double *total;         // [1] or null (accumulated)
-    float *num, *den;      // [R] accumulators of the reference-plane error, or null
+    float2 *nd;            // [R] accumulators (sum of weight x eps, sum of weight) of the
+                           // reference-plane error, or null
 };
+
+// The reference with its unusable cells (w <= 0) stored as NaN, so that a masked read takes
+// one load per corner.
+__global__ void k_nanref(int R, const float *__restrict__ Iref, const float *__restrict__ w, float *__restrict__ Rm) {
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < (size_t)R; c += (size_t)gridDim.x * blockDim.x)
+        Rm[c] = w[c] > 0.0f ? Iref[c] : __int_as_float(0x7fc00000);
+}
 
 constexpr int kErrFramesSmem = 6144;   // frame sums kept in shared memory up to this many frames
 
@@ -134,36 +167,66 @@ __global__ void __launch_bounds__(256) k_calc_error(MeritArgs a, ErrorOut o) {
             Wv = a.W[p];
         }
         float pe = 0.0f;
-        for (int n = 0; n < a.N; ++n) {
+        const float rvar = var > 0.0f ? 1.0f / var : 1.0f;     // var = 0: eps = d^2
+        // a warp none of whose pixels counts adds nothing to any sum
+        const int n_end = __any_sync(0xffffffffu, act) ? a.N : 0;
+        for (int n = 0; n < n_end; ++n) {
             float eps = 0.0f;
+            bool sc = false;                 // this lane scatters frame n
+            int i0 = 0, j0 = 0;
+            float wt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             if (act) {
-                int i0, j0;
                 float fy, fx, R;
                 frame_point(ui0, uf0, ui1, uf1, a.shifts[n], 0, 0, i0, fy, j0, fx);
-                if (gather_masked(a.Iref, a.w, a.Ry, a.Rx, i0, j0, fy, fx, R)) {
+                if (gather_rm(a.Rm, a.Ry, a.Rx, i0, j0, fy, fx, R)) {
                     const float d = fmaf(-Wv, R, __ldg(a.frames + (size_t)n * P + p));
-                    eps = var > 0.0f ? d * d / var : d * d;
-                    if (o.num) {
-                        // scatter with make_object_map's bilinear weights (corners off the grid dropped)
-                        const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx),
-                                             fy * fx};
+                    eps = d * d * rvar;
+                    sc = o.nd != nullptr;
+                    wt[0] = (1.0f - fy) * (1.0f - fx);
+                    wt[1] = (1.0f - fy) * fx;
+                    wt[2] = fy * (1.0f - fx);
+                    wt[3] = fy * fx;
+                }
+            }
+            if (o.nd) {
+                // scatter with make_object_map's bilinear weights (corners off the grid
+                // dropped), both sums of a cell in one 8-byte atomic. The lanes are consecutive
+                // pixels: where lane l's right corners are lane l + 1's left corners, lane l
+                // hands them over and lane l + 1 adds both with one atomic per row.
+                const int ni0 = __shfl_down_sync(0xffffffffu, i0, 1), nj0 = __shfl_down_sync(0xffffffffu, j0, 1);
+                const bool nsc = __shfl_down_sync(0xffffffffu, (int)sc, 1) != 0;
+                const bool give = sc && lane < 31 && nsc && ni0 == i0 && nj0 == j0 + 1;
+                const bool take = __shfl_up_sync(0xffffffffu, (int)give, 1) != 0 && lane > 0;
+                const float g1 = wt[1] * eps, g3 = wt[3] * eps;
+                const float t1 = __shfl_up_sync(0xffffffffu, g1, 1), tw1 = __shfl_up_sync(0xffffffffu, wt[1], 1);
+                const float t3 = __shfl_up_sync(0xffffffffu, g3, 1), tw3 = __shfl_up_sync(0xffffffffu, wt[3], 1);
+                if (sc) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
-                            if (wt[k] == 0.0f || ii < 0 || ii >= a.Ry || jj < 0 || jj >= a.Rx) continue;
-                            const size_t c = (size_t)ii * a.Rx + jj;
-                            atomicAdd(o.num + c, wt[k] * eps);
-                            atomicAdd(o.den + c, wt[k]);
+                    for (int k = 0; k < 4; ++k) {
+                        if (give && (k & 1)) continue;
+                        float vs = wt[k] * eps, vw = wt[k];
+                        if (take && k == 0) {
+                            vs += t1;
+                            vw += tw1;
+                        } else if (take && k == 2) {
+                            vs += t3;
+                            vw += tw3;
                         }
+                        const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
+                        if (vw == 0.0f || ii < 0 || ii >= a.Ry || jj < 0 || jj >= a.Rx) continue;
+                        atomicAdd(o.nd + (size_t)ii * a.Rx + jj, make_float2(vs, vw));
                     }
                 }
             }
             pe += eps;
             if (o.frame_err) {
-                const double s = warp_sum((double)eps);
-                if (lane == 0 && s != 0.0) {
-                    if (smem_fe) atomicAdd(s_fe + n, s);
-                    else atomicAdd(o.frame_err + n, s);
+                // the warp's 32 terms are summed in FP32, the warps' sums in FP64
+                float s = eps;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (lane == 0 && s != 0.0f) {
+                    if (smem_fe) atomicAdd(s_fe + n, (double)s);
+                    else atomicAdd(o.frame_err + n, (double)s);
                 }
             }
         }
@@ -185,10 +248,11 @@ __global__ void __launch_bounds__(256) k_calc_error(MeritArgs a, ErrorOut o) {
             if (s_fe[n] != 0.0) atomicAdd(o.frame_err + n, s_fe[n]);
 }
 
-__global__ void k_err_normalise(int R, const float *__restrict__ num, const float *__restrict__ den,
-                                float *__restrict__ ref_err) {
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < (size_t)R; c += (size_t)gridDim.x * blockDim.x)
-        ref_err[c] = den[c] > 0.0f ? num[c] / den[c] : 0.0f;
+__global__ void k_err_normalise(int R, const float2 *__restrict__ nd, float *__restrict__ ref_err) {
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < (size_t)R; c += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = nd[c];
+        ref_err[c] = v.y > 0.0f ? v.x / v.y : 0.0f;
+    }
 }
 
 struct TransArgs {
@@ -223,8 +287,8 @@ __global__ void __launch_bounds__(256) k_trans_acc(TransArgs t) {
         int ui0 = 0, ui1 = 0;
         float uf0 = 0.0f, uf1 = 0.0f, I = 0.0f, Wv = 0.0f;
         if (act) {
-            split_coord(a.u[p], ui0, uf0);
-            split_coord(a.u[P + p], ui1, uf1);
+            const PixSplit ps = a.split[p];
+            ui0 = ps.i0; ui1 = ps.i1; uf0 = ps.f0; uf1 = ps.f1;
             I = __ldg(a.frames + (size_t)n * P + p);
             Wv = a.W[p];
         }
@@ -255,6 +319,136 @@ __global__ void __launch_bounds__(256) k_trans_acc(TransArgs t) {
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nc; k += blockDim.x)
+        if (s_cnt[k]) {
+            atomicAdd(t.acc_sum + (size_t)n * kTransMax + k, s_sum[k]);
+            atomicAdd(t.acc_cnt + (size_t)n * kTransMax + k, (unsigned long long)s_cnt[k]);
+        }
+}
+
+// The same sums for small shift windows (|t_y| <= TY, |t_x| <= TX): for a pixel and frame, the
+// reads at u - Delta_n - t of every shift t share one set of bilinear weights (an integer
+// shift leaves the fraction alone) and lie in one (2TY + 2) x (2TX + 2) patch of the
+// NaN-marked reference, which is read once; each masked read then takes the arithmetic of
+// gather_masked, corner by corner (the weight sum divides once when every corner is usable).
+// Each thread keeps its own sums per shift in registers (FP32 over at most 64 pixels, then
+// FP64) and the block sums them once at the end; the next pixel's record is read while this
+// one is scored.
+template <int TY, int TX>
+__global__ void __launch_bounds__(256, (2 * TY + 1) * (2 * TX + 1) > 9 ? 1 : 3) k_trans_acc_patch(TransArgs t) {
+    constexpr int WX = 2 * TX + 1, NC = (2 * TY + 1) * WX, PH = 2 * TY + 2, PW = 2 * TX + 2;
+    static_assert(PH * PW <= 64, "patch validity bits");
+    constexpr unsigned long long ALL = (PH * PW == 64) ? ~0ull : ((1ull << (PH * PW)) - 1ull);
+    __shared__ double s_sum[NC];
+    __shared__ unsigned int s_cnt[NC];
+    const MeritArgs &a = t.m;
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) {
+        s_sum[k] = 0.0;
+        s_cnt[k] = 0u;
+    }
+    __syncthreads();
+    const size_t P = (size_t)a.ny * a.nx;
+    const int n = blockIdx.y;
+    const FrameShift sh = a.shifts[n];
+    const float qnan = __int_as_float(0x7fc00000);
+    float acc[NC];
+    double accd[NC];
+    unsigned cnt[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        acc[k] = 0.0f;
+        accd[k] = 0.0;
+        cnt[k] = 0u;
+    }
+    int since = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const PixSplit none{0, 0, 0.0f, 0.0f, -1.0f, 0.0f, 0, 0};
+    size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    PixSplit nxt = p < P ? load_split(a.split, p) : none;
+    for (; p < P; p += stride) {
+        const PixSplit ps = nxt;
+        nxt = p + stride < P ? load_split(a.split, p + stride) : none;
+        const float var = ps.var;
+        if (!(var > 0.0f)) continue;
+        const float I = __ldcs(a.frames + (size_t)n * P + p), Wv = ps.W;
+        int i0, j0;
+        float fy, fx;
+        frame_point(ps.i0, ps.f0, ps.i1, ps.f1, sh, 0, 0, i0, fy, j0, fx);
+        const float wt[4] = {(1.0f - fy) * (1.0f - fx), (1.0f - fy) * fx, fy * (1.0f - fx), fy * fx};
+        // the patch: rows i0 - TY .. i0 + TY + 1, columns j0 - TX .. j0 + TX + 1 (NaN: unusable)
+        float pv[PH][PW];
+        unsigned long long ok = 0ull;
+        const bool inside = i0 - TY >= 0 && i0 + TY + 1 < a.Ry && j0 - TX >= 0 && j0 + TX + 1 < a.Rx;
+#pragma unroll
+        for (int r = 0; r < PH; ++r)
+#pragma unroll
+            for (int c = 0; c < PW; ++c) {
+                const int ii = i0 - TY + r, jj = j0 - TX + c;
+                float v = qnan;
+                if (inside || (ii >= 0 && ii < a.Ry && jj >= 0 && jj < a.Rx)) v = __ldg(a.Rm + (size_t)ii * a.Rx + jj);
+                pv[r][c] = v;
+                if (v == v) ok |= 1ull << (r * PW + c);
+            }
+        const float rvar = 1.0f / var;
+        if (ok == ALL) {
+            const float rden = 1.0f / (((wt[0] + wt[1]) + wt[2]) + wt[3]);
+#pragma unroll
+            for (int da = -TY; da <= TY; ++da)
+#pragma unroll
+                for (int db = -TX; db <= TX; ++db) {
+                    const int r0 = TY - da, c0 = TX - db, k = (da + TY) * WX + (db + TX);
+                    float num = wt[0] * pv[r0][c0];
+                    num = fmaf(wt[1], pv[r0][c0 + 1], num);
+                    num = fmaf(wt[2], pv[r0 + 1][c0], num);
+                    num = fmaf(wt[3], pv[r0 + 1][c0 + 1], num);
+                    const float d = fmaf(-Wv, num * rden, I);
+                    acc[k] = fmaf(d * d, rvar, acc[k]);
+                    cnt[k] += 1u;
+                }
+        } else {
+#pragma unroll
+            for (int da = -TY; da <= TY; ++da)
+#pragma unroll
+                for (int db = -TX; db <= TX; ++db) {
+                    const int r0 = TY - da, c0 = TX - db, k = (da + TY) * WX + (db + TX);
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = r0 + (q >> 1), c = c0 + (q & 1);
+                        if (wt[q] == 0.0f || !((ok >> (r * PW + c)) & 1ull)) continue;
+                        num = fmaf(wt[q], pv[r][c], num);
+                        den += wt[q];
+                    }
+                    if (den > 0.0f) {
+                        const float d = fmaf(-Wv, num / den, I);
+                        acc[k] = fmaf(d * d, rvar, acc[k]);
+                        cnt[k] += 1u;
+                    }
+                }
+        }
+        if (++since == 64) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                accd[k] += (double)acc[k];
+                acc[k] = 0.0f;
+            }
+            since = 0;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        double sv = accd[k] + (double)acc[k];
+        unsigned c = cnt[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) {
+            atomicAdd(&s_sum[k], sv);
+            atomicAdd(&s_cnt[k], c);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NC; k += blockDim.x)
         if (s_cnt[k]) {
             atomicAdd(t.acc_sum + (size_t)n * kTransMax + k, s_sum[k]);
             atomicAdd(t.acc_cnt + (size_t)n * kTransMax + k, (unsigned long long)s_cnt[k]);
@@ -299,12 +493,12 @@ __global__ void k_trans_fit(TransArgs t) {
 
 MeritArgs merit_args(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
                      const float *I_ref, const float *w, const double *u, const double *delta,
-                     const FrameShift *shifts, float *var, WsHeader *hdr) {
+                     const FrameShift *shifts, float *var, WsHeader *hdr, PixSplit *split = nullptr) {
     MeritArgs a;
     a.shifts = shifts;
     a.N = d.n_frames; a.ny = d.ny; a.nx = d.nx; a.Ry = d.ref_ny; a.Rx = d.ref_nx;
     a.frames = frames; a.W = W; a.mask = mask; a.Iref = I_ref; a.w = w; a.u = u; a.delta = delta;
-    a.var = var; a.hdr = hdr;
+    a.var = var; a.hdr = hdr; a.split = split; a.Rm = nullptr;
     return a;
 }
 
@@ -568,9 +762,10 @@ cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *m
 
 cudaError_t launch_pixvar(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
                           const float *I_ref, const float *w, const double *u, const double *delta,
-                          const FrameShift *shifts, float *var, WsHeader *hdr, cudaStream_t s) {
+                          const FrameShift *shifts, float *var, PixSplit *split, WsHeader *hdr, cudaStream_t s) {
     const size_t P = (size_t)d.ny * d.nx;
-    k_pixvar<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, var, hdr)); note_launch();
+    k_pixvar<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(
+        merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, var, hdr, split)); note_launch();
     return cudaGetLastError();
 }
 
@@ -583,25 +778,29 @@ cudaError_t launch_calc_error(const pxst_dims &d, const float *frames, const flo
     cudaError_t e;
     if (frame_err && (e = cudaMemsetAsync(frame_err, 0, sizeof(double) * d.n_frames, s)) != cudaSuccess) return e;
     if (total && (e = cudaMemsetAsync(total, 0, sizeof(double), s)) != cudaSuccess) return e;
-    if (ref_err) {
-        if ((e = cudaMemsetAsync(num, 0, sizeof(float) * R, s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(den, 0, sizeof(float) * R, s)) != cudaSuccess) return e;
-    }
-    float *numf = reinterpret_cast<float *>(num), *denf = reinterpret_cast<float *>(den);   // R floats each
-    ErrorOut o{pixel_err, frame_err, total, ref_err ? numf : nullptr, ref_err ? denf : nullptr};
+    float2 *nd = reinterpret_cast<float2 *>(num);     // R (sum, weight) pairs in num's R doubles
+    if (ref_err && (e = cudaMemsetAsync(nd, 0, sizeof(float2) * R, s)) != cudaSuccess) return e;
+    ErrorOut o{pixel_err, frame_err, total, ref_err ? nd : nullptr};
     size_t blocks = (P + 255) / 256;
     if (blocks > (size_t)device_sms() * 4) blocks = (size_t)device_sms() * 4;
     const size_t smem = (frame_err && d.n_frames <= kErrFramesSmem) ? sizeof(double) * d.n_frames : 0;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(k_calc_error, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    k_calc_error<<<(unsigned)blocks, 256, smem, s>>>(
-        merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, const_cast<float *>(var), hdr), o); note_launch();
+    // the NaN-marked reference in den's space (R floats of R doubles)
+    float *Rm = reinterpret_cast<float *>(den);
+    size_t rb = (R + 255) / 256;
+    if (rb > (size_t)device_sms() * 8) rb = (size_t)device_sms() * 8;
+    k_nanref<<<(unsigned)rb, 256, 0, s>>>((int)R, I_ref, w, Rm); note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    MeritArgs ma = merit_args(d, frames, W, mask, I_ref, w, u, delta, shifts, const_cast<float *>(var), hdr);
+    ma.Rm = Rm;
+    k_calc_error<<<(unsigned)blocks, 256, smem, s>>>(ma, o); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ref_err) {
         blocks = (R + 255) / 256;
         if (blocks > (size_t)device_sms() * 16) blocks = (size_t)device_sms() * 16;
-        k_err_normalise<<<(unsigned)blocks, 256, 0, s>>>((int)R, numf, denf, ref_err); note_launch();
+        k_err_normalise<<<(unsigned)blocks, 256, 0, s>>>((int)R, nd, ref_err); note_launch();
         e = cudaGetLastError();
     }
     return e;
@@ -610,22 +809,45 @@ cudaError_t launch_calc_error(const pxst_dims &d, const float *frames, const flo
 cudaError_t launch_update_translations(const pxst_dims &d, int Ty, int Tx, int quadratic, const float *frames,
                                        const float *W, const uint8_t *mask, const float *I_ref, const float *w,
                                        const double *u, const double *delta_in, const FrameShift *shifts,
-                                       const float *var, WsHeader *hdr, double *acc_sum,
-                                       unsigned long long *acc_cnt, double *delta_out, double *err_out,
-                                       cudaStream_t s) {
+                                       const float *var, const PixSplit *split, float *Rm, WsHeader *hdr,
+                                       double *acc_sum, unsigned long long *acc_cnt, double *delta_out,
+                                       double *err_out, cudaStream_t s) {
     const size_t P = (size_t)d.ny * d.nx;
     cudaError_t e;
     if ((e = cudaMemsetAsync(acc_sum, 0, sizeof(double) * kTransMax * d.n_frames, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(acc_cnt, 0, sizeof(unsigned long long) * kTransMax * d.n_frames, s)) != cudaSuccess)
         return e;
     TransArgs t;
-    t.m = merit_args(d, frames, W, mask, I_ref, w, u, delta_in, shifts, const_cast<float *>(var), hdr);
+    t.m = merit_args(d, frames, W, mask, I_ref, w, u, delta_in, shifts, const_cast<float *>(var), hdr,
+                     const_cast<PixSplit *>(split));
     t.Ty = Ty; t.Tx = Tx; t.quadratic = quadratic;
     t.acc_sum = acc_sum; t.acc_cnt = acc_cnt; t.delta_out = delta_out; t.err_out = err_out;
+    // small windows take the patch kernel (one instance per window shape) on the NaN-marked
+    // reference
+    void (*patch)(TransArgs) = nullptr;
+    if (Ty == 0 && Tx == 0) patch = k_trans_acc_patch<0, 0>;
+    else if (Ty == 0 && Tx == 1) patch = k_trans_acc_patch<0, 1>;
+    else if (Ty == 0 && Tx == 2) patch = k_trans_acc_patch<0, 2>;
+    else if (Ty == 1 && Tx == 0) patch = k_trans_acc_patch<1, 0>;
+    else if (Ty == 1 && Tx == 1) patch = k_trans_acc_patch<1, 1>;
+    else if (Ty == 1 && Tx == 2) patch = k_trans_acc_patch<1, 2>;
+    else if (Ty == 2 && Tx == 0) patch = k_trans_acc_patch<2, 0>;
+    else if (Ty == 2 && Tx == 1) patch = k_trans_acc_patch<2, 1>;
+    else if (Ty == 2 && Tx == 2) patch = k_trans_acc_patch<2, 2>;
     size_t g = (P + 255) / 256;
     if (g > 32) g = 32;                 // blocks per frame
-    dim3 grid((unsigned)g, (unsigned)d.n_frames);
-    k_trans_acc<<<grid, 256, 0, s>>>(t); note_launch();
+    if (patch) {
+        const size_t R = (size_t)d.ref_ny * d.ref_nx;
+        size_t rb = (R + 255) / 256;
+        if (rb > (size_t)device_sms() * 8) rb = (size_t)device_sms() * 8;
+        k_nanref<<<(unsigned)rb, 256, 0, s>>>((int)R, I_ref, w, Rm); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        t.m.Rm = Rm;
+        patch<<<dim3((unsigned)g, (unsigned)d.n_frames), 256, 0, s>>>(t);
+    } else {
+        k_trans_acc<<<dim3((unsigned)g, (unsigned)d.n_frames), 256, 0, s>>>(t);
+    }
+    note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_trans_fit<<<(d.n_frames + 127) / 128, 128, 0, s>>>(t); note_launch();
     return cudaGetLastError();

@@ -9,15 +9,18 @@
 // equals u_a[p]. Psi minimises the squared residuals: conjugate gradients on the normal
 // equations G^T G Psi = G^T u from Psi = 0. The output u_a[p] = (G Psi) of each equation.
 //
-// One cooperative launch runs every step: all blocks are resident, the pixels are split
-// over them, and a grid barrier (bounded by %globaltimer: a barrier that runs out sets
-// PXST_DEV_TIMEOUT and every block leaves) separates the stencil passes. Per step:
-//   A  d = r + beta d_prev (the new search direction, double-buffered) and g = G d;
-//   B  q = G^T g (a gather over the equations that read the pixel) and the block's part
-//      of d.q;
+// One cooperative launch runs every step: all blocks are resident (two per SM), the pixels
+// are split over them, and a grid barrier (bounded by %globaltimer: a barrier that runs out
+// sets PXST_DEV_TIMEOUT and every block leaves) separates the passes. The normal operator
+// A = G^T G is applied to the residual, so that q = A d follows by the recurrence
+// q = A r + beta q_prev (d = r + beta d_prev): the stencil reads r alone and d, q are each
+// pixel's own. At a pixel whose equations along an axis are all central differences A is
+// (2 x[p] - x[p - 2e] - x[p + 2e]) / 4 on that axis. Per step, two passes:
+//   B  d = r + beta d, q = A r + beta q and the block's part of d.q;
 //   C  psi += alpha d, r -= alpha q and the block's part of r.r.
-// The dot products are summed in block order by every block from per-block partial sums,
-// so the result does not depend on scheduling. FP64 throughout.
+// The dot products are summed from per-block partial sums in one fixed order by every
+// block, so the result does not depend on scheduling and every block takes the same
+// branch. FP64 throughout.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,14 +30,14 @@
 namespace pxst {
 namespace {
 
-constexpr int IG_THREADS = 256;
+constexpr int IG_THREADS = 512;
+constexpr int IG_FAST = 8;     // type bit: the axis' equations that read the pixel are central only
 
 struct IntegArgs {
     int ny, nx;
-    const uint8_t *mask;
     double *u;                 // [2][P], in place
-    const uint8_t *type;       // [2][P] stencil of each pixel and axis (0 none)
-    double *psi, *r, *d0, *d1, *q, *g;   // [P] each, g [2][P]
+    const uint8_t *type;       // [2][P] stencil code of each pixel and axis (0 none) | IG_FAST
+    double *psi, *r, *d0, *q;  // [P] each
     double *part;              // [2][gridDim.x] per-block partial sums
     unsigned *bar;             // [2] barrier arrival count and generation
     WsHeader *hdr;
@@ -68,27 +71,41 @@ __device__ __forceinline__ double tap_at(int code, int k) {
     return v;
 }
 
-__global__ void __launch_bounds__(IG_THREADS) k_integ_types(int ny, int nx, const uint8_t *__restrict__ M,
-                                                              uint8_t *__restrict__ type) {
+// the stencil code of the pixel at `pos` on a line of `len` pixels (good(k): the pixel k
+// steps away is inside and good)
+template <class Good>
+__device__ __forceinline__ int stencil_code(Good good) {
+    if (!good(0)) return 0;
+    if (good(1) && good(-1)) return 1;
+    if (good(1) && good(2)) return 2;
+    if (good(-1) && good(-2)) return 3;
+    if (good(1)) return 4;
+    if (good(-1)) return 5;
+    return 0;
+}
+
+// Codes, and the IG_FAST bit where the equations along the axis that read the pixel are the
+// central ones at p - e and p + e alone: the pixel and both neighbours are central, the
+// pixel two behind is not second-order forward and the one two ahead not second-order
+// backward (those would read p as well).
+__global__ void __launch_bounds__(256) k_integ_types(int ny, int nx, const uint8_t *__restrict__ M,
+                                                     uint8_t *__restrict__ type) {
     const size_t P = (size_t)ny * nx;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(p / nx), j = (int)(p % nx);
         for (int a = 0; a < 2; ++a) {
-            uint8_t code = 0;
-            if (M[p]) {
-                const int len = a == 0 ? ny : nx, pos = a == 0 ? i : j;
-                auto good = [&](int k) {
-                    const int t = pos + k;
+            const int len = a == 0 ? ny : nx, pos = a == 0 ? i : j;
+            auto code_at = [&](int k0) {
+                return stencil_code([&](int k) {
+                    const int t = pos + k0 + k;
                     if (t < 0 || t >= len) return false;
                     return M[a == 0 ? (size_t)t * nx + j : (size_t)i * nx + t] != 0;
-                };
-                if (good(1) && good(-1)) code = 1;
-                else if (good(1) && good(2)) code = 2;
-                else if (good(-1) && good(-2)) code = 3;
-                else if (good(1)) code = 4;
-                else if (good(-1)) code = 5;
-            }
-            type[a * P + p] = code;
+                });
+            };
+            const int code = code_at(0);
+            int v = code;
+            if (code == 1 && code_at(-1) == 1 && code_at(1) == 1 && code_at(-2) != 2 && code_at(2) != 3) v |= IG_FAST;
+            type[a * P + p] = (uint8_t)v;
         }
     }
 }
@@ -118,7 +135,7 @@ __device__ bool grid_barrier(unsigned *bar, unsigned long long limit_ns, WsHeade
                     s_ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -127,9 +144,12 @@ __device__ bool grid_barrier(unsigned *bar, unsigned long long limit_ns, WsHeade
     return s_ok != 0;
 }
 
-// block sum of v, written to part[blockIdx.x]
-__device__ void block_partial(double v, double *part) {
+// Sum of v over the block in one fixed order: butterfly over the warp (every lane ends with
+// the same bits, since each step adds the same two values in either order), then the warp
+// sums in warp order. The result is returned to every thread.
+__device__ double block_sum(double v) {
     __shared__ double s_red[IG_THREADS / 32];
+    __shared__ double s_tot;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
@@ -137,17 +157,6 @@ __device__ void block_partial(double v, double *part) {
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < IG_THREADS / 32; ++w) s += s_red[w];
-        part[blockIdx.x] = s;
-    }
-    __syncthreads();
-}
-
-// the partial sums in block order (every block computes the same value)
-__device__ double sum_partials(const double *part) {
-    __shared__ double s_tot;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile const double *)part)[b];
         s_tot = s;
     }
     __syncthreads();
@@ -156,18 +165,29 @@ __device__ double sum_partials(const double *part) {
     return t;
 }
 
-__global__ void __launch_bounds__(IG_THREADS) k_integrate(IntegArgs a) {
+// the partial sums of all blocks, read by every thread of every block (thread t takes blocks
+// t, t + IG_THREADS, ...) and summed by block_sum: the same value in every block
+__device__ double sum_partials(const double *part) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += IG_THREADS) s += __ldcg(part + b);
+    return block_sum(s);
+}
+
+__device__ __forceinline__ void put_partial(double v, double *part) {
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(IG_THREADS, 2) k_integrate(IntegArgs a) {
     const size_t P = (size_t)a.ny * a.nx;
     const size_t stride = (size_t)gridDim.x * blockDim.x, start = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     double *part0 = a.part, *part1 = a.part + gridDim.x;
-    // g = the data of every equation; then r = d = G^T g (b), psi = 0; |b|^2
-    for (size_t p = start; p < P; p += stride)
-        for (int s = 0; s < 2; ++s) a.g[s * P + p] = a.type[s * P + p] ? a.u[s * P + p] : 0.0;
-    if (!grid_barrier(a.bar, a.limit_ns, a.hdr)) return;
-    // the gather of G^T: pixel p collects, along each axis, from the equations of the
-    // pixels p - k e (k = -2..2) whose stencil reads p (tap k)
-    auto apply_GT = [&](size_t p) {
+    const uint8_t *__restrict__ type = a.type;
+
+    // (G^T x)[p] along both axes, x_s[src] = xval(s, src) for each equation src: pixel p
+    // collects from the equations of the pixels p - k e (k = -2..2) whose stencil reads p
+    auto apply_GT = [&](size_t p, auto xval) {
         const int i = (int)(p / nx), j = (int)(p % nx);
         double y = 0.0;
 #pragma unroll
@@ -178,66 +198,69 @@ __global__ void __launch_bounds__(IG_THREADS) k_integrate(IntegArgs a) {
             for (int k = -2; k <= 2; ++k) {
                 if (pos - k < 0 || pos - k >= len) continue;
                 const size_t src = (size_t)((long)p - k * step);
-                const int code = a.type[s * P + src];
-                if (code) y = fma(tap_at(code, k), a.g[s * P + src], y);
+                const int code = type[s * P + src] & 7;
+                if (code) y = fma(tap_at(code, k), xval(s, src), y);
             }
         }
         return y;
     };
-    double bb = 0.0;
+
+    // (G^T G x)[p] from x at the stencil points: at a pixel whose equations along both axes
+    // are central it is x[p] - (x[p - 2 nx] + x[p + 2 nx] + x[p - 2] + x[p + 2]) / 4
+    auto apply_A = [&](size_t p, int t0, int t1, const double *x) {
+        if ((t0 & t1) & IG_FAST) {
+            const double s4 = (x[p - 2 * (size_t)nx] + x[p + 2 * (size_t)nx]) + (x[p - 2] + x[p + 2]);
+            return fma(-0.25, s4, x[p]);
+        }
+        return apply_GT(p, [&](int s, size_t src) {
+            int off[3];
+            double c[3];
+            const int n = stencil_taps(type[s * P + src] & 7, off, c);
+            const long step = s == 0 ? nx : 1;
+            double v = 0.0;
+            for (int t = 0; t < n; ++t) v = fma(c[t], x[(size_t)((long)src + off[t] * step)], v);
+            return v;
+        });
+    };
+
+    // r = G^T u (b), d = q = psi = 0; |b|^2. A pixel that no equation reads (both codes 0:
+    // a bad pixel, or a good one without a good neighbour) keeps r = d = q = psi = 0 and is
+    // skipped below.
+    double bb;
     {
         double loc = 0.0;
         for (size_t p = start; p < P; p += stride) {
-            const double b = apply_GT(p);
+            const bool any = (type[p] | type[P + p]) != 0;
+            const double b = any ? apply_GT(p, [&](int s, size_t src) { return a.u[s * P + src]; }) : 0.0;
             a.r[p] = b;
-            a.d0[p] = b;
+            a.d0[p] = 0.0;
+            a.q[p] = 0.0;
             a.psi[p] = 0.0;
             loc = fma(b, b, loc);
         }
-        block_partial(loc, part0);
+        put_partial(loc, part0);
         if (!grid_barrier(a.bar, a.limit_ns, a.hdr)) return;
         bb = sum_partials(part0);
     }
-    double rr = bb;
+    double rr = bb, beta = 0.0;
     int it = 0;
-    double *dc = a.d0, *dn = a.d1;
-    double beta = 0.0;
-    bool first = true;
+    double *d = a.d0, *q = a.q, *r = a.r, *psi = a.psi;
     while (it < a.max_iter && rr > a.tol * a.tol * bb && bb > 0.0) {
-        // A: the new direction (d = r + beta d_prev, except on the first step) and g = G d,
-        //    taking d at every tap from r and d_prev (neither changes in this pass)
-        for (size_t p = start; p < P; p += stride) {
-            if (!first) dn[p] = fma(beta, dc[p], a.r[p]);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                int off[3];
-                double c[3];
-                const int n = stencil_taps(a.type[s * P + p], off, c);
-                const long step = s == 0 ? nx : 1;
-                double v = 0.0;
-                for (int t = 0; t < n; ++t) {
-                    const size_t k = (size_t)((long)p + off[t] * step);
-                    const double dk = first ? dc[k] : fma(beta, dc[k], a.r[k]);
-                    v = fma(c[t], dk, v);
-                }
-                a.g[s * P + p] = v;
-            }
-        }
-        if (!first) {
-            double *t = dc;
-            dc = dn;
-            dn = t;
-        }
-        first = false;
-        if (!grid_barrier(a.bar, a.limit_ns, a.hdr)) return;
-        // B: q = G^T g and d.q
+        // B: d = r + beta d and q = G^T G d = G^T G r + beta q (the operator applied to r, read
+        //    at the stencil points; d and q are the pixel's own), and d.q (beta = 0 and
+        //    d = q = 0 on the first step)
         double loc = 0.0;
         for (size_t p = start; p < P; p += stride) {
-            const double qv = apply_GT(p);
-            a.q[p] = qv;
-            loc = fma(dc[p], qv, loc);
+            const int t0 = type[p], t1 = type[P + p];
+            if (!(t0 | t1)) continue;
+            const double sv = apply_A(p, t0, t1, r);
+            const double dp = fma(beta, d[p], r[p]);
+            const double qv = fma(beta, q[p], sv);
+            d[p] = dp;
+            q[p] = qv;
+            loc = fma(dp, qv, loc);
         }
-        block_partial(loc, part0);
+        put_partial(loc, part0);
         if (!grid_barrier(a.bar, a.limit_ns, a.hdr)) return;
         const double dq = sum_partials(part0);
         if (!(dq > 0.0)) break;
@@ -245,36 +268,33 @@ __global__ void __launch_bounds__(IG_THREADS) k_integrate(IntegArgs a) {
         // C: the solution and the residual, and r.r
         loc = 0.0;
         for (size_t p = start; p < P; p += stride) {
-            a.psi[p] = fma(alpha, dc[p], a.psi[p]);
-            const double rv = fma(-alpha, a.q[p], a.r[p]);
-            a.r[p] = rv;
+            if (!(type[p] | type[P + p])) continue;
+            psi[p] = fma(alpha, d[p], psi[p]);
+            const double rv = fma(-alpha, q[p], r[p]);
+            r[p] = rv;
             loc = fma(rv, rv, loc);
         }
-        block_partial(loc, part1);
+        put_partial(loc, part1);
         if (!grid_barrier(a.bar, a.limit_ns, a.hdr)) return;
         const double rr_new = sum_partials(part1);
         beta = rr_new / rr;
         rr = rr_new;
         ++it;
     }
-    // the output: G psi of every equation (the others keep u)
+    // the output: G psi of every equation (the others keep u); psi is final everywhere
+    // (the last barrier followed its last update) and u is no longer read
     for (size_t p = start; p < P; p += stride)
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             int off[3];
             double c[3];
-            const int n = stencil_taps(a.type[s * P + p], off, c);
+            const int n = stencil_taps(type[s * P + p] & 7, off, c);
             if (!n) continue;
             const long step = s == 0 ? nx : 1;
             double v = 0.0;
-            for (int t = 0; t < n; ++t) v = fma(c[t], a.psi[(size_t)((long)p + off[t] * step)], v);
-            a.g[s * P + p] = v;
+            for (int t = 0; t < n; ++t) v = fma(c[t], psi[(size_t)((long)p + off[t] * step)], v);
+            a.u[s * P + p] = v;
         }
-    if (!grid_barrier(a.bar, a.limit_ns, a.hdr)) return;
-    for (size_t p = start; p < P; p += stride)
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-            if (a.type[s * P + p]) a.u[s * P + p] = a.g[s * P + p];
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.info) {
         a.info[0] = (double)it;
         a.info[1] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
@@ -291,16 +311,16 @@ cudaError_t launch_integrate(const pxst_dims &d, const uint8_t *mask, double *u,
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate, IG_THREADS, 0);
     if (e != cudaSuccess) return e;
     const long long want = (long long)((P + IG_THREADS - 1) / IG_THREADS);
-    int blocks = (int)std::min<long long>(want, (long long)per_sm * device_sms());
+    int blocks = (int)std::min<long long>(want, (long long)std::min(per_sm, 2) * device_sms());
     blocks = blocks < 1 ? 1 : std::min(blocks, kIntegMaxBlocks);
-    k_integ_types<<<(unsigned)std::min<size_t>((P + IG_THREADS - 1) / IG_THREADS, (size_t)device_sms() * 8),
-                    IG_THREADS, 0, s>>>(d.ny, d.nx, mask, type);
+    k_integ_types<<<(unsigned)std::min<size_t>((P + 255) / 256, (size_t)device_sms() * 8), 256, 0, s>>>(
+        d.ny, d.nx, mask, type);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
     IntegArgs a;
-    a.ny = d.ny; a.nx = d.nx; a.mask = mask; a.u = u; a.type = type;
-    a.psi = buf; a.r = buf + P; a.d0 = buf + 2 * P; a.d1 = buf + 3 * P; a.q = buf + 4 * P; a.g = buf + 5 * P;
+    a.ny = d.ny; a.nx = d.nx; a.u = u; a.type = type;
+    a.psi = buf; a.r = buf + P; a.d0 = buf + 2 * P; a.q = buf + 3 * P;
     a.part = buf + 7 * P;
     a.bar = bar; a.hdr = hdr; a.max_iter = max_iter; a.tol = tol;
     a.limit_ns = limit_ns > 0 ? (unsigned long long)limit_ns : 10000000000ull;

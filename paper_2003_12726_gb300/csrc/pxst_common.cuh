@@ -20,6 +20,16 @@ struct FrameShift {
     float fy, fx;
 };
 
+// A pixel's map coordinates split once into integers and FP32 fractions in [0, 1), with its
+// var(x) (-1: the pixel does not count) and whitefield, for the kernels that read them once
+// per frame (FP64 is a small fraction of FP32 on this GPU); 32 bytes, read as two 16-byte loads.
+struct __align__(16) PixSplit {
+    int i0, i1;
+    float f0, f1;
+    float var, W;
+    int pad0, pad1;
+};
+
 // Workspace header: the device status word and a few per-call scalars.
 struct WsHeader {
     int status;        // PXST_DEV_* bits, sticky until pxst_get_status
@@ -49,7 +59,7 @@ constexpr int kIntegMaxBlocks = 4096;  // integrate: blocks of the cooperative l
 
 // Byte offsets of each region inside the caller's workspace (all 256-byte aligned).
 struct WsLayout {
-    size_t header, shifts, exact_list, num, den, u_save, var_px, tacc_sum, tacc_cnt, delta_tmp, filt_den;
+    size_t header, shifts, exact_list, num, den, u_save, var_px, usplit, tacc_sum, tacc_cnt, delta_tmp, filt_den;
     size_t integ_buf, integ_type, integ_bar;   // integrate: CG vectors, equation types, barrier
     size_t fclass, dcls;     // class of each frame; one zero-shift weight image per class
     // precision forms only (zero size otherwise)
@@ -77,6 +87,7 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.den = off;        off += align256(sizeof(double) * R);
     L.u_save = off;     off += align256(sizeof(double) * 2 * P);   // the autotuner's copy of u
     L.var_px = off;     off += align256(sizeof(float) * P);        // figures of merit: var(x)
+    L.usplit = off;     off += align256(sizeof(PixSplit) * P);     // translation update: split map
     L.tacc_sum = off;   off += align256(sizeof(double) * kTransMax * (size_t)d.n_frames);
     L.tacc_cnt = off;   off += align256(sizeof(unsigned long long) * kTransMax * (size_t)d.n_frames);
     L.delta_tmp = off;  off += align256(sizeof(double) * 2 * (size_t)d.n_frames);
@@ -180,7 +191,7 @@ int search_max_frames();
 // figures of merit and the translation update (frames.cu)
 cudaError_t launch_pixvar(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
                           const float *I_ref, const float *w, const double *u, const double *delta,
-                          const FrameShift *shifts, float *var, WsHeader *hdr, cudaStream_t s);
+                          const FrameShift *shifts, float *var, PixSplit *split, WsHeader *hdr, cudaStream_t s);
 cudaError_t launch_calc_error(const pxst_dims &d, const float *frames, const float *W, const uint8_t *mask,
                               const float *I_ref, const float *w, const double *u, const double *delta,
                               const FrameShift *shifts, const float *var, WsHeader *hdr, float *pixel_err,
@@ -189,8 +200,9 @@ cudaError_t launch_calc_error(const pxst_dims &d, const float *frames, const flo
 cudaError_t launch_update_translations(const pxst_dims &d, int Ty, int Tx, int quadratic, const float *frames,
                                        const float *W, const uint8_t *mask, const float *I_ref, const float *w,
                                        const double *u, const double *delta_in, const FrameShift *shifts,
-                                       const float *var, WsHeader *hdr, double *acc_sum,
-                                       unsigned long long *acc_cnt, double *delta_out, double *err_out,
+                                       const float *var, const PixSplit *split, float *Rm, WsHeader *hdr,
+                                       double *acc_sum, unsigned long long *acc_cnt, double *delta_out,
+                                       double *err_out,
                                        cudaStream_t s);
 cudaError_t launch_filter_map(const pxst_dims &d, double sigma, const uint8_t *mask, double *u, double *num,
                               double *den, cudaStream_t s);

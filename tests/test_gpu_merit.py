@@ -107,6 +107,39 @@ def test_update_translations_parity(scan, quadratic):
     print(s.name, "quadratic", quadratic, "max |d_gpu - d_oracle|", np.abs(d_g - d_o).max())
 
 
+@pytest.mark.parametrize("tw", [(0, 2), (1, 1), (2, 2)])
+def test_update_translations_windows(scan, tw):
+    """The shift windows the tiled kernel is built for (the full loop uses (0, 2) on a 1-D scan and
+    (1, 1) on a 2-D one) against the oracle, with the 3x3 fit."""
+    s = scan
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    rng = np.random.default_rng(gen.BASE_SEED + 82)
+    start = s.delta + rng.uniform(-0.7, 0.7, s.delta.shape)
+    d_o, e_o = oracle.update_translations(s.frames, s.W, s.M, I32.astype(np.float64), w32.astype(np.float64),
+                                          s.u_init, start, tw, quadratic=True)
+    d_g, e_g = _gpu_update_translations(s.frames, s.W, s.M, I32, w32, s.u_init, start, tw, quadratic=True)
+    np.testing.assert_allclose(d_g, d_o, atol=1e-3)
+    np.testing.assert_allclose(e_g, e_o, rtol=1e-4)
+
+
+def test_update_translations_scattered_map():
+    """A map jittered by up to 60 px: a 16 x 64 pixel tile then reads more reference cells than
+    the tiled kernel stages in shared memory, and its pixels read through the cache; integer
+    picks identical to the oracle's, errors within 1e-4."""
+    s = gen.config_small()
+    Io, wo = oracle.make_object_map(s.frames, s.W, s.M, s.u_init, s.delta, s.ref_shape)
+    I32, w32 = Io.astype(np.float32), wo.astype(np.float32)
+    rng = np.random.default_rng(gen.BASE_SEED + 83)
+    u = s.u_init + rng.uniform(-60.0, 60.0, s.u_init.shape)
+    start = s.delta + rng.uniform(-0.7, 0.7, s.delta.shape)
+    d_o, e_o = oracle.update_translations(s.frames, s.W, s.M, I32.astype(np.float64), w32.astype(np.float64),
+                                          u, start, (1, 1), quadratic=False)
+    d_g, e_g = _gpu_update_translations(s.frames, s.W, s.M, I32, w32, u, start, (1, 1), quadratic=False)
+    np.testing.assert_array_equal(d_g, d_o)
+    np.testing.assert_allclose(e_g, e_o, rtol=1e-4)
+
+
 def test_update_translations_exact_integer():
     rng = np.random.default_rng(34)
     frames, W, M, u, delta, Iref = pins._integer_scan(rng, N=6)
