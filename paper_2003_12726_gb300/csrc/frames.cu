@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(256) k_pixvar(MeritArgs a) {
             split_coord(u1, ui1, uf1);
             rec = PixSplit{ui0, ui1, uf0, uf1, -1.0f, Wv, 0, 0};
             float s2 = 0.0f;
+            // four frames per pass, so that their loads are in flight together
+#pragma unroll 4
             for (int n = 0; n < a.N; ++n) {
                 int i0, j0;
                 float f0, f1;
@@ -94,12 +96,12 @@ __global__ void __launch_bounds__(256) k_pixvar(MeritArgs a) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int ii = i0 + (k >> 1), jj = j0 + (k & 1);
-                    if (wt[k] == 0.0f || ii < 0 || ii >= a.Ry || jj < 0 || jj >= a.Rx) continue;
-                    valid = valid || __ldg(a.w + (size_t)ii * a.Rx + jj) > 0.0f;
+                    const bool on = wt[k] != 0.0f && ii >= 0 && ii < a.Ry && jj >= 0 && jj < a.Rx;
+                    const float wk = on ? __ldg(a.w + (size_t)ii * a.Rx + jj) : 0.0f;
+                    valid = valid || wk > 0.0f;
                 }
-                if (!valid) continue;
-                const float t = __ldg(a.frames + (size_t)n * P + p) - Wv;
-                s2 = fmaf(t, t, s2);
+                const float t = __ldcs(a.frames + (size_t)n * P + p) - Wv;
+                s2 = valid ? fmaf(t, t, s2) : s2;
             }
             v = s2;
         }
