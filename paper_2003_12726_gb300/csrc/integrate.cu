@@ -144,20 +144,37 @@ __device__ bool grid_barrier(unsigned *bar, unsigned long long limit_ns, WsHeade
     return s_ok != 0;
 }
 
-// Sum of v over the block in one fixed order: butterfly over the warp (every lane ends with
-// the same bits, since each step adds the same two values in either order), then the warp
-// sums in warp order. The result is returned to every thread.
+// Sum over the block of every thread's v, in one fixed order: the values go to shared memory
+// and warp 0 adds them (lane l takes threads l, l + 32, ..., then a butterfly, in which every
+// lane ends with the same bits since each step adds the same two values in either order).
+// FP64 adds are scarce on this GPU, so the other warps do none. Returned to every thread.
 __device__ double block_sum(double v) {
-    __shared__ double s_red[IG_THREADS / 32];
+    __shared__ double s_val[IG_THREADS];
     __shared__ double s_tot;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    s_val[threadIdx.x] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < IG_THREADS / 32; ++w) s += s_red[w];
-        s_tot = s;
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < IG_THREADS / 32; ++k) t += s_val[threadIdx.x + 32 * k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) s_tot = t;
+    }
+    __syncthreads();
+    return s_tot;
+}
+
+// the partial sums of all blocks, read and added by warp 0 of every block (lane l takes
+// blocks l, l + 32, ..., then a butterfly): the same value in every block
+__device__ double sum_partials(const double *part) {
+    __shared__ double s_tot;
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) t += __ldcg(part + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) s_tot = t;
     }
     __syncthreads();
     const double t = s_tot;
@@ -165,14 +182,7 @@ __device__ double block_sum(double v) {
     return t;
 }
 
-// the partial sums of all blocks, read by every thread of every block (thread t takes blocks
-// t, t + IG_THREADS, ...) and summed by block_sum: the same value in every block
-__device__ double sum_partials(const double *part) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += IG_THREADS) s += __ldcg(part + b);
-    return block_sum(s);
-}
-
+// the block's sum of v, written to part[blockIdx.x]
 __device__ __forceinline__ void put_partial(double v, double *part) {
     const double s = block_sum(v);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
