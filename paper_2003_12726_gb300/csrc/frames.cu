@@ -1,15 +1,19 @@
 // frames.cu -- figures of merit (section "Calculate figures of merit") and the
 // translation update (section "Update translations") on sm_103a.
 //
-//   k_pixvar      var(x) = sum over the frames valid at u(x) - Delta_n of (I_n - W)^2
+//   k_pixvar      var(x) = sum over the frames valid at u(x) - Delta_n of (I_n - W)^2, and
+//                 (for the translation update) each pixel's record: its map split into
+//                 integers and FP32 fractions, var(x) and W
+//   k_nanref      the reference with unusable cells (w <= 0) stored as NaN
 //   k_calc_error  eps[n,x] = (I_n - W R_n)^2 / var(x) per pixel and frame: the pixel error
-//                 (sum over n), the frame errors (warp sums, FP64 atomics), the total and
-//                 the reference-plane error (eps scattered with the bilinear weights to
-//                 u - Delta_n, FP64 atomics into the workspace accumulators, then divided
-//                 by the weights that landed)
-//   k_trans_acc   per frame and integer shift t of its translation: the sum of eps over the
-//                 pixels whose read at u - Delta_n - t is valid, and their count (one block
-//                 per 256 pixels and frame; warp sums, shared and then FP64 global atomics)
+//                 (sum over n), the frame errors (FP32 warp sums, FP64 block sums and
+//                 atomics), the total and the reference-plane error (eps scattered with the
+//                 bilinear weights to u - Delta_n into (sum, weight) pairs by 8-byte atomics,
+//                 then divided by the weights that landed)
+//   k_trans_acc_patch  per frame and integer shift t (|t| <= 2 per axis) of its translation:
+//                 the sum of eps over the pixels whose read at u - Delta_n - t is valid, and
+//                 their count; each pixel and frame reads one patch of the reference for
+//                 all shifts (k_trans_acc: the same for wider windows, read by read)
 //   k_trans_fit   per frame: the mean, the first minimum, the 3x3 paraboloid, Delta_n update
 #include <cmath>
 
