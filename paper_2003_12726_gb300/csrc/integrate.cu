@@ -331,7 +331,7 @@ cudaError_t launch_integrate(const pxst_dims &d, const uint8_t *mask, double *u,
     IntegArgs a;
     a.ny = d.ny; a.nx = d.nx; a.u = u; a.type = type;
     a.psi = buf; a.r = buf + P; a.d0 = buf + 2 * P; a.q = buf + 3 * P;
-    a.part = buf + 7 * P;
+    a.part = buf + 4 * P;
     a.bar = bar; a.hdr = hdr; a.max_iter = max_iter; a.tol = tol;
     a.limit_ns = limit_ns > 0 ? (unsigned long long)limit_ns : 10000000000ull;
     a.info = info;

@@ -94,8 +94,8 @@ inline WsLayout ws_layout(const pxst_dims &d, int form = PXST_FORM_FP32) {
     L.filt_den = off;   off += align256(sizeof(double) * P);        // the map filter's row pass
     L.fclass = off;     off += align256(sizeof(int) * (size_t)d.n_frames);
     L.dcls = off;       off += align256(sizeof(float) * kMaxClasses * R);
-    // integrate: psi, r, two directions, q, G d (2 per pixel), per-block partial sums
-    L.integ_buf = off;  off += align256(sizeof(double) * (7 * P + 2 * (size_t)kIntegMaxBlocks));
+    // integrate: psi, r, the search direction d, q = A d, per-block partial sums
+    L.integ_buf = off;  off += align256(sizeof(double) * (4 * P + 2 * (size_t)kIntegMaxBlocks));
     L.integ_type = off; off += align256(2 * P);
     L.integ_bar = off;  off += align256(2 * sizeof(unsigned));
     L.Npad = 0;
