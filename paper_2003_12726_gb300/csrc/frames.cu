@@ -176,16 +176,20 @@ __global__ void __launch_bounds__(256) k_calc_error(MeritArgs a, ErrorOut o) {
         const float rvar = var > 0.0f ? 1.0f / var : 1.0f;     // var = 0: eps = d^2
         // a warp none of whose pixels counts adds nothing to any sum
         const int n_end = __any_sync(0xffffffffu, act) ? a.N : 0;
+        // the next frame's value is read while this one is scored
+        float Inxt = (act && n_end > 0) ? __ldcs(a.frames + p) : 0.0f;
         for (int n = 0; n < n_end; ++n) {
             float eps = 0.0f;
             bool sc = false;                 // this lane scatters frame n
             int i0 = 0, j0 = 0;
             float wt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const float I = Inxt;
+            if (act && n + 1 < n_end) Inxt = __ldcs(a.frames + (size_t)(n + 1) * P + p);
             if (act) {
                 float fy, fx, R;
                 frame_point(ui0, uf0, ui1, uf1, a.shifts[n], 0, 0, i0, fy, j0, fx);
                 if (gather_rm(a.Rm, a.Ry, a.Rx, i0, j0, fy, fx, R)) {
-                    const float d = fmaf(-Wv, R, __ldg(a.frames + (size_t)n * P + p));
+                    const float d = fmaf(-Wv, R, I);
                     eps = d * d * rvar;
                     sc = o.nd != nullptr;
                     wt[0] = (1.0f - fy) * (1.0f - fx);
