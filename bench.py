@@ -561,6 +561,24 @@ def time_form(args, s, base, u0, form_name, dist, world, orc, sampler):
     return res
 
 
+def full_loop_entry(r, s, ev_step, form, pk, basis, sms, sm_mhz, sampler=None):
+    """The full-iteration run of time_form (loop = full) as an entry of the bench line: per
+    kernel group its average time per launch and roofline, the dominant group, the launches."""
+    kt = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in r["ktimes"].items() if v[0]}
+    roofs = {k: kernel_roofline(k, kt[k], s, ev_step, FORMS[form], pk, basis, sms, sm_mhz, r.get("extra"))
+             for k in kt if k not in ("prepare", "omap_normalise", "upm_exact")}
+    dom = max(kt, key=lambda k: kt[k] * r["ktimes"][k][0])
+    extra = r.get("extra") or {}
+    return {"form": form, "ms_per_step": r["ms_per_step"], "steps": 5, "warmup": 3,
+            "step": "one full iteration from the scan's initial map and translations: reference image, pixel map "
+                    "(3x3 fit), map filter (sigma 1), integration (at most 200 conjugate-gradient steps, tolerance "
+                    "1e-8), translation update, figures of merit",
+            "translation_window": list(extra.get("tw") or ()), "integrate_steps": extra.get("integ_steps"),
+            "dominant_kernel": dom, "roofline": roofs.get(dom), "kernel_ms": kt, "kernel_rooflines": roofs,
+            "gpu_launches": r["launches"], "defocus_sweep": r.get("sweep"),
+            "clocks": sampler.summary(r["t_wall"][0] - 0.2, r["t_wall"][1] + 0.2) if sampler else None}
+
+
 def pxst_arm(args, rank, world, local_rank):
     import torch
     import paper_2003_12726_gb300 as px
@@ -594,6 +612,12 @@ def pxst_arm(args, rank, world, local_rank):
                     "coverage_mismatch": int(np.count_nonzero((wg > 0) != (orc["wo"] > 0))),
                     "over": "reference pixels with oracle weight > 1e-4 max (I_ref); all (w)"}
     results = {f: time_form(args, s, base, u0, f, dist, world, orc, sampler) for f in forms}
+    # the paper's full iteration in the headline form, beside the main-loop line (one GPU)
+    full = None
+    if world == 1 and args.form == "all" and args.loop == "main" and not args.frac and not args.no_full_loop:
+        fa = argparse.Namespace(**vars(args))
+        fa.loop, fa.steps, fa.warmup, fa.no_autotune = "full", 5, 3, True
+        full = time_form(fa, s, base, u0, headline, dist, world, None, sampler)
     if sampler:
         sampler.stop()
     # the batched and served workloads of the same run (one GPU, the default line only)
@@ -669,6 +693,8 @@ def pxst_arm(args, rank, world, local_rank):
                            "error back; the next step's copy overlaps this step's compute"},
             "gpu_launches": h["gpu_launches"], "kernel_ms": h["kernel_ms"], "exact_path_pixels": h["exact_path_pixels"],
             "forms": per_form, "iref_error_vs_oracle": iref_err, "clocks": clocks}
+    if full:
+        line["full_loop"] = full_loop_entry(full, s, ev_step, headline, pk, basis, sms, sm_mhz, sampler)
     if batch:
         line["batch64"] = dict(batch, form="bf16", workload="64 scans of the batched configuration")
     if serve:
@@ -875,6 +901,8 @@ def main():
                          "bf16/tf32")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-full-loop", action="store_true",
+                    help="with --form all: skip the full-iteration run of the headline form")
     ap.add_argument("--no-extra", action="store_true",
                     help="default line without the batched and served workloads")
     ap.add_argument("--branches", type=int, default=8, help="batch64: parallel graph branches")

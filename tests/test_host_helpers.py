@@ -43,3 +43,35 @@ def test_reference_arm_prints_the_contract_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_full_loop_entry_of_the_bench_line():
+    """The full-iteration entry of the default bench line, built from a time_form result:
+    per-group averages, FP64/ALU/HBM rooflines with the work the groups are defined by, and
+    a JSON-serialisable result."""
+    from types import SimpleNamespace
+    sys.path.insert(0, ROOT)
+    import bench
+    s = SimpleNamespace(frames=np.zeros((4, 8, 16), np.float32), ref_shape=(12, 20),
+                        M=np.ones((8, 16), np.uint8), window=(2, 2))
+    r = {"ktimes": {"omap_scatter": (5, 1.0), "integrate": (5, 20.0), "update_translations": (5, 2.0),
+                    "calc_error": (5, 3.0), "filter_map": (5, 0.5), "prepare": (5, 0.05), "upm_exact": (0, 0.0)},
+         "ms_per_step": 5.5, "launches": 60, "sweep": {"pairs": 25, "ms": 1.0},
+         "extra": {"tw": (1, 1), "filter_r": 4, "integ_steps": 200}, "t_wall": (0.0, 1.0)}
+    pk = {"hbm_gbs": 6662.9, "bf16_tflops": 1942.8}
+    e = bench.full_loop_entry(r, s, 1.0, "bf16", pk, "measured", 152, 2070.0)
+    assert e["dominant_kernel"] == "integrate" and e["kernel_ms"]["integrate"] == 4.0
+    assert "upm_exact" not in e["kernel_ms"] and "prepare" not in e["kernel_rooflines"]
+    roof = e["kernel_rooflines"]
+    assert roof["integrate"]["bound"] == "fp64" and roof["filter_map"]["bound"] == "fp64"
+    assert roof["update_translations"]["bound"] == "alu" and roof["calc_error"]["bound"] == "hbm"
+    # integrate: 17 flop per good pixel and step over the average launch time
+    want = 17.0 * 8 * 16 * 200 / 1e12 / (4.0e-3)
+    assert abs(roof["integrate"]["achieved"] - want) < 1e-12 * max(want, 1.0)
+    fp64_peak = 152 * 2 * 2 * 2070.0e6 / 1e12
+    assert abs(roof["integrate"]["peak"] - fp64_peak) < 1e-12
+    # update_translations: 12 flop per pixel, frame and shift of the 3 x 3 window
+    want = 12.0 * 4 * 8 * 16 * 9 / 1e12 / (0.4e-3)
+    assert abs(roof["update_translations"]["achieved"] - want) < 1e-9 * want
+    assert e["translation_window"] == [1, 1] and e["integrate_steps"] == 200
+    json.dumps(e)
