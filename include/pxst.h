@@ -312,7 +312,9 @@ pxst_status pxst_defocus_sweep(const pxst_dims *dims, const float *frames, const
  * map that is one (the gradient of a quadratic Psi, for instance) is returned unchanged.
  * info_out (device double[2], nullable): the steps taken and the final relative residual.
  * One cooperative launch (every block resident) runs the solve; its grid barriers give up
- * after timeout_ns (0 = 10 s), set PXST_DEV_TIMEOUT and leave u unchanged. */
+ * after timeout_ns (0 = 10 s) and set PXST_DEV_TIMEOUT, and every block then leaves: u is
+ * left unchanged, except where a block gave up at the solve's last barrier just as the
+ * others passed it (they then write their pixels' G Psi); the status reports it either way. */
 pxst_status pxst_integrate_map(const pxst_dims *dims, const uint8_t *mask, double *u_inout, int32_t max_iter,
                                double tol, int64_t timeout_ns, double *info_out, void *workspace, size_t ws_bytes,
                                void *stream);
