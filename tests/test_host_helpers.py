@@ -75,3 +75,61 @@ def test_full_loop_entry_of_the_bench_line():
     assert abs(roof["update_translations"]["achieved"] - want) < 1e-9 * want
     assert e["translation_window"] == [1, 1] and e["integrate_steps"] == 200
     json.dumps(e)
+
+
+def test_integrate_central_stencil_identity():
+    """The identity behind the integration kernel's fast path: where a pixel's equations along
+    an axis are central at p - e, p and p + e, and neither the pixel two behind is second-order
+    forward nor the one two ahead second-order backward, (G^T G x)[p] on that axis is
+    (2 x[p] - x[p - 2e] - x[p + 2e]) / 4. Checked against G^T G built as a dense matrix from
+    the stencil rule (section "Update pixel mapping", the integrate option) on a masked grid."""
+    rng = np.random.default_rng(12726 + 907)
+    ny, nx = 19, 27
+    M = (rng.random((ny, nx)) > 0.04).astype(np.uint8)
+    M[4:7, 9:] = 0
+
+    def code(i, j, a):
+        L, pos = (ny, i) if a == 0 else (nx, j)
+
+        def good(k):
+            t = pos + k
+            if t < 0 or t >= L:
+                return False
+            return bool(M[t, j] if a == 0 else M[i, t])
+        if not good(0):
+            return 0
+        if good(1) and good(-1):
+            return 1
+        if good(1) and good(2):
+            return 2
+        if good(-1) and good(-2):
+            return 3
+        return 4 if good(1) else (5 if good(-1) else 0)
+
+    taps = {1: [(1, .5), (-1, -.5)], 2: [(0, -1.5), (1, 2.), (2, -.5)], 3: [(0, 1.5), (-1, -2.), (-2, .5)],
+            4: [(1, 1.), (0, -1.)], 5: [(0, 1.), (-1, -1.)]}
+    rows = []
+    for a in range(2):
+        for i in range(ny):
+            for j in range(nx):
+                c = code(i, j, a)
+                if c:
+                    row = np.zeros(ny * nx)
+                    for off, cf in taps[c]:
+                        row[(i + off) * nx + j if a == 0 else i * nx + j + off] += cf
+                    rows.append(row)
+    G = np.array(rows)
+    x = rng.normal(size=ny * nx)
+    q = (G.T @ (G @ x)).reshape(ny, nx)
+    X = x.reshape(ny, nx)
+    n_fast = 0
+    for i in range(ny):
+        for j in range(nx):
+            def fast(a):
+                cc = lambda k: code(i + k, j, a) if a == 0 else code(i, j + k, a)
+                return cc(0) == 1 and cc(-1) == 1 and cc(1) == 1 and cc(-2) != 2 and cc(2) != 3
+            if fast(0) and fast(1):
+                n_fast += 1
+                v = X[i, j] - 0.25 * (X[i - 2, j] + X[i + 2, j] + X[i, j - 2] + X[i, j + 2])
+                assert abs(v - q[i, j]) < 1e-12
+    assert n_fast > 50
